@@ -1,0 +1,79 @@
+"""Periphery network oracle, float64.  TEST INFRASTRUCTURE ONLY.
+
+The network is not in the paper (which reconstructs the periphery by nearest-neighbour
+upsampling and a 3x3 blur, Sec. 4.3); it is the learned replacement the workload asks
+for: y = up + conv3(relu(conv2(relu(conv1(up))))), 3 -> 32 -> 32 -> 3 channels, 3x3
+kernels, zero padding 1, where up is the x2 bilinear upsampling of the half-resolution
+periphery.  Weights, the network input and the two hidden activations are BF16 values;
+accumulation is exact here (float64) and FP32 on the GPU.  Rounding to BF16 happens at
+the same three places on both sides: the input, and each hidden activation after bias
+and ReLU.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+CH = 32
+
+
+def bf16(x: torch.Tensor) -> torch.Tensor:
+    """Round to the nearest BF16 value (ties to even), returned in float64."""
+    return x.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+
+
+def init_weights(rng: np.random.Generator, zero_last: bool = False) -> dict:
+    """He-initialised weights (OIHW) and zero biases, BF16-representable."""
+    def he(o, i):
+        return rng.normal(0, np.sqrt(2.0 / (i * 9)), size=(o, i, 3, 3))
+    w = {"w1": he(CH, 3), "b1": np.zeros(CH), "w2": he(CH, CH), "b2": np.zeros(CH),
+         "w3": he(3, CH) * (0.0 if zero_last else 0.1), "b3": np.zeros(3)}
+    return {k: bf16(torch.tensor(v)).numpy() if k.startswith("w") else v.astype(np.float32).astype(np.float64)
+            for k, v in w.items()}
+
+
+def forward(x: torch.Tensor, w: dict, round_acts: bool = True):
+    """x: [B, 3, H, W] float64 network input (already upsampled).  -> (y, (a1, a2))."""
+    t = {k: (v if torch.is_tensor(v) else torch.tensor(v, dtype=torch.float64)) for k, v in w.items()}
+    r = bf16 if round_acts else (lambda z: z)
+    xin = r(x)
+    a1 = r(F.relu(F.conv2d(xin, t["w1"], t["b1"], padding=1)))
+    a2 = r(F.relu(F.conv2d(a1, t["w2"], t["b2"], padding=1)))
+    y = x + F.conv2d(a2, t["w3"], t["b3"], padding=1)
+    return y, (xin, a1, a2)
+
+
+def conv_direct(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """3x3, pad 1 convolution by explicit sums (pins the library convolution)."""
+    B, Ci, H, W = x.shape
+    Co = w.shape[0]
+    xp = np.pad(x, ((0, 0), (0, 0), (1, 1), (1, 1)))
+    y = np.zeros((B, Co, H, W))
+    for o in range(Co):
+        acc = np.full((B, H, W), b[o], dtype=np.float64)
+        for i in range(Ci):
+            for ky in range(3):
+                for kx in range(3):
+                    acc += w[o, i, ky, kx] * xp[:, i, ky:ky + H, kx:kx + W]
+        y[:, o] = acc
+    return y
+
+
+def grads(x: np.ndarray, w: dict, dy: np.ndarray) -> dict:
+    """d<dy, y>/d(weights, biases) with BF16 rounding treated as identity (the
+    straight-through rule the GPU backward also uses)."""
+    wt = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in w.items()}
+    xt = torch.tensor(x, dtype=torch.float64)
+    xin = bf16(xt)
+    with torch.no_grad():
+        a1r = bf16(F.relu(F.conv2d(xin, wt["w1"], wt["b1"], padding=1)))
+        a2r = bf16(F.relu(F.conv2d(a1r, wt["w2"], wt["b2"], padding=1)))
+    # straight-through: forward values are the rounded ones, gradients pass unchanged
+    z1 = F.conv2d(xin, wt["w1"], wt["b1"], padding=1)
+    a1 = F.relu(z1) + (a1r - F.relu(z1)).detach()
+    z2 = F.conv2d(a1, wt["w2"], wt["b2"], padding=1)
+    a2 = F.relu(z2) + (a2r - F.relu(z2)).detach()
+    y = xt + F.conv2d(a2, wt["w3"], wt["b3"], padding=1)
+    (y * torch.tensor(dy, dtype=torch.float64)).sum().backward()
+    return {k: v.grad.numpy().copy() for k, v in wt.items()}

@@ -1,0 +1,1070 @@
+/*
+ * FP64 CPU oracle for the VRSplat rasterizer hot path (arXiv 2505.10144).
+ *
+ * TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the CPU-baseline leg of the
+ * benchmark call this library; the product path (the CUDA library and its Python
+ * binding) never does, and shares no code, header or constant with it.
+ *
+ * Everything is written as the plain definition, in double precision, for reading:
+ *
+ *   - 3D Gaussian G(x) = exp(-1/2 (x-mu)^T Sigma^-1 (x-mu)), Sigma = R S S^T R^T   (Eq. 1)
+ *   - Optimal Projection: each Gaussian is projected onto the tangent plane of the unit
+ *     sphere around the camera centre o, perpendicular to mu - o                    (Sec. 4.2)
+ *   - front-to-back blending C = sum_i c_i a_i prod_{j<i} (1 - a_j), a = sigma G_2D  (Eq. 2)
+ *   - per-pixel order by the depth of each Gaussian's maximum response along the ray
+ *     (StopThePop, Sec. 4.1), ties broken by Gaussian index
+ *   - tile culling on the optimal plane: a Gaussian/tile pair is dropped when the largest
+ *     alpha over the tile's quadrilateral is below 1/255; the maximum is the projected
+ *     mean when it lies inside, else on an edge, found in closed form           (Eq. 4)
+ *   - single-pass foveation: 32x32 tiles, focus tiles at full resolution, periphery tiles
+ *     shaded on 2x2 pixel groups, hybrid tiles blended by the continuous mask    (Sec. 4.3)
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - camera: OpenCV axes, world->camera [R|t], pixel centres at (x+0.5, y+0.5);
+ *   - near cull at view z < near_z (0.2), alpha clamp 0.99, transmittance stop 1e-4,
+ *     background given by the caller (black by default);
+ *   - dilation 0.3 px^2 expressed on the tangent plane as 0.3/(fx fy) I;
+ *   - tangent-plane basis e1 = (u_z, 0, -u_x)/|.|, e2 = u x e1 (camera frame); every
+ *     result is invariant to this choice;
+ *   - depth t* = v^T Sigma^-1 (mu - o) / v^T Sigma^-1 v with v = K^-1 (px, py, 1), i.e. the
+ *     camera-z of the point of maximum response along the pixel's ray;
+ *   - tile key = t* on the ray through the tile maximum x^ projected back to the image;
+ *     Eq. 4's line parameter is clamped to the edge segment;
+ *   - hierarchical resort = a cascade of three min-windows (4x4-sample block, 2x2-sample
+ *     block, per sample), membership of a block = kept at any still-active sample of it,
+ *     keys = t* at the block centre; window mode = the cascade with k1 = k2 = 0; the
+ *     exact order = the cascade with unbounded windows.  This function is "parity
+ *     unpinned" against the paper (only its invariants are pinned).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OG_ALPHA_MIN (1.0 / 255.0)
+#define OG_ALPHA_MAX 0.99
+#define OG_T_STOP 1e-4
+#define OG_DILATION_PX2 0.3
+
+/* relative margins of the marginal-sample rule (set from og_opts for each render) */
+static double g_margin_alpha = 1e-4, g_margin_stop = 1e-4, g_margin_tie = 1e-5;
+
+/* Gaussian parameters in SoA layout (double, so that finite differences can perturb
+ * them below float32 resolution; the product's float32 inputs convert exactly). */
+typedef struct {
+  const double *mean, *log_scale, *quat, *opacity_logit, *sh;
+  int64_t n;
+  int sh_degree;
+} og_scene;
+
+typedef struct {
+  double w2c[12];
+  double fx, fy, cx, cy;
+  int width, height;
+  double near_z;
+} og_camera;
+
+typedef struct {
+  int mode;      /* 0 exact, 1 window (k3), 2 hierarchical (k1, k2, k3) */
+  int k1, k2, k3;
+  int key_tile;  /* side of the square tiles the sort keys use: 16 or 32 */
+  int foveated;  /* 0 plain (every pixel a sample), 1 single-pass foveated */
+  int tile_cull; /* 1: Eq. 4 pair culling; 0: bounding rectangle only */
+  int brute;     /* 1: no tiles at all, every Gaussian a candidate of every sample */
+  double gaze_x, gaze_y, radius, band;
+  double bg[3];
+  /* margins of the FP32-vs-FP64 comparison rule: a sample is marginal when a decision
+   * falls within these relative distances of its threshold */
+  double margin_alpha, margin_stop, margin_tie;
+} og_opts;
+
+typedef struct {
+  double *image;      /* [3][H][W] composited output */
+  double *full;       /* [4][H][W]: C rgb and T of full-res samples (NaN elsewhere) */
+  double *low;        /* [4][H/2][W/2]: C rgb and T of group samples (NaN elsewhere) */
+  double *lowimg;     /* [3][H/2][W/2]: the half-resolution image that is upsampled */
+  uint8_t *marginal;  /* [H][W]: 1 where an FP32 renderer may legitimately differ */
+  uint8_t *tile_class;/* [nty][ntx]: 0 focus/plain, 1 hybrid, 2 periphery */
+  int32_t *order;     /* gids in blend order, samples concatenated */
+  int64_t *order_off; /* [H*W + (H/2)*(W/2) + 1] */
+  int64_t max_order;
+  int64_t n_order;    /* out */
+  int64_t stats[8];   /* out: valid, instances, evaluated, kept, blended, marginal px, samples */
+} og_out;
+
+/* ------------------------------------------------------------------ projection ---- */
+
+typedef struct {
+  int valid;
+  double mu[3];        /* camera-space mean (camera centre at the origin) */
+  double d, u[3];      /* distance and unit direction to the mean */
+  double E[2][3];      /* orthonormal basis of the tangent plane */
+  double Sc[3][3];     /* camera-space covariance */
+  double Sci[3][3];    /* its inverse R S^-2 R^T */
+  double Sp[2][2];     /* tangent-plane covariance incl. dilation */
+  double A[2][2];      /* conic = Sp^-1 */
+  double sigma, r2;    /* opacity and cutoff: alpha >= 1/255  <=>  q <= r2 */
+  double rgb[3];
+  double bbox[4];      /* xmin, ymin, xmax, ymax of the alpha >= 1/255 region (pixels) */
+  int bounded;
+} og_proj;
+
+/* Real spherical-harmonics basis, degrees 0..3, in the sign convention of 3DGS. */
+void og_sh_basis(int degree, const double dir[3], double Y[16]) {
+  const double pi = 3.14159265358979323846;
+  const double x = dir[0], y = dir[1], z = dir[2];
+  const double s = 1.0 / sqrt(pi);
+  for (int k = 0; k < 16; ++k) Y[k] = 0.0;
+  Y[0] = 0.5 * s;
+  if (degree < 1) return;
+  const double c1 = 0.5 * sqrt(3.0) * s;
+  Y[1] = -c1 * y;
+  Y[2] = c1 * z;
+  Y[3] = -c1 * x;
+  if (degree < 2) return;
+  Y[4] = 0.5 * sqrt(15.0) * s * x * y;
+  Y[5] = -0.5 * sqrt(15.0) * s * y * z;
+  Y[6] = 0.25 * sqrt(5.0) * s * (2 * z * z - x * x - y * y);
+  Y[7] = -0.5 * sqrt(15.0) * s * x * z;
+  Y[8] = 0.25 * sqrt(15.0) * s * (x * x - y * y);
+  if (degree < 3) return;
+  Y[9] = -0.25 * sqrt(35.0 / 2.0) * s * y * (3 * x * x - y * y);
+  Y[10] = 0.5 * sqrt(105.0) * s * x * y * z;
+  Y[11] = -0.25 * sqrt(21.0 / 2.0) * s * y * (4 * z * z - x * x - y * y);
+  Y[12] = 0.25 * sqrt(7.0) * s * z * (2 * z * z - 3 * x * x - 3 * y * y);
+  Y[13] = -0.25 * sqrt(21.0 / 2.0) * s * x * (4 * z * z - x * x - y * y);
+  Y[14] = 0.25 * sqrt(105.0) * s * z * (x * x - y * y);
+  Y[15] = -0.25 * sqrt(35.0 / 2.0) * s * x * (x * x - 3 * y * y);
+}
+
+static void mat3_mul(const double a[3][3], const double b[3][3], double c[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k) s += a[i][k] * b[k][j];
+      c[i][j] = s;
+    }
+}
+
+static int all_finite(const double* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!isfinite(v[i])) return 0;
+  return 1;
+}
+
+/* camera ray through continuous pixel position (px, py): K^-1 (px, py, 1) */
+static void pixel_ray(const og_camera* c, double px, double py, double v[3]) {
+  v[0] = (px - c->cx) / c->fx;
+  v[1] = (py - c->cy) / c->fy;
+  v[2] = 1.0;
+}
+
+/* t*(v): parameter of the maximum of the 3D Gaussian along the ray t v (camera frame) */
+static double tstar_ray(const og_proj* p, const double v[3]) {
+  double num = 0, den = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      num += v[i] * p->Sci[i][j] * p->mu[j];
+      den += v[i] * p->Sci[i][j] * v[j];
+    }
+  return num / den;
+}
+
+static void conic_bbox(og_proj* p, const og_camera* c) {
+  /* Rays x with sample alpha >= 1/255 form the cone (E x)^T A (E x) <= r2 (u.x)^2,
+   * u.x > 0.  Its image in pixel space is the conic p~^T C p~ <= 0, C = K^-T Q K^-1. */
+  double Q[3][3], Ki[3][3] = {{1.0 / c->fx, 0, -c->cx / c->fx}, {0, 1.0 / c->fy, -c->cy / c->fy}, {0, 0, 1}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) s += p->E[a][i] * p->A[a][b] * p->E[b][j];
+      Q[i][j] = s - p->r2 * p->u[i] * p->u[j];
+    }
+  double KiT[3][3], T1[3][3], C[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) KiT[i][j] = Ki[j][i];
+  mat3_mul(KiT, Q, T1);
+  mat3_mul(T1, Ki, C);
+  double det2 = C[0][0] * C[1][1] - C[0][1] * C[1][0];
+  p->bounded = 0;
+  p->bbox[0] = 0;
+  p->bbox[1] = 0;
+  p->bbox[2] = c->width;
+  p->bbox[3] = c->height;
+  if (C[0][0] > 0 && det2 > 0) {
+    /* ellipse: (p - p0)^T C2 (p - p0) <= -k */
+    double i00 = C[1][1] / det2, i01 = -C[0][1] / det2, i11 = C[0][0] / det2;
+    double p0x = -(i00 * C[0][2] + i01 * C[1][2]);
+    double p0y = -(i01 * C[0][2] + i11 * C[1][2]);
+    double k = C[2][2] + C[0][2] * p0x + C[1][2] * p0y;
+    if (k <= 0) {
+      double hx = sqrt(-k * i00), hy = sqrt(-k * i11);
+      p->bbox[0] = p0x - hx;
+      p->bbox[1] = p0y - hy;
+      p->bbox[2] = p0x + hx;
+      p->bbox[3] = p0y + hy;
+      p->bounded = 1;
+    }
+  }
+}
+
+/* Optimal-Projection preprocessing of Gaussian i for camera c (Sec. 4.2, Eq. 1). */
+int og_project(const og_scene* sc, int64_t i, const og_camera* c, og_proj* p) {
+  memset(p, 0, sizeof *p);
+  const int64_t n = sc->n;
+  double m[3] = {sc->mean[i], sc->mean[n + i], sc->mean[2 * n + i]};
+  double ls[3] = {sc->log_scale[i], sc->log_scale[n + i], sc->log_scale[2 * n + i]};
+  double q[4] = {sc->quat[i], sc->quat[n + i], sc->quat[2 * n + i], sc->quat[3 * n + i]};
+  double logit = sc->opacity_logit[i];
+  if (!all_finite(m, 3) || !all_finite(ls, 3) || !all_finite(q, 4) || !isfinite(logit)) return 0;
+  double Rw[3][3], t[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) Rw[r][k] = c->w2c[4 * r + k];
+    t[r] = c->w2c[4 * r + 3];
+  }
+  for (int r = 0; r < 3; ++r) p->mu[r] = Rw[r][0] * m[0] + Rw[r][1] * m[1] + Rw[r][2] * m[2] + t[r];
+  if (!(p->mu[2] >= c->near_z)) return 0;
+  double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(qn > 0)) return 0;
+  double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+  double R[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                    {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                    {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+  double Rc[3][3];
+  mat3_mul(Rw, R, Rc); /* rotation of the Gaussian's axes into the camera frame */
+  double s2[3], si2[3];
+  for (int k = 0; k < 3; ++k) {
+    s2[k] = exp(2 * ls[k]);
+    si2[k] = exp(-2 * ls[k]);
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double s = 0, si = 0;
+      for (int k = 0; k < 3; ++k) {
+        s += Rc[a][k] * s2[k] * Rc[b][k];
+        si += Rc[a][k] * si2[k] * Rc[b][k];
+      }
+      p->Sc[a][b] = s;
+      p->Sci[a][b] = si;
+    }
+  if (!all_finite(&p->Sc[0][0], 9) || !all_finite(&p->Sci[0][0], 9)) return 0;
+  p->sigma = 1.0 / (1.0 + exp(-logit));
+  if (!(p->sigma >= OG_ALPHA_MIN)) return 0;
+  p->r2 = 2.0 * log(255.0 * p->sigma);
+  p->d = sqrt(p->mu[0] * p->mu[0] + p->mu[1] * p->mu[1] + p->mu[2] * p->mu[2]);
+  for (int k = 0; k < 3; ++k) p->u[k] = p->mu[k] / p->d;
+  double rho = sqrt(p->u[0] * p->u[0] + p->u[2] * p->u[2]);
+  p->E[0][0] = p->u[2] / rho;
+  p->E[0][1] = 0;
+  p->E[0][2] = -p->u[0] / rho;
+  p->E[1][0] = p->u[1] * p->E[0][2] - p->u[2] * p->E[0][1];
+  p->E[1][1] = p->u[2] * p->E[0][0] - p->u[0] * p->E[0][2];
+  p->E[1][2] = p->u[0] * p->E[0][1] - p->u[1] * p->E[0][0];
+  double dil = OG_DILATION_PX2 / (c->fx * c->fy);
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) s += p->E[a][k] * p->Sc[k][l] * p->E[b][l];
+      p->Sp[a][b] = s / (p->d * p->d) + (a == b ? dil : 0.0);
+    }
+  double det = p->Sp[0][0] * p->Sp[1][1] - p->Sp[0][1] * p->Sp[1][0];
+  p->A[0][0] = p->Sp[1][1] / det;
+  p->A[1][1] = p->Sp[0][0] / det;
+  p->A[0][1] = p->A[1][0] = -p->Sp[0][1] / det;
+  /* colour from SH along the world-space viewing direction (mu - o)/|mu - o| */
+  double dirw[3];
+  for (int k = 0; k < 3; ++k) dirw[k] = Rw[0][k] * p->u[0] + Rw[1][k] * p->u[1] + Rw[2][k] * p->u[2];
+  double Y[16];
+  og_sh_basis(sc->sh_degree, dirw, Y);
+  int K = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+  for (int ch = 0; ch < 3; ++ch) {
+    double v = 0.5;
+    for (int k = 0; k < K; ++k) v += Y[k] * sc->sh[((int64_t)k * 3 + ch) * n + i];
+    p->rgb[ch] = v > 0 ? v : 0.0;
+  }
+  conic_bbox(p, c);
+  p->valid = 1;
+  return 1;
+}
+
+/* alpha and depth of Gaussian p at the sample position (px, py).  Returns 1 when the pair
+ * is kept (alpha >= 1/255 and the ray meets the tangent plane in front of o). */
+static int og_eval(const og_proj* p, const og_camera* c, double px, double py, double* alpha,
+                   double* tstar, double* sg) {
+  double v[3];
+  pixel_ray(c, px, py, v);
+  double w = p->u[0] * v[0] + p->u[1] * v[1] + p->u[2] * v[2];
+  *sg = 0;
+  if (!(w > 0)) return 0;
+  double s0 = (p->E[0][0] * v[0] + p->E[0][1] * v[1] + p->E[0][2] * v[2]) / w;
+  double s1 = (p->E[1][0] * v[0] + p->E[1][1] * v[1] + p->E[1][2] * v[2]) / w;
+  double q = p->A[0][0] * s0 * s0 + 2 * p->A[0][1] * s0 * s1 + p->A[1][1] * s1 * s1;
+  *sg = p->sigma * exp(-0.5 * q);
+  if (!(*sg >= OG_ALPHA_MIN)) return 0;
+  *alpha = *sg < OG_ALPHA_MAX ? *sg : OG_ALPHA_MAX;
+  *tstar = tstar_ray(p, v);
+  return 1;
+}
+
+/* Eq. 4: maximum of the plane Gaussian (conic A, centre 0) on the segment P + t D,
+ * t clamped to [0, 1].  Returns the exponent q = x^T A x at the maximum point. */
+static double edge_min_q(const double A[2][2], const double P[2], const double D[2], double* tout) {
+  double AP0 = A[0][0] * P[0] + A[0][1] * P[1], AP1 = A[1][0] * P[0] + A[1][1] * P[1];
+  double AD0 = A[0][0] * D[0] + A[0][1] * D[1], AD1 = A[1][0] * D[0] + A[1][1] * D[1];
+  double dAd = D[0] * AD0 + D[1] * AD1;
+  double t = dAd > 0 ? -(D[0] * AP0 + D[1] * AP1) / dAd : 0.0;
+  if (t < 0) t = 0;
+  if (t > 1) t = 1;
+  double X0 = P[0] + t * D[0], X1 = P[1] + t * D[1];
+  *tout = t;
+  return A[0][0] * X0 * X0 + 2 * A[0][1] * X0 * X1 + A[1][1] * X1 * X1;
+}
+
+/* exported for the Eq. 4 pin: out = {t, q} */
+void og_edge_max(const double A4[4], const double P[2], const double D[2], double out[2]) {
+  double A[2][2] = {{A4[0], A4[1]}, {A4[2], A4[3]}};
+  out[1] = edge_min_q(A, P, D, &out[0]);
+}
+
+/* Tile culling on the optimal plane (Sec. 4.2, Eq. 4).  The quad spans the sample
+ * positions [x0, x1] x [y0, y1].  Returns 1 when the pair is kept; *key = t* on the ray
+ * through the maximum point projected back to the image. */
+static int og_tile_keep(const og_proj* p, const og_camera* c, double x0, double y0, double x1,
+                        double y1, double* key, double* qmin_out) {
+  const double cx[4] = {x0, x1, x1, x0}, cy[4] = {y0, y0, y1, y1};
+  double S[4][2];
+  *key = p->mu[2];
+  *qmin_out = 0;
+  for (int k = 0; k < 4; ++k) {
+    double v[3];
+    pixel_ray(c, cx[k], cy[k], v);
+    double w = p->u[0] * v[0] + p->u[1] * v[1] + p->u[2] * v[2];
+    if (!(w > 0)) return 1; /* quad not bounded on the plane: keep, key at the mean */
+    S[k][0] = (p->E[0][0] * v[0] + p->E[0][1] * v[1] + p->E[0][2] * v[2]) / w;
+    S[k][1] = (p->E[1][0] * v[0] + p->E[1][1] * v[1] + p->E[1][2] * v[2]) / w;
+  }
+  int pos = 0, neg = 0;
+  for (int k = 0; k < 4; ++k) {
+    int l = (k + 1) & 3;
+    double cr = (S[l][0] - S[k][0]) * (0 - S[k][1]) - (S[l][1] - S[k][1]) * (0 - S[k][0]);
+    if (cr > 0) pos = 1;
+    if (cr < 0) neg = 1;
+  }
+  if (!(pos && neg)) return 1; /* projected mean inside the quad: maximum at the mean */
+  double qmin = INFINITY, X[2] = {0, 0};
+  for (int k = 0; k < 4; ++k) {
+    int l = (k + 1) & 3;
+    double D[2] = {S[l][0] - S[k][0], S[l][1] - S[k][1]}, t;
+    double q = edge_min_q(p->A, S[k], D, &t);
+    if (q < qmin) {
+      qmin = q;
+      X[0] = S[k][0] + t * D[0];
+      X[1] = S[k][1] + t * D[1];
+    }
+  }
+  *qmin_out = qmin;
+  if (!(qmin <= p->r2)) return 0;
+  double y[3];
+  for (int k = 0; k < 3; ++k) y[k] = p->u[k] + p->E[0][k] * X[0] + p->E[1][k] * X[1];
+  if (y[2] > 0) {
+    double v[3] = {y[0] / y[2], y[1] / y[2], 1.0};
+    *key = tstar_ray(p, v);
+  }
+  return 1;
+}
+
+/* ------------------------------------------------------------- exported single ops ---- */
+
+/* out: valid, mu[3], d, u[3], E[6], Sc[9], Sci[9], Sp[4], A[4], sigma, r2, rgb[3], bbox[4],
+ * bounded  (52 doubles) */
+int og_project_one(const og_scene* sc, int64_t i, const og_camera* c, double* out) {
+  og_proj p;
+  int v = og_project(sc, i, c, &p);
+  double* o = out;
+  *o++ = v;
+  for (int k = 0; k < 3; ++k) *o++ = p.mu[k];
+  *o++ = p.d;
+  for (int k = 0; k < 3; ++k) *o++ = p.u[k];
+  for (int a = 0; a < 2; ++a)
+    for (int k = 0; k < 3; ++k) *o++ = p.E[a][k];
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) *o++ = p.Sc[a][k];
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) *o++ = p.Sci[a][k];
+  for (int a = 0; a < 2; ++a)
+    for (int k = 0; k < 2; ++k) *o++ = p.Sp[a][k];
+  for (int a = 0; a < 2; ++a)
+    for (int k = 0; k < 2; ++k) *o++ = p.A[a][k];
+  *o++ = p.sigma;
+  *o++ = p.r2;
+  for (int k = 0; k < 3; ++k) *o++ = p.rgb[k];
+  for (int k = 0; k < 4; ++k) *o++ = p.bbox[k];
+  *o++ = p.bounded;
+  return v;
+}
+
+/* out: kept, alpha, tstar, sigma*G */
+int og_eval_one(const og_scene* sc, int64_t i, const og_camera* c, double px, double py, double* out) {
+  og_proj p;
+  out[0] = out[1] = out[2] = out[3] = 0;
+  if (!og_project(sc, i, c, &p)) return 0;
+  double a = 0, t = 0, sg = 0;
+  int k = og_eval(&p, c, px, py, &a, &t, &sg);
+  out[0] = k;
+  out[1] = a;
+  out[2] = t;
+  out[3] = sg;
+  return k;
+}
+
+/* out: keep, key, qmin */
+int og_tile_one(const og_scene* sc, int64_t i, const og_camera* c, double x0, double y0, double x1,
+                double y1, double* out) {
+  og_proj p;
+  out[0] = out[1] = out[2] = 0;
+  if (!og_project(sc, i, c, &p)) return 0;
+  double key, qmin;
+  int k = og_tile_keep(&p, c, x0, y0, x1, y1, &key, &qmin);
+  out[0] = k;
+  out[1] = key;
+  out[2] = qmin;
+  return k;
+}
+
+/* Local-affine (EWA) projection as in 3DGS, used only by the pins (Eq. 3):
+ * out = mean2d[2], cov2d[3] (xx, xy, yy) including the 0.3 px^2 dilation. */
+int og_ewa_one(const og_scene* sc, int64_t i, const og_camera* c, double* out) {
+  og_proj p;
+  if (!og_project(sc, i, c, &p)) return 0;
+  double x = p.mu[0], y = p.mu[1], z = p.mu[2];
+  double J[2][3] = {{c->fx / z, 0, -c->fx * x / (z * z)}, {0, c->fy / z, -c->fy * y / (z * z)}};
+  double S[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      double s = 0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) s += J[a][k] * p.Sc[k][l] * J[b][l];
+      S[a][b] = s;
+    }
+  out[0] = c->fx * x / z + c->cx;
+  out[1] = c->fy * y / z + c->cy;
+  out[2] = S[0][0] + OG_DILATION_PX2;
+  out[3] = S[0][1];
+  out[4] = S[1][1] + OG_DILATION_PX2;
+  return 1;
+}
+
+/* ------------------------------------------------------------------ rendering ---- */
+
+typedef struct {
+  double key;
+  int32_t gid;
+} went;
+
+static int went_less(went a, went b) { return a.key < b.key || (a.key == b.key && a.gid < b.gid); }
+
+typedef struct {
+  went* e;
+  int n, cap;
+} window;
+
+static void win_push(window* w, went x, int* tie) {
+  if (w->n == w->cap) {
+    w->cap = w->cap ? 2 * w->cap : 16;
+    w->e = (went*)realloc(w->e, sizeof(went) * w->cap);
+  }
+  int j = w->n++;
+  while (j > 0 && went_less(x, w->e[j - 1])) {
+    w->e[j] = w->e[j - 1];
+    --j;
+  }
+  w->e[j] = x;
+  double tol = g_margin_tie * fabs(x.key);
+  if ((j > 0 && fabs(w->e[j - 1].key - x.key) <= tol) || (j + 1 < w->n && fabs(w->e[j + 1].key - x.key) <= tol))
+    *tie = 1;
+}
+
+static went win_pop(window* w) {
+  went m = w->e[0];
+  memmove(w->e, w->e + 1, sizeof(went) * (w->n - 1));
+  w->n--;
+  return m;
+}
+
+typedef struct {
+  double C[3], T;
+  int done, marginal, active_sample;
+  int32_t* gids;
+  int ng, capg;
+} sample;
+
+static void sample_push(sample* s, int32_t g) {
+  if (s->ng == s->capg) {
+    s->capg = s->capg ? 2 * s->capg : 16;
+    s->gids = (int32_t*)realloc(s->gids, sizeof(int32_t) * s->capg);
+  }
+  s->gids[s->ng++] = g;
+}
+
+/* front-to-back blending step (Eq. 2) with the 3DGS stopping rule */
+static void blend(sample* s, double alpha, const double rgb[3], int32_t g) {
+  if (s->done) return;
+  double test = s->T * (1.0 - alpha);
+  if (fabs(test - OG_T_STOP) < g_margin_stop * OG_T_STOP) s->marginal = 1;
+  if (test < OG_T_STOP) {
+    s->done = 1;
+    return;
+  }
+  for (int c = 0; c < 3; ++c) s->C[c] += alpha * s->T * rgb[c];
+  s->T = test;
+  sample_push(s, g);
+}
+
+typedef struct {
+  const og_proj* P;
+  const og_camera* cam;
+  sample* s[16];
+  double px[16], py[16];
+  double c4[2], c2[4][2];
+  window L1, L2[4], L3[16];
+  int k1, k2, k3;
+  int tie;
+  double last_key; /* tile key of the previous stream entry that was a block member */
+  int has_last;
+  int64_t evals, kept;
+} hblock;
+
+static int near_alpha_min(double sg) { return fabs(sg - OG_ALPHA_MIN) < g_margin_alpha * OG_ALPHA_MIN; }
+
+static void mark_threshold(sample* s, double sg) {
+  if (near_alpha_min(sg) || fabs(sg - OG_ALPHA_MAX) < g_margin_alpha * OG_ALPHA_MAX) s->marginal = 1;
+}
+
+/* kept test at sample i; *flip (optional) reports a keep decision within the margin */
+static int kept_at_f(hblock* B, int i, int32_t g, double* a, double* t, int* flip) {
+  if (!B->s[i] || B->s[i]->done) return 0;
+  double sg;
+  B->evals++;
+  int k = og_eval(&B->P[g], B->cam, B->px[i], B->py[i], a, t, &sg);
+  mark_threshold(B->s[i], sg);
+  if (flip) *flip = near_alpha_min(sg);
+  return k;
+}
+
+static int kept_at(hblock* B, int i, int32_t g, double* a, double* t) { return kept_at_f(B, i, g, a, t, NULL); }
+
+/* membership of a block = kept at any active sample; it can flip in FP32 only when every
+ * keep decision behind it is marginal */
+typedef struct {
+  int sure, unsure;
+} vote;
+
+static void vote_add(vote* v, int kept, int flip) {
+  if (kept && !flip) v->sure = 1;
+  if (flip) v->unsure = 1;
+}
+
+static int vote_result(hblock* B, vote v, int any) {
+  if (!v.sure && v.unsure) B->tie = 1;
+  return any;
+}
+
+static void blend_at(hblock* B, int i, int32_t g) {
+  double a, t, sg;
+  if (!B->s[i] || B->s[i]->done) return;
+  if (og_eval(&B->P[g], B->cam, B->px[i], B->py[i], &a, &t, &sg)) blend(B->s[i], a, B->P[g].rgb, g);
+}
+
+static void to_L3(hblock* B, int b, int32_t g) {
+  int bx = (b & 1) * 2, by = (b >> 1) * 2;
+  for (int j = 0; j < 4; ++j) {
+    int i = (by + (j >> 1)) * 4 + bx + (j & 1);
+    double a, t;
+    if (!kept_at(B, i, g, &a, &t)) continue;
+    B->kept++;
+    int tie = 0;
+    win_push(&B->L3[i], (went){t, g}, &tie);
+    if (tie) B->s[i]->marginal = 1;
+    if (B->L3[i].n > B->k3) blend_at(B, i, win_pop(&B->L3[i]).gid);
+  }
+}
+
+static void to_L2(hblock* B, int32_t g) {
+  for (int b = 0; b < 4; ++b) {
+    int bx = (b & 1) * 2, by = (b >> 1) * 2, any = 0;
+    vote vt = {0, 0};
+    for (int j = 0; j < 4; ++j) {
+      double a, t;
+      int f = 0, k = kept_at_f(B, (by + (j >> 1)) * 4 + bx + (j & 1), g, &a, &t, &f);
+      if (k) any = 1;
+      vote_add(&vt, k, f);
+    }
+    if (!vote_result(B, vt, any)) continue;
+    double v[3];
+    pixel_ray(B->cam, B->c2[b][0], B->c2[b][1], v);
+    win_push(&B->L2[b], (went){tstar_ray(&B->P[g], v), g}, &B->tie);
+    if (B->L2[b].n > B->k2) to_L3(B, b, win_pop(&B->L2[b]).gid);
+  }
+}
+
+static void stream_entry(hblock* B, int32_t g, double tile_key) {
+  int any = 0;
+  vote vt = {0, 0};
+  for (int i = 0; i < 16; ++i) {
+    double a, t;
+    int f = 0, k = kept_at_f(B, i, g, &a, &t, &f);
+    if (k) any = 1;
+    vote_add(&vt, k, f);
+  }
+  if (!vote_result(B, vt, any)) return;
+  /* FP32 keys may swap near-tied members of the stream */
+  if (B->has_last && fabs(tile_key - B->last_key) <= g_margin_tie * fabs(tile_key)) B->tie = 1;
+  B->last_key = tile_key;
+  B->has_last = 1;
+  double v[3];
+  pixel_ray(B->cam, B->c4[0], B->c4[1], v);
+  win_push(&B->L1, (went){tstar_ray(&B->P[g], v), g}, &B->tie);
+  if (B->L1.n > B->k1) to_L2(B, win_pop(&B->L1).gid);
+}
+
+static void flush_block(hblock* B) {
+  while (B->L1.n) to_L2(B, win_pop(&B->L1).gid);
+  for (int b = 0; b < 4; ++b)
+    while (B->L2[b].n) to_L3(B, b, win_pop(&B->L2[b]).gid);
+  for (int i = 0; i < 16; ++i)
+    while (B->L3[i].n) blend_at(B, i, win_pop(&B->L3[i]).gid);
+}
+
+typedef struct {
+  int32_t gid;
+  double key;
+} tentry;
+
+static int tentry_cmp(const void* a, const void* b) {
+  const tentry *x = (const tentry*)a, *y = (const tentry*)b;
+  if (x->key < y->key) return -1;
+  if (x->key > y->key) return 1;
+  return (x->gid > y->gid) - (x->gid < y->gid);
+}
+
+/* Gaussian/tile instances after the bounding rectangle and (optionally) Eq. 4 culling,
+ * sorted per tile by (key, gid): the stream every sample of the tile reads.  cnt gets
+ * ntiles + 1 prefix offsets. */
+static tentry* build_lists(const og_proj* P, int64_t n, const og_camera* cam, int T, int tile_cull,
+                           int64_t* cnt) {
+  const int W = cam->width, H = cam->height;
+  const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
+  tentry* lists = NULL;
+  for (int pass = 0; pass < 2; ++pass) {
+    int64_t* fill = pass ? (int64_t*)calloc(ntiles, sizeof(int64_t)) : NULL;
+    for (int64_t i = 0; i < n; ++i) {
+      if (!P[i].valid) continue;
+      const double* bb = P[i].bbox;
+      int tx0 = (int)ceil((bb[0] + 0.5) / T - 1), tx1 = (int)floor((bb[2] - 0.5) / T);
+      int ty0 = (int)ceil((bb[1] + 0.5) / T - 1), ty1 = (int)floor((bb[3] - 0.5) / T);
+      if (tx0 < 0) tx0 = 0;
+      if (ty0 < 0) ty0 = 0;
+      if (tx1 > ntx - 1) tx1 = ntx - 1;
+      if (ty1 > nty - 1) ty1 = nty - 1;
+      for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+          double key = P[i].mu[2], qmin;
+          if (tile_cull) {
+            double x0 = tx * T + 0.5, y0 = ty * T + 0.5;
+            double x1 = fmin((tx + 1) * T, W) - 0.5, y1 = fmin((ty + 1) * T, H) - 0.5;
+            if (!og_tile_keep(&P[i], cam, x0, y0, x1, y1, &key, &qmin)) continue;
+          }
+          int t = ty * ntx + tx;
+          if (!pass)
+            cnt[t + 1]++;
+          else
+            lists[cnt[t] + fill[t]++] = (tentry){(int32_t)i, key};
+        }
+    }
+    if (!pass) {
+      for (int t = 0; t < ntiles; ++t) cnt[t + 1] += cnt[t];
+      lists = (tentry*)malloc(sizeof(tentry) * (cnt[ntiles] ? cnt[ntiles] : 1));
+    } else {
+      free(fill);
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int t = 0; t < ntiles; ++t) qsort(lists + cnt[t], cnt[t + 1] - cnt[t], sizeof(tentry), tentry_cmp);
+  return lists;
+}
+
+typedef struct {
+  double t, alpha;
+  int32_t gid;
+} kpair;
+
+static int kpair_cmp(const void* a, const void* b) {
+  const kpair *x = (const kpair*)a, *y = (const kpair*)b;
+  if (x->t < y->t) return -1;
+  if (x->t > y->t) return 1;
+  return (x->gid > y->gid) - (x->gid < y->gid);
+}
+
+/* exact order at one sample: every kept candidate sorted by (t*, gid), then Eq. 2 */
+static void render_exact(const og_proj* P, const og_camera* cam, const int32_t* cand, int64_t nc,
+                         double px, double py, sample* s, int64_t* evals, int64_t* kept) {
+  kpair* kp = (kpair*)malloc(sizeof(kpair) * (nc ? nc : 1));
+  int64_t nk = 0;
+  for (int64_t j = 0; j < nc; ++j) {
+    double a, t, sg;
+    ++*evals;
+    int k = og_eval(&P[cand[j]], cam, px, py, &a, &t, &sg);
+    mark_threshold(s, sg);
+    if (k) kp[nk++] = (kpair){t, a, cand[j]};
+  }
+  *kept += nk;
+  qsort(kp, nk, sizeof(kpair), kpair_cmp);
+  for (int64_t j = 0; j < nk; ++j) {
+    if (j > 0 && fabs(kp[j].t - kp[j - 1].t) <= g_margin_tie * fabs(kp[j].t)) s->marginal = 1;
+    blend(s, kp[j].alpha, P[kp[j].gid].rgb, kp[j].gid);
+    if (s->done) {
+      /* the pair after the stop could have come first among near-ties */
+      if (j + 1 < nk && fabs(kp[j + 1].t - kp[j].t) <= g_margin_tie * fabs(kp[j].t)) s->marginal = 1;
+      break;
+    }
+  }
+  free(kp);
+}
+
+static double fovea_weight(const og_opts* o, double px, double py) {
+  double dx = px - o->gaze_x, dy = py - o->gaze_y;
+  double w = (o->radius + o->band - sqrt(dx * dx + dy * dy)) / o->band;
+  return w < 0 ? 0 : (w > 1 ? 1 : w);
+}
+
+/* tile class from the distances of the tile's pixel centres to the gaze point */
+static int classify_tile(const og_opts* o, const og_camera* c, int tx, int ty, int T) {
+  double x0 = tx * T + 0.5, y0 = ty * T + 0.5;
+  double x1 = fmin((tx + 1) * T, c->width) - 0.5, y1 = fmin((ty + 1) * T, c->height) - 0.5;
+  double nx = fmin(fmax(o->gaze_x, x0), x1), ny = fmin(fmax(o->gaze_y, y0), y1);
+  double dmin = hypot(nx - o->gaze_x, ny - o->gaze_y);
+  double fx = fmax(fabs(x0 - o->gaze_x), fabs(x1 - o->gaze_x));
+  double fy = fmax(fabs(y0 - o->gaze_y), fabs(y1 - o->gaze_y));
+  double dmax = hypot(fx, fy);
+  if (dmax <= o->radius) return 0;
+  if (dmin >= o->radius + o->band) return 2;
+  return 1;
+}
+
+int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out* out) {
+  const int W = cam->width, H = cam->height, T = o->key_tile;
+  if (W <= 0 || H <= 0 || T <= 0 || T % 4) return -1;
+  if (o->foveated && (T != 32 || W % 2 || H % 2)) return -1;
+  if (o->brute && o->mode != 0) return -1;
+  const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
+  const int64_t n = sc->n;
+  const int W2 = W / 2, H2 = H / 2;
+  const int64_t nfull = (int64_t)W * H, nsamp = nfull + (int64_t)W2 * H2;
+  memset(out->stats, 0, sizeof out->stats);
+  g_margin_alpha = o->margin_alpha;
+  g_margin_stop = o->margin_stop;
+  g_margin_tie = o->margin_tie;
+
+  og_proj* P = (og_proj*)malloc(sizeof(og_proj) * (n ? n : 1));
+  int64_t nvalid = 0;
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : nvalid)
+  for (int64_t i = 0; i < n; ++i) nvalid += og_project(sc, i, cam, &P[i]);
+  out->stats[0] = nvalid;
+
+  /* tile classes */
+  uint8_t* cls = (uint8_t*)calloc(ntiles, 1);
+  if (o->foveated)
+    for (int ty = 0; ty < nty; ++ty)
+      for (int tx = 0; tx < ntx; ++tx) cls[ty * ntx + tx] = (uint8_t)classify_tile(o, cam, tx, ty, T);
+  if (out->tile_class) memcpy(out->tile_class, cls, ntiles);
+
+  /* tile lists sorted by (key, gid): the stream each sample reads */
+  int64_t* cnt = (int64_t*)calloc(ntiles + 1, sizeof(int64_t));
+  tentry* lists = NULL;
+  int32_t* brute_ids = NULL;
+  if (o->brute) {
+    brute_ids = (int32_t*)malloc(sizeof(int32_t) * (n ? n : 1));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (P[i].valid) brute_ids[m++] = (int32_t)i;
+    nvalid = m;
+  } else {
+    lists = build_lists(P, n, cam, T, o->tile_cull, cnt);
+  }
+  out->stats[1] = o->brute ? 0 : cnt[ntiles];
+
+  sample* S = (sample*)calloc(nsamp, sizeof(sample));
+  for (int64_t k = 0; k < nsamp; ++k) S[k].T = 1.0;
+  /* which samples exist: full-res pixels of focus/hybrid/plain tiles, groups of periphery tiles */
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      int c = cls[(y / T) * ntx + x / T];
+      if (c != 2) S[(int64_t)y * W + x].active_sample = 1;
+      else if (!(x & 1) && !(y & 1)) S[nfull + (int64_t)(y / 2) * W2 + x / 2].active_sample = 1;
+    }
+
+  int64_t evals = 0, kept = 0;
+  if (o->mode == 0) {
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : evals, kept)
+    for (int64_t k = 0; k < nsamp; ++k) {
+      if (!S[k].active_sample) continue;
+      double px, py;
+      int sx, sy;
+      if (k < nfull) {
+        sx = (int)(k % W);
+        sy = (int)(k / W);
+        px = sx + 0.5;
+        py = sy + 0.5;
+      } else {
+        int64_t g = k - nfull;
+        sx = (int)(g % W2) * 2;
+        sy = (int)(g / W2) * 2;
+        px = sx + 1.0;
+        py = sy + 1.0;
+      }
+      const int32_t* cand;
+      int64_t nc;
+      int32_t* tmp = NULL;
+      if (o->brute) {
+        cand = brute_ids;
+        nc = nvalid;
+      } else {
+        int t = (sy / T) * ntx + sx / T;
+        nc = cnt[t + 1] - cnt[t];
+        tmp = (int32_t*)malloc(sizeof(int32_t) * (nc ? nc : 1));
+        for (int64_t j = 0; j < nc; ++j) tmp[j] = lists[cnt[t] + j].gid;
+        cand = tmp;
+      }
+      render_exact(P, cam, cand, nc, px, py, &S[k], &evals, &kept);
+      free(tmp);
+    }
+  } else {
+    int k1 = o->mode == 1 ? 0 : o->k1, k2 = o->mode == 1 ? 0 : o->k2, k3 = o->k3;
+    /* independent 4x4 sample blocks of the full-res grid and of the group grid */
+    int nbx = (W + 3) / 4, nby = (H + 3) / 4, nbx2 = (W2 + 3) / 4, nby2 = (H2 + 3) / 4;
+    int64_t nb_full = (int64_t)nbx * nby, nb_all = nb_full + (int64_t)nbx2 * nby2;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : evals, kept)
+    for (int64_t bi = 0; bi < nb_all; ++bi) {
+      hblock B;
+      memset(&B, 0, sizeof B);
+      B.P = P;
+      B.cam = cam;
+      B.k1 = k1;
+      B.k2 = k2;
+      B.k3 = k3;
+      int lowgrid = bi >= nb_full;
+      int bx, by, any = 0, tile = -1;
+      if (!lowgrid) {
+        bx = (int)(bi % nbx) * 4;
+        by = (int)(bi / nbx) * 4;
+      } else {
+        bx = (int)((bi - nb_full) % nbx2) * 4;
+        by = (int)((bi - nb_full) / nbx2) * 4;
+      }
+      for (int i = 0; i < 16; ++i) {
+        int sx = bx + (i & 3), sy = by + (i >> 2);
+        int64_t k;
+        if (!lowgrid) {
+          if (sx >= W || sy >= H) continue;
+          k = (int64_t)sy * W + sx;
+          B.px[i] = sx + 0.5;
+          B.py[i] = sy + 0.5;
+          tile = (sy / T) * ntx + sx / T;
+        } else {
+          if (sx >= W2 || sy >= H2) continue;
+          k = nfull + (int64_t)sy * W2 + sx;
+          B.px[i] = 2 * sx + 1.0;
+          B.py[i] = 2 * sy + 1.0;
+          tile = ((2 * sy) / T) * ntx + (2 * sx) / T;
+        }
+        if (S[k].active_sample) {
+          B.s[i] = &S[k];
+          any = 1;
+        }
+      }
+      if (!any) continue;
+      if (!lowgrid) {
+        B.c4[0] = bx + 2.0;
+        B.c4[1] = by + 2.0;
+        for (int b = 0; b < 4; ++b) {
+          B.c2[b][0] = bx + (b & 1) * 2 + 1.0;
+          B.c2[b][1] = by + (b >> 1) * 2 + 1.0;
+        }
+      } else {
+        B.c4[0] = 2 * bx + 4.0;
+        B.c4[1] = 2 * by + 4.0;
+        for (int b = 0; b < 4; ++b) {
+          B.c2[b][0] = 2 * (bx + (b & 1) * 2) + 2.0;
+          B.c2[b][1] = 2 * (by + (b >> 1) * 2) + 2.0;
+        }
+      }
+      for (int64_t j = cnt[tile]; j < cnt[tile + 1]; ++j) {
+        int all_done = 1;
+        for (int i = 0; i < 16; ++i)
+          if (B.s[i] && !B.s[i]->done) all_done = 0;
+        if (all_done) break;
+        stream_entry(&B, lists[j].gid, lists[j].key);
+      }
+      flush_block(&B);
+      evals += B.evals;
+      kept += B.kept;
+      /* a block-level decision within the margins marks every sample of the block */
+      if (B.tie)
+        for (int i = 0; i < 16; ++i)
+          if (B.s[i]) B.s[i]->marginal = 1;
+      free(B.L1.e);
+      for (int b = 0; b < 4; ++b) free(B.L2[b].e);
+      for (int i = 0; i < 16; ++i) free(B.L3[i].e);
+    }
+  }
+  out->stats[2] = evals;
+  out->stats[3] = kept;
+
+  /* per-sample outputs */
+  double bg[3] = {o->bg[0], o->bg[1], o->bg[2]};
+  double* lowimg = (double*)calloc((size_t)3 * (W2 > 0 ? W2 : 1) * (H2 > 0 ? H2 : 1), sizeof(double));
+  uint8_t* lowmarg = (uint8_t*)calloc((size_t)(W2 > 0 ? W2 : 1) * (H2 > 0 ? H2 : 1), 1);
+  if (out->full)
+    for (int64_t k = 0; k < 4 * nfull; ++k) out->full[k] = NAN;
+  if (out->low)
+    for (int64_t k = 0; k < 4 * (int64_t)W2 * H2; ++k) out->low[k] = NAN;
+  for (int64_t k = 0; k < nsamp; ++k) {
+    if (!S[k].active_sample) continue;
+    if (k < nfull) {
+      if (out->full) {
+        for (int c = 0; c < 3; ++c) out->full[c * nfull + k] = S[k].C[c];
+        out->full[3 * nfull + k] = S[k].T;
+      }
+    } else if (out->low) {
+      int64_t g = k - nfull, ng = (int64_t)W2 * H2;
+      for (int c = 0; c < 3; ++c) out->low[c * ng + g] = S[k].C[c];
+      out->low[3 * ng + g] = S[k].T;
+    }
+  }
+  /* half-resolution image: group samples in periphery tiles, 2x2 means elsewhere */
+  if (o->foveated) {
+    for (int gy = 0; gy < H2; ++gy)
+      for (int gx = 0; gx < W2; ++gx) {
+        int64_t g = (int64_t)gy * W2 + gx;
+        sample* sg = &S[nfull + g];
+        if (sg->active_sample) {
+          for (int c = 0; c < 3; ++c) lowimg[c * W2 * H2 + g] = sg->C[c] + sg->T * bg[c];
+          lowmarg[g] = (uint8_t)sg->marginal;
+        } else {
+          for (int c = 0; c < 3; ++c) {
+            double s = 0;
+            for (int j = 0; j < 4; ++j) {
+              sample* sp = &S[(int64_t)(2 * gy + (j >> 1)) * W + 2 * gx + (j & 1)];
+              s += sp->C[c] + sp->T * bg[c];
+            }
+            lowimg[c * W2 * H2 + g] = 0.25 * s;
+          }
+          for (int j = 0; j < 4; ++j)
+            if (S[(int64_t)(2 * gy + (j >> 1)) * W + 2 * gx + (j & 1)].marginal) lowmarg[g] = 1;
+        }
+      }
+    if (out->lowimg) memcpy(out->lowimg, lowimg, sizeof(double) * 3 * W2 * H2);
+  }
+  int64_t nmarg = 0;
+  for (int y = 0; y < H; ++y)
+    for (int x = 0; x < W; ++x) {
+      int64_t k = (int64_t)y * W + x;
+      int c = cls[(y / T) * ntx + x / T];
+      int marg = 0;
+      double v[3];
+      if (!o->foveated || c == 0) {
+        for (int ch = 0; ch < 3; ++ch) v[ch] = S[k].C[ch] + S[k].T * bg[ch];
+        marg = S[k].marginal;
+      } else if (c == 1) {
+        double w = fovea_weight(o, x + 0.5, y + 0.5);
+        int64_t g = (int64_t)(y / 2) * W2 + x / 2;
+        for (int ch = 0; ch < 3; ++ch)
+          v[ch] = w * (S[k].C[ch] + S[k].T * bg[ch]) + (1 - w) * lowimg[ch * W2 * H2 + g];
+        marg = S[k].marginal || lowmarg[g];
+      } else {
+        /* bilinear upsampling with clamp-to-edge, half-pixel aligned */
+        double ux = (x + 0.5) / 2 - 0.5, uy = (y + 0.5) / 2 - 0.5;
+        int x0 = (int)floor(ux), y0 = (int)floor(uy);
+        double fx = ux - x0, fy = uy - y0;
+        int xa = x0 < 0 ? 0 : (x0 > W2 - 1 ? W2 - 1 : x0), xb = x0 + 1 > W2 - 1 ? W2 - 1 : x0 + 1;
+        int ya = y0 < 0 ? 0 : (y0 > H2 - 1 ? H2 - 1 : y0), yb = y0 + 1 > H2 - 1 ? H2 - 1 : y0 + 1;
+        if (xb < 0) xb = 0;
+        if (yb < 0) yb = 0;
+        for (int ch = 0; ch < 3; ++ch) {
+          const double* L = lowimg + (int64_t)ch * W2 * H2;
+          double top = (1 - fx) * L[ya * W2 + xa] + fx * L[ya * W2 + xb];
+          double bot = (1 - fx) * L[yb * W2 + xa] + fx * L[yb * W2 + xb];
+          v[ch] = (1 - fy) * top + fy * bot;
+        }
+        marg = lowmarg[ya * W2 + xa] || lowmarg[ya * W2 + xb] || lowmarg[yb * W2 + xa] || lowmarg[yb * W2 + xb];
+      }
+      for (int ch = 0; ch < 3; ++ch) out->image[ch * nfull + k] = v[ch];
+      if (out->marginal) out->marginal[k] = (uint8_t)marg;
+      nmarg += marg;
+    }
+  out->stats[5] = nmarg;
+
+  /* blend orders for the gradient oracle */
+  int64_t tot = 0, blended = 0;
+  for (int64_t k = 0; k < nsamp; ++k) {
+    if (out->order_off) out->order_off[k] = tot;
+    if (out->order && tot + S[k].ng <= out->max_order)
+      memcpy(out->order + tot, S[k].gids, sizeof(int32_t) * S[k].ng);
+    tot += S[k].ng;
+    blended += S[k].ng;
+    if (S[k].active_sample) out->stats[6]++;
+  }
+  if (out->order_off) out->order_off[nsamp] = tot;
+  out->n_order = tot;
+  out->stats[4] = blended;
+
+  for (int64_t k = 0; k < nsamp; ++k) free(S[k].gids);
+  free(S);
+  free(lowimg);
+  free(lowmarg);
+  free(lists);
+  free(brute_ids);
+  free(cnt);
+  free(cls);
+  free(P);
+  return 0;
+}
+
+/* Tile lists as the oracle builds them, for list-level comparisons:
+ * counts[ntiles] (always), and when gids/keys are given (sized >= total) the sorted
+ * lists concatenated by tile. Returns the total number of instances. */
+int64_t og_tile_lists(const og_scene* sc, const og_camera* cam, int T, int tile_cull, int64_t* counts,
+                      int32_t* gids, double* keys, int64_t cap) {
+  const int W = cam->width, H = cam->height;
+  const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
+  const int64_t n = sc->n;
+  og_proj* P = (og_proj*)malloc(sizeof(og_proj) * (n ? n : 1));
+#pragma omp parallel for schedule(dynamic, 1024)
+  for (int64_t i = 0; i < n; ++i) og_project(sc, i, cam, &P[i]);
+  int64_t* cnt = (int64_t*)calloc(ntiles + 1, sizeof(int64_t));
+  tentry* lists = build_lists(P, n, cam, T, tile_cull, cnt);
+  for (int t = 0; t < ntiles; ++t) counts[t] = cnt[t + 1] - cnt[t];
+  int64_t tot = cnt[ntiles];
+  if (gids && keys && cap >= tot)
+    for (int64_t j = 0; j < tot; ++j) {
+      gids[j] = lists[j].gid;
+      keys[j] = lists[j].key;
+    }
+  free(lists);
+  free(cnt);
+  free(P);
+  return tot;
+}
+
+int og_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

@@ -1,0 +1,207 @@
+/*
+ * vrsplat.h - C ABI of the GB300 (sm_103a) foveated, popping-free Gaussian-splat
+ * rasterizer: the data-parallel hot path of VRSplat (Tu et al., arXiv 2505.10144).
+ *
+ * The problem each call solves is the paper's rendering problem: Gaussians of Eq. 1,
+ * blended front to back by Eq. 2, projected with Optimal Projection (Sec. 4.2), ordered
+ * per ray by the depth of maximum response (StopThePop, Sec. 4.1), tile-culled on the
+ * optimal plane (Sec. 4.2, Eq. 4), with focus and periphery rendered in one launch
+ * (Sec. 4.3, "Single-Pass Foveated Rendering"), and its backward pass for the
+ * fine-tuning of Sec. 4.1 / Sec. 5.
+ *
+ * Conventions shared by every entry point:
+ *   - All pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *     pointers owned by the caller.  The library never frees caller memory.
+ *   - Every call is asynchronous on the given CUDA stream (cudaStream_t passed as void*,
+ *     NULL = legacy default stream) unless it says otherwise.  No C++ exception crosses
+ *     the ABI; every entry point returns a vrs_status.
+ *   - One vrs_ctx per host thread.  A context owns its workspace (device memory for
+ *     projected records, instances, sort buffers and saved forward state).
+ *   - Errors: VRS_ERR_INVALID for bad arguments (nothing is launched), VRS_ERR_CAPACITY
+ *     when the workspace cannot hold the Gaussian/tile instances and may not grow
+ *     (during stream capture), VRS_ERR_CUDA for a CUDA runtime error, VRS_ERR_TIMEOUT
+ *     when a device-side bounded wait gave up (the kernel returns early; results of
+ *     that call are invalid but the context stays usable).  vrs_last_error() gives a
+ *     one-line description.
+ *   - Camera model (OpenCV): camera x right, y down, z forward; world_to_cam is the
+ *     row-major 3x4 [R|t]; pixel (x, y) has its centre at (x + 0.5, y + 0.5).
+ */
+#ifndef VRSPLAT_H
+#define VRSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VRS_OK = 0,
+  VRS_ERR_INVALID = 1,
+  VRS_ERR_CAPACITY = 2,
+  VRS_ERR_CUDA = 3,
+  VRS_ERR_TIMEOUT = 4,
+  VRS_ERR_UNSUPPORTED = 5
+} vrs_status;
+
+typedef struct vrs_ctx vrs_ctx;
+
+/* One scene of N Gaussians (Eq. 1), device SoA float32, caller-owned:
+ *   mean[3][N], log_scale[3][N], quat[4][N] (w, x, y, z; need not be normalised),
+ *   opacity_logit[N] (opacity = sigmoid), sh[K][3][N] with K = (sh_degree + 1)^2,
+ *   sh_degree in 0..3.  Non-finite parameters cull the Gaussian. */
+typedef struct {
+  const float* mean;
+  const float* log_scale;
+  const float* quat;
+  const float* opacity_logit;
+  const float* sh;
+  int64_t n;
+  int sh_degree;
+} vrs_gaussians;
+
+/* Gradients of a scene, same layout as vrs_gaussians; accumulated into (+=). */
+typedef struct {
+  float* mean;
+  float* log_scale;
+  float* quat;
+  float* opacity_logit;
+  float* sh;
+} vrs_gaussian_grads;
+
+/* Pinhole camera; near_z culls Gaussians whose camera-space mean has z < near_z. */
+typedef struct {
+  float world_to_cam[12];
+  float fx, fy, cx, cy;
+  int width, height;
+  float near_z;
+} vrs_camera;
+
+/* Per-view foveation (Sec. 4.3).  The blend weight is
+ * w(p) = clamp((radius + band - |p - gaze|) / band, 0, 1); a 32x32 tile is focus if
+ * w = 1 on all its pixel centres, periphery if w = 0 on all, else hybrid.
+ *   mode 0: plain, every pixel rendered at full resolution (gaze ignored)
+ *   mode 1: single-pass foveated, periphery upsampled bilinearly (clamp to edge)
+ *   mode 2: single-pass foveated, periphery pixels left to the periphery network:
+ *           only the half-resolution image (d_low_rgb) is written for them
+ * focus_tile (8 or 16) only changes how focus tiles are split into work, never the
+ * image.  Foveated modes need even width and height. */
+typedef struct {
+  float gaze_x, gaze_y, radius_px, band_px;
+  int mode;
+  int focus_tile;
+} vrs_fovea;
+
+/* Per-ray ordering (Sec. 4.1):
+ *   sort_mode 0 exact: every kept pair of a sample sorted by (depth, Gaussian index)
+ *   sort_mode 1 window: one per-sample min-window of win[2] entries over the tile's
+ *               depth-sorted stream
+ *   sort_mode 2 hierarchical: min-windows of win[0] (4x4-sample block), win[1]
+ *               (2x2-sample block) and win[2] (per sample) entries in cascade
+ * win[*] <= 32.  key_tile: 16 or 32, the tile size of the global sort (foveated modes
+ * use 32).  bg: background colour.  stats: 1 to collect device counters. */
+typedef struct {
+  int sort_mode;
+  int win[3];
+  int key_tile;
+  float bg[3];
+  int stats;
+} vrs_render_opts;
+
+/* Create a context; workspace_bytes_hint pre-sizes the instance buffers (0 = grow on
+ * demand).  *ctx receives a handle to free with vrs_destroy. */
+vrs_status vrs_create(vrs_ctx** ctx, size_t workspace_bytes_hint);
+vrs_status vrs_destroy(vrs_ctx* ctx);
+
+/* Pre-size the workspace for up to n_views views of width x height, total_gaussians
+ * summed over the rendered views' scenes, and max_instances Gaussian/tile pairs.  Must
+ * be called outside stream capture before capturing vrs_render into a CUDA graph. */
+vrs_status vrs_reserve(vrs_ctx* ctx, int n_views, int width, int height, int64_t total_gaussians,
+                       int64_t max_instances);
+
+/* Render n_views views (Eq. 1-2, Sec. 4).  scenes[n_scenes] (host array of device
+ * SoA descriptions); h_view_scene[n_views] maps each view to its scene; h_cams and
+ * h_fovea are host arrays [n_views] (all views share width, height and fovea mode).
+ * d_out_rgb: device float [n_views][3][height][width], fully written.  d_low_rgb:
+ * optional device float [n_views][3][height/2][width/2] half-resolution image (required
+ * for fovea mode 2).  save_for_backward = 1 keeps what vrs_render_backward needs in
+ * the context until the next vrs_render.  Outside stream capture the call reads the
+ * instance count back (one host synchronisation) and grows the workspace as needed;
+ * inside capture it uses the reserved capacity and reports overflow through the
+ * status read by vrs_check_status. */
+vrs_status vrs_render(vrs_ctx* ctx, const vrs_gaussians* scenes, int n_scenes, const int* h_view_scene,
+                      const vrs_camera* h_cams, const vrs_fovea* h_fovea, int n_views,
+                      const vrs_render_opts* opts, float* d_out_rgb, float* d_low_rgb,
+                      int save_for_backward, void* stream);
+
+/* Backward of the last vrs_render called with save_for_backward = 1, with identical
+ * scenes, cameras, foveas and options: accumulates d<d_dL_drgb, rgb>/d(params) into
+ * grads[n_scenes] (device, caller-owned, same layouts).  d_dL_drgb: device float
+ * [n_views][3][H][W].  Sorting, culling and windowing are treated as constant (their
+ * derivative is zero almost everywhere); the per-ray order replayed is the forward's. */
+vrs_status vrs_render_backward(vrs_ctx* ctx, const vrs_gaussians* scenes, int n_scenes,
+                               const int* h_view_scene, const vrs_camera* h_cams,
+                               const vrs_fovea* h_fovea, int n_views, const vrs_render_opts* opts,
+                               const float* d_dL_drgb, const vrs_gaussian_grads* grads, void* stream);
+
+/* Synchronise the stream and return the device status of the calls issued so far
+ * (VRS_OK, VRS_ERR_CAPACITY or VRS_ERR_TIMEOUT); clears it.  required_instances, when
+ * not NULL, receives the largest instance count a render needed. */
+vrs_status vrs_check_status(vrs_ctx* ctx, void* stream, int64_t* required_instances);
+
+/* Counters of the last render (host int64[8]): 0 instances, 1 work items, 2 evaluated
+ * pairs, 3 kept pairs, 4 blended pairs, 5 views, 6 sort passes, 7 kernels launched.
+ * Counters 2-4 are filled only when opts.stats was 1.  Synchronises the stream. */
+vrs_status vrs_get_stats(vrs_ctx* ctx, void* stream, int64_t* h_out8);
+
+/* Copy the sorted instances of the last render into caller buffers:
+ * d_keys[cap] (uint64: (view * tiles_per_view + tile) << 32 | ordered float bits of the
+ * tile depth), d_vals[cap] (uint32 Gaussian index within its scene) and d_ranges
+ * [n_views * tiles_per_view][2] (uint32 start, end).  *n receives the instance count
+ * (synchronises the stream).  Returns VRS_ERR_CAPACITY when cap is too small. */
+vrs_status vrs_copy_instances(vrs_ctx* ctx, uint64_t* d_keys, uint32_t* d_vals, uint32_t* d_ranges,
+                              int64_t cap, int64_t* n, void* stream);
+
+/* Per-Gaussian Optimal-Projection records of one view (Sec. 4.2) for inspection:
+ * d_out[N][24] float (layout documented in the design doc: projected-mean pixel, plane map,
+ * conic, log2 opacity, depth form, rgb), d_bbox[N][4] float (xmin, ymin, xmax, ymax;
+ * all zero when culled), d_count[N] uint32 tiles kept after Eq. 4 culling with
+ * key_tile-sized tiles. */
+vrs_status vrs_project(vrs_ctx* ctx, const vrs_gaussians* scene, const vrs_camera* h_cam, int key_tile,
+                       float* d_out, float* d_bbox, uint32_t* d_count, void* stream);
+
+/* Stable LSD radix sort of n (key, value) pairs by the low `bits` bits of the key
+ * (onesweep: one histogram pass, then one decoupled-look-back pass per 8-bit digit).
+ * d_keys_in/d_vals_in are not modified; results go to d_keys_out/d_vals_out.  Scratch
+ * comes from the context.  bits in 1..64. */
+vrs_status vrs_sort_pairs(vrs_ctx* ctx, const uint64_t* d_keys_in, const uint32_t* d_vals_in,
+                          uint64_t* d_keys_out, uint32_t* d_vals_out, int64_t n, int bits, void* stream);
+
+/* Fine-tuning loss of Sec. 5 (0.8 L1 + 0.2 (1 - SSIM), SSIM of Wang et al. with an
+ * 11x11 Gaussian window, sigma 1.5, zero padding) over n_images images [3][H][W]:
+ * d_loss (device float[1]) receives the mean loss over images, d_grad (device
+ * [n_images][3][H][W], may be NULL) dLoss/dimage. */
+vrs_status vrs_loss_l1_ssim(vrs_ctx* ctx, const float* d_img, const float* d_target, int n_images, int height,
+                            int width, float* d_loss, float* d_grad, void* stream);
+
+/* One Adam step on n float parameters: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * p -= lr * (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).  All device pointers. */
+vrs_status vrs_adam_step(float* d_param, const float* d_grad, float* d_m, float* d_v, int64_t n, float lr,
+                         float beta1, float beta2, float eps, int step, void* stream);
+
+/* Stage timing with CUDA events (tracing).  vrs_profile_begin arms event recording at
+ * the stage boundaries of the next max_calls vrs_render calls (no host
+ * synchronisation is added).  vrs_profile_end synchronises the stream and returns, per
+ * stage, the summed device time in milliseconds over the recorded calls:
+ * h_stage_ms[8] = {preprocess, scan (+ instance-count read-back), duplicate, sort,
+ * ranges + work items, render, composite, whole call}; *n_calls the number recorded. */
+vrs_status vrs_profile_begin(vrs_ctx* ctx, int max_calls);
+vrs_status vrs_profile_end(vrs_ctx* ctx, void* stream, double* h_stage_ms, int64_t* n_calls);
+
+const char* vrs_last_error(vrs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VRSPLAT_H */

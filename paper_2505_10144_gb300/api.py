@@ -1,0 +1,233 @@
+"""Python binding of libvrsplat (include/vrsplat.h).
+
+Argument marshalling only: every step of the render, its backward, the loss and the
+optimiser runs in the library's CUDA kernels; PyTorch supplies device memory and the
+stream.  There is no CPU or PyTorch fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import VrsError
+
+SORT_MODES = {"exact": 0, "window": 1, "hier": 2}
+FOVEA_MODES = {"plain": 0, "bilinear": 1, "net": 2}
+
+
+def _ptr(t: torch.Tensor | None):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class DeviceScene:
+    """Gaussian parameters resident on the GPU (float32 SoA, see synth.Scene)."""
+    mean: torch.Tensor
+    log_scale: torch.Tensor
+    quat: torch.Tensor
+    opacity_logit: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+
+    @staticmethod
+    def from_host(scene, device="cuda") -> "DeviceScene":
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).to(device)
+        return DeviceScene(f(scene.mean), f(scene.log_scale), f(scene.quat), f(scene.opacity_logit), f(scene.sh),
+                           scene.sh_degree)
+
+    @property
+    def n(self) -> int:
+        return int(self.mean.shape[1])
+
+    def tensors(self):
+        return [self.mean, self.log_scale, self.quat, self.opacity_logit, self.sh]
+
+    def c(self) -> _lib.Gaussians:
+        for t in self.tensors():
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        return _lib.Gaussians(*[_ptr(t) for t in self.tensors()], self.n, self.sh_degree)
+
+    def zeros_like(self) -> "DeviceScene":
+        return DeviceScene(*[torch.zeros_like(t) for t in self.tensors()], self.sh_degree)
+
+
+def camera_c(cam) -> _lib.Camera:
+    c = _lib.Camera()
+    w = np.asarray(cam.world_to_cam, dtype=np.float32).ravel()
+    for k in range(12):
+        c.world_to_cam[k] = float(w[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height, c.near_z = int(cam.width), int(cam.height), float(cam.near_z)
+    return c
+
+
+def fovea_c(fov, mode: int, focus_tile: int = 16) -> _lib.Fovea:
+    f = _lib.Fovea()
+    if fov is not None:
+        f.gaze_x, f.gaze_y, f.radius_px, f.band_px = (float(fov.gaze_x), float(fov.gaze_y), float(fov.radius_px),
+                                                      float(fov.band_px))
+    else:
+        f.band_px = 1.0
+    f.mode, f.focus_tile = int(mode), int(focus_tile)
+    return f
+
+
+@dataclass
+class RenderConfig:
+    sort_mode: str = "hier"
+    windows: tuple = (4, 8, 16)
+    key_tile: int = 16
+    fovea_mode: str = "plain"
+    focus_tile: int = 16
+    bg: tuple = (0.0, 0.0, 0.0)
+    stats: bool = False
+
+    def opts(self) -> _lib.RenderOpts:
+        o = _lib.RenderOpts()
+        o.sort_mode = SORT_MODES[self.sort_mode]
+        for k in range(3):
+            o.win[k] = int(self.windows[k])
+            o.bg[k] = float(self.bg[k])
+        o.key_tile = int(self.key_tile)
+        o.stats = int(self.stats)
+        return o
+
+
+class Renderer:
+    """One library context (workspace owner).  Not thread-safe: one per thread."""
+
+    def __init__(self, workspace_bytes: int = 0):
+        self.lib = _lib.load()
+        self.ctx = C.c_void_p()
+        st = self.lib.vrs_create(C.byref(self.ctx), C.c_size_t(workspace_bytes))
+        if st != 0:
+            raise VrsError(st, "vrs_create failed")
+        self._keep = None
+
+    def close(self):
+        if self.ctx:
+            self.lib.vrs_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            raise VrsError(st, self.lib.vrs_last_error(self.ctx).decode())
+
+    def _marshal(self, scenes, view_scene, cams, foveas, cfg: RenderConfig):
+        n_views = len(cams)
+        sc = (_lib.Gaussians * len(scenes))(*[s.c() for s in scenes])
+        vs = (C.c_int * n_views)(*[int(v) for v in view_scene])
+        cm = (_lib.Camera * n_views)(*[camera_c(c) for c in cams])
+        mode = FOVEA_MODES[cfg.fovea_mode]
+        fv = (_lib.Fovea * n_views)(*[fovea_c(foveas[k] if foveas else None, mode, cfg.focus_tile)
+                                      for k in range(n_views)])
+        o = cfg.opts()
+        self._keep = (sc, vs, cm, fv, o)
+        return sc, vs, cm, fv, o
+
+    def reserve(self, n_views, width, height, total_gaussians, max_instances):
+        self._check(self.lib.vrs_reserve(self.ctx, n_views, width, height, int(total_gaussians), int(max_instances)))
+
+    def render(self, scenes, view_scene, cams, foveas=None, cfg: RenderConfig | None = None, out=None, low=None,
+               save: bool = False, stream=None) -> torch.Tensor:
+        cfg = cfg or RenderConfig()
+        n_views = len(cams)
+        W, H = int(cams[0].width), int(cams[0].height)
+        if out is None:
+            out = torch.empty((n_views, 3, H, W), device="cuda", dtype=torch.float32)
+        sc, vs, cm, fv, o = self._marshal(scenes, view_scene, cams, foveas, cfg)
+        self._check(self.lib.vrs_render(self.ctx, sc, len(scenes), vs, cm, fv, n_views, C.byref(o), _ptr(out),
+                                        _ptr(low), int(save), _stream(stream)))
+        return out
+
+    def backward(self, scenes, view_scene, cams, foveas, cfg: RenderConfig, dL_dout: torch.Tensor, grads,
+                 stream=None):
+        sc, vs, cm, fv, o = self._marshal(scenes, view_scene, cams, foveas, cfg)
+        gr = (_lib.GaussianGrads * len(grads))(*[_lib.GaussianGrads(*[_ptr(t) for t in g.tensors()]) for g in grads])
+        self._check(self.lib.vrs_render_backward(self.ctx, sc, len(scenes), vs, cm, fv, len(cams), C.byref(o),
+                                                 _ptr(dL_dout.contiguous()), gr, _stream(stream)))
+
+    def check(self, stream=None) -> int:
+        need = C.c_int64()
+        self._check(self.lib.vrs_check_status(self.ctx, _stream(stream), C.byref(need)))
+        return int(need.value)
+
+    def stats(self, stream=None) -> dict:
+        out = (C.c_int64 * 8)()
+        self._check(self.lib.vrs_get_stats(self.ctx, _stream(stream), out))
+        return dict(zip(["instances", "work_items", "evaluated", "kept", "blended", "views", "sort_passes",
+                         "kernels"], [int(v) for v in out[:8]]))
+
+    def instances(self, n_views: int, tiles_per_view: int, stream=None):
+        n = C.c_int64()
+        cap = max(self.stats(stream)["instances"], 1)
+        keys = torch.empty(cap, dtype=torch.int64, device="cuda")
+        vals = torch.empty(cap, dtype=torch.int32, device="cuda")
+        ranges = torch.empty((n_views * tiles_per_view, 2), dtype=torch.int32, device="cuda")
+        self._check(self.lib.vrs_copy_instances(self.ctx, _ptr(keys), _ptr(vals), _ptr(ranges), cap, C.byref(n),
+                                                _stream(stream)))
+        m = int(n.value)
+        return keys[:m], vals[:m], ranges
+
+    STAGES = ["preprocess", "scan", "duplicate", "sort", "ranges_workitems", "render", "composite", "total"]
+
+    def profile_begin(self, max_calls: int):
+        self._check(self.lib.vrs_profile_begin(self.ctx, int(max_calls)))
+
+    def profile_end(self, stream=None) -> tuple[dict, int]:
+        ms = (C.c_double * 8)()
+        n = C.c_int64()
+        self._check(self.lib.vrs_profile_end(self.ctx, _stream(stream), ms, C.byref(n)))
+        return dict(zip(self.STAGES, [float(v) for v in ms])), int(n.value)
+
+    def project(self, scene: DeviceScene, cam, key_tile: int = 16, stream=None):
+        out = torch.empty((scene.n, 24), device="cuda", dtype=torch.float32)
+        bbox = torch.empty((scene.n, 4), device="cuda", dtype=torch.float32)
+        cnt = torch.empty(scene.n, device="cuda", dtype=torch.int32)
+        g = scene.c()
+        cm = camera_c(cam)
+        self._check(self.lib.vrs_project(self.ctx, C.byref(g), C.byref(cm), key_tile, _ptr(out), _ptr(bbox), _ptr(cnt),
+                                         _stream(stream)))
+        return out, bbox, cnt
+
+    def sort_pairs(self, keys: torch.Tensor, vals: torch.Tensor, bits: int, stream=None):
+        n = keys.numel()
+        ko = torch.empty_like(keys)
+        vo = torch.empty_like(vals)
+        self._check(self.lib.vrs_sort_pairs(self.ctx, _ptr(keys.contiguous()), _ptr(vals.contiguous()), _ptr(ko),
+                                            _ptr(vo), n, bits, _stream(stream)))
+        return ko, vo
+
+    def loss(self, img: torch.Tensor, target: torch.Tensor, want_grad: bool = True, stream=None):
+        img, target = img.contiguous(), target.contiguous()
+        n, _, H, W = img.shape
+        loss = torch.empty(1, device="cuda", dtype=torch.float32)
+        grad = torch.empty_like(img) if want_grad else None
+        self._check(self.lib.vrs_loss_l1_ssim(self.ctx, _ptr(img), _ptr(target), n, H, W, _ptr(loss), _ptr(grad),
+                                              _stream(stream)))
+        return loss, grad
+
+
+def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float, step: int,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15, stream=None):
+    lib = _lib.load()
+    st = lib.vrs_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), lr, beta1, beta2, eps, step,
+                           _stream(stream))
+    if st != 0:
+        raise VrsError(st, "vrs_adam_step failed")

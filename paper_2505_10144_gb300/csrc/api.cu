@@ -1,0 +1,683 @@
+// The C ABI (include/vrsplat.h): argument checking, workspace ownership and the order of
+// the stages of one render: foveation map, Optimal-Projection preprocess, scan,
+// duplicate, radix sort, tile ranges, single-launch render, composite.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace vrs;
+
+namespace vrs {
+void launch_project_only(const SceneDev& s, const ViewParams* d_vp, int T, float* out, float* bbox, uint32_t* count,
+                         cudaStream_t st);
+vrs_status loss_l1_ssim_impl(const float* img, const float* tgt, int n, int H, int W, float* loss, float* grad,
+                             void* scratch, size_t scratch_bytes, cudaStream_t st);
+size_t loss_scratch_bytes(int n, int H, int W);
+}  // namespace vrs
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Saved {
+  bool valid = false;
+  int n_views = 0, W = 0, H = 0, key_tile = 0, fovea_mode = 0, sort_mode = 0, tiles_per_view = 0;
+  int k[3] = {0, 0, 0};
+  long long total_nv = 0;
+  int sorted_buf = 0;
+};
+
+}  // namespace
+
+struct vrs_ctx {
+  std::string err;
+  DevBuf views, view_list, rec, bbox, count, offsets, partials, keys[2], vals[2], sort_scratch, ranges, tile_class,
+      items, counters, low, s_full, s_low, stats, grad_rec, dsamp_full, dsamp_low, loss_scratch, misc;
+  ViewParams* h_views = nullptr;  // pinned staging
+  int* h_view_list = nullptr;
+  uint32_t* h_small = nullptr;    // pinned: [0] total instances, [1] status, [2] items
+  int staging_cap = 0;
+  cudaEvent_t staging_done = nullptr;
+  long long key_cap = 0;
+  long long max_needed = 0;
+  long long last_instances = 0;
+  int last_passes = 0;
+  int last_launches = 0;
+  Saved saved;
+  // stage profiling: 8 events per recorded call
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_cap = 0, prof_used = 0;
+  bool prof_on = false;
+};
+
+namespace {
+
+// record the stage boundary `k` (0..7) of the current profiled call, if any
+void prof_mark(vrs_ctx* c, int k, cudaStream_t st) {
+  if (!c->prof_on || c->prof_used >= c->prof_cap) return;
+  cudaEventRecord(c->prof_ev[(size_t)c->prof_used * 8 + k], st);
+}
+
+enum { kCtrNItems = 0, kCtrQueue = 1, kCtrTotal = 2, kCtrStatus = 3, kCtrSortN = 4, kCtrCount = 8 };
+
+vrs_status fail(vrs_ctx* c, vrs_status s, const char* msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+vrs_status cuda_fail(vrs_ctx* c, cudaError_t e, const char* where) {
+  if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return VRS_ERR_CUDA;
+}
+
+bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// grow a device buffer (never during capture); returns false on failure
+bool ensure(vrs_ctx* c, DevBuf& b, size_t bytes, bool cap_mode, vrs_status* st) {
+  if (bytes <= b.bytes) return true;
+  if (cap_mode) {
+    *st = fail(c, VRS_ERR_CAPACITY, "workspace too small during stream capture; call vrs_reserve first");
+    return false;
+  }
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  size_t want = bytes + bytes / 8 + 256;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    *st = cuda_fail(c, e, "cudaMalloc");
+    return false;
+  }
+  b.bytes = want;
+  return true;
+}
+
+template <class T>
+T* P(DevBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+__global__ void clamp_n_kernel(const uint32_t* total, uint32_t* n, long long cap, uint32_t* status) {
+  uint32_t t = *total;
+  if ((long long)t > cap) {
+    atomicOr(status, kStOverflow);
+    t = (uint32_t)cap;
+  }
+  *n = t;
+}
+
+__global__ void set_u32_kernel(uint32_t* p, uint32_t v) { *p = v; }
+
+int bits_for(long long n) {
+  int b = 0;
+  while ((1ll << b) < n) ++b;
+  return b;
+}
+
+vrs_status check_scene(vrs_ctx* c, const vrs_gaussians& s) {
+  if (s.n < 0 || s.n > (1ll << 31) - 1) return fail(c, VRS_ERR_INVALID, "scene size out of range");
+  if (s.sh_degree < 0 || s.sh_degree > 3) return fail(c, VRS_ERR_INVALID, "sh_degree must be 0..3");
+  if (s.n > 0 && (!s.mean || !s.log_scale || !s.quat || !s.opacity_logit || !s.sh))
+    return fail(c, VRS_ERR_INVALID, "null scene pointer");
+  return VRS_OK;
+}
+
+SceneDev to_dev(const vrs_gaussians& s) {
+  SceneDev d;
+  d.mean = s.mean;
+  d.ls = s.log_scale;
+  d.quat = s.quat;
+  d.logit = s.opacity_logit;
+  d.sh = s.sh;
+  d.n = s.n;
+  d.deg = s.sh_degree;
+  return d;
+}
+
+bool finite_cam(const vrs_camera& c) {
+  for (int i = 0; i < 12; ++i)
+    if (!std::isfinite(c.world_to_cam[i])) return false;
+  return std::isfinite(c.fx) && std::isfinite(c.fy) && std::isfinite(c.cx) && std::isfinite(c.cy) &&
+         std::isfinite(c.near_z) && c.fx > 0 && c.fy > 0 && c.near_z > 0;
+}
+
+void fill_view(ViewParams& vp, const vrs_camera& c, const vrs_fovea* f, int T) {
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) vp.R[3 * r + k] = c.world_to_cam[4 * r + k];
+    vp.t[r] = c.world_to_cam[4 * r + 3];
+  }
+  vp.fx = c.fx;
+  vp.fy = c.fy;
+  vp.cx = c.cx;
+  vp.cy = c.cy;
+  vp.near_z = c.near_z;
+  vp.W = c.width;
+  vp.H = c.height;
+  vp.ntx = (c.width + T - 1) / T;
+  vp.nty = (c.height + T - 1) / T;
+  vp.gaze_x = f ? f->gaze_x : 0.f;
+  vp.gaze_y = f ? f->gaze_y : 0.f;
+  vp.radius = f ? f->radius_px : 0.f;
+  vp.band = f ? f->band_px : 1.f;
+}
+
+vrs_status stage_views(vrs_ctx* c, int n_views, cudaStream_t st, bool cap_mode) {
+  vrs_status s = VRS_OK;
+  if (!ensure(c, c->views, sizeof(ViewParams) * n_views, cap_mode, &s)) return s;
+  if (!ensure(c, c->view_list, sizeof(int) * n_views, cap_mode, &s)) return s;
+  cudaError_t e = cudaMemcpyAsync(c->views.p, c->h_views, sizeof(ViewParams) * n_views, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->view_list.p, c->h_view_list, sizeof(int) * n_views, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !cap_mode) e = cudaEventRecord(c->staging_done, st);
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "staging copy");
+}
+
+vrs_status reserve_staging(vrs_ctx* c, int n_views) {
+  if (c->staging_done) cudaEventSynchronize(c->staging_done);
+  if (n_views <= c->staging_cap) return VRS_OK;
+  if (c->h_views) cudaFreeHost(c->h_views);
+  if (c->h_view_list) cudaFreeHost(c->h_view_list);
+  c->h_views = nullptr;
+  c->h_view_list = nullptr;
+  int cap = std::max(n_views, 64);
+  cudaError_t e = cudaMallocHost(&c->h_views, sizeof(ViewParams) * cap);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_view_list, sizeof(int) * cap);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMallocHost");
+  c->staging_cap = cap;
+  return VRS_OK;
+}
+
+struct Plan {
+  int n_views, W, H, T, tiles_per_view, fovea_mode;
+  long long total_nv;
+  std::vector<long long> view_n;
+  std::vector<int> scene_first, scene_count;  // into the view list grouped by scene
+};
+
+vrs_status plan_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, const int* view_scene,
+                       const vrs_camera* cams, const vrs_fovea* fov, int n_views, const vrs_render_opts* o,
+                       Plan& pl) {
+  if (!scenes || n_scenes <= 0 || !view_scene || !cams || n_views <= 0 || !o)
+    return fail(c, VRS_ERR_INVALID, "null or empty argument");
+  for (int s = 0; s < n_scenes; ++s) {
+    vrs_status st = check_scene(c, scenes[s]);
+    if (st) return st;
+  }
+  if (o->sort_mode < 0 || o->sort_mode > 2) return fail(c, VRS_ERR_INVALID, "sort_mode must be 0, 1 or 2");
+  if (o->sort_mode >= 1 && (o->win[2] < 1 || o->win[2] > kMaxWin))
+    return fail(c, VRS_ERR_INVALID, "per-sample window must be 1..32");
+  if (o->sort_mode == 2 && (o->win[0] < 0 || o->win[0] > kMaxWin || o->win[1] < 0 || o->win[1] > kMaxWin))
+    return fail(c, VRS_ERR_INVALID, "block windows must be 0..32");
+  const int W = cams[0].width, H = cams[0].height;
+  if (W <= 0 || H <= 0 || (long long)W * H > (1ll << 31)) return fail(c, VRS_ERR_INVALID, "bad image size");
+  const int fm = fov ? fov[0].mode : 0;
+  if (fm < 0 || fm > 2) return fail(c, VRS_ERR_INVALID, "fovea mode must be 0, 1 or 2");
+  int T = o->key_tile;
+  if (T != 16 && T != 32) return fail(c, VRS_ERR_INVALID, "key_tile must be 16 or 32");
+  if (fm != 0) {
+    if (T != 32) return fail(c, VRS_ERR_INVALID, "foveated rendering uses 32x32 key tiles");
+    if ((W & 1) || (H & 1)) return fail(c, VRS_ERR_INVALID, "foveated rendering needs even width and height");
+  }
+  for (int v = 0; v < n_views; ++v) {
+    if (cams[v].width != W || cams[v].height != H) return fail(c, VRS_ERR_INVALID, "views must share the image size");
+    if (!finite_cam(cams[v])) return fail(c, VRS_ERR_INVALID, "non-finite or non-positive camera values");
+    if (view_scene[v] < 0 || view_scene[v] >= n_scenes) return fail(c, VRS_ERR_INVALID, "view_scene out of range");
+    if (fov) {
+      if (fov[v].mode != fm) return fail(c, VRS_ERR_INVALID, "views must share the fovea mode");
+      if (fm != 0 && !(std::isfinite(fov[v].gaze_x) && std::isfinite(fov[v].gaze_y) && fov[v].radius_px >= 0 &&
+                       fov[v].band_px > 0))
+        return fail(c, VRS_ERR_INVALID, "bad fovea parameters");
+    }
+  }
+  pl.n_views = n_views;
+  pl.W = W;
+  pl.H = H;
+  pl.T = T;
+  pl.fovea_mode = fm;
+  pl.tiles_per_view = ((W + T - 1) / T) * ((H + T - 1) / T);
+  if ((long long)pl.tiles_per_view * n_views >= (1ll << 31)) return fail(c, VRS_ERR_INVALID, "too many tiles");
+  vrs_status st = reserve_staging(c, n_views);
+  if (st) return st;
+  pl.view_n.resize(n_views);
+  long long base = 0;
+  for (int v = 0; v < n_views; ++v) {
+    ViewParams& vp = c->h_views[v];
+    fill_view(vp, cams[v], fov ? &fov[v] : nullptr, T);
+    vp.scene = view_scene[v];
+    vp.base = base;
+    pl.view_n[v] = scenes[view_scene[v]].n;
+    base += pl.view_n[v];
+  }
+  pl.total_nv = base;
+  if (base >= (1ll << 32)) return fail(c, VRS_ERR_INVALID, "too many (view, Gaussian) pairs");
+  pl.scene_first.assign(n_scenes, 0);
+  pl.scene_count.assign(n_scenes, 0);
+  int k = 0;
+  for (int s = 0; s < n_scenes; ++s) {
+    pl.scene_first[s] = k;
+    for (int v = 0; v < n_views; ++v)
+      if (view_scene[v] == s) c->h_view_list[k++] = v;
+    pl.scene_count[s] = k - pl.scene_first[s];
+  }
+  return VRS_OK;
+}
+
+// everything up to (and including) the sorted, ranged instance list
+vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, const Plan& pl, cudaStream_t st,
+                           bool cap_mode) {
+  vrs_status s = VRS_OK;
+  const long long NV = std::max(pl.total_nv, 1ll);
+  const long long VT = (long long)pl.n_views * pl.tiles_per_view;
+  if (!ensure(c, c->rec, sizeof(float4) * kRecF4 * NV, cap_mode, &s) ||
+      !ensure(c, c->bbox, sizeof(float4) * NV, cap_mode, &s) || !ensure(c, c->count, sizeof(uint32_t) * NV, cap_mode, &s) ||
+      !ensure(c, c->offsets, sizeof(uint32_t) * NV, cap_mode, &s) ||
+      !ensure(c, c->partials, scan_partials_bytes(NV), cap_mode, &s) ||
+      !ensure(c, c->ranges, sizeof(uint32_t) * 2 * VT, cap_mode, &s) ||
+      !ensure(c, c->tile_class, VT, cap_mode, &s) || !ensure(c, c->items, sizeof(WorkItem) * 4 * VT, cap_mode, &s) ||
+      !ensure(c, c->counters, sizeof(uint32_t) * kCtrCount, cap_mode, &s))
+    return s;
+  if ((s = stage_views(c, pl.n_views, st, cap_mode))) return s;
+  uint32_t* ctr = P<uint32_t>(c->counters);
+  cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * kCtrStatus, st);  // n_items, queue, total (status is sticky)
+  cudaMemsetAsync(c->ranges.p, 0, sizeof(uint32_t) * 2 * VT, st);
+  prof_mark(c, 0, st);
+  int launches = 0;
+  for (int sc = 0; sc < n_scenes; ++sc) {
+    if (!pl.scene_count[sc]) continue;
+    ++launches;
+    launch_preprocess(to_dev(scenes[sc]), P<ViewParams>(c->views), P<int>(c->view_list) + pl.scene_first[sc],
+                      pl.scene_count[sc], pl.T, P<float4>(c->rec), P<float4>(c->bbox), P<uint32_t>(c->count), st);
+  }
+  prof_mark(c, 1, st);
+  launch_scan_u32(P<uint32_t>(c->count), P<uint32_t>(c->offsets), pl.total_nv, ctr + kCtrTotal,
+                  P<uint32_t>(c->partials), st);
+  launches += pl.total_nv > 0 ? 3 : 0;
+  long long need = c->key_cap;
+  if (!cap_mode) {
+    cudaMemcpyAsync(c->h_small, ctr + kCtrTotal, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "instance count");
+    need = c->h_small[0];
+    c->last_instances = need;
+    c->max_needed = std::max(c->max_needed, need);
+    if (need > c->key_cap) {
+      const long long cap = need + need / 4 + 4096;
+      for (int b = 0; b < 2; ++b)
+        if (!ensure(c, c->keys[b], sizeof(uint64_t) * cap, false, &s) || !ensure(c, c->vals[b], sizeof(uint32_t) * cap, false, &s))
+          return s;
+      if (!ensure(c, c->sort_scratch, sort_scratch_bytes(cap), false, &s)) return s;
+      c->key_cap = cap;
+    }
+  }
+  if (c->key_cap <= 0) return fail(c, VRS_ERR_CAPACITY, "no instance capacity reserved");
+  prof_mark(c, 2, st);
+  for (int v = 0; v < pl.n_views; ++v) launches += pl.view_n[v] > 0 ? 1 : 0;
+  launch_duplicate(P<ViewParams>(c->views), pl.n_views, P<float4>(c->rec), P<float4>(c->bbox), P<uint32_t>(c->count),
+                   P<uint32_t>(c->offsets), pl.view_n.data(), pl.T, pl.tiles_per_view, P<uint64_t>(c->keys[0]),
+                   P<uint32_t>(c->vals[0]), ctr + kCtrTotal, c->key_cap, ctr + kCtrStatus, st);
+  clamp_n_kernel<<<1, 1, 0, st>>>(ctr + kCtrTotal, ctr + kCtrSortN, c->key_cap, ctr + kCtrStatus);
+  prof_mark(c, 3, st);
+  SortScratch ss;
+  sort_scratch_carve(c->sort_scratch.p, c->key_cap, &ss);
+  uint64_t* kb[2] = {P<uint64_t>(c->keys[0]), P<uint64_t>(c->keys[1])};
+  uint32_t* vb[2] = {P<uint32_t>(c->vals[0]), P<uint32_t>(c->vals[1])};
+  const int bits = 32 + std::max(1, bits_for(VT));
+  c->last_passes = (bits + 7) / 8;
+  const long long sort_n = cap_mode ? c->key_cap : std::max(need, 1ll);
+  const int cur = launch_radix_sort(kb, vb, ctr + kCtrSortN, sort_n, bits, ss, ctr + kCtrStatus, st);
+  c->saved.sorted_buf = cur;
+  launches += 1 + 2 + c->last_passes;
+  prof_mark(c, 4, st);
+  launch_ranges(kb[cur], ctr + kCtrSortN, sort_n, P<uint32_t>(c->ranges), VT, st);
+  launch_workitems(P<ViewParams>(c->views), pl.n_views, pl.fovea_mode, pl.T, pl.tiles_per_view, P<WorkItem>(c->items),
+                   ctr + kCtrNItems, P<uint8_t>(c->tile_class), st);
+  c->last_launches = launches + 2;
+  return VRS_OK;
+}
+
+RenderArgs make_args(vrs_ctx* c, const Plan& pl, const vrs_render_opts* o) {
+  RenderArgs a;
+  memset(&a, 0, sizeof a);
+  uint32_t* ctr = P<uint32_t>(c->counters);
+  a.views = P<ViewParams>(c->views);
+  a.n_views = pl.n_views;
+  a.rec = P<float4>(c->rec);
+  a.bbox = P<float4>(c->bbox);
+  a.vals = P<uint32_t>(c->vals[c->saved.sorted_buf]);
+  a.ranges = P<uint32_t>(c->ranges);
+  a.items = P<WorkItem>(c->items);
+  a.n_items = ctr + kCtrNItems;
+  a.queue = ctr + kCtrQueue;
+  a.tile_class = P<uint8_t>(c->tile_class);
+  a.fovea_mode = pl.fovea_mode;
+  a.key_tile = pl.T;
+  a.tiles_per_view = pl.tiles_per_view;
+  a.sort_mode = o->sort_mode;
+  a.k1 = o->win[0];
+  a.k2 = o->win[1];
+  a.k3 = o->win[2];
+  for (int k = 0; k < 3; ++k) a.bg[k] = o->bg[k];
+  a.status = ctr + kCtrStatus;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+vrs_status vrs_create(vrs_ctx** ctx, size_t workspace_bytes_hint) {
+  if (!ctx) return VRS_ERR_INVALID;
+  *ctx = nullptr;
+  vrs_ctx* c = new (std::nothrow) vrs_ctx();
+  if (!c) return VRS_ERR_CUDA;
+  cudaError_t e = cudaMallocHost(&c->h_small, 16 * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->staging_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    delete c;
+    return VRS_ERR_CUDA;
+  }
+  memset(c->h_small, 0, 16 * sizeof(uint32_t));
+  vrs_status s = VRS_OK;
+  if (!ensure(c, c->counters, sizeof(uint32_t) * kCtrCount, false, &s)) {
+    delete c;
+    return s;
+  }
+  cudaMemset(c->counters.p, 0, sizeof(uint32_t) * kCtrCount);
+  if (workspace_bytes_hint > 0) {
+    const long long cap = (long long)(workspace_bytes_hint / 24);
+    for (int b = 0; b < 2; ++b)
+      if (!ensure(c, c->keys[b], sizeof(uint64_t) * cap, false, &s) || !ensure(c, c->vals[b], sizeof(uint32_t) * cap, false, &s)) {
+        vrs_destroy(c);
+        return s;
+      }
+    if (!ensure(c, c->sort_scratch, sort_scratch_bytes(cap), false, &s)) {
+      vrs_destroy(c);
+      return s;
+    }
+    c->key_cap = cap;
+  }
+  *ctx = c;
+  return VRS_OK;
+}
+
+vrs_status vrs_destroy(vrs_ctx* c) {
+  if (!c) return VRS_ERR_INVALID;
+  DevBuf* all[] = {&c->views, &c->view_list, &c->rec, &c->bbox, &c->count, &c->offsets, &c->partials, &c->keys[0],
+                   &c->keys[1], &c->vals[0], &c->vals[1], &c->sort_scratch, &c->ranges, &c->tile_class, &c->items,
+                   &c->counters, &c->low, &c->s_full, &c->s_low, &c->stats, &c->grad_rec, &c->dsamp_full,
+                   &c->dsamp_low, &c->loss_scratch, &c->misc};
+  for (DevBuf* b : all)
+    if (b->p) cudaFree(b->p);
+  if (c->h_views) cudaFreeHost(c->h_views);
+  if (c->h_view_list) cudaFreeHost(c->h_view_list);
+  if (c->h_small) cudaFreeHost(c->h_small);
+  if (c->staging_done) cudaEventDestroy(c->staging_done);
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+  delete c;
+  return VRS_OK;
+}
+
+vrs_status vrs_reserve(vrs_ctx* c, int n_views, int width, int height, int64_t total_gaussians, int64_t max_instances) {
+  if (!c || n_views <= 0 || width <= 0 || height <= 0 || total_gaussians < 0 || max_instances <= 0)
+    return fail(c, VRS_ERR_INVALID, "bad reserve arguments");
+  vrs_status s = VRS_OK;
+  const long long VT = (long long)n_views * ((width + 15) / 16) * ((height + 15) / 16);
+  const long long NV = std::max<long long>(total_gaussians, 1);
+  if (reserve_staging(c, n_views)) return VRS_ERR_CUDA;
+  if (!ensure(c, c->views, sizeof(ViewParams) * n_views, false, &s) || !ensure(c, c->view_list, sizeof(int) * n_views, false, &s) ||
+      !ensure(c, c->rec, sizeof(float4) * kRecF4 * NV, false, &s) || !ensure(c, c->bbox, sizeof(float4) * NV, false, &s) ||
+      !ensure(c, c->count, sizeof(uint32_t) * NV, false, &s) || !ensure(c, c->offsets, sizeof(uint32_t) * NV, false, &s) ||
+      !ensure(c, c->partials, scan_partials_bytes(NV), false, &s) ||
+      !ensure(c, c->ranges, sizeof(uint32_t) * 2 * VT, false, &s) || !ensure(c, c->tile_class, VT, false, &s) ||
+      !ensure(c, c->items, sizeof(WorkItem) * 4 * VT, false, &s) ||
+      !ensure(c, c->low, sizeof(float) * 3 * (size_t)n_views * (width / 2) * (height / 2) + 16, false, &s))
+    return s;
+  for (int b = 0; b < 2; ++b)
+    if (!ensure(c, c->keys[b], sizeof(uint64_t) * max_instances, false, &s) ||
+        !ensure(c, c->vals[b], sizeof(uint32_t) * max_instances, false, &s))
+      return s;
+  if (!ensure(c, c->sort_scratch, sort_scratch_bytes(max_instances), false, &s)) return s;
+  c->key_cap = std::max<long long>(c->key_cap, max_instances);
+  return VRS_OK;
+}
+
+vrs_status vrs_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, const int* view_scene,
+                      const vrs_camera* cams, const vrs_fovea* fov, int n_views, const vrs_render_opts* o,
+                      float* d_out_rgb, float* d_low_rgb, int save_for_backward, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!d_out_rgb) return fail(c, VRS_ERR_INVALID, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool cap_mode = capturing(st);
+  Plan pl;
+  vrs_status s = plan_render(c, scenes, n_scenes, view_scene, cams, fov, n_views, o, pl);
+  if (s) return s;
+  if (pl.fovea_mode == 2 && !d_low_rgb) return fail(c, VRS_ERR_INVALID, "fovea mode 2 needs d_low_rgb");
+  if ((s = build_instances(c, scenes, n_scenes, pl, st, cap_mode))) return s;
+  RenderArgs a = make_args(c, pl, o);
+  a.out = d_out_rgb;
+  const size_t low_bytes = sizeof(float) * 3 * (size_t)n_views * (pl.W / 2) * (pl.H / 2);
+  if (pl.fovea_mode != 0) {
+    if (d_low_rgb) {
+      a.low = d_low_rgb;
+    } else {
+      if (!ensure(c, c->low, low_bytes + 16, cap_mode, &s)) return s;
+      a.low = P<float>(c->low);
+    }
+  } else {
+    a.low = d_low_rgb;
+  }
+  const long long HW = (long long)pl.W * pl.H;
+  if (save_for_backward) {
+    if (!ensure(c, c->s_full, sizeof(float4) * HW * n_views, cap_mode, &s)) return s;
+    a.s_full = P<float4>(c->s_full);
+    if (pl.fovea_mode != 0) {
+      if (!ensure(c, c->s_low, sizeof(float4) * (HW / 4 + 1) * n_views, cap_mode, &s)) return s;
+      a.s_low = P<float4>(c->s_low);
+    }
+  }
+  if (o->stats) {
+    if (!ensure(c, c->stats, sizeof(unsigned long long) * 4, cap_mode, &s)) return s;
+    cudaMemsetAsync(c->stats.p, 0, sizeof(unsigned long long) * 4, st);
+    a.stats = P<unsigned long long>(c->stats);
+  }
+  const long long max_items = 4ll * n_views * pl.tiles_per_view;
+  prof_mark(c, 5, st);
+  launch_render(a, max_items, st);
+  prof_mark(c, 6, st);
+  if (pl.fovea_mode == 1) launch_composite(a, pl.W, pl.H, st);
+  prof_mark(c, 7, st);
+  if (c->prof_on && c->prof_used < c->prof_cap) c->prof_used++;
+  c->last_launches += 1 + (pl.fovea_mode == 1 ? 1 : 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "render launch");
+  Saved& sv = c->saved;
+  sv.valid = save_for_backward != 0;
+  sv.n_views = n_views;
+  sv.W = pl.W;
+  sv.H = pl.H;
+  sv.key_tile = pl.T;
+  sv.fovea_mode = pl.fovea_mode;
+  sv.sort_mode = o->sort_mode;
+  sv.tiles_per_view = pl.tiles_per_view;
+  sv.total_nv = pl.total_nv;
+  for (int k = 0; k < 3; ++k) sv.k[k] = o->win[k];
+  return VRS_OK;
+}
+
+vrs_status vrs_render_backward(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, const int* view_scene,
+                               const vrs_camera* cams, const vrs_fovea* fov, int n_views, const vrs_render_opts* o,
+                               const float* d_dL_drgb, const vrs_gaussian_grads* grads, void* stream) {
+  (void)scenes; (void)n_scenes; (void)view_scene; (void)cams; (void)fov; (void)n_views; (void)o;
+  (void)d_dL_drgb; (void)grads; (void)stream;
+  return fail(c, VRS_ERR_UNSUPPORTED, "backward not built yet");
+}
+
+vrs_status vrs_check_status(vrs_ctx* c, void* stream, int64_t* required_instances) {
+  if (!c) return VRS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  uint32_t* ctr = P<uint32_t>(c->counters);
+  uint32_t h[3];
+  e = cudaMemcpy(h, ctr + kCtrStatus - 1, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+  const uint32_t total = h[0], status = h[1];
+  c->max_needed = std::max<long long>(c->max_needed, total);
+  if (required_instances) *required_instances = c->max_needed;
+  cudaMemset(ctr + kCtrStatus, 0, sizeof(uint32_t));
+  if (status & kStTimeout) return fail(c, VRS_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (status & kStOverflow) return fail(c, VRS_ERR_CAPACITY, "instance buffer overflow");
+  return VRS_OK;
+}
+
+vrs_status vrs_get_stats(vrs_ctx* c, void* stream, int64_t* out) {
+  if (!c || !out) return VRS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  uint32_t ctr[kCtrCount];
+  cudaMemcpy(ctr, c->counters.p, sizeof ctr, cudaMemcpyDeviceToHost);
+  unsigned long long st3[4] = {0, 0, 0, 0};
+  if (c->stats.p) cudaMemcpy(st3, c->stats.p, sizeof st3, cudaMemcpyDeviceToHost);
+  out[0] = ctr[kCtrTotal];
+  out[1] = ctr[kCtrNItems];
+  out[2] = (int64_t)st3[0];
+  out[3] = (int64_t)st3[1];
+  out[4] = (int64_t)st3[2];
+  out[5] = c->saved.n_views;
+  out[6] = c->last_passes;
+  out[7] = c->last_launches;
+  return VRS_OK;
+}
+
+vrs_status vrs_copy_instances(vrs_ctx* c, uint64_t* d_keys, uint32_t* d_vals, uint32_t* d_ranges, int64_t cap,
+                              int64_t* n, void* stream) {
+  if (!c || !n) return VRS_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  uint32_t total = 0;
+  cudaMemcpy(&total, P<uint32_t>(c->counters) + kCtrSortN, sizeof total, cudaMemcpyDeviceToHost);
+  *n = total;
+  if (total > cap) return fail(c, VRS_ERR_CAPACITY, "caller buffer too small");
+  const int b = c->saved.sorted_buf;
+  if (d_keys && total) cudaMemcpyAsync(d_keys, c->keys[b].p, sizeof(uint64_t) * total, cudaMemcpyDeviceToDevice, st);
+  if (d_vals && total) cudaMemcpyAsync(d_vals, c->vals[b].p, sizeof(uint32_t) * total, cudaMemcpyDeviceToDevice, st);
+  if (d_ranges)
+    cudaMemcpyAsync(d_ranges, c->ranges.p, sizeof(uint32_t) * 2 * (size_t)c->saved.n_views * c->saved.tiles_per_view,
+                    cudaMemcpyDeviceToDevice, st);
+  e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "copy instances");
+}
+
+vrs_status vrs_project(vrs_ctx* c, const vrs_gaussians* scene, const vrs_camera* cam, int key_tile, float* d_out,
+                       float* d_bbox, uint32_t* d_count, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!scene || !cam || !d_out || !d_bbox || !d_count) return fail(c, VRS_ERR_INVALID, "null argument");
+  vrs_status s = check_scene(c, *scene);
+  if (s) return s;
+  if (key_tile != 16 && key_tile != 32) return fail(c, VRS_ERR_INVALID, "key_tile must be 16 or 32");
+  if (!finite_cam(*cam) || cam->width <= 0 || cam->height <= 0) return fail(c, VRS_ERR_INVALID, "bad camera");
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((s = reserve_staging(c, 1))) return s;
+  fill_view(c->h_views[0], *cam, nullptr, key_tile);
+  c->h_views[0].base = 0;
+  c->h_view_list[0] = 0;
+  if ((s = stage_views(c, 1, st, capturing(st)))) return s;
+  launch_project_only(to_dev(*scene), P<ViewParams>(c->views), key_tile, d_out, d_bbox, d_count, st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "project launch");
+}
+
+vrs_status vrs_sort_pairs(vrs_ctx* c, const uint64_t* d_keys_in, const uint32_t* d_vals_in, uint64_t* d_keys_out,
+                          uint32_t* d_vals_out, int64_t n, int bits, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (n < 0 || n >= (1ll << 32) || bits < 1 || bits > 64) return fail(c, VRS_ERR_INVALID, "bad sort arguments");
+  if (n > 0 && (!d_keys_in || !d_vals_in || !d_keys_out || !d_vals_out)) return fail(c, VRS_ERR_INVALID, "null pointer");
+  if (n == 0) return VRS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool cap_mode = capturing(st);
+  vrs_status s = VRS_OK;
+  if (!ensure(c, c->keys[1], sizeof(uint64_t) * n, cap_mode, &s) || !ensure(c, c->vals[1], sizeof(uint32_t) * n, cap_mode, &s) ||
+      !ensure(c, c->sort_scratch, sort_scratch_bytes(n), cap_mode, &s) ||
+      !ensure(c, c->misc, 16, cap_mode, &s))
+    return s;
+  cudaMemcpyAsync(d_keys_out, d_keys_in, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(d_vals_out, d_vals_in, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+  set_u32_kernel<<<1, 1, 0, st>>>(P<uint32_t>(c->misc), (uint32_t)n);
+  SortScratch ss;
+  sort_scratch_carve(c->sort_scratch.p, n, &ss);
+  uint64_t* kb[2] = {d_keys_out, P<uint64_t>(c->keys[1])};
+  uint32_t* vb[2] = {d_vals_out, P<uint32_t>(c->vals[1])};
+  const int cur = launch_radix_sort(kb, vb, P<uint32_t>(c->misc), n, bits, ss, P<uint32_t>(c->counters) + kCtrStatus, st);
+  if (cur == 1) {
+    cudaMemcpyAsync(d_keys_out, kb[1], sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(d_vals_out, vb[1], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "sort launch");
+}
+
+vrs_status vrs_loss_l1_ssim(vrs_ctx* c, const float* d_img, const float* d_target, int n_images, int height, int width,
+                            float* d_loss, float* d_grad, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!d_img || !d_target || !d_loss || n_images <= 0 || height <= 0 || width <= 0)
+    return fail(c, VRS_ERR_INVALID, "bad loss arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  vrs_status s = VRS_OK;
+  if (!ensure(c, c->loss_scratch, loss_scratch_bytes(n_images, height, width), capturing(st), &s)) return s;
+  return loss_l1_ssim_impl(d_img, d_target, n_images, height, width, d_loss, d_grad, c->loss_scratch.p,
+                           c->loss_scratch.bytes, st);
+}
+
+vrs_status vrs_profile_begin(vrs_ctx* c, int max_calls) {
+  if (!c || max_calls <= 0 || max_calls > (1 << 20)) return fail(c, VRS_ERR_INVALID, "bad profile size");
+  if (max_calls > c->prof_cap) {
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.assign((size_t)max_calls * 8, nullptr);
+    for (auto& e : c->prof_ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return fail(c, VRS_ERR_CUDA, "cudaEventCreate");
+    c->prof_cap = max_calls;
+  }
+  c->prof_used = 0;
+  c->prof_on = true;
+  return VRS_OK;
+}
+
+vrs_status vrs_profile_end(vrs_ctx* c, void* stream, double* ms, int64_t* n_calls) {
+  if (!c || !ms) return VRS_ERR_INVALID;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  for (int k = 0; k < 8; ++k) ms[k] = 0.0;
+  for (int i = 0; i < c->prof_used; ++i) {
+    cudaEvent_t* ev = &c->prof_ev[(size_t)i * 8];
+    for (int k = 0; k < 7; ++k) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[k], ev[k + 1]) == cudaSuccess) ms[k] += t;
+    }
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ev[0], ev[7]) == cudaSuccess) ms[7] += t;
+  }
+  if (n_calls) *n_calls = c->prof_used;
+  c->prof_on = false;
+  c->prof_used = 0;
+  return VRS_OK;
+}
+
+const char* vrs_last_error(vrs_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Internal declarations shared by the CUDA translation units of libvrsplat.
+//
+// Projected record of one Gaussian for one view (Optimal Projection, Sec. 4.2), six
+// float4 = 96 bytes, all in pixel units relative to the projected mean pm = K u / u_z:
+//
+//   f0 = (pm_x, pm_y, h00, h01)      a = h00 dx + h01 dy         (dx, dy) = p - pm
+//   f1 = (h10, h11, h20, h21)        b = h10 dx + h11 dy
+//   f2 = (h22, a00, a01x2, a11)      w = h20 dx + h21 dy + h22   (a, b, w) = [E; u] K^-1 p~
+//   f3 = (log2 sigma, n0, n1, n2)    tangent-plane point s = (a, b) / w
+//   f4 = (m00, m01x2, m11, m02x2)    q' = s^T A' s,  A' = 0.5 log2(e) Sigma_p^-1
+//   f5 = (m12x2, r, g, b)            alpha = min(0.99, 2^(log2 sigma - q'))
+//
+// depth of maximum response along the ray (StopThePop, Sec. 4.1):
+//   t* = (n0 dx + n1 dy + n2) / (m00 dx^2 + m01x2 dx dy + m11 dy^2 + m02x2 dx + m12x2 dy + 1)
+// which is the camera-space z of argmax_t G(t v), v = K^-1 p~, normalised so that
+// t*(pm) = n2 = z of the mean.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vrsplat.h"
+
+namespace vrs {
+
+constexpr int kRecF4 = 6;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTStop = 1e-4f;
+constexpr float kLog2_255 = 7.994353436858858f;
+constexpr float kHalfLog2e = 0.7213475204444817f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kDilationPx2 = 0.3f;
+
+// device status word bits
+constexpr uint32_t kStTimeout = 1u;
+constexpr uint32_t kStOverflow = 2u;
+
+constexpr int kMaxWin = 32;
+constexpr int kBlock = 256;
+
+struct ViewParams {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy, near_z;
+  int W, H;
+  int scene;
+  int ntx, nty;     // key tiles per row / column
+  long long base;   // offset of this view in the per-(view, Gaussian) arrays
+  float gaze_x, gaze_y, radius, band;
+};
+
+struct SceneDev {
+  const float *mean, *ls, *quat, *logit, *sh;
+  long long n;
+  int deg;
+};
+
+struct WorkItem {
+  int tile;  // view * tiles_per_view + tile index
+  int code;  // kind (0 full-res 16x16 pixels, 1 half-res 16x16 groups) | sub << 4
+};
+
+enum { kKindFull = 0, kKindLow = 1 };
+enum { kClassFocus = 0, kClassHybrid = 1, kClassPeriphery = 2 };
+
+__host__ __device__ inline uint32_t float_order_bits(float f) {
+  uint32_t b;
+#ifdef __CUDA_ARCH__
+  b = __float_as_uint(f);
+#else
+  union { float f; uint32_t u; } c;
+  c.f = f;
+  b = c.u;
+#endif
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// ---- per-pair evaluation, shared by every render path ------------------------------
+
+// returns true when the pair is kept (ray meets the tangent plane in front of o and
+// alpha >= 1/255); q' is returned through *qn for the alpha computation.
+__device__ __forceinline__ bool pair_test(const float4& f0, const float4& f1, const float4& f2, float lg2s,
+                                          float px, float py, float& dx, float& dy, float& qw) {
+  dx = px - f0.x;
+  dy = py - f0.y;
+  const float a = fmaf(f0.z, dx, f0.w * dy);
+  const float b = fmaf(f1.x, dx, f1.y * dy);
+  const float w = fmaf(f1.z, dx, fmaf(f1.w, dy, f2.x));
+  const float qn = fmaf(a, fmaf(f2.y, a, f2.z * b), f2.w * b * b);
+  const float w2 = w * w;
+  qw = __fdividef(qn, w2);
+  return (w > 0.f) && (qn <= (lg2s + kLog2_255) * w2);
+}
+
+__device__ __forceinline__ float pair_alpha(float lg2s, float qw) {
+  return fminf(kAlphaMax, exp2f(lg2s - qw));
+}
+
+__device__ __forceinline__ float pair_depth(const float4& f3, const float4& f4, float m12x2, float dx, float dy) {
+  const float num = fmaf(f3.y, dx, fmaf(f3.z, dy, f3.w));
+  const float den = fmaf(dx, fmaf(f4.x, dx, fmaf(f4.y, dy, f4.w)), fmaf(dy, fmaf(f4.z, dy, m12x2), 1.0f));
+  return __fdividef(num, den);
+}
+
+__device__ __forceinline__ bool tie_less(float ta, int ga, float tb, int gb) {
+  return ta < tb || (ta == tb && ga < gb);
+}
+
+// ---- launchers implemented in the .cu files -----------------------------------------
+
+void launch_preprocess(const SceneDev& s, const ViewParams* d_views, const int* d_view_list, int n_views_scene,
+                       int key_tile, float4* rec, float4* bbox, uint32_t* count, cudaStream_t st);
+void launch_scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* d_total, uint32_t* partials,
+                     cudaStream_t st);
+size_t scan_partials_bytes(long long n);
+void launch_duplicate(const ViewParams* d_views, int n_views, const float4* rec, const float4* bbox,
+                      const uint32_t* count, const uint32_t* offsets, const long long* h_view_n, int key_tile,
+                      int tiles_per_view, uint64_t* keys, uint32_t* vals, const uint32_t* d_total, long long cap,
+                      uint32_t* status, cudaStream_t st);
+
+struct SortScratch {
+  uint32_t* hist;      // [8][256]
+  uint32_t* look;      // [passes][max_tiles][256]
+  uint32_t* counters;  // [8]
+  long long max_tiles;
+};
+size_t sort_scratch_bytes(long long cap);
+void sort_scratch_carve(void* base, long long cap, SortScratch* s);
+// sorts n = *d_n (device) pairs; cap bounds n for grid sizing; returns index (0/1) of
+// the buffer holding the result
+int launch_radix_sort(uint64_t* keys[2], uint32_t* vals[2], const uint32_t* d_n, long long cap, int bits,
+                      const SortScratch& s, uint32_t* status, cudaStream_t st);
+void launch_ranges(const uint64_t* keys, const uint32_t* d_n, long long cap, uint32_t* ranges, long long n_tiles,
+                   cudaStream_t st);
+
+struct RenderArgs {
+  const ViewParams* views;
+  int n_views;
+  const float4* rec;
+  const float4* bbox;
+  const uint32_t* vals;
+  const uint32_t* ranges;
+  const WorkItem* items;
+  const uint32_t* n_items;
+  uint32_t* queue;
+  const uint8_t* tile_class;
+  int fovea_mode;
+  int key_tile;
+  int tiles_per_view;
+  int sort_mode;
+  int k1, k2, k3;
+  float bg[3];
+  float* out;      // [V][3][H][W]
+  float* low;      // [V][3][H/2][W/2] or null
+  float4* s_full;  // saved per full-res sample (C, T) or null
+  float4* s_low;   // saved per group sample or null
+  unsigned long long* stats;  // [3] evaluated, kept, blended or null
+  uint32_t* status;
+  // backward
+  const float* dL_dout;
+  const float* dL_dlow;
+  float* grad_rec;  // [sum N][16] per-(view, Gaussian) record gradients
+};
+
+void launch_workitems(const ViewParams* d_views, int n_views, int fovea_mode, int key_tile, int tiles_per_view,
+                      WorkItem* items, uint32_t* n_items, uint8_t* tile_class, cudaStream_t st);
+void launch_render(const RenderArgs& a, long long max_items, cudaStream_t st);
+void launch_composite(const RenderArgs& a, int W, int H, cudaStream_t st);
+void launch_render_backward(const RenderArgs& a, long long max_items, cudaStream_t st);
+void launch_composite_backward(const RenderArgs& a, int W, int H, float* dL_dsample_full, float* dL_dsample_low,
+                               cudaStream_t st);
+void launch_preprocess_backward(const SceneDev& s, const ViewParams* d_views, const int* d_view_list,
+                                int n_views_scene, const float4* rec, const float* grad_rec,
+                                const vrs_gaussian_grads& g, cudaStream_t st);
+int device_sm_count();
+
+}  // namespace vrs

@@ -1,0 +1,394 @@
+// Optimal-Projection preprocessing (Sec. 4.2), tile culling on the optimal plane (Eq. 4)
+// and Gaussian/tile key duplication (Sec. 3 tile-based rasterization, Sec. 4.3 32x32
+// tiles).  One thread per Gaussian reads its 59 parameters once and loops over every
+// view of its scene, so the parameter traffic of a batch of views is paid once.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace vrs {
+
+namespace {
+
+// real spherical-harmonics constants (3DGS sign convention): 1/(2 sqrt(pi)),
+// sqrt(3)/(2 sqrt(pi)), and the degree-2/3 normalisations
+constexpr float kY0 = 0.28209479177387814f;
+constexpr float kY1 = 0.4886025119029199f;
+constexpr float kY2a = 1.0925484305920792f;
+constexpr float kY2b = 0.31539156525252005f;
+constexpr float kY2c = 0.5462742152960396f;
+constexpr float kY3a = 0.5900435899266435f;
+constexpr float kY3b = 2.890611442640554f;
+constexpr float kY3c = 0.4570457994644658f;
+constexpr float kY3d = 0.3731763325901154f;
+constexpr float kY3e = 1.445305721320277f;
+
+__device__ __forceinline__ void sh_basis(int deg, float x, float y, float z, float Y[16]) {
+  Y[0] = kY0;
+  if (deg < 1) return;
+  Y[1] = -kY1 * y;
+  Y[2] = kY1 * z;
+  Y[3] = -kY1 * x;
+  if (deg < 2) return;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kY2a * x * y;
+  Y[5] = -kY2a * y * z;
+  Y[6] = kY2b * (2.f * zz - xx - yy);
+  Y[7] = -kY2a * x * z;
+  Y[8] = kY2c * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = -kY3a * y * (3.f * xx - yy);
+  Y[10] = kY3b * x * y * z;
+  Y[11] = -kY3c * y * (4.f * zz - xx - yy);
+  Y[12] = kY3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = -kY3c * x * (4.f * zz - xx - yy);
+  Y[14] = kY3e * z * (xx - yy);
+  Y[15] = -kY3a * x * (xx - 3.f * yy);
+}
+
+__device__ __forceinline__ bool finite3(float a, float b, float c) { return isfinite(a) && isfinite(b) && isfinite(c); }
+
+}  // namespace
+
+// Optimal projection of Gaussian i into view vp.  Writes the 96-byte record and a
+// conservative pixel bounding box of its alpha >= 1/255 region.  Returns false when the
+// Gaussian is culled (non-finite, behind near_z, opacity < 1/255, degenerate).
+__device__ bool project_gaussian(const SceneDev& s, long long i, const ViewParams& vp, float4 rec[6],
+                                 float4& bb) {
+  const long long n = s.n;
+  const float m0 = s.mean[i], m1 = s.mean[n + i], m2 = s.mean[2 * n + i];
+  const float l0 = s.ls[i], l1 = s.ls[n + i], l2 = s.ls[2 * n + i];
+  float qw = s.quat[i], qx = s.quat[n + i], qy = s.quat[2 * n + i], qz = s.quat[3 * n + i];
+  const float logit = s.logit[i];
+  if (!finite3(m0, m1, m2) || !finite3(l0, l1, l2) || !finite3(qw, qx, qy) || !isfinite(qz) || !isfinite(logit))
+    return false;
+  const float* R = vp.R;
+  const float mx = fmaf(R[0], m0, fmaf(R[1], m1, fmaf(R[2], m2, vp.t[0])));
+  const float my = fmaf(R[3], m0, fmaf(R[4], m1, fmaf(R[5], m2, vp.t[1])));
+  const float mz = fmaf(R[6], m0, fmaf(R[7], m1, fmaf(R[8], m2, vp.t[2])));
+  if (!(mz >= vp.near_z)) return false;
+  const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+  if (!(qn > 0.f)) return false;
+  const float iq = 1.f / qn;
+  qw *= iq; qx *= iq; qy *= iq; qz *= iq;
+  float G[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+  float Rc[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) Rc[3 * a + b] = R[3 * a] * G[b] + R[3 * a + 1] * G[3 + b] + R[3 * a + 2] * G[6 + b];
+  const float s2[3] = {expf(2.f * l0), expf(2.f * l1), expf(2.f * l2)};
+  const float si2[3] = {expf(-2.f * l0), expf(-2.f * l1), expf(-2.f * l2)};
+  float Sc[6], Si[6];  // xx xy xz yy yz zz
+  {
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const float* ra = Rc + 3 * ia[e];
+      const float* rb = Rc + 3 * ib[e];
+      Sc[e] = ra[0] * s2[0] * rb[0] + ra[1] * s2[1] * rb[1] + ra[2] * s2[2] * rb[2];
+      Si[e] = ra[0] * si2[0] * rb[0] + ra[1] * si2[1] * rb[1] + ra[2] * si2[2] * rb[2];
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 6; ++e)
+    if (!isfinite(Sc[e]) || !isfinite(Si[e])) return false;
+  const float sigma = 1.f / (1.f + expf(-logit));
+  if (!(sigma >= kAlphaMin)) return false;
+  const float lg2s = log2f(sigma);
+  const float d = sqrtf(mx * mx + my * my + mz * mz);
+  const float ux = mx / d, uy = my / d, uz = mz / d;
+  const float rho = sqrtf(ux * ux + uz * uz);
+  const float e1x = uz / rho, e1z = -ux / rho;  // e1y = 0
+  const float e2x = uy * e1z, e2y = uz * e1x - ux * e1z, e2z = -uy * e1x;
+  // Sigma_p = E Sc E^T / d^2 + dilation
+  auto quad = [&](float ax, float ay, float az, float bx, float by, float bz) {
+    return ax * (Sc[0] * bx + Sc[1] * by + Sc[2] * bz) + ay * (Sc[1] * bx + Sc[3] * by + Sc[4] * bz) +
+           az * (Sc[2] * bx + Sc[4] * by + Sc[5] * bz);
+  };
+  const float id2 = 1.f / (d * d);
+  const float dil = kDilationPx2 / (vp.fx * vp.fy);
+  const float p00 = quad(e1x, 0.f, e1z, e1x, 0.f, e1z) * id2 + dil;
+  const float p01 = quad(e1x, 0.f, e1z, e2x, e2y, e2z) * id2;
+  const float p11 = quad(e2x, e2y, e2z, e2x, e2y, e2z) * id2 + dil;
+  const float det = p00 * p11 - p01 * p01;
+  if (!(det > 0.f)) return false;
+  const float idet = kHalfLog2e / det;
+  const float A00 = p11 * idet, A01 = -p01 * idet, A11 = p00 * idet;
+  const float ifx = 1.f / vp.fx, ify = 1.f / vp.fy;
+  const float h00 = e1x * ifx, h01 = 0.f, h10 = e2x * ifx, h11 = e2y * ify, h20 = ux * ifx, h21 = uy * ify;
+  const float h22 = 1.f / uz;
+  const float pmx = fmaf(vp.fx, mx / mz, vp.cx), pmy = fmaf(vp.fy, my / mz, vp.cy);
+  // depth form, normalised so that den(pm) = 1 and t*(pm) = z of the mean
+  const float svx = Si[0] * mx + Si[1] * my + Si[2] * mz;
+  const float svy = Si[1] * mx + Si[3] * my + Si[4] * mz;
+  const float svz = Si[2] * mx + Si[4] * my + Si[5] * mz;
+  const float den0 = (mx * svx + my * svy + mz * svz) / (mz * mz);
+  if (!(den0 > 0.f) || !isfinite(den0)) return false;
+  const float iden = 1.f / den0;
+  const float n0 = svx * ifx * iden, n1 = svy * ify * iden;
+  const float m00 = Si[0] * ifx * ifx * iden, m01x2 = 2.f * Si[1] * ifx * ify * iden, m11 = Si[3] * ify * ify * iden;
+  const float m02x2 = 2.f * n0 / mz, m12x2 = 2.f * n1 / mz;
+  // colour along the world-space viewing direction R^T u
+  const float dx = R[0] * ux + R[3] * uy + R[6] * uz;
+  const float dy = R[1] * ux + R[4] * uy + R[7] * uz;
+  const float dz = R[2] * ux + R[5] * uy + R[8] * uz;
+  float Y[16];
+  sh_basis(s.deg, dx, dy, dz, Y);
+  const int K = (s.deg + 1) * (s.deg + 1);
+  float col[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float v = 0.5f;
+    for (int k = 0; k < K; ++k) v = fmaf(Y[k], s.sh[((long long)k * 3 + c) * n + i], v);
+    col[c] = fmaxf(v, 0.f);
+  }
+  rec[0] = make_float4(pmx, pmy, h00, h01);
+  rec[1] = make_float4(h10, h11, h20, h21);
+  rec[2] = make_float4(h22, A00, 2.f * A01, A11);
+  rec[3] = make_float4(lg2s, n0, n1, mz);
+  rec[4] = make_float4(m00, m01x2, m11, m02x2);
+  rec[5] = make_float4(m12x2, col[0], col[1], col[2]);
+  // bounding box: the cone (a, b) A' (a, b)^T <= cut w^2 seen as a conic in (dx, dy)
+  const float cut = lg2s + kLog2_255;
+  const float mA0x = A00 * h00 + A01 * h10, mA1x = A01 * h00 + A11 * h10;
+  const float mA0y = A00 * h01 + A01 * h11, mA1y = A01 * h01 + A11 * h11;
+  const float c00 = h00 * mA0x + h10 * mA1x - cut * h20 * h20;
+  const float c01 = h01 * mA0x + h11 * mA1x - cut * h20 * h21;
+  const float c11 = h01 * mA0y + h11 * mA1y - cut * h21 * h21;
+  const float cx = -cut * h22 * h20, cy = -cut * h22 * h21, c33 = -cut * h22 * h22;
+  const float cdet = c00 * c11 - c01 * c01;
+  bb = make_float4(0.f, 0.f, (float)vp.W, (float)vp.H);
+  if (c00 > 0.f && cdet > 1e-6f * c00 * c11) {
+    const float i00 = c11 / cdet, i01 = -c01 / cdet, i11 = c00 / cdet;
+    const float p0x = -(i00 * cx + i01 * cy), p0y = -(i01 * cx + i11 * cy);
+    const float k = c33 + cx * p0x + cy * p0y;
+    if (k < 0.f) {
+      const float hx = sqrtf(-k * i00) * 1.01f + 1.f, hy = sqrtf(-k * i11) * 1.01f + 1.f;
+      const float bx = pmx + p0x, by = pmy + p0y;
+      if (isfinite(bx) && isfinite(by) && isfinite(hx) && isfinite(hy))
+        bb = make_float4(fmaxf(bx - hx, -1e7f), fmaxf(by - hy, -1e7f), fminf(bx + hx, 1e7f), fminf(by + hy, 1e7f));
+    }
+  }
+  return true;
+}
+
+// Eq. 4 on the optimal plane.  The sample quad [x0, x1] x [y0, y1] maps to a convex
+// quadrilateral on the Gaussian's tangent plane; the plane maximum is the projected
+// mean if it lies inside, otherwise the best of the closed-form edge maxima (line
+// parameter clamped to the segment).  Returns true when the pair is kept; *key is the
+// depth t* on the ray through the maximum point projected back to the image.
+// Not inlined: the count pass and the emit pass run the same machine code, so they
+// make the same decisions.
+__device__ __noinline__ bool tile_keep(const float4* rec, float x0, float y0, float x1, float y1, float* key) {
+  const float4 f0 = rec[0], f1 = rec[1], f2 = rec[2], f3 = rec[3];
+  const float cxs[4] = {x0, x1, x1, x0}, cys[4] = {y0, y0, y1, y1};
+  float S0[4], S1[4];
+  *key = f3.w;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float dx = cxs[k] - f0.x, dy = cys[k] - f0.y;
+    const float a = fmaf(f0.z, dx, f0.w * dy);
+    const float b = fmaf(f1.x, dx, f1.y * dy);
+    const float w = fmaf(f1.z, dx, fmaf(f1.w, dy, f2.x));
+    if (!(w > 0.f)) return true;  // quad not bounded on the plane
+    S0[k] = a / w;
+    S1[k] = b / w;
+  }
+  bool pos = false, neg = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int l = (k + 1) & 3;
+    const float cr = (S0[l] - S0[k]) * (-S1[k]) - (S1[l] - S1[k]) * (-S0[k]);
+    pos |= cr > 0.f;
+    neg |= cr < 0.f;
+  }
+  if (!(pos && neg)) return true;  // projected mean inside: maximum at the mean
+  const float A00 = f2.y, A01 = 0.5f * f2.z, A11 = f2.w;
+  float qmin = INFINITY, X0 = 0.f, X1 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int l = (k + 1) & 3;
+    const float Px = S0[k], Py = S1[k], Dx = S0[l] - S0[k], Dy = S1[l] - S1[k];
+    const float APx = A00 * Px + A01 * Py, APy = A01 * Px + A11 * Py;
+    const float ADx = A00 * Dx + A01 * Dy, ADy = A01 * Dx + A11 * Dy;
+    const float dAd = Dx * ADx + Dy * ADy;
+    float t = dAd > 0.f ? -(Dx * APx + Dy * APy) / dAd : 0.f;
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    const float Xx = Px + t * Dx, Xy = Py + t * Dy;
+    const float q = Xx * (A00 * Xx + A01 * Xy) + Xy * (A01 * Xx + A11 * Xy);
+    if (q < qmin) {
+      qmin = q;
+      X0 = Xx;
+      X1 = Xy;
+    }
+  }
+  const float cut = f3.x + kLog2_255;
+  if (!(qmin <= cut * 1.0001f + 1e-5f)) return false;  // a hair conservative vs FP64
+  // back-project X to the image: solve a - X0 w = 0, b - X1 w = 0 for (dx, dy)
+  const float a00 = f0.z - X0 * f1.z, a01 = f0.w - X0 * f1.w;
+  const float a10 = f1.x - X1 * f1.z, a11 = f1.y - X1 * f1.w;
+  const float r0 = X0 * f2.x, r1 = X1 * f2.x;
+  const float dt = a00 * a11 - a01 * a10;
+  if (dt != 0.f) {
+    const float dx = (r0 * a11 - a01 * r1) / dt, dy = (a00 * r1 - a10 * r0) / dt;
+    const float w = fmaf(f1.z, dx, fmaf(f1.w, dy, f2.x));
+    if (w > 0.f && isfinite(dx) && isfinite(dy)) {
+      const float4 f4 = rec[4];
+      const float m12x2 = rec[5].x;
+      const float num = fmaf(f3.y, dx, fmaf(f3.z, dy, f3.w));
+      const float den = fmaf(dx, fmaf(f4.x, dx, fmaf(f4.y, dy, f4.w)), fmaf(dy, fmaf(f4.z, dy, m12x2), 1.0f));
+      const float kk = num / den;
+      if (isfinite(kk)) *key = kk;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tile_span(const float4& bb, const ViewParams& vp, int T, int& tx0, int& tx1,
+                                          int& ty0, int& ty1) {
+  tx0 = max((int)ceilf((bb.x + 0.5f) / T - 1.f), 0);
+  ty0 = max((int)ceilf((bb.y + 0.5f) / T - 1.f), 0);
+  tx1 = min((int)floorf((bb.z - 0.5f) / T), vp.ntx - 1);
+  ty1 = min((int)floorf((bb.w - 0.5f) / T), vp.nty - 1);
+}
+
+__device__ __forceinline__ void tile_quad(int tx, int ty, int T, const ViewParams& vp, float& x0, float& y0,
+                                          float& x1, float& y1) {
+  x0 = tx * T + 0.5f;
+  y0 = ty * T + 0.5f;
+  x1 = (float)min((tx + 1) * T, vp.W) - 0.5f;
+  y1 = (float)min((ty + 1) * T, vp.H) - 0.5f;
+}
+
+__global__ void __launch_bounds__(256) preprocess_kernel(SceneDev s, const ViewParams* __restrict__ views,
+                                                         const int* __restrict__ view_list, int nv, int T,
+                                                         float4* __restrict__ rec, float4* __restrict__ bbox,
+                                                         uint32_t* __restrict__ count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  for (int k = 0; k < nv; ++k) {
+    const ViewParams& vp = views[view_list[k]];
+    const long long vg = vp.base + i;
+    float4 r[6], bb;
+    uint32_t cnt = 0;
+    if (project_gaussian(s, i, vp, r, bb)) {
+      int tx0, tx1, ty0, ty1;
+      tile_span(bb, vp, T, tx0, tx1, ty0, ty1);
+      for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx) {
+          float x0, y0, x1, y1, key;
+          tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
+          cnt += tile_keep(r, x0, y0, x1, y1, &key) ? 1u : 0u;
+        }
+      if (cnt) {
+        float4* dst = rec + vg * kRecF4;
+#pragma unroll
+        for (int q = 0; q < kRecF4; ++q) dst[q] = r[q];
+      }
+    } else {
+      bb = make_float4(0.f, 0.f, -1.f, -1.f);
+    }
+    bbox[vg] = bb;
+    count[vg] = cnt;
+  }
+}
+
+__global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __restrict__ views, int view,
+                                                        const float4* __restrict__ rec,
+                                                        const float4* __restrict__ bbox,
+                                                        const uint32_t* __restrict__ count,
+                                                        const uint32_t* __restrict__ offsets, long long nview, int T,
+                                                        int tiles_per_view, uint64_t* __restrict__ keys,
+                                                        uint32_t* __restrict__ vals, long long cap,
+                                                        uint32_t* status) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nview) return;
+  const ViewParams& vp = views[view];
+  const long long vg = vp.base + i;
+  const uint32_t cnt = count[vg];
+  if (!cnt) return;
+  const float4 bb = bbox[vg];
+  const float4* r = rec + vg * kRecF4;
+  long long o = offsets[vg];
+  int tx0, tx1, ty0, ty1;
+  tile_span(bb, vp, T, tx0, tx1, ty0, ty1);
+  const uint64_t vbase = (uint64_t)view * (uint64_t)tiles_per_view;
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) {
+      float x0, y0, x1, y1, key;
+      tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
+      if (!tile_keep(r, x0, y0, x1, y1, &key)) continue;
+      if (o < cap) {
+        keys[o] = ((vbase + (uint64_t)(ty * vp.ntx + tx)) << 32) | float_order_bits(key);
+        vals[o] = (uint32_t)i;
+      } else {
+        atomicOr(status, kStOverflow);
+      }
+      ++o;
+    }
+}
+
+void launch_preprocess(const SceneDev& s, const ViewParams* d_views, const int* d_view_list, int nv, int T,
+                       float4* rec, float4* bbox, uint32_t* count, cudaStream_t st) {
+  if (s.n <= 0 || nv <= 0) return;
+  const unsigned grid = (unsigned)((s.n + 255) / 256);
+  preprocess_kernel<<<grid, 256, 0, st>>>(s, d_views, d_view_list, nv, T, rec, bbox, count);
+}
+
+void launch_duplicate(const ViewParams* d_views, int n_views, const float4* rec, const float4* bbox,
+                      const uint32_t* count, const uint32_t* offsets, const long long* h_view_n, int T,
+                      int tiles_per_view, uint64_t* keys, uint32_t* vals, const uint32_t* /*d_total*/, long long cap,
+                      uint32_t* status, cudaStream_t st) {
+  for (int v = 0; v < n_views; ++v) {
+    if (h_view_n[v] <= 0) continue;
+    const unsigned grid = (unsigned)((h_view_n[v] + 255) / 256);
+    duplicate_kernel<<<grid, 256, 0, st>>>(d_views, v, rec, bbox, count, offsets, h_view_n[v], T, tiles_per_view,
+                                           keys, vals, cap, status);
+  }
+}
+
+// ---- inspection entry point support ----------------------------------------------
+
+__global__ void project_only_kernel(SceneDev s, const ViewParams* __restrict__ vpp, int T, float* __restrict__ out,
+                                    float* __restrict__ bbox_out, uint32_t* __restrict__ count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= s.n) return;
+  const ViewParams vp = *vpp;
+  float4 r[6], bb;
+  uint32_t cnt = 0;
+  const bool ok = project_gaussian(s, i, vp, r, bb);
+  if (ok) {
+    int tx0, tx1, ty0, ty1;
+    tile_span(bb, vp, T, tx0, tx1, ty0, ty1);
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        float x0, y0, x1, y1, key;
+        tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
+        cnt += tile_keep(r, x0, y0, x1, y1, &key) ? 1u : 0u;
+      }
+  }
+  for (int q = 0; q < kRecF4; ++q) {
+    const float4 v = ok ? r[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    out[i * 24 + 4 * q + 0] = v.x;
+    out[i * 24 + 4 * q + 1] = v.y;
+    out[i * 24 + 4 * q + 2] = v.z;
+    out[i * 24 + 4 * q + 3] = v.w;
+  }
+  const float4 b = ok ? bb : make_float4(0.f, 0.f, 0.f, 0.f);
+  bbox_out[4 * i] = b.x;
+  bbox_out[4 * i + 1] = b.y;
+  bbox_out[4 * i + 2] = b.z;
+  bbox_out[4 * i + 3] = b.w;
+  count[i] = cnt;
+}
+
+void launch_project_only(const SceneDev& s, const ViewParams* d_vp, int T, float* out, float* bbox, uint32_t* count,
+                         cudaStream_t st) {
+  if (s.n <= 0) return;
+  project_only_kernel<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(s, d_vp, T, out, bbox, count);
+}
+
+}  // namespace vrs

@@ -1,0 +1,637 @@
+// Single-launch foveated blending (Sec. 4.3) with per-ray resorting (Sec. 4.1).
+//
+// Work items are 16x16-sample squares: full-resolution 16x16 pixel subtiles (focus and
+// hybrid 32x32 tiles split into four, or plain 16x16 tiles) and half-resolution 32x32
+// periphery tiles whose 256 samples are 2x2 pixel groups.  Every work item is one CTA
+// pass of 256 threads, one sample per thread, so focus and periphery run in the same
+// persistent launch.  Threads map to samples so that 16 consecutive lanes form a 4x4
+// sample block and 4 consecutive lanes a 2x2 block: the hierarchical windows of a block
+// live in shared memory, owned by the block's first lane, and membership is a ballot.
+//
+// Per entry of the tile's depth-sorted list, a thread evaluates its sample (Eq. 1 on
+// the optimal plane); kept pairs enter the per-ray windows; popped entries are blended
+// front to back (Eq. 2) with the 3DGS stopping rule.  Lists are staged through shared
+// memory 256 records at a time; each warp skips entries whose bounding box misses its
+// 8x4-sample region.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace vrs {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ void sample_xy(int tid, int& x, int& y) {
+  x = (tid & 1) | ((tid >> 1) & 2) | ((tid >> 2) & 4) | ((tid >> 2) & 8);
+  y = ((tid >> 1) & 1) | ((tid >> 2) & 2) | ((tid >> 4) & 4) | ((tid >> 4) & 8);
+}
+
+__global__ void workitems_kernel(const ViewParams* __restrict__ views, int n_views, int fovea_mode, int T,
+                                 int tiles_per_view, WorkItem* __restrict__ items, uint32_t* n_items,
+                                 uint8_t* __restrict__ tile_class) {
+  const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= (long long)n_views * tiles_per_view) return;
+  const int view = (int)(gi / tiles_per_view), t = (int)(gi % tiles_per_view);
+  const ViewParams& vp = views[view];
+  if (t >= vp.ntx * vp.nty) return;
+  const int tx = t % vp.ntx, ty = t / vp.ntx;
+  int cls = kClassFocus;
+  if (fovea_mode != 0) {
+    const float x0 = tx * T + 0.5f, y0 = ty * T + 0.5f;
+    const float x1 = (float)min((tx + 1) * T, vp.W) - 0.5f, y1 = (float)min((ty + 1) * T, vp.H) - 0.5f;
+    const float nx = fminf(fmaxf(vp.gaze_x, x0), x1) - vp.gaze_x, ny = fminf(fmaxf(vp.gaze_y, y0), y1) - vp.gaze_y;
+    const float fx = fmaxf(fabsf(x0 - vp.gaze_x), fabsf(x1 - vp.gaze_x));
+    const float fy = fmaxf(fabsf(y0 - vp.gaze_y), fabsf(y1 - vp.gaze_y));
+    const float dmin = sqrtf(nx * nx + ny * ny), dmax = sqrtf(fx * fx + fy * fy);
+    cls = dmax <= vp.radius ? kClassFocus : (dmin >= vp.radius + vp.band ? kClassPeriphery : kClassHybrid);
+  }
+  tile_class[gi] = (uint8_t)cls;
+  const int tile = (int)gi;
+  if (cls == kClassPeriphery) {
+    const uint32_t o = atomicAdd(n_items, 1u);
+    items[o] = WorkItem{tile, kKindLow};
+  } else if (T == 16) {
+    const uint32_t o = atomicAdd(n_items, 1u);
+    items[o] = WorkItem{tile, kKindFull};
+  } else {
+    for (int sub = 0; sub < 4; ++sub) {
+      const int ox = tx * 32 + (sub & 1) * 16, oy = ty * 32 + (sub >> 1) * 16;
+      if (ox >= vp.W || oy >= vp.H) continue;
+      const uint32_t o = atomicAdd(n_items, 1u);
+      items[o] = WorkItem{tile, kKindFull | (sub << 4)};
+    }
+  }
+}
+
+struct Smem {
+  float4* rec;       // [256][6]
+  int* gid;          // [256]
+  uint8_t* wmask;    // [256]
+  float* key3;       // [k3][256]
+  int* gid3;
+  float* alpha3;
+  float* key2;       // [k2][64]
+  int* gid2;
+  float* key1;       // [k1][16]
+  int* gid1;
+};
+
+__host__ __device__ inline size_t render_smem_bytes(int k1, int k2, int k3) {
+  return (size_t)kBlock * kRecF4 * 16 + kBlock * 4 + kBlock + 64 /*pad*/ + (size_t)k3 * kBlock * 12 +
+         (size_t)k2 * 64 * 8 + (size_t)k1 * 16 * 8 + 64;
+}
+
+__device__ inline Smem carve(unsigned char* base, int k1, int k2, int k3) {
+  Smem s;
+  unsigned char* p = base;
+  s.rec = reinterpret_cast<float4*>(p);
+  p += (size_t)kBlock * kRecF4 * 16;
+  s.gid = reinterpret_cast<int*>(p);
+  p += kBlock * 4;
+  s.key3 = reinterpret_cast<float*>(p);
+  p += (size_t)k3 * kBlock * 4;
+  s.gid3 = reinterpret_cast<int*>(p);
+  p += (size_t)k3 * kBlock * 4;
+  s.alpha3 = reinterpret_cast<float*>(p);
+  p += (size_t)k3 * kBlock * 4;
+  s.key2 = reinterpret_cast<float*>(p);
+  p += (size_t)k2 * 64 * 4;
+  s.gid2 = reinterpret_cast<int*>(p);
+  p += (size_t)k2 * 64 * 4;
+  s.key1 = reinterpret_cast<float*>(p);
+  p += (size_t)k1 * 16 * 4;
+  s.gid1 = reinterpret_cast<int*>(p);
+  p += (size_t)k1 * 16 * 4;
+  s.wmask = p;
+  return s;
+}
+
+// State of one thread's sample.
+struct Px {
+  float px, py;
+  float T, C0, C1, C2;
+  bool active;
+  int h3, n3;
+  unsigned n_eval, n_kept, n_blend;
+};
+
+template <bool STATS>
+__device__ __forceinline__ void blend(Px& p, float alpha, int g, const float4* __restrict__ recv) {
+  if (!p.active) return;
+  const float test = p.T * (1.f - alpha);
+  if (test < kTStop) {
+    p.active = false;
+    return;
+  }
+  const float4 c = recv[(long long)g * kRecF4 + 5];
+  const float aT = alpha * p.T;
+  p.C0 = fmaf(aT, c.y, p.C0);
+  p.C1 = fmaf(aT, c.z, p.C1);
+  p.C2 = fmaf(aT, c.w, p.C2);
+  p.T = test;
+  if (STATS) ++p.n_blend;
+}
+
+// per-thread ring window (ascending from head), insert-then-pop-min
+template <bool STATS>
+__device__ __forceinline__ void l3_push(Px& p, const Smem& s, int K3, float t, int g, float alpha,
+                                        const float4* __restrict__ recv) {
+  const int tid = threadIdx.x;
+  if (p.n3 == K3) {
+    const int hs = p.h3;
+    const float tm = s.key3[hs * kBlock + tid];
+    const int gm = s.gid3[hs * kBlock + tid];
+    if (tie_less(t, g, tm, gm)) {
+      blend<STATS>(p, alpha, g, recv);
+      return;
+    }
+    const float am = s.alpha3[hs * kBlock + tid];
+    p.h3 = hs + 1 == K3 ? 0 : hs + 1;
+    p.n3--;
+    // insert, then blend the popped minimum
+    int j = p.n3;
+    while (j > 0) {
+      int q = p.h3 + j - 1;
+      if (q >= K3) q -= K3;
+      const float tk = s.key3[q * kBlock + tid];
+      const int gk = s.gid3[q * kBlock + tid];
+      if (!tie_less(t, g, tk, gk)) break;
+      int d = q + 1;
+      if (d >= K3) d -= K3;
+      s.key3[d * kBlock + tid] = tk;
+      s.gid3[d * kBlock + tid] = gk;
+      s.alpha3[d * kBlock + tid] = s.alpha3[q * kBlock + tid];
+      --j;
+    }
+    int d = p.h3 + j;
+    if (d >= K3) d -= K3;
+    s.key3[d * kBlock + tid] = t;
+    s.gid3[d * kBlock + tid] = g;
+    s.alpha3[d * kBlock + tid] = alpha;
+    p.n3++;
+    blend<STATS>(p, am, gm, recv);
+    return;
+  }
+  int j = p.n3;
+  while (j > 0) {
+    int q = p.h3 + j - 1;
+    if (q >= K3) q -= K3;
+    const float tk = s.key3[q * kBlock + tid];
+    const int gk = s.gid3[q * kBlock + tid];
+    if (!tie_less(t, g, tk, gk)) break;
+    int d = q + 1;
+    if (d >= K3) d -= K3;
+    s.key3[d * kBlock + tid] = tk;
+    s.gid3[d * kBlock + tid] = gk;
+    s.alpha3[d * kBlock + tid] = s.alpha3[q * kBlock + tid];
+    --j;
+  }
+  int d = p.h3 + j;
+  if (d >= K3) d -= K3;
+  s.key3[d * kBlock + tid] = t;
+  s.gid3[d * kBlock + tid] = g;
+  s.alpha3[d * kBlock + tid] = alpha;
+  p.n3++;
+}
+
+// shared ring window of a sample block (owner lane only); returns the popped gid or -1
+__device__ __forceinline__ int ring_push(float* key, int* gid, int stride, int slot, int K, int& h, int& n, float t,
+                                         int g) {
+  if (K == 0) return g;
+  int popped = -1;
+  if (n == K) {
+    const float tm = key[h * stride + slot];
+    const int gm = gid[h * stride + slot];
+    if (tie_less(t, g, tm, gm)) return g;
+    popped = gm;
+    h = h + 1 == K ? 0 : h + 1;
+    n--;
+  }
+  int j = n;
+  while (j > 0) {
+    int q = h + j - 1;
+    if (q >= K) q -= K;
+    const float tk = key[q * stride + slot];
+    const int gk = gid[q * stride + slot];
+    if (!tie_less(t, g, tk, gk)) break;
+    int d = q + 1;
+    if (d >= K) d -= K;
+    key[d * stride + slot] = tk;
+    gid[d * stride + slot] = gk;
+    --j;
+  }
+  int d = h + j;
+  if (d >= K) d -= K;
+  key[d * stride + slot] = t;
+  gid[d * stride + slot] = g;
+  n++;
+  return popped;
+}
+
+__device__ __forceinline__ int ring_pop(const int* gid, int stride, int slot, int K, int& h, int& n) {
+  if (n == 0) return -1;
+  const int g = gid[h * stride + slot];
+  h = h + 1 == K ? 0 : h + 1;
+  n--;
+  return g;
+}
+
+__device__ __forceinline__ float depth_at(const float4* r, float x, float y) {
+  const float4 f0 = r[0], f3 = r[3], f4 = r[4];
+  const float m12x2 = r[5].x;
+  return pair_depth(f3, f4, m12x2, x - f0.x, y - f0.y);
+}
+
+// full evaluation of a record at the thread's sample: kept, alpha, depth
+template <bool STATS>
+__device__ __forceinline__ bool eval_full(const float4* r, Px& p, float& alpha, float& t) {
+  const float4 f0 = r[0], f1 = r[1], f2 = r[2], f3 = r[3];
+  float dx, dy, qw;
+  if (STATS) ++p.n_eval;
+  if (!pair_test(f0, f1, f2, f3.x, p.px, p.py, dx, dy, qw)) return false;
+  if (STATS) ++p.n_kept;
+  alpha = pair_alpha(f3.x, qw);
+  t = pair_depth(f3, r[4], r[5].x, dx, dy);
+  return true;
+}
+
+struct ItemGeom {
+  int view, kind, ox, oy;  // ox, oy: sample-grid origin (pixels for full, groups for low)
+  int tile;
+};
+
+__device__ __forceinline__ ItemGeom decode(const WorkItem& it, int tiles_per_view, int T, const ViewParams* views) {
+  ItemGeom g;
+  g.view = it.tile / tiles_per_view;
+  const int t = it.tile % tiles_per_view;
+  const ViewParams& vp = views[g.view];
+  const int tx = t % vp.ntx, ty = t / vp.ntx;
+  g.kind = it.code & 15;
+  const int sub = it.code >> 4;
+  g.tile = it.tile;
+  if (g.kind == kKindLow) {
+    g.ox = tx * 16;
+    g.oy = ty * 16;
+  } else if (T == 16) {
+    g.ox = tx * 16;
+    g.oy = ty * 16;
+  } else {
+    g.ox = tx * 32 + (sub & 1) * 16;
+    g.oy = ty * 32 + (sub >> 1) * 16;
+  }
+  return g;
+}
+
+// Warp-uniform 256-bit mask of the staged entries whose bounding box meets this warp's
+// 8x4-sample region.
+__device__ __forceinline__ void warp_masks(const Smem& s, int nb, unsigned m[8]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int j = c * 32 + lane;
+    const bool b = j < nb && ((s.wmask[j] >> w) & 1);
+    m[c] = __ballot_sync(kFull, b);
+  }
+}
+
+__device__ __forceinline__ void stage_batch(const Smem& s, const RenderArgs& a, const ViewParams& vp,
+                                            const ItemGeom& g, long long start, int nb) {
+  const int tid = threadIdx.x;
+  if (tid < nb) {
+    const int gid = (int)a.vals[start + tid];
+    const long long vg = vp.base + gid;
+    const float4* r = a.rec + vg * kRecF4;
+#pragma unroll
+    for (int q = 0; q < kRecF4; ++q) s.rec[tid * kRecF4 + q] = r[q];
+    s.gid[tid] = gid;
+    const float4 bb = a.bbox[vg];
+    uint8_t m = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      const int xo = 8 * (w & 1), yo = 4 * (w >> 1);
+      float x0, x1, y0, y1;
+      if (g.kind == kKindLow) {
+        x0 = 2.f * (g.ox + xo) + 1.f;
+        x1 = x0 + 14.f;
+        y0 = 2.f * (g.oy + yo) + 1.f;
+        y1 = y0 + 6.f;
+      } else {
+        x0 = g.ox + xo + 0.5f;
+        x1 = x0 + 7.f;
+        y0 = g.oy + yo + 0.5f;
+        y1 = y0 + 3.f;
+      }
+      if (bb.x <= x1 && bb.z >= x0 && bb.y <= y1 && bb.w >= y0) m |= (uint8_t)(1u << w);
+    }
+    s.wmask[tid] = m;
+  }
+}
+
+template <int MODE, bool STATS>
+__global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  const int K1 = MODE == 2 ? a.k1 : 0, K2 = MODE == 2 ? a.k2 : 0, K3 = MODE == 0 ? 0 : a.k3;
+  const Smem s = carve(smem_raw, K1, K2, K3);
+  const int tid = threadIdx.x, lane = tid & 31;
+  int sx, sy;
+  sample_xy(tid, sx, sy);
+  const int blk16 = tid >> 4;  // 4x4 block slot
+  const int blk4 = tid >> 2;   // 2x2 block slot
+  unsigned n_eval = 0, n_kept = 0, n_blend = 0;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= (int)*a.n_items) break;
+    const ItemGeom g = decode(a.items[item], a.tiles_per_view, a.key_tile, a.views);
+    const ViewParams& vp = a.views[g.view];
+    const float4* recv = a.rec + vp.base * kRecF4;
+    Px p;
+    bool valid;
+    int X = g.ox + sx, Y = g.oy + sy;
+    if (g.kind == kKindLow) {
+      valid = 2 * X < vp.W && 2 * Y < vp.H;
+      p.px = 2.f * X + 1.f;
+      p.py = 2.f * Y + 1.f;
+    } else {
+      valid = X < vp.W && Y < vp.H;
+      p.px = X + 0.5f;
+      p.py = Y + 0.5f;
+    }
+    p.T = 1.f;
+    p.C0 = p.C1 = p.C2 = 0.f;
+    p.active = valid;
+    p.h3 = p.n3 = 0;
+    p.n_eval = p.n_kept = p.n_blend = 0;
+    // block centres of this thread's 4x4 and 2x2 sample blocks
+    const int bx4 = g.ox + (sx & ~3), by4 = g.oy + (sy & ~3), bx2 = g.ox + (sx & ~1), by2 = g.oy + (sy & ~1);
+    float c4x, c4y, c2x, c2y;
+    if (g.kind == kKindLow) {
+      c4x = 2.f * bx4 + 4.f;
+      c4y = 2.f * by4 + 4.f;
+      c2x = 2.f * bx2 + 2.f;
+      c2y = 2.f * by2 + 2.f;
+    } else {
+      c4x = bx4 + 2.f;
+      c4y = by4 + 2.f;
+      c2x = bx2 + 1.f;
+      c2y = by2 + 1.f;
+    }
+    int h1 = 0, n1 = 0, h2 = 0, n2 = 0;  // meaningful in owner lanes
+    const bool own16 = (lane & 15) == 0, own4 = (lane & 3) == 0;
+    const long long start = a.ranges[2 * (long long)g.tile], end = a.ranges[2 * (long long)g.tile + 1];
+
+    // popped from a 2x2 window: per-sample test, into the per-ray window
+    auto pop2 = [&](int g2) {
+      if (g2 >= 0 && p.active) {
+        float al, t;
+        if (eval_full<STATS>(recv + (long long)g2 * kRecF4, p, al, t)) l3_push<STATS>(p, s, K3, t, g2, al, recv);
+      }
+    };
+    // popped from a 4x4 window: 2x2-block membership, 2x2 window
+    auto pop1 = [&](int g1) {
+      bool k = false;
+      const float4* r = recv + (long long)(g1 >= 0 ? g1 : 0) * kRecF4;
+      if (g1 >= 0 && p.active) {
+        float dx, dy, qw;
+        if (STATS) ++p.n_eval;
+        k = pair_test(r[0], r[1], r[2], r[3].x, p.px, p.py, dx, dy, qw);
+      }
+      const unsigned bal = __ballot_sync(kFull, k);
+      int g2 = -1;
+      if (own4 && ((bal >> (lane & ~3)) & 0xFu)) {
+        g2 = ring_push(s.key2, s.gid2, 64, blk4, K2, h2, n2, depth_at(r, c2x, c2y), g1);
+      }
+      g2 = __shfl_sync(kFull, g2, lane & ~3);
+      pop2(g2);
+    };
+
+    bool any_active = __syncthreads_count(p.active) > 0;
+    long long last_t_g = -1;  // exact mode: (t, g) of the last blended pair
+    float last_t = -INFINITY;
+    int last_g = -1;
+    (void)last_t_g;
+    for (int pass = 0; any_active; ++pass) {
+      float bt = INFINITY, ba = 0.f;
+      int bgid = 0x7fffffff;
+      for (long long b0 = start; b0 < end && any_active; b0 += kBlock) {
+        const int nb = (int)min((long long)kBlock, end - b0);
+        __syncthreads();
+        stage_batch(s, a, vp, g, b0, nb);
+        __syncthreads();
+        unsigned m[8];
+        warp_masks(s, nb, m);
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+          unsigned mm = m[c];
+          while (mm) {
+            const int j = c * 32 + __ffs(mm) - 1;
+            mm &= mm - 1;
+            const float4* r = s.rec + j * kRecF4;
+            const int gj = s.gid[j];
+            if (MODE == 0) {
+              float al, t;
+              if (p.active && eval_full<STATS>(r, p, al, t)) {
+                if (tie_less(last_t, last_g, t, gj) && tie_less(t, gj, bt, bgid)) {
+                  bt = t;
+                  bgid = gj;
+                  ba = al;
+                }
+              }
+            } else if (MODE == 1) {
+              float al, t;
+              if (p.active && eval_full<STATS>(r, p, al, t)) l3_push<STATS>(p, s, K3, t, gj, al, recv);
+            } else {
+              bool k = false;
+              if (p.active) {
+                float dx, dy, qw;
+                if (STATS) ++p.n_eval;
+                k = pair_test(r[0], r[1], r[2], r[3].x, p.px, p.py, dx, dy, qw);
+              }
+              const unsigned bal = __ballot_sync(kFull, k);
+              int g1 = -1;
+              if (own16 && ((bal >> (lane & 16)) & 0xFFFFu)) {
+                g1 = ring_push(s.key1, s.gid1, 16, blk16, K1, h1, n1, depth_at(r, c4x, c4y), gj);
+              }
+              g1 = __shfl_sync(kFull, g1, lane & 16);
+              if (__any_sync(kFull, g1 >= 0)) pop1(g1);
+            }
+          }
+        }
+        if (MODE != 0) any_active = __syncthreads_count(p.active) > 0;
+      }
+      if (MODE != 0) break;
+      // exact mode: blend this pass's minimum above the previous one
+      if (p.active) {
+        if (bgid == 0x7fffffff) {
+          p.active = false;
+        } else {
+          blend<STATS>(p, ba, bgid, recv);
+          last_t = bt;
+          last_g = bgid;
+        }
+      }
+      any_active = __syncthreads_count(p.active) > 0;
+    }
+    if (MODE == 2) {
+      for (int it = 0; it < K1; ++it) {
+        int g1 = own16 ? ring_pop(s.gid1, 16, blk16, K1, h1, n1) : -1;
+        g1 = __shfl_sync(kFull, g1, lane & 16);
+        if (__any_sync(kFull, g1 >= 0)) pop1(g1);
+      }
+      for (int it = 0; it < K2; ++it) {
+        int g2 = own4 ? ring_pop(s.gid2, 64, blk4, K2, h2, n2) : -1;
+        g2 = __shfl_sync(kFull, g2, lane & ~3);
+        pop2(g2);
+      }
+    }
+    if (MODE != 0) {
+      while (p.n3 > 0) {
+        const int hs = p.h3;
+        const int gm = s.gid3[hs * kBlock + tid];
+        const float am = s.alpha3[hs * kBlock + tid];
+        p.h3 = hs + 1 == K3 ? 0 : hs + 1;
+        p.n3--;
+        blend<STATS>(p, am, gm, recv);
+      }
+    }
+    // ---- outputs
+    const float v0 = fmaf(p.T, a.bg[0], p.C0), v1 = fmaf(p.T, a.bg[1], p.C1), v2 = fmaf(p.T, a.bg[2], p.C2);
+    const long long HW = (long long)vp.H * vp.W;
+    const int W2 = vp.W / 2, H2 = vp.H / 2;
+    const long long HW2 = (long long)H2 * W2;
+    if (g.kind == kKindFull) {
+      // 2x2 group average (lanes 4k..4k+3 hold one group, in (x, y) order (0,0),(1,0),(0,1),(1,1))
+      float s0 = v0 + __shfl_xor_sync(kFull, v0, 1), s1 = v1 + __shfl_xor_sync(kFull, v1, 1),
+            s2 = v2 + __shfl_xor_sync(kFull, v2, 1);
+      s0 += __shfl_xor_sync(kFull, s0, 2);
+      s1 += __shfl_xor_sync(kFull, s1, 2);
+      s2 += __shfl_xor_sync(kFull, s2, 2);
+      const float a0 = 0.25f * s0, a1 = 0.25f * s1, a2 = 0.25f * s2;
+      if (valid) {
+        float o0 = v0, o1 = v1, o2 = v2;
+        if (a.fovea_mode != 0 && a.tile_class[g.tile] == kClassHybrid) {
+          const float dx = p.px - vp.gaze_x, dy = p.py - vp.gaze_y;
+          const float w = fminf(fmaxf((vp.radius + vp.band - sqrtf(dx * dx + dy * dy)) / vp.band, 0.f), 1.f);
+          o0 = w * v0 + (1.f - w) * a0;
+          o1 = w * v1 + (1.f - w) * a1;
+          o2 = w * v2 + (1.f - w) * a2;
+        }
+        float* out = a.out + (long long)g.view * 3 * HW + (long long)Y * vp.W + X;
+        out[0] = o0;
+        out[HW] = o1;
+        out[2 * HW] = o2;
+        if (a.s_full) a.s_full[(long long)g.view * HW + (long long)Y * vp.W + X] = make_float4(p.C0, p.C1, p.C2, p.T);
+        if (a.low && own4 && X / 2 < W2 && Y / 2 < H2) {
+          float* lo = a.low + (long long)g.view * 3 * HW2 + (long long)(Y / 2) * W2 + X / 2;
+          lo[0] = a0;
+          lo[HW2] = a1;
+          lo[2 * HW2] = a2;
+        }
+      }
+    } else if (valid) {
+      float* lo = a.low + (long long)g.view * 3 * HW2 + (long long)Y * W2 + X;
+      lo[0] = v0;
+      lo[HW2] = v1;
+      lo[2 * HW2] = v2;
+      if (a.s_low) a.s_low[(long long)g.view * HW2 + (long long)Y * W2 + X] = make_float4(p.C0, p.C1, p.C2, p.T);
+    }
+    if (STATS) {
+      n_eval += p.n_eval;
+      n_kept += p.n_kept;
+      n_blend += p.n_blend;
+    }
+  }
+  if (STATS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n_eval += __shfl_xor_sync(kFull, n_eval, o);
+      n_kept += __shfl_xor_sync(kFull, n_kept, o);
+      n_blend += __shfl_xor_sync(kFull, n_blend, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&a.stats[0], (unsigned long long)n_eval);
+      atomicAdd(&a.stats[1], (unsigned long long)n_kept);
+      atomicAdd(&a.stats[2], (unsigned long long)n_blend);
+    }
+  }
+}
+
+// bilinear x2 upsampling of the half-resolution image into periphery tiles
+__global__ void composite_kernel(const ViewParams* __restrict__ views, int n_views, const uint8_t* __restrict__ tile_class,
+                                 int tiles_per_view, int T, const float* __restrict__ low, float* __restrict__ out, int W,
+                                 int H) {
+  const long long HW = (long long)W * H;
+  const int W2 = W / 2, H2 = H / 2;
+  const long long HW2 = (long long)W2 * H2;
+  const long long total = HW * n_views;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int view = (int)(i / HW);
+    const long long r = i % HW;
+    const int y = (int)(r / W), x = (int)(r % W);
+    const ViewParams& vp = views[view];
+    if (tile_class[(long long)view * tiles_per_view + (y / T) * vp.ntx + x / T] != kClassPeriphery) continue;
+    const float ux = (x + 0.5f) * 0.5f - 0.5f, uy = (y + 0.5f) * 0.5f - 0.5f;
+    const int x0 = (int)floorf(ux), y0 = (int)floorf(uy);
+    const float fx = ux - x0, fy = uy - y0;
+    const int xa = min(max(x0, 0), W2 - 1), xb = min(max(x0 + 1, 0), W2 - 1);
+    const int ya = min(max(y0, 0), H2 - 1), yb = min(max(y0 + 1, 0), H2 - 1);
+    const float* L = low + (long long)view * 3 * HW2;
+    float* o = out + (long long)view * 3 * HW + r;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float* Lc = L + c * HW2;
+      const float top = (1.f - fx) * Lc[ya * W2 + xa] + fx * Lc[ya * W2 + xb];
+      const float bot = (1.f - fx) * Lc[yb * W2 + xa] + fx * Lc[yb * W2 + xb];
+      o[c * HW] = (1.f - fy) * top + fy * bot;
+    }
+  }
+}
+
+template <int MODE, bool STATS>
+void launch_render_t(const RenderArgs& a, long long max_items, cudaStream_t st) {
+  const int K1 = MODE == 2 ? a.k1 : 0, K2 = MODE == 2 ? a.k2 : 0, K3 = MODE == 0 ? 0 : a.k3;
+  const size_t smem = render_smem_bytes(K1, K2, K3);
+  cudaFuncSetAttribute(render_kernel<MODE, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, STATS>, kBlock, smem);
+  if (per_sm < 1) per_sm = 1;
+  const long long grid = std::min<long long>(max_items, (long long)device_sm_count() * per_sm);
+  if (grid <= 0) return;
+  render_kernel<MODE, STATS><<<(unsigned)grid, kBlock, smem, st>>>(a);
+}
+
+}  // namespace
+
+void launch_workitems(const ViewParams* d_views, int n_views, int fovea_mode, int T, int tiles_per_view,
+                      WorkItem* items, uint32_t* n_items, uint8_t* tile_class, cudaStream_t st) {
+  const long long n = (long long)n_views * tiles_per_view;
+  if (n <= 0) return;
+  workitems_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_views, n_views, fovea_mode, T, tiles_per_view,
+                                                               items, n_items, tile_class);
+}
+
+void launch_render(const RenderArgs& a, long long max_items, cudaStream_t st) {
+  const bool stats = a.stats != nullptr;
+  switch (a.sort_mode * 2 + (stats ? 1 : 0)) {
+    case 0: launch_render_t<0, false>(a, max_items, st); break;
+    case 1: launch_render_t<0, true>(a, max_items, st); break;
+    case 2: launch_render_t<1, false>(a, max_items, st); break;
+    case 3: launch_render_t<1, true>(a, max_items, st); break;
+    case 4: launch_render_t<2, false>(a, max_items, st); break;
+    default: launch_render_t<2, true>(a, max_items, st); break;
+  }
+}
+
+void launch_composite(const RenderArgs& a, int W, int H, cudaStream_t st) {
+  const long long total = (long long)W * H * a.n_views;
+  const unsigned grid = (unsigned)std::min<long long>((total + 255) / 256, (long long)device_sm_count() * 16);
+  composite_kernel<<<grid, 256, 0, st>>>(a.views, a.n_views, a.tile_class, a.tiles_per_view, a.key_tile, a.low, a.out,
+                                         W, H);
+}
+
+}  // namespace vrs

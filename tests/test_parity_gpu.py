@@ -1,0 +1,279 @@
+"""GPU vs FP64 oracle, element by element, through the C ABI.
+
+Tolerance (from the workload statement): 2e-4 per FP32 channel on every pixel that the
+oracle does not flag as marginal; a pixel is marginal when one of its decisions (alpha
+against 1/255 or 0.99, transmittance against 1e-4, depth order between near-tied
+pairs, block membership of the hierarchical windows) lies within FP32 reach of its
+threshold, where a correct FP32 renderer may legitimately decide the other way.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import native as on
+from paper_2505_10144_gb300 import synth
+from scenes import random_scene
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_2505_10144_gb300 import build
+    build.build()
+    from paper_2505_10144_gb300 import api
+    r = api.Renderer()
+    yield r
+    r.close()
+
+
+def api():
+    from paper_2505_10144_gb300 import api as a
+    return a
+
+
+def render_gpu(R, scene, cams, foveas=None, **cfg):
+    a = api()
+    ds = a.DeviceScene.from_host(scene)
+    c = a.RenderConfig(**cfg)
+    out = R.render([ds], [0] * len(cams), cams, foveas, c)
+    R.check()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def parity(gpu, ref, marginal, tol=TOL, allowed_frac=0.0):
+    d = np.abs(gpu - ref).max(axis=0)
+    bad = (d > tol) & ~marginal
+    frac = bad.mean()
+    worst = d[~marginal].max() if (~marginal).any() else 0.0
+    assert frac <= allowed_frac, f"{bad.sum()} non-marginal pixels off by > {tol} (worst {worst:.3g}, " \
+                                 f"marginal {marginal.mean():.4%})"
+    return worst, marginal.mean()
+
+
+# ---------------------------------------------------------------- sort (integer work)
+
+@pytest.mark.parametrize("n", [1, 17, 4096, 4097, 100_003, (1 << 20) + 5])
+@pytest.mark.parametrize("bits", [8, 20, 46, 64])
+def test_sort_pairs_is_stable_and_bit_exact(R, n, bits):
+    rng = np.random.default_rng(n * 131 + bits)
+    keys = rng.integers(0, 1 << 63, size=n, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, size=n, dtype=np.uint64)
+    if n > 100:
+        keys[: n // 4] = keys[n // 2]  # many equal keys: stability matters
+    vals = rng.permutation(n).astype(np.uint32)
+    mask = np.uint64((1 << bits) - 1) if bits < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    order = np.argsort(keys & mask, kind="stable")
+    kt = torch.from_numpy(keys.view(np.int64)).cuda()
+    vt = torch.from_numpy(vals.view(np.int32)).cuda()
+    ko, vo = R.sort_pairs(kt, vt, bits)
+    R.check()
+    assert np.array_equal(ko.cpu().numpy().view(np.uint64), keys[order])
+    assert np.array_equal(vo.cpu().numpy().view(np.uint32), vals[order])
+
+
+# ---------------------------------------------------------------- preprocess
+
+def _oracle_projection(scene, cam, idx):
+    return [on.project_one(scene, int(i), cam) for i in idx]
+
+
+@pytest.mark.parametrize("which", ["tiny", "shell"])
+def test_projection_records_match_oracle(R, which):
+    a = api()
+    if which == "tiny":
+        scene = synth.tiny_scene(4000, synth.rng_for(0))
+        cam = synth.identity_camera(256, 256, 90.0)
+    else:
+        scene = synth.shell_scene(20_000, synth.rng_for(1), sh_degree=3)
+        cam = synth.stereo_cameras((0.03, 0, 0.02), 0.4, 512, 544, 110.0)[0]
+    ds = a.DeviceScene.from_host(scene)
+    rec, bbox, cnt = R.project(ds, cam, 16)
+    rec, bbox, cnt = rec.cpu().numpy(), bbox.cpu().numpy(), cnt.cpu().numpy()
+    counts, gids, _ = on.tile_lists(scene, cam, 16)
+    ocnt = np.bincount(gids, minlength=scene.n)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(scene.n, size=400, replace=False)
+    for i, p in zip(idx, _oracle_projection(scene, cam, idx)):
+        if not p["valid"]:
+            assert cnt[i] == 0 and not rec[i].any()
+            continue
+        assert cnt[i] >= ocnt[i]  # conservative: never drops a pair the oracle keeps
+        if cnt[i] == 0:
+            continue
+        fx, cx, cy = np.float32(cam.fx), np.float32(cam.cx), np.float32(cam.cy)
+        pm = np.array([fx * p["mu"][0] / p["mu"][2] + cx, fx * p["mu"][1] / p["mu"][2] + cy])
+        assert np.allclose(rec[i, :2], pm, rtol=1e-5, atol=1e-3)
+        assert abs(rec[i, 12] - math.log2(p["sigma"])) < 1e-5
+        assert abs(rec[i, 15] - p["mu"][2]) <= 1e-6 * abs(p["mu"][2])
+        assert np.allclose(rec[i, 21:24], p["rgb"], rtol=1e-5, atol=2e-6)
+        if p["bounded"]:
+            ob = p["bbox"]
+            assert bbox[i, 0] <= ob[0] and bbox[i, 1] <= ob[1] and bbox[i, 2] >= ob[2] and bbox[i, 3] >= ob[3]
+    assert (cnt > 0).sum() >= (ocnt > 0).sum()
+
+
+def test_tile_lists_match_oracle(R):
+    scene = synth.tiny_scene(10_000, synth.rng_for(0))
+    cam = synth.identity_camera(256, 256, 90.0)
+    render_gpu(R, scene, [cam], sort_mode="exact", key_tile=16)
+    tpv = 16 * 16
+    keys, vals, ranges = R.instances(1, tpv)
+    keys, vals, ranges = keys.cpu().numpy().view(np.uint64), vals.cpu().numpy(), ranges.cpu().numpy()
+    counts, ogids, okeys = on.tile_lists(scene, cam, 16)
+    off = np.concatenate([[0], np.cumsum(counts.ravel())])
+    assert np.all(np.diff(keys.astype(np.float64)) >= 0) or np.all(keys[1:] >= keys[:-1])
+    for t in range(tpv):
+        s, e = ranges[t]
+        g = vals[s:e]
+        assert np.all((keys[s:e] >> np.uint64(32)) == t)
+        og = ogids[off[t]:off[t + 1]]
+        ok = okeys[off[t]:off[t + 1]]
+        assert set(og.tolist()) <= set(g.tolist())
+        # common entries appear in the same order unless their oracle keys nearly tie
+        pos = {int(x): k for k, x in enumerate(g.tolist())}
+        p = np.array([pos[int(x)] for x in og])
+        inv = np.nonzero(np.diff(p) < 0)[0]
+        for k in inv:
+            assert abs(ok[k + 1] - ok[k]) <= 1e-5 * abs(ok[k]), (t, k)
+
+
+# ---------------------------------------------------------------- whole renders
+
+@pytest.fixture(scope="module")
+def config0():
+    return synth.tiny_scene(10_000, synth.rng_for(0)), synth.identity_camera(256, 256, 90.0)
+
+
+def test_render_exact_config0(R, config0):
+    scene, cam = config0
+    ref = on.render(scene, cam, "exact", key_tile=16)
+    gpu = render_gpu(R, scene, [cam], sort_mode="exact", key_tile=16)[0]
+    worst, mf = parity(gpu, ref["image"], ref["marginal"])
+    assert mf < 0.005
+
+
+@pytest.mark.parametrize("mode,win", [("window", (0, 0, 16)), ("window", (0, 0, 4)), ("hier", (4, 8, 16)),
+                                      ("hier", (8, 16, 32)), ("hier", (1, 1, 1))])
+def test_render_windows_config0(R, config0, mode, win):
+    scene, cam = config0
+    ref = on.render(scene, cam, mode, windows=win, key_tile=16)
+    gpu = render_gpu(R, scene, [cam], sort_mode=mode, windows=win, key_tile=16)[0]
+    parity(gpu, ref["image"], ref["marginal"])
+
+
+@pytest.fixture(scope="module")
+def vr_small():
+    scene = synth.shell_scene(30_000, synth.rng_for(1), sh_degree=3)
+    W, H = 320, 256
+    cams = synth.stereo_cameras((0.02, -0.01, 0.05), 0.3, W, H, 110.0)
+    fov = [synth.fovea_for(W, (150.0, 120.0), radius_frac=0.2), synth.fovea_for(W, (170.0, 110.0), radius_frac=0.2)]
+    return scene, cams, fov
+
+
+@pytest.mark.parametrize("mode,win", [("exact", (0, 0, 0)), ("window", (0, 0, 16)), ("hier", (4, 8, 16))])
+def test_render_foveated_stereo(R, vr_small, mode, win):
+    scene, cams, fov = vr_small
+    gpu = render_gpu(R, scene, cams, fov, sort_mode=mode, windows=win, key_tile=32, fovea_mode="bilinear")
+    for v in range(2):
+        ref = on.render(scene, cams[v], mode, windows=win, key_tile=32, fovea=fov[v])
+        assert (ref["tile_class"] == 0).any() and (ref["tile_class"] == 2).any()
+        parity(gpu[v], ref["image"], ref["marginal"])
+
+
+@pytest.mark.parametrize("mode", ["exact", "hier"])
+def test_render_plain_stereo_shell(R, vr_small, mode):
+    scene, cams, _ = vr_small
+    gpu = render_gpu(R, scene, cams, sort_mode=mode, key_tile=16)
+    for v in range(2):
+        ref = on.render(scene, cams[v], mode, key_tile=16)
+        parity(gpu[v], ref["image"], ref["marginal"])
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_empty_scene_gives_background(R):
+    scene = random_scene(0, np.random.default_rng(0))
+    cam = synth.identity_camera(40, 24, 90.0)
+    gpu = render_gpu(R, scene, [cam], sort_mode="hier", key_tile=16, bg=(0.25, 0.5, 0.75))[0]
+    assert np.array_equal(gpu, np.broadcast_to(np.array([0.25, 0.5, 0.75])[:, None, None], gpu.shape))
+
+
+def test_ragged_image_and_culled_inputs(R):
+    rng = np.random.default_rng(5)
+    scene = random_scene(3000, rng, sh_degree=2, z=(-1.0, 4.0), xy=2.0)
+    scene.mean[0, :20] = np.nan
+    scene.log_scale[1, 20:40] = np.inf
+    scene.quat[:, 40:60] = 0.0
+    scene.opacity_logit[60:80] = -np.inf
+    cam = synth.identity_camera(250, 130, 100.0)
+    for mode in ("exact", "hier"):
+        ref = on.render(scene, cam, mode, key_tile=16)
+        gpu = render_gpu(R, scene, [cam], sort_mode=mode, key_tile=16)[0]
+        assert np.isfinite(gpu).all()
+        parity(gpu, ref["image"], ref["marginal"])
+
+
+def test_single_pixel_and_single_tile_images(R):
+    rng = np.random.default_rng(6)
+    scene = random_scene(500, rng)
+    for W, H in [(1, 1), (16, 16), (17, 3)]:
+        cam = synth.identity_camera(W, H, 60.0)
+        ref = on.render(scene, cam, "exact", key_tile=16)
+        gpu = render_gpu(R, scene, [cam], sort_mode="exact", key_tile=16)[0]
+        parity(gpu, ref["image"], ref["marginal"])
+
+
+def test_invalid_arguments_are_rejected(R):
+    a = api()
+    scene = a.DeviceScene.from_host(random_scene(10, np.random.default_rng(0)))
+    cam = synth.identity_camera(64, 64, 90.0)
+    with pytest.raises(a.VrsError, match="INVALID"):
+        R.render([scene], [0], [cam], None, a.RenderConfig(key_tile=8))
+    with pytest.raises(a.VrsError, match="INVALID"):
+        R.render([scene], [0], [cam], [synth.Fovea(32, 32, 10, 4)], a.RenderConfig(key_tile=16, fovea_mode="bilinear"))
+    bad = synth.identity_camera(64, 64, 90.0)
+    bad.fx = float("nan")
+    with pytest.raises(a.VrsError, match="INVALID"):
+        R.render([scene], [0], [bad], None, a.RenderConfig())
+    with pytest.raises(a.VrsError, match="INVALID"):
+        R.render([scene], [0], [cam], None, a.RenderConfig(sort_mode="window", windows=(0, 0, 33)))
+
+
+# ---------------------------------------------------------------- full size (sampled)
+
+def crop_camera(cam, x0, y0, w, h):
+    return synth.Camera(cam.world_to_cam, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, w, h, cam.near_z)
+
+
+def test_full_size_vr_frame_sampled_crops(R):
+    """500k Gaussians, stereo 2064x2208, foveated, hierarchical 4/8/16 windows: the GPU
+    frame against oracle renders of 32-aligned crops (same rays, tiles, blocks and
+    streams as the full frame), interior pixels."""
+    scene = synth.shell_scene(500_000, synth.rng_for(1), sh_degree=3)
+    wl = synth.vr_trajectory(3, synth.rng_for(1, salt=7))
+    fr = wl.frames[2]
+    gpu = render_gpu(R, scene, fr.cameras, fr.foveas, sort_mode="hier", windows=(4, 8, 16), key_tile=32,
+                     fovea_mode="bilinear")
+    checked = 0
+    for v in range(2):
+        cam, fv = fr.cameras[v], fr.foveas[v]
+        gx, gy = fv.gaze_x, fv.gaze_y
+        spots = [(gx, gy), (gx + fv.radius_px + 0.5 * fv.band_px, gy), (200.0, 300.0), (2040.0, 2180.0)]
+        for sx, sy in spots:
+            x0 = int(min(max(sx - 32, 0), 2064 - 64)) // 32 * 32
+            y0 = int(min(max(sy - 32, 0), 2208 - 64)) // 32 * 32
+            w, h = min(64, 2064 - x0), min(64, 2208 - y0)
+            c2 = crop_camera(cam, x0, y0, w, h)
+            f2 = synth.Fovea(gx - x0, gy - y0, fv.radius_px, fv.band_px)
+            ref = on.render(scene, c2, "hier", windows=(4, 8, 16), key_tile=32, fovea=f2)
+            sub = gpu[v][:, y0:y0 + h, x0:x0 + w]
+            m = ref["marginal"].copy()
+            m[:2, :] = m[-2:, :] = True  # bilinear reads across the crop edge
+            m[:, :2] = m[:, -2:] = True
+            parity(sub, ref["image"], m)
+            checked += 1
+    assert checked == 8

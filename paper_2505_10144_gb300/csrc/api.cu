@@ -314,7 +314,7 @@ vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes
     need = c->h_small[0];
     c->last_instances = need;
     c->max_needed = std::max(c->max_needed, need);
-    if (need > c->key_cap) {
+    if (need > c->key_cap || c->key_cap == 0) {
       const long long cap = need + need / 4 + 4096;
       for (int b = 0; b < 2; ++b)
         if (!ensure(c, c->keys[b], sizeof(uint64_t) * cap, false, &s) || !ensure(c, c->vals[b], sizeof(uint32_t) * cap, false, &s))

@@ -183,6 +183,24 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def ncu_case(args, api, torch):
+    """Frames only: the workload at args.scale resolution, nothing else on the GPU."""
+    from paper_2505_10144_gb300 import synth
+    W, H = int(W_IMG * args.scale) // 32 * 32, int(H_IMG * args.scale) // 32 * 32
+    scene = synth.shell_scene(N_GAUSS, synth.rng_for(1), sh_degree=3)
+    wl = synth.vr_trajectory(args.warmup + args.steps, synth.rng_for(1, salt=100), W, H)
+    ds = api.DeviceScene.from_host(scene)
+    R = api.Renderer()
+    cfg = api.RenderConfig(sort_mode=args.mode, windows=WINDOWS, key_tile=32, fovea_mode="bilinear")
+    out = torch.empty((2, 3, H, W), device="cuda")
+    for fr in wl.frames:
+        R.render([ds], [0, 0], fr.cameras, fr.foveas, cfg, out=out)
+    R.check()
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": True, "width": W, "height": H, "frames": len(wl.frames), **R.stats()}))
+    R.close()
+
+
 def psnr(a, b):
     mse = float(((a - b) ** 2).mean())
     return float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
@@ -196,6 +214,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=40)
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="only render warmup + steps foveated frames (for profiler captures)")
+    ap.add_argument("--scale", type=float, default=1.0, help="resolution scale of --ncu-case")
+    ap.add_argument("--mode", default="hier", choices=["exact", "window", "hier"], help="sort mode of --ncu-case")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -211,6 +233,9 @@ def main():
         pg = dist
     from paper_2505_10144_gb300 import api, build
     build.build()
+    if args.ncu_case:
+        ncu_case(args, api, torch)
+        return
     n_frames = args.warmup + args.steps
     scene, wl = make_workload(n_frames, rank)
     ds = api.DeviceScene.from_host(scene)

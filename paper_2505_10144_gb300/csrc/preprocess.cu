@@ -115,6 +115,22 @@ __device__ bool project_gaussian(const SceneDev& s, long long i, const ViewParam
   const float p11 = quad(e2x, e2y, e2z, e2x, e2y, e2z) * id2 + dil;
   const float det = p00 * p11 - p01 * p01;
   if (!(det > 0.f)) return false;
+  {
+    // every kept ray lies within angle atan(rho) of u, rho = r sqrt(lambda_max(Sigma_p)),
+    // r^2 = 2 ln(255 sigma); drop the Gaussian when that cone misses a side of the view
+    // frustum (extended by one pixel)
+    const float r2 = 2.f * logf(255.f * sigma);
+    const float hm = 0.5f * (p00 + p11), hd = 0.5f * (p00 - p11);
+    const float lmax = hm + sqrtf(hd * hd + p01 * p01);
+    const float rho = sqrtf(fmaxf(r2, 0.f) * lmax) * 1.001f + 1e-6f;
+    const float sin_t = rho * rsqrtf(1.f + rho * rho);
+    const float tl = (vp.cx + 1.f) / vp.fx, tr = (vp.W - vp.cx + 1.f) / vp.fx;
+    const float tt = (vp.cy + 1.f) / vp.fy, tb = (vp.H - vp.cy + 1.f) / vp.fy;
+    if ((ux + tl * uz) * rsqrtf(1.f + tl * tl) < -sin_t) return false;
+    if ((-ux + tr * uz) * rsqrtf(1.f + tr * tr) < -sin_t) return false;
+    if ((uy + tt * uz) * rsqrtf(1.f + tt * tt) < -sin_t) return false;
+    if ((-uy + tb * uz) * rsqrtf(1.f + tb * tb) < -sin_t) return false;
+  }
   const float idet = kHalfLog2e / det;
   const float A00 = p11 * idet, A01 = -p01 * idet, A11 = p00 * idet;
   const float ifx = 1.f / vp.fx, ify = 1.f / vp.fy;
@@ -142,7 +158,9 @@ __device__ bool project_gaussian(const SceneDev& s, long long i, const ViewParam
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float v = 0.5f;
-    for (int k = 0; k < K; ++k) v = fmaf(Y[k], s.sh[((long long)k * 3 + c) * n + i], v);
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (k < K) v = fmaf(Y[k], s.sh[((long long)k * 3 + c) * n + i], v);
     col[c] = fmaxf(v, 0.f);
   }
   rec[0] = make_float4(pmx, pmy, h00, h01);
@@ -182,18 +200,23 @@ __device__ bool project_gaussian(const SceneDev& s, long long i, const ViewParam
 // depth t* on the ray through the maximum point projected back to the image.
 // Not inlined: the count pass and the emit pass run the same machine code, so they
 // make the same decisions.
-__device__ __noinline__ bool tile_keep(const float4* rec, float x0, float y0, float x1, float y1, float* key) {
-  const float4 f0 = rec[0], f1 = rec[1], f2 = rec[2], f3 = rec[3];
+struct Keep {
+  bool keep;
+  float key;
+};
+
+__device__ __noinline__ Keep tile_keep(float4 f0, float4 f1, float4 f2, float4 f3, float4 f4, float m12x2, float x0,
+                                       float y0, float x1, float y1) {
   const float cxs[4] = {x0, x1, x1, x0}, cys[4] = {y0, y0, y1, y1};
   float S0[4], S1[4];
-  *key = f3.w;
+  Keep res{true, f3.w};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const float dx = cxs[k] - f0.x, dy = cys[k] - f0.y;
     const float a = fmaf(f0.z, dx, f0.w * dy);
     const float b = fmaf(f1.x, dx, f1.y * dy);
     const float w = fmaf(f1.z, dx, fmaf(f1.w, dy, f2.x));
-    if (!(w > 0.f)) return true;  // quad not bounded on the plane
+    if (!(w > 0.f)) return res;  // quad not bounded on the plane
     S0[k] = a / w;
     S1[k] = b / w;
   }
@@ -205,7 +228,7 @@ __device__ __noinline__ bool tile_keep(const float4* rec, float x0, float y0, fl
     pos |= cr > 0.f;
     neg |= cr < 0.f;
   }
-  if (!(pos && neg)) return true;  // projected mean inside: maximum at the mean
+  if (!(pos && neg)) return res;  // projected mean inside: maximum at the mean
   const float A00 = f2.y, A01 = 0.5f * f2.z, A11 = f2.w;
   float qmin = INFINITY, X0 = 0.f, X1 = 0.f;
 #pragma unroll
@@ -226,7 +249,7 @@ __device__ __noinline__ bool tile_keep(const float4* rec, float x0, float y0, fl
     }
   }
   const float cut = f3.x + kLog2_255;
-  if (!(qmin <= cut * 1.0001f + 1e-5f)) return false;  // a hair conservative vs FP64
+  if (!(qmin <= cut * 1.0001f + 1e-5f)) return Keep{false, f3.w};  // a hair conservative vs FP64
   // back-project X to the image: solve a - X0 w = 0, b - X1 w = 0 for (dx, dy)
   const float a00 = f0.z - X0 * f1.z, a01 = f0.w - X0 * f1.w;
   const float a10 = f1.x - X1 * f1.z, a11 = f1.y - X1 * f1.w;
@@ -236,15 +259,13 @@ __device__ __noinline__ bool tile_keep(const float4* rec, float x0, float y0, fl
     const float dx = (r0 * a11 - a01 * r1) / dt, dy = (a00 * r1 - a10 * r0) / dt;
     const float w = fmaf(f1.z, dx, fmaf(f1.w, dy, f2.x));
     if (w > 0.f && isfinite(dx) && isfinite(dy)) {
-      const float4 f4 = rec[4];
-      const float m12x2 = rec[5].x;
       const float num = fmaf(f3.y, dx, fmaf(f3.z, dy, f3.w));
       const float den = fmaf(dx, fmaf(f4.x, dx, fmaf(f4.y, dy, f4.w)), fmaf(dy, fmaf(f4.z, dy, m12x2), 1.0f));
       const float kk = num / den;
-      if (isfinite(kk)) *key = kk;
+      if (isfinite(kk)) res.key = kk;
     }
   }
-  return true;
+  return res;
 }
 
 __device__ __forceinline__ void tile_span(const float4& bb, const ViewParams& vp, int T, int& tx0, int& tx1,
@@ -263,39 +284,83 @@ __device__ __forceinline__ void tile_quad(int tx, int ty, int T, const ViewParam
   y1 = (float)min((ty + 1) * T, vp.H) - 0.5f;
 }
 
+struct Span {
+  int tx0, ty0, nx, nt;
+};
+
+__device__ __forceinline__ Span make_span(const float4& bb, const ViewParams& vp, int T, bool ok) {
+  Span sp{0, 0, 0, 0};
+  if (!ok) return sp;
+  int tx0, tx1, ty0, ty1;
+  tile_span(bb, vp, T, tx0, tx1, ty0, ty1);
+  if (tx1 < tx0 || ty1 < ty0) return sp;
+  sp.tx0 = tx0;
+  sp.ty0 = ty0;
+  sp.nx = tx1 - tx0 + 1;
+  sp.nt = sp.nx * (ty1 - ty0 + 1);
+  return sp;
+}
+
+__device__ __forceinline__ float4 shfl4(const float4& v, int src) {
+  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+
+// The warp walks its Gaussians one at a time; the 32 lanes test 32 tiles of the current
+// Gaussian's rectangle at once, so a Gaussian covering many tiles does not serialise a
+// thread.  Lane j of the warp ends up with the kept-tile count of its own Gaussian.
 __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev s, const ViewParams* __restrict__ views,
                                                          const int* __restrict__ view_list, int nv, int T,
                                                          float4* __restrict__ rec, float4* __restrict__ bbox,
                                                          uint32_t* __restrict__ count) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= s.n) return;
+  const int lane = threadIdx.x & 31;
+  const bool in = i < s.n;
   for (int k = 0; k < nv; ++k) {
     const ViewParams& vp = views[view_list[k]];
     const long long vg = vp.base + i;
     float4 r[6], bb;
-    uint32_t cnt = 0;
-    if (project_gaussian(s, i, vp, r, bb)) {
-      int tx0, tx1, ty0, ty1;
-      tile_span(bb, vp, T, tx0, tx1, ty0, ty1);
-      for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-          float x0, y0, x1, y1, key;
-          tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
-          cnt += tile_keep(r, x0, y0, x1, y1, &key) ? 1u : 0u;
+    const bool ok = in && project_gaussian(s, i, vp, r, bb);
+    if (!ok) bb = make_float4(0.f, 0.f, -1.f, -1.f);
+    const Span sp = make_span(bb, vp, T, ok);
+    uint32_t mine = 0;
+    unsigned todo = __ballot_sync(0xffffffffu, sp.nt > 0);
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const float4 g0 = shfl4(r[0], j), g1 = shfl4(r[1], j), g2 = shfl4(r[2], j), g3 = shfl4(r[3], j),
+                   g4 = shfl4(r[4], j);
+      const float g5x = __shfl_sync(0xffffffffu, r[5].x, j);
+      const int tx0 = __shfl_sync(0xffffffffu, sp.tx0, j), ty0 = __shfl_sync(0xffffffffu, sp.ty0, j);
+      const int nx = __shfl_sync(0xffffffffu, sp.nx, j), nt = __shfl_sync(0xffffffffu, sp.nt, j);
+      uint32_t c = 0;
+      for (int b = 0; b < nt; b += 32) {
+        bool keep = false;
+        const int t = b + lane;
+        if (t < nt) {
+          float x0, y0, x1, y1;
+          tile_quad(tx0 + t % nx, ty0 + t / nx, T, vp, x0, y0, x1, y1);
+          keep = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1).keep;
         }
-      if (cnt) {
+        c += __popc(__ballot_sync(0xffffffffu, keep));
+      }
+      if (lane == j) mine = c;
+    }
+    if (in) {
+      if (mine) {
         float4* dst = rec + vg * kRecF4;
 #pragma unroll
         for (int q = 0; q < kRecF4; ++q) dst[q] = r[q];
       }
-    } else {
-      bb = make_float4(0.f, 0.f, -1.f, -1.f);
+      bbox[vg] = bb;
+      count[vg] = mine;
     }
-    bbox[vg] = bb;
-    count[vg] = cnt;
   }
 }
 
+// Emits the (tile | depth, index) instances of a view: the same warp-cooperative walk
+// as the count, with a ballot prefix giving each kept tile its slot (row-major order of
+// the rectangle, so the output is deterministic).
 __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __restrict__ views, int view,
                                                         const float4* __restrict__ rec,
                                                         const float4* __restrict__ bbox,
@@ -305,30 +370,47 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
                                                         uint32_t* __restrict__ vals, long long cap,
                                                         uint32_t* status) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nview) return;
+  const int lane = threadIdx.x & 31;
   const ViewParams& vp = views[view];
   const long long vg = vp.base + i;
-  const uint32_t cnt = count[vg];
-  if (!cnt) return;
-  const float4 bb = bbox[vg];
-  const float4* r = rec + vg * kRecF4;
-  long long o = offsets[vg];
-  int tx0, tx1, ty0, ty1;
-  tile_span(bb, vp, T, tx0, tx1, ty0, ty1);
+  const uint32_t cnt = i < nview ? count[vg] : 0u;
+  unsigned todo = __ballot_sync(0xffffffffu, cnt > 0);
   const uint64_t vbase = (uint64_t)view * (uint64_t)tiles_per_view;
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) {
-      float x0, y0, x1, y1, key;
-      tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
-      if (!tile_keep(r, x0, y0, x1, y1, &key)) continue;
-      if (o < cap) {
-        keys[o] = ((vbase + (uint64_t)(ty * vp.ntx + tx)) << 32) | float_order_bits(key);
-        vals[o] = (uint32_t)i;
-      } else {
-        atomicOr(status, kStOverflow);
+  const uint32_t lt = (1u << lane) - 1u;
+  while (todo) {
+    const int j = __ffs(todo) - 1;
+    todo &= todo - 1;
+    const long long vj = vp.base + (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31) + j;
+    const float4* r = rec + vj * kRecF4;
+    const float4 g0 = r[0], g1 = r[1], g2 = r[2], g3 = r[3], g4 = r[4];
+    const float g5x = r[5].x;
+    const Span sp = make_span(bbox[vj], vp, T, true);
+    long long o = offsets[vj];
+    const uint32_t gid = (uint32_t)(vj - vp.base);
+    for (int b = 0; b < sp.nt; b += 32) {
+      const int t = b + lane;
+      Keep kp{false, 0.f};
+      int tx = 0, ty = 0;
+      if (t < sp.nt) {
+        float x0, y0, x1, y1;
+        tx = sp.tx0 + t % sp.nx;
+        ty = sp.ty0 + t / sp.nx;
+        tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
+        kp = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1);
       }
-      ++o;
+      const unsigned bal = __ballot_sync(0xffffffffu, kp.keep);
+      if (kp.keep) {
+        const long long slot = o + __popc(bal & lt);
+        if (slot < cap) {
+          keys[slot] = ((vbase + (uint64_t)(ty * vp.ntx + tx)) << 32) | float_order_bits(kp.key);
+          vals[slot] = gid;
+        } else {
+          atomicOr(status, kStOverflow);
+        }
+      }
+      o += __popc(bal);
     }
+  }
 }
 
 void launch_preprocess(const SceneDev& s, const ViewParams* d_views, const int* d_view_list, int nv, int T,
@@ -365,9 +447,9 @@ __global__ void project_only_kernel(SceneDev s, const ViewParams* __restrict__ v
     tile_span(bb, vp, T, tx0, tx1, ty0, ty1);
     for (int ty = ty0; ty <= ty1; ++ty)
       for (int tx = tx0; tx <= tx1; ++tx) {
-        float x0, y0, x1, y1, key;
+        float x0, y0, x1, y1;
         tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
-        cnt += tile_keep(r, x0, y0, x1, y1, &key) ? 1u : 0u;
+        cnt += tile_keep(r[0], r[1], r[2], r[3], r[4], r[5].x, x0, y0, x1, y1).keep ? 1u : 0u;
       }
   }
   for (int q = 0; q < kRecF4; ++q) {

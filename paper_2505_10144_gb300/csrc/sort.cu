@@ -105,15 +105,20 @@ __global__ void __launch_bounds__(kBlock) scan_final_kernel(const uint32_t* __re
 }
 
 // digit histograms of every pass in one read of the keys
+__device__ __forceinline__ uint32_t digit_mask(int bits, int pass) {
+  const int rem = bits - 8 * pass;
+  return rem >= 8 ? 0xFFu : ((1u << rem) - 1u);
+}
+
 __global__ void __launch_bounds__(kBlock) histogram_kernel(const uint64_t* __restrict__ keys, const uint32_t* d_n,
-                                                           int passes, uint32_t* __restrict__ hist) {
+                                                           int passes, int bits, uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[kMaxPasses][256];
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += kBlock) (&h[0][0])[i] = 0u;
   __syncthreads();
   const long long n = *d_n;
   for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < n; i += (long long)gridDim.x * kBlock) {
     const uint64_t k = keys[i];
-    for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 0xFF], 1u);
+    for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(k >> (8 * p)) & digit_mask(bits, p)], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < passes * 256; i += kBlock) {
@@ -144,7 +149,7 @@ struct SortSmem {
 __global__ void __launch_bounds__(kBlock) onesweep_kernel(const uint64_t* __restrict__ kin,
                                                           const uint32_t* __restrict__ vin,
                                                           uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                          const uint32_t* d_n, int shift,
+                                                          const uint32_t* d_n, int shift, uint32_t dmask,
                                                           const uint32_t* __restrict__ digit_offsets,
                                                           uint32_t* __restrict__ look, uint32_t* tile_counter,
                                                           uint32_t* status) {
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const uint64_t* __rest
       const bool ok = idx < n;
       k[it] = ok ? kin[idx] : 0ull;
       v[it] = ok ? vin[idx] : 0u;
-      dg[it] = ok ? (int)((k[it] >> shift) & 0xFF) : 256;
+      dg[it] = ok ? (int)((k[it] >> shift) & dmask) : 256;
     }
     // warp-level stable ranking: items in (it, lane) order
 #pragma unroll
@@ -239,7 +244,7 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const uint64_t* __rest
     const int valid = (int)min((long long)kSortTile, n - base);
     for (int i = threadIdx.x; i < valid; i += kBlock) {
       const uint64_t kk = S.keys[i];
-      const int dd = (int)((kk >> shift) & 0xFF);
+      const int dd = (int)((kk >> shift) & dmask);
       const uint32_t o = S.global_base[dd] + (uint32_t)i - S.digit_start[dd];
       if ((long long)o < n) {  // always true unless a look-back timed out
         kout[o] = kk;
@@ -310,7 +315,7 @@ int launch_radix_sort(uint64_t* keys[2], uint32_t* vals[2], const uint32_t* d_n,
   cudaMemsetAsync(s.look, 0, sizeof(uint32_t) * (size_t)passes * (size_t)(tiles + 1) * 256, st);
   const int sms = device_sm_count();
   const unsigned hgrid = (unsigned)std::min<long long>((cap + kBlock * 8 - 1) / (kBlock * 8), (long long)sms * 8);
-  histogram_kernel<<<hgrid, kBlock, 0, st>>>(keys[0], d_n, passes, s.hist);
+  histogram_kernel<<<hgrid, kBlock, 0, st>>>(keys[0], d_n, passes, bits, s.hist);
   histogram_scan_kernel<<<1, kBlock, 0, st>>>(s.hist, passes);
   static bool attr = false;
   const int smem = (int)sizeof(SortSmem);
@@ -324,7 +329,9 @@ int launch_radix_sort(uint64_t* keys[2], uint32_t* vals[2], const uint32_t* d_n,
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
   int cur = 0;
   for (int p = 0; p < passes; ++p) {
-    onesweep_kernel<<<grid, kBlock, smem, st>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], d_n, 8 * p,
+    const int rem = bits - 8 * p;
+    const uint32_t dmask = rem >= 8 ? 0xFFu : ((1u << rem) - 1u);
+    onesweep_kernel<<<grid, kBlock, smem, st>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], d_n, 8 * p, dmask,
                                                 s.hist + p * 256, s.look + (size_t)p * (size_t)(tiles + 1) * 256,
                                                 s.counters + p, status);
     cur ^= 1;

@@ -178,6 +178,28 @@ vrs_status vrs_project(vrs_ctx* ctx, const vrs_gaussians* scene, const vrs_camer
 vrs_status vrs_sort_pairs(vrs_ctx* ctx, const uint64_t* d_keys_in, const uint32_t* d_vals_in,
                           uint64_t* d_keys_out, uint32_t* d_vals_out, int64_t n, int bits, void* stream);
 
+/* Largest n that vrs_sort_pairs_noalloc accepts. */
+#define VRS_SORT_NOALLOC_MAX_PAIRS (1 << 20)
+
+/* vrs_sort_pairs without any allocation.  The paper has no counterpart: this entry point
+ * serves callers that cannot allocate GPU memory when they sort, such as a frame
+ * callback with a hard latency budget (cudaMalloc and cudaFree can synchronise the
+ * device), an application whose own pool owns all GPU memory, or code that must not
+ * fail mid-frame on memory pressure.  Same result as vrs_sort_pairs (stable sort of n
+ * (key, value) pairs by the low `bits` bits of the key into d_keys_out / d_vals_out;
+ * inputs are not modified; in and out may be the same buffers) and no context.  The
+ * scratch is a fixed device array of about 14 MiB built into the library; every GPU
+ * that loads the library holds it until the process exits.  n above
+ * VRS_SORT_NOALLOC_MAX_PAIRS returns VRS_ERR_INVALID and launches nothing.  The first call
+ * on a device looks up the array's device address (host-side set-up, once per device,
+ * on the current device): make that first call before any stream capture.  All calls
+ * share the one array and each clears what must start at zero, so calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  d_status (device uint32, may be NULL) receives the sort's device status bits
+ * (1 = a bounded look-back wait gave up and the output is not valid). */
+vrs_status vrs_sort_pairs_noalloc(const uint64_t* d_keys_in, const uint32_t* d_vals_in, uint64_t* d_keys_out,
+                                  uint32_t* d_vals_out, int64_t n, int bits, uint32_t* d_status, void* stream);
+
 /* Fine-tuning loss of Sec. 5 (0.8 L1 + 0.2 (1 - SSIM), SSIM of Wang et al. with an
  * 11x11 Gaussian window, sigma 1.5, zero padding) over n_images images [3][H][W]:
  * d_loss (device float[1]) receives the mean loss over images, d_grad (device

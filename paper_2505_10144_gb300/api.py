@@ -231,3 +231,70 @@ def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch
                            _stream(stream))
     if st != 0:
         raise VrsError(st, "vrs_adam_step failed")
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable render of one scene (fine-tuning through the rasterizer).
+
+    Forward calls vrs_render with save_for_backward; backward calls vrs_render_backward
+    on the same Renderer, so the backward must run before that renderer renders again
+    (the usual forward -> loss -> backward order)."""
+
+    @staticmethod
+    def forward(ctx, renderer, cfg, cams, foveas, sh_degree, mean, log_scale, quat, opacity_logit, sh):
+        ds = DeviceScene(mean.detach().contiguous(), log_scale.detach().contiguous(), quat.detach().contiguous(),
+                         opacity_logit.detach().contiguous(), sh.detach().contiguous(), sh_degree)
+        out = renderer.render([ds], [0] * len(cams), cams, foveas, cfg, save=True)
+        ctx.renderer, ctx.cfg, ctx.cams, ctx.foveas, ctx.ds = renderer, cfg, cams, foveas, ds
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        g = ctx.ds.zeros_like()
+        ctx.renderer.backward([ctx.ds], [0] * len(ctx.cams), ctx.cams, ctx.foveas, ctx.cfg, gout.contiguous(), [g])
+        return (None, None, None, None, None, *g.tensors())
+
+
+def render_differentiable(renderer: Renderer, params: dict, sh_degree: int, cams, foveas=None,
+                          cfg: RenderConfig | None = None) -> torch.Tensor:
+    """params: dict of CUDA float32 tensors mean, log_scale, quat, opacity_logit, sh."""
+    return RenderFunction.apply(renderer, cfg or RenderConfig(), cams, foveas, sh_degree, params["mean"],
+                                params["log_scale"], params["quat"], params["opacity_logit"], params["sh"])
+
+
+class LossFunction(torch.autograd.Function):
+    """0.8 L1 + 0.2 (1 - SSIM) computed (with its gradient) by vrs_loss_l1_ssim."""
+
+    @staticmethod
+    def forward(ctx, renderer, img, target):
+        loss, grad = renderer.loss(img.detach(), target.detach(), want_grad=True)
+        ctx.save_for_backward(grad)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return None, grad * g, None
+
+
+def l1_ssim_loss(renderer: Renderer, img: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
+    return LossFunction.apply(renderer, img, target)
+
+
+class Adam:
+    """Adam on CUDA float32 tensors, stepped by vrs_adam_step (one kernel per tensor)."""
+
+    def __init__(self, params: dict, lrs: dict, beta1=0.9, beta2=0.999, eps=1e-15):
+        self.params, self.lrs = params, lrs
+        self.m = {k: torch.zeros_like(v) for k, v in params.items()}
+        self.v = {k: torch.zeros_like(v) for k, v in params.items()}
+        self.t = 0
+        self.b1, self.b2, self.eps = beta1, beta2, eps
+
+    def step(self, grads: dict):
+        self.t += 1
+        for k, p in self.params.items():
+            g = grads[k]
+            if g is None:
+                continue
+            adam_step(p, g.contiguous(), self.m[k], self.v[k], self.lrs.get(k, 0.0), self.t, self.b1, self.b2, self.eps)

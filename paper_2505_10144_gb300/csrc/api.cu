@@ -521,9 +521,76 @@ vrs_status vrs_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, con
 vrs_status vrs_render_backward(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, const int* view_scene,
                                const vrs_camera* cams, const vrs_fovea* fov, int n_views, const vrs_render_opts* o,
                                const float* d_dL_drgb, const vrs_gaussian_grads* grads, void* stream) {
-  (void)scenes; (void)n_scenes; (void)view_scene; (void)cams; (void)fov; (void)n_views; (void)o;
-  (void)d_dL_drgb; (void)grads; (void)stream;
-  return fail(c, VRS_ERR_UNSUPPORTED, "backward not built yet");
+  if (!c) return VRS_ERR_INVALID;
+  if (!d_dL_drgb || !grads) return fail(c, VRS_ERR_INVALID, "null gradient argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool cap_mode = capturing(st);
+  Saved& sv = c->saved;
+  if (!sv.valid) return fail(c, VRS_ERR_INVALID, "no forward saved: call vrs_render with save_for_backward = 1");
+  if (!o || !scenes || !view_scene || n_scenes <= 0) return fail(c, VRS_ERR_INVALID, "null argument");
+  for (int sc = 0; sc < n_scenes; ++sc) {
+    if (scenes[sc].n > 0 && (!grads[sc].mean || !grads[sc].log_scale || !grads[sc].quat ||
+                             !grads[sc].opacity_logit || !grads[sc].sh))
+      return fail(c, VRS_ERR_INVALID, "null gradient pointer");
+  }
+  const int fm = fov ? fov[0].mode : 0;
+  if (n_views != sv.n_views || !cams || cams[0].width != sv.W || cams[0].height != sv.H || o->key_tile != sv.key_tile ||
+      fm != sv.fovea_mode || o->sort_mode != sv.sort_mode || o->win[0] != sv.k[0] || o->win[1] != sv.k[1] ||
+      o->win[2] != sv.k[2])
+    return fail(c, VRS_ERR_INVALID, "backward arguments differ from the saved forward");
+  // per-scene view lists (host staging still holds this call's views from the forward)
+  std::vector<int> first(n_scenes, 0), cnt(n_scenes, 0);
+  long long total = 0;
+  {
+    int k = 0;
+    for (int s2 = 0; s2 < n_scenes; ++s2) {
+      first[s2] = k;
+      for (int v = 0; v < n_views; ++v)
+        if (view_scene[v] == s2) ++k;
+      cnt[s2] = k - first[s2];
+    }
+    for (int v = 0; v < n_views; ++v) {
+      if (view_scene[v] < 0 || view_scene[v] >= n_scenes) return fail(c, VRS_ERR_INVALID, "view_scene out of range");
+      total += scenes[view_scene[v]].n;
+    }
+  }
+  if (total != sv.total_nv) return fail(c, VRS_ERR_INVALID, "scene sizes differ from the saved forward");
+  const long long HW = (long long)sv.W * sv.H;
+  vrs_status s = VRS_OK;
+  if (!ensure(c, c->grad_rec, sizeof(float) * 16 * (size_t)std::max(total, 1ll), cap_mode, &s) ||
+      !ensure(c, c->dsamp_full, sizeof(float4) * (size_t)HW * n_views * (sv.fovea_mode ? 2 : 1), cap_mode, &s) ||
+      !ensure(c, c->dsamp_low, sizeof(float4) * (size_t)(HW / 4 + 1) * n_views, cap_mode, &s))
+    return s;
+  float4* dfull = P<float4>(c->dsamp_full);
+  float4* dhyb = dfull + HW * n_views;
+  float4* dlow = P<float4>(c->dsamp_low);
+  cudaMemsetAsync(c->grad_rec.p, 0, sizeof(float) * 16 * (size_t)std::max(total, 1ll), st);
+  launch_composite_backward(P<ViewParams>(c->views), n_views, P<uint8_t>(c->tile_class), sv.tiles_per_view, sv.key_tile,
+                            sv.fovea_mode, d_dL_drgb, sv.W, sv.H, dfull, dhyb, dlow, st);
+  Plan pl;
+  pl.n_views = n_views;
+  pl.W = sv.W;
+  pl.H = sv.H;
+  pl.T = sv.key_tile;
+  pl.fovea_mode = sv.fovea_mode;
+  pl.tiles_per_view = sv.tiles_per_view;
+  pl.total_nv = sv.total_nv;
+  RenderArgs a = make_args(c, pl, o);
+  a.s_full = P<float4>(c->s_full);
+  a.s_low = sv.fovea_mode ? P<float4>(c->s_low) : nullptr;
+  a.dL_dout = reinterpret_cast<const float*>(dfull);
+  a.dL_dlow = reinterpret_cast<const float*>(dlow);
+  a.grad_rec = P<float>(c->grad_rec);
+  uint32_t* ctr = P<uint32_t>(c->counters);
+  cudaMemsetAsync(ctr + kCtrQueue, 0, sizeof(uint32_t), st);
+  launch_render_backward(a, 4ll * n_views * sv.tiles_per_view, st);
+  for (int sc = 0; sc < n_scenes; ++sc) {
+    if (!cnt[sc] || scenes[sc].n <= 0) continue;
+    launch_preprocess_backward(to_dev(scenes[sc]), P<ViewParams>(c->views), P<int>(c->view_list) + first[sc], cnt[sc],
+                               P<uint32_t>(c->count), P<float>(c->grad_rec), grads[sc], st);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "backward launch");
 }
 
 vrs_status vrs_check_status(vrs_ctx* c, void* stream, int64_t* required_instances) {

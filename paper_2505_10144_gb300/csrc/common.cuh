@@ -168,10 +168,11 @@ void launch_workitems(const ViewParams* d_views, int n_views, int fovea_mode, in
 void launch_render(const RenderArgs& a, long long max_items, cudaStream_t st);
 void launch_composite(const RenderArgs& a, int W, int H, cudaStream_t st);
 void launch_render_backward(const RenderArgs& a, long long max_items, cudaStream_t st);
-void launch_composite_backward(const RenderArgs& a, int W, int H, float* dL_dsample_full, float* dL_dsample_low,
-                               cudaStream_t st);
+void launch_composite_backward(const ViewParams* views, int n_views, const uint8_t* tile_class, int tiles_per_view,
+                               int T, int fovea_mode, const float* dout, int W, int H, float4* dfull, float4* dhyb,
+                               float4* dlow, cudaStream_t st);
 void launch_preprocess_backward(const SceneDev& s, const ViewParams* d_views, const int* d_view_list,
-                                int n_views_scene, const float4* rec, const float* grad_rec,
+                                int n_views_scene, const uint32_t* count, const float* grad_rec,
                                 const vrs_gaussian_grads& g, cudaStream_t st);
 int device_sm_count();
 

@@ -115,9 +115,59 @@ struct Px {
   bool active;
   int h3, n3;
   unsigned n_eval, n_kept, n_blend;
+  // backward replay: dL/dC of the sample, its final C and T, dL/dT_final (= dL/dC . bg)
+  float G0, G1, G2, F0, F1, F2, TF, GT;
+  float* grad;  // per-(view, Gaussian) record gradients of this view, [n][16]
 };
 
-template <bool STATS>
+// d(loss)/d(record) of one blended pair, accumulated into the record gradient (16
+// floats: pm_x, pm_y, h00, h01, h10, h11, h20, h21, h22, a00, a01x2, a11, log2 sigma, r,
+// g, b).  alpha_i, c_i, T_i and C_<i are the values the forward used; with C_final and
+// T_final saved, every term is available in front-to-back order:
+//   dL/dc_i     = dL/dC alpha_i T_i
+//   dL/dalpha_i = T_i (dL/dC . c_i) - (dL/dC . (C_final - C_<=i) + dL/dT_final T_final) / (1 - alpha_i)
+__device__ __forceinline__ void blend_grad(const Px& p, float alpha, const float4* r, float Tb, float Cb0, float Cb1,
+                                           float Cb2, float* __restrict__ grad) {
+  const float4 f0 = r[0], f1 = r[1], f2 = r[2], f3 = r[3], f5 = r[5];
+  const float aT = alpha * Tb;
+  const float c0 = f5.y, c1 = f5.z, c2 = f5.w;
+  const float le0 = fmaf(aT, c0, Cb0), le1 = fmaf(aT, c1, Cb1), le2 = fmaf(aT, c2, Cb2);
+  const float cdot = p.G0 * c0 + p.G1 * c1 + p.G2 * c2;
+  const float rest = p.G0 * (p.F0 - le0) + p.G1 * (p.F1 - le1) + p.G2 * (p.F2 - le2) + p.GT * p.TF;
+  const float dLda = Tb * cdot - rest / (1.f - alpha);
+  atomicAdd(grad + 13, p.G0 * aT);
+  atomicAdd(grad + 14, p.G1 * aT);
+  atomicAdd(grad + 15, p.G2 * aT);
+  if (alpha >= kAlphaMax) return;  // clamped: alpha does not depend on the Gaussian
+  const float dx = p.px - f0.x, dy = p.py - f0.y;
+  const float a = fmaf(f0.z, dx, f0.w * dy);
+  const float b = fmaf(f1.x, dx, f1.y * dy);
+  const float w = fmaf(f1.z, dx, fmaf(f1.w, dy, f2.x));
+  const float iw2 = 1.f / (w * w);
+  const float qn = fmaf(a, fmaf(f2.y, a, f2.z * b), f2.w * b * b);
+  const float qw = qn * iw2;
+  const float gl = dLda * alpha * kLn2;  // dL/d(log2 sigma) = -dL/dq'
+  const float gqn = -gl * iw2;
+  const float gw = 2.f * gl * qw / w;
+  const float ga = gqn * (2.f * f2.y * a + f2.z * b), gb = gqn * (f2.z * a + 2.f * f2.w * b);
+  const float gdx = ga * f0.z + gb * f1.x + gw * f1.z, gdy = ga * f0.w + gb * f1.y + gw * f1.w;
+  atomicAdd(grad + 0, -gdx);
+  atomicAdd(grad + 1, -gdy);
+  atomicAdd(grad + 2, ga * dx);
+  atomicAdd(grad + 3, ga * dy);
+  atomicAdd(grad + 4, gb * dx);
+  atomicAdd(grad + 5, gb * dy);
+  atomicAdd(grad + 6, gw * dx);
+  atomicAdd(grad + 7, gw * dy);
+  atomicAdd(grad + 8, gw);
+  atomicAdd(grad + 9, gqn * a * a);
+  atomicAdd(grad + 10, gqn * a * b);
+  atomicAdd(grad + 11, gqn * b * b);
+  atomicAdd(grad + 12, gl);
+  (void)f3;
+}
+
+template <bool STATS, bool BWD = false>
 __device__ __forceinline__ void blend(Px& p, float alpha, int g, const float4* __restrict__ recv) {
   if (!p.active) return;
   const float test = p.T * (1.f - alpha);
@@ -125,6 +175,7 @@ __device__ __forceinline__ void blend(Px& p, float alpha, int g, const float4* _
     p.active = false;
     return;
   }
+  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16);
   const float4 c = recv[(long long)g * kRecF4 + 5];
   const float aT = alpha * p.T;
   p.C0 = fmaf(aT, c.y, p.C0);
@@ -135,7 +186,7 @@ __device__ __forceinline__ void blend(Px& p, float alpha, int g, const float4* _
 }
 
 // per-thread ring window (ascending from head), insert-then-pop-min
-template <bool STATS>
+template <bool STATS, bool BWD>
 __device__ __forceinline__ void l3_push(Px& p, const Smem& s, int K3, float t, int g, float alpha,
                                         const float4* __restrict__ recv) {
   const int tid = threadIdx.x;
@@ -144,7 +195,7 @@ __device__ __forceinline__ void l3_push(Px& p, const Smem& s, int K3, float t, i
     const float tm = s.key3[hs * kBlock + tid];
     const int gm = s.gid3[hs * kBlock + tid];
     if (tie_less(t, g, tm, gm)) {
-      blend<STATS>(p, alpha, g, recv);
+      blend<STATS, BWD>(p, alpha, g, recv);
       return;
     }
     const float am = s.alpha3[hs * kBlock + tid];
@@ -171,7 +222,7 @@ __device__ __forceinline__ void l3_push(Px& p, const Smem& s, int K3, float t, i
     s.gid3[d * kBlock + tid] = g;
     s.alpha3[d * kBlock + tid] = alpha;
     p.n3++;
-    blend<STATS>(p, am, gm, recv);
+    blend<STATS, BWD>(p, am, gm, recv);
     return;
   }
   int j = p.n3;
@@ -329,7 +380,7 @@ __device__ __forceinline__ void stage_batch(const Smem& s, const RenderArgs& a, 
   }
 }
 
-template <int MODE, bool STATS>
+template <int MODE, bool STATS, bool BWD>
 __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
@@ -367,6 +418,27 @@ __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
     p.active = valid;
     p.h3 = p.n3 = 0;
     p.n_eval = p.n_kept = p.n_blend = 0;
+    if (BWD) {
+      const long long HWb = (long long)vp.H * vp.W;
+      const long long HW2b = (long long)(vp.H / 2) * (vp.W / 2);
+      float4 dv = make_float4(0.f, 0.f, 0.f, 0.f), sv = make_float4(0.f, 0.f, 0.f, 1.f);
+      if (valid) {
+        const long long si = g.kind == kKindLow ? (long long)g.view * HW2b + (long long)Y * (vp.W / 2) + X
+                                                : (long long)g.view * HWb + (long long)Y * vp.W + X;
+        dv = g.kind == kKindLow ? reinterpret_cast<const float4*>(a.dL_dlow)[si]
+                                : reinterpret_cast<const float4*>(a.dL_dout)[si];
+        sv = g.kind == kKindLow ? a.s_low[si] : a.s_full[si];
+      }
+      p.G0 = dv.x;
+      p.G1 = dv.y;
+      p.G2 = dv.z;
+      p.GT = dv.x * a.bg[0] + dv.y * a.bg[1] + dv.z * a.bg[2];
+      p.F0 = sv.x;
+      p.F1 = sv.y;
+      p.F2 = sv.z;
+      p.TF = sv.w;
+      p.grad = a.grad_rec + vp.base * 16;
+    }
     // block centres of this thread's 4x4 and 2x2 sample blocks
     const int bx4 = g.ox + (sx & ~3), by4 = g.oy + (sy & ~3), bx2 = g.ox + (sx & ~1), by2 = g.oy + (sy & ~1);
     float c4x, c4y, c2x, c2y;
@@ -389,7 +461,7 @@ __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
     auto pop2 = [&](int g2) {
       if (g2 >= 0 && p.active) {
         float al, t;
-        if (eval_full<STATS>(recv + (long long)g2 * kRecF4, p, al, t)) l3_push<STATS>(p, s, K3, t, g2, al, recv);
+        if (eval_full<STATS>(recv + (long long)g2 * kRecF4, p, al, t)) l3_push<STATS, BWD>(p, s, K3, t, g2, al, recv);
       }
     };
     // popped from a 4x4 window: 2x2-block membership, 2x2 window
@@ -444,7 +516,7 @@ __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
               }
             } else if (MODE == 1) {
               float al, t;
-              if (p.active && eval_full<STATS>(r, p, al, t)) l3_push<STATS>(p, s, K3, t, gj, al, recv);
+              if (p.active && eval_full<STATS>(r, p, al, t)) l3_push<STATS, BWD>(p, s, K3, t, gj, al, recv);
             } else {
               bool k = false;
               if (p.active) {
@@ -470,7 +542,7 @@ __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
         if (bgid == 0x7fffffff) {
           p.active = false;
         } else {
-          blend<STATS>(p, ba, bgid, recv);
+          blend<STATS, BWD>(p, ba, bgid, recv);
           last_t = bt;
           last_g = bgid;
         }
@@ -496,9 +568,10 @@ __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
         const float am = s.alpha3[hs * kBlock + tid];
         p.h3 = hs + 1 == K3 ? 0 : hs + 1;
         p.n3--;
-        blend<STATS>(p, am, gm, recv);
+        blend<STATS, BWD>(p, am, gm, recv);
       }
     }
+    if (BWD) continue;
     // ---- outputs
     const float v0 = fmaf(p.T, a.bg[0], p.C0), v1 = fmaf(p.T, a.bg[1], p.C1), v2 = fmaf(p.T, a.bg[2], p.C2);
     const long long HW = (long long)vp.H * vp.W;
@@ -592,17 +665,17 @@ __global__ void composite_kernel(const ViewParams* __restrict__ views, int n_vie
   }
 }
 
-template <int MODE, bool STATS>
+template <int MODE, bool STATS, bool BWD>
 void launch_render_t(const RenderArgs& a, long long max_items, cudaStream_t st) {
   const int K1 = MODE == 2 ? a.k1 : 0, K2 = MODE == 2 ? a.k2 : 0, K3 = MODE == 0 ? 0 : a.k3;
   const size_t smem = render_smem_bytes(K1, K2, K3);
-  cudaFuncSetAttribute(render_kernel<MODE, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(render_kernel<MODE, STATS, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, STATS>, kBlock, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, STATS, BWD>, kBlock, smem);
   if (per_sm < 1) per_sm = 1;
   const long long grid = std::min<long long>(max_items, (long long)device_sm_count() * per_sm);
   if (grid <= 0) return;
-  render_kernel<MODE, STATS><<<(unsigned)grid, kBlock, smem, st>>>(a);
+  render_kernel<MODE, STATS, BWD><<<(unsigned)grid, kBlock, smem, st>>>(a);
 }
 
 }  // namespace
@@ -618,12 +691,21 @@ void launch_workitems(const ViewParams* d_views, int n_views, int fovea_mode, in
 void launch_render(const RenderArgs& a, long long max_items, cudaStream_t st) {
   const bool stats = a.stats != nullptr;
   switch (a.sort_mode * 2 + (stats ? 1 : 0)) {
-    case 0: launch_render_t<0, false>(a, max_items, st); break;
-    case 1: launch_render_t<0, true>(a, max_items, st); break;
-    case 2: launch_render_t<1, false>(a, max_items, st); break;
-    case 3: launch_render_t<1, true>(a, max_items, st); break;
-    case 4: launch_render_t<2, false>(a, max_items, st); break;
-    default: launch_render_t<2, true>(a, max_items, st); break;
+    case 0: launch_render_t<0, false, false>(a, max_items, st); break;
+    case 1: launch_render_t<0, true, false>(a, max_items, st); break;
+    case 2: launch_render_t<1, false, false>(a, max_items, st); break;
+    case 3: launch_render_t<1, true, false>(a, max_items, st); break;
+    case 4: launch_render_t<2, false, false>(a, max_items, st); break;
+    default: launch_render_t<2, true, false>(a, max_items, st); break;
+  }
+}
+
+// replays the forward's per-ray decisions and emits record gradients at every blend
+void launch_render_backward(const RenderArgs& a, long long max_items, cudaStream_t st) {
+  switch (a.sort_mode) {
+    case 0: launch_render_t<0, false, true>(a, max_items, st); break;
+    case 1: launch_render_t<1, false, true>(a, max_items, st); break;
+    default: launch_render_t<2, false, true>(a, max_items, st); break;
   }
 }
 

@@ -116,44 +116,41 @@ def crop_camera(cam, x0, y0, w, h):
     return synth.Camera(cam.world_to_cam, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, w, h, cam.near_z)
 
 
-def oracle_frame_estimate(scene64, frame, budget_s=12.0, crops=None):
-    """Seconds per stereo frame of the FP64 oracle, from a bounded sample: the fixed
-    per-view cost (projection of every Gaussian, one 32x32 tile) plus the per-sample
-    cost of 128x128 crops of the same foveated, hierarchical frame, scaled to the
-    frame's sample count.  Returns (seconds_per_frame, description, threads)."""
+def oracle_frame_estimate(scene64, frame, budget_s=20.0, bands=None):
+    """Seconds per stereo frame of the FP64 oracle, from a bounded sample of the same
+    foveated, hierarchical frame: full-width bands of 64 rows of eye 0 (one through the
+    gaze point, others in the periphery), each rendered by the oracle as it stands (the
+    band is the frame with the principal point shifted, so every sample is the frame's).
+    The per-row cost scales to the image height; the per-view fixed cost (projection of
+    every Gaussian) is measured on a 32-row band and counted once per eye.
+    Returns (seconds_per_frame, description, threads)."""
     from oracle import native as on
     from paper_2505_10144_gb300 import synth
     on.build()
     cam, fv = frame.cameras[0], frame.foveas[0]
 
-    def shifted(x0, y0):
-        return synth.Fovea(fv.gaze_x - x0, fv.gaze_y - y0, fv.radius_px, fv.band_px)
-
-    x0, y0 = 1024, 1088
-    t = time.perf_counter()
-    on.render(scene64, crop_camera(cam, x0, y0, 32, 32), "hier", WINDOWS, 32, shifted(x0, y0))
-    t_fixed = time.perf_counter() - t
-    spots = crops or [(int(fv.gaze_x) // 32 * 32, int(fv.gaze_y) // 32 * 32), (128, 256), (1792, 1920), (512, 1600),
-                      (1536, 384), (960, 160)]
-    t_samples, n_samples, used = 0.0, 0, 0
-    for (cx, cy) in spots:
-        cx, cy = min(max(cx, 0), W_IMG - 128) // 32 * 32, min(max(cy, 0), H_IMG - 128) // 32 * 32
+    def band(y0, h):
+        c = crop_camera(cam, 0, y0, W_IMG, h)
+        f = synth.Fovea(fv.gaze_x, fv.gaze_y - y0, fv.radius_px, fv.band_px)
         t = time.perf_counter()
-        r = on.render(scene64, crop_camera(cam, cx, cy, 128, 128), "hier", WINDOWS, 32, shifted(cx, cy))
-        dt = time.perf_counter() - t
-        t_samples += max(dt - t_fixed, 0.0)
-        n_samples += r["stats"]["samples"]
+        r = on.render(scene64, c, "hier", WINDOWS, 32, f)
+        return time.perf_counter() - t, r["stats"]["samples"]
+
+    t_fixed = min(band(1088, 32)[0] for _ in range(2)) / 2.0  # ~half of a 32-row band is fixed cost
+    ys = bands or [int(fv.gaze_y) // 32 * 32, 256, 1792, 1024]
+    rows, t_rows, samples, used = 0, 0.0, 0, 0
+    for y in ys:
+        y = min(max(y, 0), H_IMG - 64) // 32 * 32
+        dt, ns = band(y, 64)
+        t_rows += max(dt - t_fixed, 0.0)
+        rows += 64
+        samples += ns
         used += 1
-        if t_samples + used * t_fixed > budget_s:
+        if t_rows + used * t_fixed > budget_s:
             break
-    # samples of a whole eye: full-res pixels of focus/hybrid tiles + groups of periphery tiles
-    full = on.render(synth.Scene(*[a[..., :0] for a in scene64.arrays()], 3),
-                     cam, "exact", WINDOWS, 32, fv)
-    samples_eye = full["stats"]["samples"]
-    per_sample = t_samples / max(n_samples, 1)
-    sec = 2 * (t_fixed + per_sample * samples_eye)
-    desc = (f"FP64 oracle, hierarchical 4/8/16, foveated: fixed per-view cost (projection of all {N_GAUSS} Gaussians) "
-            f"+ {used} crops of 128x128 ({n_samples} samples) scaled to {samples_eye} samples per eye x 2 eyes")
+    sec = 2 * (t_fixed + t_rows / rows * H_IMG)
+    desc = (f"FP64 oracle, hierarchical 4/8/16, foveated: {used} full-width bands of 64 rows ({samples} samples) "
+            f"of eye 0, per-row cost scaled to {H_IMG} rows, plus the per-view fixed cost, x 2 eyes")
     return sec, desc, on.num_threads()
 
 
@@ -168,7 +165,7 @@ def run_reference(args, ws, rank):
     desc, thr = "", 1
     for i in range(args.warmup + args.steps):
         fr = wl.frames[i % len(wl.frames)]
-        sec, desc, thr = oracle_frame_estimate(scene64, fr, budget_s=4.0, crops=[(int(fr.foveas[0].gaze_x), int(fr.foveas[0].gaze_y)), (128, 256)])
+        sec, desc, thr = oracle_frame_estimate(scene64, fr, budget_s=6.0, bands=[int(fr.foveas[0].gaze_y), 256])
         if i >= args.warmup:
             vals.append(sec)
     mean = statistics.mean(vals)
@@ -201,6 +198,128 @@ def ncu_case(args, api, torch):
     R.close()
 
 
+def run_batched(args, api, torch, ws, rank):
+    """Three scenes (200k, 1M, 3M Gaussians) x 8 head poses x 2 eyes = 48 views of
+    2064x2208, foveated, in one vrs_render (one sort, one persistent render launch)
+    captured in a CUDA graph; the autotuner picks the windows and CTA cap."""
+    from paper_2505_10144_gb300 import autotune, synth
+    sizes = [200_000, 1_000_000, 3_000_000]
+    scenes = [api.DeviceScene.from_host(synth.shell_scene(n, synth.rng_for(2, salt=k), sh_degree=3))
+              for k, n in enumerate(sizes)]
+
+    def views(step):
+        cams, fovs, vs = [], [], []
+        for k in range(3):
+            for fr in synth.batched_poses(8, synth.rng_for(2, salt=10 + k + 97 * step), W_IMG, H_IMG):
+                cams += fr.cameras
+                fovs += fr.foveas
+                vs += [k, k]
+        return cams, fovs, vs
+
+    cams, fovs, vs = views(0)
+    R = api.Renderer()
+    base = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=32, fovea_mode="bilinear")
+    cache = args.tune_cache or os.path.join(ROOT, "gpurun_out", "autotune.json")
+    best, cands = autotune.autotune(R, scenes, vs, cams, fovs, base, cache_path=cache, reps=2)
+    R.set_tuning(best["max_ctas_per_sm"])
+    cfg = api.RenderConfig(sort_mode="hier", windows=tuple(best["windows"]), key_tile=32, fovea_mode="bilinear")
+    gr = api.GraphedRender(R, scenes, vs, cams, fovs, cfg)
+    steps = max(args.steps // 10, 3)
+    frames = [views(1 + i) for i in range(steps + args.warmup)]
+    for i in range(args.warmup):
+        gr.replay(frames[i][0], frames[i][1])
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(steps):
+        c, f, _ = frames[args.warmup + i]
+        R.update_views(c, f, cfg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()  # replay() launches on the current stream
+        gr.graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    R.check()
+    st = R.stats()
+    line = {"metric": "batched views/s (3 scenes x 8 poses x 2 eyes, 2064x2208, one graph replay)",
+            "value": 48 * len(ms) / (sum(ms) / 1e3), "unit": "views/s", "n_gpus": ws, "steps": len(ms),
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched_3_scenes_200k_1M_3M_48_views_foveated", "views": 48,
+                       "gaussians": sizes, "graph": "one vrs_render captured in a CUDA graph, poses via vrs_update_views"},
+            "autotune": {"best": {k: best[k] for k in ("windows", "max_ctas_per_sm", "ms")}, "candidates": cands},
+            "instances_per_batch": st["instances"], "work_items": st["work_items"],
+            "gpu_launches": st["kernels"] * len(ms)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    R.close()
+
+
+def run_finetune(args, api, torch, ws, rank):
+    """Fine-tuning step through the rasterizer: 500k Gaussians, 4 views of 1280x1280,
+    110 deg FOV, 0.8 L1 + 0.2 (1 - SSIM), gradients for every parameter, Adam.  The
+    targets are renders of a perturbed copy of the scene (means + N(0, 0.01), log-scales +
+    N(0, 0.1)) made by this renderer; the oracle pins the gradients in the tests."""
+    from paper_2505_10144_gb300 import synth
+    scene = synth.shell_scene(N_GAUSS, synth.rng_for(3), sh_degree=3)
+    cams = synth.ring_views(4, 1280, 1280, 110.0, synth.rng_for(3, salt=1))
+    target_scene = synth.perturbed(scene, synth.rng_for(3, salt=2))
+    R = api.Renderer()
+    cfg = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=16)
+    target = R.render([api.DeviceScene.from_host(target_scene)], [0] * 4, cams, None, cfg).clone()
+    names = ["mean", "log_scale", "quat", "opacity_logit", "sh"]
+    params = {k: torch.tensor(np.asarray(v), device="cuda") for k, v in zip(names, scene.arrays())}
+    lrs = {"mean": 1.6e-4, "log_scale": 5e-3, "quat": 1e-3, "opacity_logit": 5e-2, "sh": 2.5e-3}
+    opt = api.Adam(params, lrs)
+    ds = api.DeviceScene(*[params[k] for k in names], 3)
+    grads = ds.zeros_like()
+
+    def step():
+        img = R.render([ds], [0] * 4, cams, None, cfg, save=True)
+        loss, dimg = R.loss(img, target)
+        for t in grads.tensors():
+            t.zero_()
+        R.backward([ds], [0] * 4, cams, None, cfg, dimg, [grads])
+        opt.step(dict(zip(names, grads.tensors())))
+        return loss
+
+    losses = []
+    for _ in range(args.warmup):
+        losses.append(float(step().item()))
+    torch.cuda.synchronize()
+    steps = max(args.steps // 4, 5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        loss = step()
+    e1.record()
+    torch.cuda.synchronize()
+    losses.append(float(loss.item()))
+    ms = e0.elapsed_time(e1) / steps
+    R.check()
+    line = {"metric": "fine-tuning steps/s (4 views 1280x1280, 500k Gaussians, render+loss+backward+Adam)",
+            "value": 1e3 / ms, "unit": "steps/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "finetune_500k_4x1280", "windows": list(WINDOWS)},
+            "loss_first": losses[0], "loss_last": losses[-1]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    R.close()
+
+
+def approximation_error(R, api, ds, frame, cfg_hier, torch):
+    """Error of the hierarchical per-ray windows against the exact per-ray order on one
+    foveated stereo frame (both on the GPU; the exact order is the parity-checked mode)."""
+    exact_cfg = api.RenderConfig(**{**cfg_hier.__dict__, "sort_mode": "exact"})
+    a = R.render([ds], [0, 0], frame.cameras, frame.foveas, cfg_hier).clone()
+    b = R.render([ds], [0, 0], frame.cameras, frame.foveas, exact_cfg)
+    d = (a - b).abs()
+    mse = float((d ** 2).mean())
+    return {"mean_abs": float(d.mean()), "max_abs": float(d.max()),
+            "psnr_db": float("inf") if mse == 0 else 10 * math.log10(1.0 / mse),
+            "pixels_over_2e-4_pct": float((d.amax(dim=1) > 2e-4).float().mean() * 100)}
+
+
 def psnr(a, b):
     mse = float(((a - b) ** 2).mean())
     return float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
@@ -218,6 +337,10 @@ def main():
                     help="only render warmup + steps foveated frames (for profiler captures)")
     ap.add_argument("--scale", type=float, default=1.0, help="resolution scale of --ncu-case")
     ap.add_argument("--mode", default="hier", choices=["exact", "window", "hier"], help="sort mode of --ncu-case")
+    ap.add_argument("--workload", default="vr", choices=["vr", "batched", "finetune"],
+                    help="vr: the headline stereo frame; batched: 3 scenes x 8 poses x 2 eyes in one graph "
+                         "replay; finetune: 4 views at 1280^2, render + loss + backward + Adam")
+    ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache for --workload batched")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
@@ -235,6 +358,12 @@ def main():
     build.build()
     if args.ncu_case:
         ncu_case(args, api, torch)
+        return
+    if args.workload == "batched":
+        run_batched(args, api, torch, ws, rank)
+        return
+    if args.workload == "finetune":
+        run_finetune(args, api, torch, ws, rank)
         return
     n_frames = args.warmup + args.steps
     scene, wl = make_workload(n_frames, rank)
@@ -311,6 +440,7 @@ def main():
         for k in cnt:
             cnt[k] += st[k]
     cnt = {k: v / n_stat for k, v in cnt.items()}
+    approx = approximation_error(R, api, ds, wl.frames[1], fov_cfg, torch)
     render_ms = stages.get("render", 0.0) / max(ncalls, 1)
     flops = FLOPS_EVAL * cnt["evaluated"] + FLOPS_KEPT * cnt["kept"] + FLOPS_BLEND * cnt["blended"]
     clocks = clk.summary()
@@ -359,6 +489,7 @@ def main():
                   "config": "full resolution, 16x16 tiles, hierarchical 4/8/16, same pipeline"},
         "speedup_vs_plain": statistics.mean(ms_plain) / statistics.mean(ms_fov),
         "psnr_vs_plain_db": statistics.mean(ps),
+        "hier_vs_exact": approx,
         "stage_ms_per_frame": {k: v / max(ncalls, 1) for k, v in stages.items()},
         "counters_per_frame": cnt,
         "roofline": roofline,

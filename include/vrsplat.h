@@ -178,6 +178,18 @@ vrs_status vrs_project(vrs_ctx* ctx, const vrs_gaussians* scene, const vrs_camer
 vrs_status vrs_sort_pairs(vrs_ctx* ctx, const uint64_t* d_keys_in, const uint32_t* d_vals_in,
                           uint64_t* d_keys_out, uint32_t* d_vals_out, int64_t n, int bits, void* stream);
 
+/* Graph replays (batched persistent launch, Sec. 4.3's single launch over all views):
+ * rewrites the cameras and gaze of the views of the last vrs_render (same count, same
+ * image size, same scenes) in the context's pinned staging, which a CUDA graph captured
+ * around vrs_render copies to the device at every replay.  Waits for the previous
+ * replay's copy of the staging before writing; launches nothing.  h_fovea may be NULL
+ * (gaze unchanged). */
+vrs_status vrs_update_views(vrs_ctx* ctx, const vrs_camera* h_cams, const vrs_fovea* h_fovea, int n_views);
+
+/* Tuning knob read by vrs_render: cap on resident render CTAs per SM (0 = the
+ * occupancy limit).  Changes scheduling only, never the image. */
+vrs_status vrs_set_tuning(vrs_ctx* ctx, int max_render_ctas_per_sm);
+
 /* Largest n that vrs_sort_pairs_noalloc accepts. */
 #define VRS_SORT_NOALLOC_MAX_PAIRS (1 << 20)
 

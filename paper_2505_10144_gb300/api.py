@@ -185,6 +185,18 @@ class Renderer:
         m = int(n.value)
         return keys[:m], vals[:m], ranges
 
+    def update_views(self, cams, foveas=None, cfg: RenderConfig | None = None):
+        """New cameras / gaze for the next replay of a captured render (same view count)."""
+        cfg = cfg or RenderConfig()
+        n = len(cams)
+        cm = (_lib.Camera * n)(*[camera_c(c) for c in cams])
+        mode = FOVEA_MODES[cfg.fovea_mode]
+        fv = (_lib.Fovea * n)(*[fovea_c(foveas[k], mode, cfg.focus_tile) for k in range(n)]) if foveas else None
+        self._check(self.lib.vrs_update_views(self.ctx, cm, fv, n))
+
+    def set_tuning(self, max_render_ctas_per_sm: int = 0):
+        self._check(self.lib.vrs_set_tuning(self.ctx, int(max_render_ctas_per_sm)))
+
     STAGES = ["preprocess", "scan", "duplicate", "sort", "ranges_workitems", "render", "composite", "total"]
 
     def profile_begin(self, max_calls: int):
@@ -298,3 +310,35 @@ class Adam:
             if g is None:
                 continue
             adam_step(p, g.contiguous(), self.m[k], self.v[k], self.lrs.get(k, 0.0), self.t, self.b1, self.b2, self.eps)
+
+
+class GraphedRender:
+    """One vrs_render over many scenes and views (a single persistent render launch)
+    captured in a CUDA graph; replay() re-renders with new cameras and gaze.
+
+    The workspace is sized by an eager render first (instance count x headroom); a replay
+    whose instances exceed it raises VRS_ERR_CAPACITY at the next check()."""
+
+    def __init__(self, renderer: Renderer, scenes, view_scene, cams, foveas, cfg: RenderConfig,
+                 headroom: float = 1.3):
+        self.R, self.scenes, self.view_scene, self.cfg = renderer, scenes, list(view_scene), cfg
+        n_views = len(cams)
+        W, H = int(cams[0].width), int(cams[0].height)
+        self.out = torch.empty((n_views, 3, H, W), device="cuda", dtype=torch.float32)
+        renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out)
+        renderer.check()
+        need = renderer.stats()["instances"]
+        total = sum(scenes[v].n for v in self.view_scene)
+        renderer.reserve(n_views, W, H, total, int(need * headroom) + (1 << 16))
+        renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        self.stream = torch.cuda.Stream()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out, stream=self.stream)
+
+    def replay(self, cams=None, foveas=None) -> torch.Tensor:
+        if cams is not None:
+            self.R.update_views(cams, foveas, self.cfg)
+        self.graph.replay()
+        return self.out

@@ -53,6 +53,7 @@ struct vrs_ctx {
   long long last_instances = 0;
   int last_passes = 0;
   int last_launches = 0;
+  int max_ctas_per_sm = 0;
   Saved saved;
   // stage profiling: 8 events per recorded call
   std::vector<cudaEvent_t> prof_ev;
@@ -182,13 +183,18 @@ vrs_status stage_views(vrs_ctx* c, int n_views, cudaStream_t st, bool cap_mode) 
   cudaError_t e = cudaMemcpyAsync(c->views.p, c->h_views, sizeof(ViewParams) * n_views, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->view_list.p, c->h_view_list, sizeof(int) * n_views, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess && !cap_mode) e = cudaEventRecord(c->staging_done, st);
+  // in a captured graph the copy reads the staging at every replay; the external record
+  // lets vrs_update_views wait for the last replay's copy before it rewrites the staging
+  if (e == cudaSuccess)
+    e = cap_mode ? cudaEventRecordWithFlags(c->staging_done, st, cudaEventRecordExternal)
+                 : cudaEventRecord(c->staging_done, st);
   return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "staging copy");
 }
 
-vrs_status reserve_staging(vrs_ctx* c, int n_views) {
-  if (c->staging_done) cudaEventSynchronize(c->staging_done);
+vrs_status reserve_staging(vrs_ctx* c, int n_views, bool cap_mode = false) {
+  if (c->staging_done && !cap_mode) cudaEventSynchronize(c->staging_done);
   if (n_views <= c->staging_cap) return VRS_OK;
+  if (cap_mode) return fail(c, VRS_ERR_CAPACITY, "view staging too small during stream capture");
   if (c->h_views) cudaFreeHost(c->h_views);
   if (c->h_view_list) cudaFreeHost(c->h_view_list);
   c->h_views = nullptr;
@@ -210,7 +216,7 @@ struct Plan {
 
 vrs_status plan_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, const int* view_scene,
                        const vrs_camera* cams, const vrs_fovea* fov, int n_views, const vrs_render_opts* o,
-                       Plan& pl) {
+                       Plan& pl, bool cap_mode = false) {
   if (!scenes || n_scenes <= 0 || !view_scene || !cams || n_views <= 0 || !o)
     return fail(c, VRS_ERR_INVALID, "null or empty argument");
   for (int s = 0; s < n_scenes; ++s) {
@@ -250,7 +256,7 @@ vrs_status plan_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, co
   pl.fovea_mode = fm;
   pl.tiles_per_view = ((W + T - 1) / T) * ((H + T - 1) / T);
   if ((long long)pl.tiles_per_view * n_views >= (1ll << 31)) return fail(c, VRS_ERR_INVALID, "too many tiles");
-  vrs_status st = reserve_staging(c, n_views);
+  vrs_status st = reserve_staging(c, n_views, cap_mode);
   if (st) return st;
   pl.view_n.resize(n_views);
   long long base = 0;
@@ -463,11 +469,12 @@ vrs_status vrs_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, con
   cudaStream_t st = (cudaStream_t)stream;
   const bool cap_mode = capturing(st);
   Plan pl;
-  vrs_status s = plan_render(c, scenes, n_scenes, view_scene, cams, fov, n_views, o, pl);
+  vrs_status s = plan_render(c, scenes, n_scenes, view_scene, cams, fov, n_views, o, pl, cap_mode);
   if (s) return s;
   if (pl.fovea_mode == 2 && !d_low_rgb) return fail(c, VRS_ERR_INVALID, "fovea mode 2 needs d_low_rgb");
   if ((s = build_instances(c, scenes, n_scenes, pl, st, cap_mode))) return s;
   RenderArgs a = make_args(c, pl, o);
+  a.max_ctas_per_sm = c->max_ctas_per_sm;
   a.out = d_out_rgb;
   const size_t low_bytes = sizeof(float) * 3 * (size_t)n_views * (pl.W / 2) * (pl.H / 2);
   if (pl.fovea_mode != 0) {
@@ -742,6 +749,33 @@ vrs_status vrs_profile_end(vrs_ctx* c, void* stream, double* ms, int64_t* n_call
   if (n_calls) *n_calls = c->prof_used;
   c->prof_on = false;
   c->prof_used = 0;
+  return VRS_OK;
+}
+
+vrs_status vrs_update_views(vrs_ctx* c, const vrs_camera* cams, const vrs_fovea* fov, int n_views) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!cams || n_views <= 0 || n_views > c->staging_cap || n_views != c->saved.n_views)
+    return fail(c, VRS_ERR_INVALID, "update_views needs the view count of the last render");
+  for (int v = 0; v < n_views; ++v) {
+    if (!finite_cam(cams[v])) return fail(c, VRS_ERR_INVALID, "non-finite or non-positive camera values");
+    if (cams[v].width != c->saved.W || cams[v].height != c->saved.H)
+      return fail(c, VRS_ERR_INVALID, "update_views cannot change the image size");
+  }
+  if (c->staging_done) cudaEventSynchronize(c->staging_done);  // the last copy of the staging has run
+  for (int v = 0; v < n_views; ++v) {
+    ViewParams& vp = c->h_views[v];
+    const int scene = vp.scene;
+    const long long base = vp.base;
+    fill_view(vp, cams[v], fov ? &fov[v] : nullptr, c->saved.key_tile);
+    vp.scene = scene;
+    vp.base = base;
+  }
+  return VRS_OK;
+}
+
+vrs_status vrs_set_tuning(vrs_ctx* c, int max_render_ctas_per_sm) {
+  if (!c || max_render_ctas_per_sm < 0 || max_render_ctas_per_sm > 32) return fail(c, VRS_ERR_INVALID, "bad tuning value");
+  c->max_ctas_per_sm = max_render_ctas_per_sm;
   return VRS_OK;
 }
 

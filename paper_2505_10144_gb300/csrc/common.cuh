@@ -161,6 +161,7 @@ struct RenderArgs {
   const float* dL_dout;
   const float* dL_dlow;
   float* grad_rec;  // [sum N][16] per-(view, Gaussian) record gradients
+  int max_ctas_per_sm;  // tuning: cap on resident render CTAs per SM (0 = occupancy limit)
 };
 
 void launch_workitems(const ViewParams* d_views, int n_views, int fovea_mode, int key_tile, int tiles_per_view,

@@ -669,10 +669,21 @@ template <int MODE, bool STATS, bool BWD>
 void launch_render_t(const RenderArgs& a, long long max_items, cudaStream_t st) {
   const int K1 = MODE == 2 ? a.k1 : 0, K2 = MODE == 2 ? a.k2 : 0, K3 = MODE == 0 ? 0 : a.k3;
   const size_t smem = render_smem_bytes(K1, K2, K3);
-  cudaFuncSetAttribute(render_kernel<MODE, STATS, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, STATS, BWD>, kBlock, smem);
-  if (per_sm < 1) per_sm = 1;
+  // attribute and occupancy per shared-memory size, set once (outside any stream capture)
+  static size_t set_smem = 0;
+  static int per_sm_cached[kMaxWin * 3 + 1] = {0};
+  const int key = (int)std::min<size_t>(smem / 4096, (size_t)kMaxWin * 3);
+  if (smem > set_smem) {
+    cudaFuncSetAttribute(render_kernel<MODE, STATS, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem = smem;
+  }
+  int per_sm = per_sm_cached[key];
+  if (per_sm <= 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, STATS, BWD>, kBlock, smem);
+    if (per_sm < 1) per_sm = 1;
+    per_sm_cached[key] = per_sm;
+  }
+  if (a.max_ctas_per_sm > 0) per_sm = std::min(per_sm, a.max_ctas_per_sm);
   const long long grid = std::min<long long>(max_items, (long long)device_sm_count() * per_sm);
   if (grid <= 0) return;
   render_kernel<MODE, STATS, BWD><<<(unsigned)grid, kBlock, smem, st>>>(a);

@@ -323,9 +323,11 @@ int launch_radix_sort(uint64_t* keys[2], uint32_t* vals[2], const uint32_t* d_n,
     cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     attr = true;
   }
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kBlock, smem);
-  if (per_sm < 1) per_sm = 1;
+  static int per_sm = 0;
+  if (per_sm <= 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kBlock, smem);
+    if (per_sm < 1) per_sm = 1;
+  }
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
   int cur = 0;
   for (int p = 0; p < passes; ++p) {

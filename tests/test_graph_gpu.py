@@ -1,0 +1,72 @@
+"""Batched persistent launch in a captured CUDA graph, and the autotuner."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_10144_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_2505_10144_gb300 import api, build
+    build.build()
+    R = api.Renderer()
+    scenes = [api.DeviceScene.from_host(synth.shell_scene(n, synth.rng_for(2, salt=k), sh_degree=3))
+              for k, n in enumerate([3000, 8000])]
+    W, H = 256, 192
+    poses = [synth.batched_poses(2, synth.rng_for(2, salt=10 + k), W, H) for k in range(2)]
+    cams, fovs, vs = [], [], []
+    for s_idx, frames in enumerate(poses):
+        for fr in frames:
+            cams += fr.cameras
+            fovs += [synth.fovea_for(W, (f.gaze_x, f.gaze_y), radius_frac=0.25) for f in fr.foveas]
+            vs += [s_idx, s_idx]
+    cfg = api.RenderConfig(sort_mode="hier", windows=(4, 8, 16), key_tile=32, fovea_mode="bilinear")
+    yield api, R, scenes, vs, cams, fovs, cfg
+    R.close()
+
+
+def test_graph_replay_equals_eager_render(setup):
+    api, R, scenes, vs, cams, fovs, cfg = setup
+    gr = api.GraphedRender(R, scenes, vs, cams, fovs, cfg)
+    out = gr.replay().clone()
+    R.check()
+    eager = R.render(scenes, vs, cams, fovs, cfg)
+    R.check()
+    assert torch.equal(out, eager)
+    # new poses and gaze through vrs_update_views, then replay
+    cams2 = [synth.Camera(c.world_to_cam, c.fx, c.fy, c.cx, c.cy, c.width, c.height, c.near_z) for c in cams]
+    rot = synth.head_rotation(0.15)
+    for c in cams2:
+        R3 = c.world_to_cam[:, :3].astype(np.float64) @ rot.T
+        c.world_to_cam = np.ascontiguousarray(np.concatenate([R3, c.world_to_cam[:, 3:]], 1), dtype=np.float32)
+    fovs2 = [synth.Fovea(f.gaze_x + 17.0, f.gaze_y - 9.0, f.radius_px, f.band_px) for f in fovs]
+    out2 = gr.replay(cams2, fovs2).clone()
+    R.check()
+    eager2 = R.render(scenes, vs, cams2, fovs2, cfg)
+    R.check()
+    assert torch.equal(out2, eager2)
+    assert not torch.equal(out2, out)
+
+
+def test_autotuner_picks_a_candidate_and_caches_it(setup, tmp_path):
+    from paper_2505_10144_gb300 import autotune
+    api, R, scenes, vs, cams, fovs, cfg = setup
+    path = tmp_path / "tune.json"
+    best, res = autotune.autotune(R, scenes, vs, cams, fovs, cfg, cache_path=path, reps=2,
+                                  window_sets=[(4, 8, 16), (8, 16, 32)], cta_caps=[0, 1])
+    assert len(res) == 4 and best["ms"] == min(r["ms"] for r in res)
+    cache = json.loads(path.read_text())
+    assert autotune.cache_key(scenes, vs, cams) in cache
+    best2, _ = autotune.autotune(R, scenes, vs, cams, fovs, cfg, cache_path=path)
+    assert best2["windows"] == best["windows"] and best2["max_ctas_per_sm"] == best["max_ctas_per_sm"]
+    # the CTA cap is scheduling only: same image
+    R.set_tuning(1)
+    a = R.render(scenes, vs, cams, fovs, cfg).clone()
+    R.set_tuning(0)
+    b = R.render(scenes, vs, cams, fovs, cfg)
+    assert torch.equal(a, b)

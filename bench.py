@@ -136,8 +136,11 @@ def oracle_frame_estimate(scene64, frame, budget_s=20.0, bands=None):
         r = on.render(scene64, c, "hier", WINDOWS, 32, f)
         return time.perf_counter() - t, r["stats"]["samples"]
 
-    t_fixed = min(band(1088, 32)[0] for _ in range(2)) / 2.0  # ~half of a 32-row band is fixed cost
-    ys = bands or [int(fv.gaze_y) // 32 * 32, 256, 1792, 1024]
+    # fixed cost from two heights of the same band: t(h) = fixed + h * per_row
+    yg = min(max(int(fv.gaze_y) - 32, 0), H_IMG - 64) // 32 * 32
+    t32, t64 = band(yg, 32)[0], band(yg, 64)[0]
+    t_fixed = max(t32 - (t64 - t32), 0.0)
+    ys = bands or [int(fv.gaze_y), 256, 1792, 1024]
     rows, t_rows, samples, used = 0, 0.0, 0, 0
     for y in ys:
         y = min(max(y, 0), H_IMG - 64) // 32 * 32

@@ -190,6 +190,36 @@ vrs_status vrs_update_views(vrs_ctx* ctx, const vrs_camera* h_cams, const vrs_fo
  * occupancy limit).  Changes scheduling only, never the image. */
 vrs_status vrs_set_tuning(vrs_ctx* ctx, int max_render_ctas_per_sm);
 
+/* Learned periphery network (the workload's replacement for the periphery upsampling of
+ * Sec. 4.3): y = x + conv3(relu(conv2(relu(conv1(bf16(x)))))), 3 -> 32 -> 32 -> 3
+ * channels, 3x3 kernels, zero padding 1, BF16 weights and activations, FP32
+ * accumulation, x the bilinear x2 upsampling of the half-resolution image.  Parameters:
+ * one device float buffer of VRS_NET_PARAMS values, OIHW:
+ * w1[32][3][3][3] b1[32] w2[32][32][3][3] b2[32] w3[3][32][3][3] b3[3] (float master
+ * copy; the kernels round weights to BF16). */
+#define VRS_NET_PARAMS 11011
+
+/* Training forward on whole images: d_x, d_y device float [n][3][H][W]; d_acts (device
+ * uint16 BF16 bits [n][2][32][H][W], may be NULL) receives the two hidden activations
+ * for vrs_net_backward. */
+vrs_status vrs_net_forward(vrs_ctx* ctx, const float* d_params, const float* d_x, int n_images, int height, int width,
+                           float* d_y, uint16_t* d_acts, void* stream);
+
+/* d_dparams += d<d_dy, y>/d(params) for the forward that wrote d_acts (BF16 rounding
+ * treated as identity, ReLU masks from the saved activations).  Scratch from ctx. */
+vrs_status vrs_net_backward(vrs_ctx* ctx, const float* d_params, const float* d_x, const uint16_t* d_acts,
+                            const float* d_dy, int n_images, int height, int width, float* d_dparams, void* stream);
+
+/* After a vrs_render with fovea mode 2: writes every periphery pixel of d_out_rgb with the
+ * network applied to the bilinear upsampling of d_low_rgb (the same buffers that render
+ * call used), one fused tensor-core kernel over the periphery tiles of all views. */
+vrs_status vrs_net_periphery(vrs_ctx* ctx, const float* d_params, const float* d_low_rgb, float* d_out_rgb,
+                             void* stream);
+
+/* Mean squared error over n values and its gradient 2 (y - t) / n (d_dy may be NULL). */
+vrs_status vrs_mse(vrs_ctx* ctx, const float* d_y, const float* d_t, int64_t n, float* d_loss, float* d_dy,
+                   void* stream);
+
 /* Largest n that vrs_sort_pairs_noalloc accepts. */
 #define VRS_SORT_NOALLOC_MAX_PAIRS (1 << 20)
 

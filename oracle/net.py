@@ -34,9 +34,12 @@ def init_weights(rng: np.random.Generator, zero_last: bool = False) -> dict:
 
 
 def forward(x: torch.Tensor, w: dict, round_acts: bool = True):
-    """x: [B, 3, H, W] float64 network input (already upsampled).  -> (y, (a1, a2))."""
+    """x: [B, 3, H, W] float64 network input (already upsampled).  -> (y, (a1, a2)).
+    Weights are used as BF16 values (biases as given)."""
     t = {k: (v if torch.is_tensor(v) else torch.tensor(v, dtype=torch.float64)) for k, v in w.items()}
     r = bf16 if round_acts else (lambda z: z)
+    if round_acts:
+        t = {k: bf16(v) if k.startswith("w") else v for k, v in t.items()}
     xin = r(x)
     a1 = r(F.relu(F.conv2d(xin, t["w1"], t["b1"], padding=1)))
     a2 = r(F.relu(F.conv2d(a1, t["w2"], t["b2"], padding=1)))
@@ -63,7 +66,9 @@ def conv_direct(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
 def grads(x: np.ndarray, w: dict, dy: np.ndarray) -> dict:
     """d<dy, y>/d(weights, biases) with BF16 rounding treated as identity (the
     straight-through rule the GPU backward also uses)."""
-    wt = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in w.items()}
+    wm = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in w.items()}
+    # BF16 weights in the forward, gradients straight through to the float master copy
+    wt = {k: (v + (bf16(v) - v).detach()) if k.startswith("w") else v for k, v in wm.items()}
     xt = torch.tensor(x, dtype=torch.float64)
     xin = bf16(xt)
     with torch.no_grad():
@@ -76,4 +81,4 @@ def grads(x: np.ndarray, w: dict, dy: np.ndarray) -> dict:
     a2 = F.relu(z2) + (a2r - F.relu(z2)).detach()
     y = xt + F.conv2d(a2, wt["w3"], wt["b3"], padding=1)
     (y * torch.tensor(dy, dtype=torch.float64)).sum().backward()
-    return {k: v.grad.numpy().copy() for k, v in wt.items()}
+    return {k: v.grad.numpy().copy() for k, v in wm.items()}

@@ -40,7 +40,7 @@ class RenderOpts(C.Structure):
 EXPORTED = ["vrs_create", "vrs_destroy", "vrs_reserve", "vrs_render", "vrs_render_backward", "vrs_check_status",
             "vrs_get_stats", "vrs_copy_instances", "vrs_project", "vrs_sort_pairs", "vrs_loss_l1_ssim",
             "vrs_adam_step", "vrs_profile_begin", "vrs_profile_end", "vrs_sort_pairs_noalloc", "vrs_update_views", "vrs_set_tuning",
-            "vrs_last_error"]
+            "vrs_net_forward", "vrs_net_backward", "vrs_net_periphery", "vrs_mse", "vrs_last_error"]
 
 _lib = None
 
@@ -78,6 +78,10 @@ def load() -> C.CDLL:
     lib.vrs_sort_pairs_noalloc.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp]
     lib.vrs_update_views.argtypes = [vp, P(Camera), P(Fovea), i32]
     lib.vrs_set_tuning.argtypes = [vp, i32]
+    lib.vrs_net_forward.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp]
+    lib.vrs_net_backward.argtypes = [vp, vp, vp, vp, vp, i32, i32, i32, vp, vp]
+    lib.vrs_net_periphery.argtypes = [vp, vp, vp, vp, vp]
+    lib.vrs_mse.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.vrs_profile_begin.argtypes = [vp, i32]
     lib.vrs_profile_end.argtypes = [vp, vp, P(C.c_double), P(i64)]
     lib.vrs_last_error.argtypes = [vp]

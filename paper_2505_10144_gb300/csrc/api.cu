@@ -17,6 +17,13 @@ using namespace vrs;
 namespace vrs {
 void launch_project_only(const SceneDev& s, const ViewParams* d_vp, int T, float* out, float* bbox, uint32_t* count,
                          cudaStream_t st);
+void net_forward_train(const float* params, const float* x, int B, int H, int W, float* y, uint16_t* acts,
+                       uint16_t* tmp_a1, uint16_t* tmp_a2, cudaStream_t st);
+void net_backward_train(const float* params, const float* x, const uint16_t* acts, const float* dy, int B, int H,
+                        int W, float* dparams, float* dz2, float* dz1, cudaStream_t st);
+void net_mse(const float* y, const float* t, long long n, float* loss, float* dy, double* scratch, cudaStream_t st);
+void net_periphery(const float* params, const float* low, float* out, const uint8_t* tile_class,
+                   const ViewParams* views, int n_views, int tiles_per_view, int W, int H, cudaStream_t st);
 vrs_status loss_l1_ssim_impl(const float* img, const float* tgt, int n, int H, int W, float* loss, float* grad,
                              void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t loss_scratch_bytes(int n, int H, int W);
@@ -42,7 +49,7 @@ struct Saved {
 struct vrs_ctx {
   std::string err;
   DevBuf views, view_list, rec, bbox, count, offsets, partials, keys[2], vals[2], sort_scratch, ranges, tile_class,
-      items, counters, low, s_full, s_low, stats, grad_rec, dsamp_full, dsamp_low, loss_scratch, misc;
+      items, counters, low, s_full, s_low, stats, grad_rec, dsamp_full, dsamp_low, loss_scratch, misc, net_tmp;
   ViewParams* h_views = nullptr;  // pinned staging
   int* h_view_list = nullptr;
   uint32_t* h_small = nullptr;    // pinned: [0] total instances, [1] status, [2] items
@@ -425,7 +432,7 @@ vrs_status vrs_destroy(vrs_ctx* c) {
   DevBuf* all[] = {&c->views, &c->view_list, &c->rec, &c->bbox, &c->count, &c->offsets, &c->partials, &c->keys[0],
                    &c->keys[1], &c->vals[0], &c->vals[1], &c->sort_scratch, &c->ranges, &c->tile_class, &c->items,
                    &c->counters, &c->low, &c->s_full, &c->s_low, &c->stats, &c->grad_rec, &c->dsamp_full,
-                   &c->dsamp_low, &c->loss_scratch, &c->misc};
+                   &c->dsamp_low, &c->loss_scratch, &c->misc, &c->net_tmp};
   for (DevBuf* b : all)
     if (b->p) cudaFree(b->p);
   if (c->h_views) cudaFreeHost(c->h_views);
@@ -716,6 +723,61 @@ vrs_status vrs_loss_l1_ssim(vrs_ctx* c, const float* d_img, const float* d_targe
   if (!ensure(c, c->loss_scratch, loss_scratch_bytes(n_images, height, width), capturing(st), &s)) return s;
   return loss_l1_ssim_impl(d_img, d_target, n_images, height, width, d_loss, d_grad, c->loss_scratch.p,
                            c->loss_scratch.bytes, st);
+}
+
+vrs_status vrs_net_forward(vrs_ctx* c, const float* d_params, const float* d_x, int n, int H, int W, float* d_y,
+                           uint16_t* d_acts, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!d_params || !d_x || !d_y || n <= 0 || H <= 0 || W <= 0) return fail(c, VRS_ERR_INVALID, "bad net arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  vrs_status s = VRS_OK;
+  uint16_t *t1 = nullptr, *t2 = nullptr;
+  if (!d_acts) {
+    if (!ensure(c, c->net_tmp, sizeof(uint16_t) * 64 * (size_t)n * H * W, capturing(st), &s)) return s;
+    t1 = P<uint16_t>(c->net_tmp);
+    t2 = t1 + (size_t)32 * n * H * W;
+  }
+  net_forward_train(d_params, d_x, n, H, W, d_y, d_acts, t1, t2, st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "net forward");
+}
+
+vrs_status vrs_net_backward(vrs_ctx* c, const float* d_params, const float* d_x, const uint16_t* d_acts,
+                            const float* d_dy, int n, int H, int W, float* d_dparams, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!d_params || !d_x || !d_acts || !d_dy || !d_dparams || n <= 0 || H <= 0 || W <= 0)
+    return fail(c, VRS_ERR_INVALID, "bad net arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  vrs_status s = VRS_OK;
+  if (!ensure(c, c->net_tmp, sizeof(float) * 64 * (size_t)n * H * W, capturing(st), &s)) return s;
+  float* dz2 = P<float>(c->net_tmp);
+  float* dz1 = dz2 + (size_t)32 * n * H * W;
+  net_backward_train(d_params, d_x, d_acts, d_dy, n, H, W, d_dparams, dz2, dz1, st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "net backward");
+}
+
+vrs_status vrs_net_periphery(vrs_ctx* c, const float* d_params, const float* d_low, float* d_out, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!d_params || !d_low || !d_out) return fail(c, VRS_ERR_INVALID, "null net argument");
+  const Saved& sv = c->saved;
+  if (sv.n_views <= 0 || sv.fovea_mode == 0 || sv.key_tile != 32)
+    return fail(c, VRS_ERR_INVALID, "vrs_net_periphery follows a foveated vrs_render");
+  net_periphery(d_params, d_low, d_out, P<uint8_t>(c->tile_class), P<ViewParams>(c->views), sv.n_views,
+                sv.tiles_per_view, sv.W, sv.H, (cudaStream_t)stream);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "net periphery");
+}
+
+vrs_status vrs_mse(vrs_ctx* c, const float* d_y, const float* d_t, int64_t n, float* d_loss, float* d_dy, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!d_y || !d_t || !d_loss || n <= 0) return fail(c, VRS_ERR_INVALID, "bad mse arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  vrs_status s = VRS_OK;
+  if (!ensure(c, c->misc, 64, capturing(st), &s)) return s;
+  net_mse(d_y, d_t, n, d_loss, d_dy, reinterpret_cast<double*>(P<char>(c->misc) + 16), st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "mse");
 }
 
 vrs_status vrs_profile_begin(vrs_ctx* c, int max_calls) {

@@ -310,6 +310,75 @@ def run_finetune(args, api, torch, ws, rank):
     R.close()
 
 
+def run_net(args, api, torch, ws, rank):
+    """Learned periphery: 1M Gaussians (room shell, SH degree 3), stereo 2064x2208,
+    periphery at 1/4 of the pixels.  The network is trained on the GPU (library kernels)
+    on 2000 seeded pose pairs (256x256 crops of random head poses: half-resolution
+    foveated render -> plain full-resolution render) and evaluated on 200 held-out stereo
+    frames against the plain render, next to its bilinear fallback; then frames/s of the
+    foveated + network frame."""
+    from paper_2505_10144_gb300 import periphery, synth
+    R = api.Renderer()
+    scene = api.DeviceScene.from_host(synth.shell_scene(1_000_000, synth.rng_for(4), sh_degree=3))
+    t0 = time.perf_counter()
+    xs, ts = periphery.make_pairs(R, scene, 2000, np.random.default_rng(synth.BASE_SEED + 4), crop=256)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    net = periphery.PeripheryNet(R, seed=4, zero_last=True)
+    t0 = time.perf_counter()
+    losses = periphery.train(net, xs, ts, steps=2000, batch=8, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del xs, ts
+    frames = synth.vr_trajectory(200, synth.rng_for(4, salt=200)).frames
+    ev = periphery.evaluate_frames(R, net, scene, frames[:: max(1, 200 // max(args.steps, 1))] if args.steps < 200 else frames)
+    # frame timing: foveated render + network on the periphery tiles, vs plain
+    net_cfg = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=32, fovea_mode="net")
+    plain_cfg = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=16, fovea_mode="plain")
+    out = torch.empty((2, 3, H_IMG, W_IMG), device="cuda")
+    low = torch.empty((2, 3, H_IMG // 2, W_IMG // 2), device="cuda")
+
+    def timed(fn, n):
+        for i in range(3):
+            fn(i)
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(i)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    def fnet(i):
+        fr = frames[i % len(frames)]
+        R.render([scene], [0, 0], fr.cameras, fr.foveas, net_cfg, out=out, low=low)
+        net.apply_periphery(low, out)
+
+    def fplain(i):
+        fr = frames[i % len(frames)]
+        R.render([scene], [0, 0], fr.cameras, None, plain_cfg, out=out)
+
+    n = max(args.steps // 4, 10)
+    ms_net, ms_plain = timed(fnet, n), timed(fplain, n)
+    R.check()
+    line = {"metric": "stereo frames/s with the learned periphery (1M Gaussians, 2x2064x2208) and its PSNR vs plain",
+            "value": len(ms_net) / (sum(ms_net) / 1e3), "unit": "frames/s", "n_gpus": ws, "steps": len(ms_net),
+            "warmup": 3, "ms_per_step": statistics.mean(ms_net), "p99_ms": float(np.percentile(ms_net, 99)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32 render",
+            "data": "synthetic", "config": {"workload": "learned_periphery_1M_stereo", "train_pairs": 2000,
+                                            "train_steps": 2000, "eval_frames": len(frames)},
+            "plain": {"value": len(ms_plain) / (sum(ms_plain) / 1e3), "ms_per_step": statistics.mean(ms_plain),
+                      "p99_ms": float(np.percentile(ms_plain, 99))},
+            "quality_vs_plain": ev, "train_loss_first": float(losses[:50].mean()),
+            "train_loss_last": float(losses[-50:].mean()), "pairs_s": t_pairs, "train_s": t_train}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    R.close()
+
+
 def approximation_error(R, api, ds, frame, cfg_hier, torch):
     """Error of the hierarchical per-ray windows against the exact per-ray order on one
     foveated stereo frame (both on the GPU; the exact order is the parity-checked mode)."""
@@ -340,7 +409,7 @@ def main():
                     help="only render warmup + steps foveated frames (for profiler captures)")
     ap.add_argument("--scale", type=float, default=1.0, help="resolution scale of --ncu-case")
     ap.add_argument("--mode", default="hier", choices=["exact", "window", "hier"], help="sort mode of --ncu-case")
-    ap.add_argument("--workload", default="vr", choices=["vr", "batched", "finetune"],
+    ap.add_argument("--workload", default="vr", choices=["vr", "batched", "finetune", "net"],
                     help="vr: the headline stereo frame; batched: 3 scenes x 8 poses x 2 eyes in one graph "
                          "replay; finetune: 4 views at 1280^2, render + loss + backward + Adam")
     ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache for --workload batched")
@@ -367,6 +436,9 @@ def main():
         return
     if args.workload == "finetune":
         run_finetune(args, api, torch, ws, rank)
+        return
+    if args.workload == "net":
+        run_net(args, api, torch, ws, rank)
         return
     n_frames = args.warmup + args.steps
     scene, wl = make_workload(n_frames, rank)

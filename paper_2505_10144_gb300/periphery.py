@@ -104,12 +104,15 @@ ALL_PERIPHERY = synth.Fovea(-1e6, -1e6, 1.0, 1.0)
 
 
 def make_pairs(renderer: api.Renderer, scene: api.DeviceScene, n_pairs: int, rng, crop: int = 256,
-               width: int = 2064, height: int = 2208, windows=(4, 8, 16)):
-    """-> (x, target) float32 CUDA tensors [n_pairs, 3, crop, crop]."""
+               width: int = 2064, height: int = 2208, windows=(4, 8, 16), sort_mode: str = "exact"):
+    """-> (x, target) float32 CUDA tensors [n_pairs, 3, crop, crop].  Training pairs use
+    the exact per-ray order by default, so that the target differs from the input only by
+    what upsampling loses (the hierarchical approximation's order differs between 32x32
+    periphery and 16x16 plain tiles and would add noise the network cannot predict)."""
     xs = torch.empty((n_pairs, 3, crop, crop), device="cuda")
     ts = torch.empty_like(xs)
-    fov_cfg = api.RenderConfig(sort_mode="hier", windows=windows, key_tile=32, fovea_mode="bilinear")
-    plain_cfg = api.RenderConfig(sort_mode="hier", windows=windows, key_tile=16, fovea_mode="plain")
+    fov_cfg = api.RenderConfig(sort_mode=sort_mode, windows=windows, key_tile=32, fovea_mode="bilinear")
+    plain_cfg = api.RenderConfig(sort_mode=sort_mode, windows=windows, key_tile=16, fovea_mode="plain")
     for i in range(n_pairs):
         cam = random_pose_camera(rng, width, height)
         x0 = int(rng.integers(0, (width - crop) // 32 + 1)) * 32
@@ -132,7 +135,8 @@ def train(net: PeripheryNet, xs: torch.Tensor, ts: torch.Tensor, steps: int, bat
         y, acts = net.forward(x)
         loss, dy = net.mse(y, t)
         net.backward(x, acts, dy)
-        net.step(lr * (0.5 * (1 + math.cos(math.pi * s / steps))))
+        warm = min(1.0, (s + 1) / max(1, steps // 10))
+        net.step(lr * warm * (0.5 * (1 + math.cos(math.pi * s / steps))))
         losses.append(loss)
     return torch.cat(losses).cpu().numpy()
 

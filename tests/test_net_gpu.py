@@ -126,14 +126,17 @@ def test_zero_last_layer_is_the_bilinear_fallback(R, vr_frame):
 
 
 def test_training_beats_bilinear_on_held_out_crops(R):
+    """Trained on the GPU by the library's own kernels, the network must reconstruct
+    held-out periphery crops better than its bilinear fallback (the untrained network with
+    a zero last layer is exactly the fallback)."""
     from paper_2505_10144_gb300 import api, periphery
     scene = api.DeviceScene.from_host(synth.shell_scene(100_000, synth.rng_for(4, salt=1), sh_degree=3))
-    xs, ts = periphery.make_pairs(R, scene, 96, np.random.default_rng(10), crop=128)
-    xv, tv = periphery.make_pairs(R, scene, 24, np.random.default_rng(11), crop=128)
+    xs, ts = periphery.make_pairs(R, scene, 128, np.random.default_rng(10), crop=128)
+    xv, tv = periphery.make_pairs(R, scene, 32, np.random.default_rng(11), crop=128)
     net = periphery.PeripheryNet(R, seed=6, zero_last=True)
     before = float(((xv - tv) ** 2).mean())
-    losses = periphery.train(net, xs, ts, steps=300, batch=8, lr=2e-3)
+    losses = periphery.train(net, xs, ts, steps=400, batch=8, lr=1e-3)
     y, _ = net.forward(xv, save=False)
     after = float(((y - tv) ** 2).mean())
-    assert losses[-20:].mean() < losses[:20].mean()
-    assert after < before, (after, before)
+    assert losses[-40:].mean() < losses[:40].mean()
+    assert after < 0.99 * before, (after, before)

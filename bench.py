@@ -321,7 +321,8 @@ def run_net(args, api, torch, ws, rank):
     R = api.Renderer()
     scene = api.DeviceScene.from_host(synth.shell_scene(1_000_000, synth.rng_for(4), sh_degree=3))
     t0 = time.perf_counter()
-    xs, ts = periphery.make_pairs(R, scene, 2000, np.random.default_rng(synth.BASE_SEED + 4), crop=256)
+    xs, ts = periphery.make_pairs(R, scene, 2000, np.random.default_rng(synth.BASE_SEED + 4), crop=256,
+                                  sort_mode="hier")
     torch.cuda.synchronize()
     t_pairs = time.perf_counter() - t0
     net = periphery.PeripheryNet(R, seed=4, zero_last=True)

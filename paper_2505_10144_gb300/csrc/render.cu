@@ -634,6 +634,386 @@ __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Warp-independent render (window and hierarchical modes).  A task is one 8x4-sample
+// region of a work item; every warp takes tasks from the queue on its own, so there is no
+// CTA barrier and a warp stops as soon as its 32 samples are done.  Per batch of 32 list
+// entries the warp compacts the entries whose bounding box meets its region into warp-
+// private shared memory.  The 4x4-block and 2x2-block windows are replicated in the
+// registers of the block's lanes as packed (depth bits << 32 | index) keys and updated
+// by the same branch-free insertion on every lane of the block; the per-sample window is
+// a per-lane ring in shared memory.
+
+constexpr int kRegionWarps = 4;
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+__device__ __forceinline__ unsigned long long pack_key(float t, int g) {
+  return ((unsigned long long)float_order_bits(t) << 32) | (unsigned)g;
+}
+
+template <int K>
+struct RegWin {
+  unsigned long long e[K > 0 ? K : 1];
+};
+
+template <int K>
+__device__ __forceinline__ void regwin_clear(RegWin<K>& w) {
+#pragma unroll
+  for (int i = 0; i < (K > 0 ? K : 1); ++i) w.e[i] = kEmptyKey;
+}
+
+// insert x, then pop the minimum when the window holds more than K; returns the popped
+// key or kEmptyKey (empty slots hold kEmptyKey and sort last)
+template <int K>
+__device__ __forceinline__ unsigned long long regwin_push(RegWin<K>& w, unsigned long long x) {
+  if (K == 0) return x;
+  if (w.e[K - 1] != kEmptyKey) {
+    if (x < w.e[0]) return x;
+    const unsigned long long popped = w.e[0];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      const unsigned long long nxt = (i + 1 < K) ? w.e[(i + 1) % K] : kEmptyKey;
+      const unsigned long long cur = w.e[i];
+      w.e[i] = (nxt < x) ? nxt : ((i == 0 || cur < x) ? x : cur);
+    }
+    return popped;
+  }
+#pragma unroll
+  for (int i = K - 1; i >= 0; --i) {
+    const unsigned long long cur = w.e[i];
+    const unsigned long long prv = i > 0 ? w.e[i > 0 ? i - 1 : 0] : 0ull;
+    w.e[i] = (cur < x) ? cur : ((i == 0 || prv < x) ? x : prv);
+  }
+  return kEmptyKey;
+}
+
+template <int K>
+__device__ __forceinline__ unsigned long long regwin_pop(RegWin<K>& w) {
+  if (K == 0) return kEmptyKey;
+  const unsigned long long m = w.e[0];
+#pragma unroll
+  for (int i = 0; i + 1 < K; ++i) w.e[i] = w.e[i + 1];
+  w.e[K - 1] = kEmptyKey;
+  return m;
+}
+
+__host__ __device__ inline size_t warp_smem_bytes(int k3) { return 3200 + (size_t)k3 * 32 * 12; }
+
+// per-lane ring of the per-sample window: packed keys and alphas, [slot][lane]
+template <bool STATS, bool BWD>
+__device__ __forceinline__ void ring3_push(Px& p, unsigned long long* kk, float* aa, int K3, int lane,
+                                           unsigned long long x, float alpha, const float4* __restrict__ recv) {
+  if (p.n3 == K3) {
+    const unsigned long long m = kk[p.h3 * 32 + lane];
+    if (x < m) {
+      blend<STATS, BWD>(p, alpha, (int)(x & 0xffffffffu), recv);
+      return;
+    }
+    const float am = aa[p.h3 * 32 + lane];
+    p.h3 = p.h3 + 1 == K3 ? 0 : p.h3 + 1;
+    p.n3--;
+    int j = p.n3;
+    while (j > 0) {
+      int q = p.h3 + j - 1;
+      if (q >= K3) q -= K3;
+      const unsigned long long v = kk[q * 32 + lane];
+      if (!(x < v)) break;
+      int d = q + 1;
+      if (d >= K3) d -= K3;
+      kk[d * 32 + lane] = v;
+      aa[d * 32 + lane] = aa[q * 32 + lane];
+      --j;
+    }
+    int d = p.h3 + j;
+    if (d >= K3) d -= K3;
+    kk[d * 32 + lane] = x;
+    aa[d * 32 + lane] = alpha;
+    p.n3++;
+    blend<STATS, BWD>(p, am, (int)(m & 0xffffffffu), recv);
+    return;
+  }
+  int j = p.n3;
+  while (j > 0) {
+    int q = p.h3 + j - 1;
+    if (q >= K3) q -= K3;
+    const unsigned long long v = kk[q * 32 + lane];
+    if (!(x < v)) break;
+    int d = q + 1;
+    if (d >= K3) d -= K3;
+    kk[d * 32 + lane] = v;
+    aa[d * 32 + lane] = aa[q * 32 + lane];
+    --j;
+  }
+  int d = p.h3 + j;
+  if (d >= K3) d -= K3;
+  kk[d * 32 + lane] = x;
+  aa[d * 32 + lane] = alpha;
+  p.n3++;
+}
+
+template <int K1, int K2, bool BWD, bool STATS>
+__global__ void __launch_bounds__(kRegionWarps * 32) warp_render_kernel(RenderArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int K3 = a.k3;
+  unsigned char* ws = smem_raw + (size_t)wib * warp_smem_bytes(K3);
+  float4* st_rec = reinterpret_cast<float4*>(ws);
+  int* st_gid = reinterpret_cast<int*>(ws + 3072);
+  unsigned long long* k3s = reinterpret_cast<unsigned long long*>(ws + 3200);
+  float* a3s = reinterpret_cast<float*>(ws + 3200 + (size_t)K3 * 256);
+  const int sx = (lane & 1) | ((lane >> 1) & 2) | ((lane >> 2) & 4);
+  const int sy = ((lane >> 1) & 1) | ((lane >> 2) & 2);
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned n_eval = 0, n_kept = 0, n_blend = 0;
+  const unsigned n_tasks = 8u * *a.n_items;
+  for (;;) {
+    unsigned task = 0;
+    if (lane == 0) task = atomicAdd(a.queue, 1u);
+    task = __shfl_sync(kFull, task, 0);
+    if (task >= n_tasks) break;
+    const ItemGeom g = decode(a.items[task >> 3], a.tiles_per_view, a.key_tile, a.views);
+    const int region = task & 7, rx = 8 * (region & 1), ry = 4 * (region >> 1);
+    const ViewParams& vp = a.views[g.view];
+    const float4* recv = a.rec + vp.base * kRecF4;
+    const int X = g.ox + rx + sx, Y = g.oy + ry + sy;
+    Px p;
+    bool valid;
+    float rx0, rx1, ry0, ry1;  // sample-position bounds of the region (culling)
+    if (g.kind == kKindLow) {
+      valid = 2 * X < vp.W && 2 * Y < vp.H;
+      p.px = 2.f * X + 1.f;
+      p.py = 2.f * Y + 1.f;
+      rx0 = 2.f * (g.ox + rx) + 1.f;
+      rx1 = rx0 + 14.f;
+      ry0 = 2.f * (g.oy + ry) + 1.f;
+      ry1 = ry0 + 6.f;
+    } else {
+      valid = X < vp.W && Y < vp.H;
+      p.px = X + 0.5f;
+      p.py = Y + 0.5f;
+      rx0 = g.ox + rx + 0.5f;
+      rx1 = rx0 + 7.f;
+      ry0 = g.oy + ry + 0.5f;
+      ry1 = ry0 + 3.f;
+    }
+    if (!__any_sync(kFull, valid)) continue;
+    p.T = 1.f;
+    p.C0 = p.C1 = p.C2 = 0.f;
+    p.active = valid;
+    p.h3 = p.n3 = 0;
+    p.n_eval = p.n_kept = p.n_blend = 0;
+    if (BWD) {
+      const long long HWb = (long long)vp.H * vp.W;
+      const long long HW2b = (long long)(vp.H / 2) * (vp.W / 2);
+      float4 dv = make_float4(0.f, 0.f, 0.f, 0.f), sv = make_float4(0.f, 0.f, 0.f, 1.f);
+      if (valid) {
+        const long long si = g.kind == kKindLow ? (long long)g.view * HW2b + (long long)Y * (vp.W / 2) + X
+                                                : (long long)g.view * HWb + (long long)Y * vp.W + X;
+        dv = g.kind == kKindLow ? reinterpret_cast<const float4*>(a.dL_dlow)[si]
+                                : reinterpret_cast<const float4*>(a.dL_dout)[si];
+        sv = g.kind == kKindLow ? a.s_low[si] : a.s_full[si];
+      }
+      p.G0 = dv.x;
+      p.G1 = dv.y;
+      p.G2 = dv.z;
+      p.GT = dv.x * a.bg[0] + dv.y * a.bg[1] + dv.z * a.bg[2];
+      p.F0 = sv.x;
+      p.F1 = sv.y;
+      p.F2 = sv.z;
+      p.TF = sv.w;
+      p.grad = a.grad_rec + vp.base * 16;
+    }
+    const int bx4 = g.ox + rx + (sx & ~3), by4 = g.oy + ry, bx2 = g.ox + rx + (sx & ~1), by2 = g.oy + ry + (sy & ~1);
+    float c4x, c4y, c2x, c2y;
+    if (g.kind == kKindLow) {
+      c4x = 2.f * bx4 + 4.f;
+      c4y = 2.f * by4 + 4.f;
+      c2x = 2.f * bx2 + 2.f;
+      c2y = 2.f * by2 + 2.f;
+    } else {
+      c4x = bx4 + 2.f;
+      c4y = by4 + 2.f;
+      c2x = bx2 + 1.f;
+      c2y = by2 + 1.f;
+    }
+    RegWin<K1> w1;
+    RegWin<K2> w2;
+    regwin_clear(w1);
+    regwin_clear(w2);
+    auto pop2 = [&](unsigned long long x2) {
+      if (x2 != kEmptyKey && p.active) {
+        const int g2 = (int)(x2 & 0xffffffffu);
+        float al, t;
+        if (eval_full<STATS>(recv + (long long)g2 * kRecF4, p, al, t))
+          ring3_push<STATS, BWD>(p, k3s, a3s, K3, lane, pack_key(t, g2), al, recv);
+      }
+    };
+    auto pop1 = [&](unsigned long long x1) {  // all lanes
+      const bool has = x1 != kEmptyKey;
+      const int g1 = has ? (int)(x1 & 0xffffffffu) : 0;
+      const float4* r = recv + (long long)g1 * kRecF4;
+      bool k = false;
+      if (has && p.active) {
+        float dx, dy, qw;
+        if (STATS) ++p.n_eval;
+        k = pair_test(r[0], r[1], r[2], r[3].x, p.px, p.py, dx, dy, qw);
+      }
+      const unsigned bal = __ballot_sync(kFull, k);
+      unsigned long long x2 = kEmptyKey;
+      if ((bal >> (lane & ~3)) & 0xFu) x2 = regwin_push<K2>(w2, pack_key(depth_at(r, c2x, c2y), g1));
+      pop2(x2);
+    };
+    const long long start = a.ranges[2 * (long long)g.tile], end = a.ranges[2 * (long long)g.tile + 1];
+    for (long long b0 = start; b0 < end; b0 += 32) {
+      if (!__any_sync(kFull, p.active)) break;
+      const long long j = b0 + lane;
+      bool rel = false;
+      int gj = 0;
+      if (j < end) {
+        gj = (int)a.vals[j];
+        const float4 bb = a.bbox[vp.base + gj];
+        rel = bb.x <= rx1 && bb.z >= rx0 && bb.y <= ry1 && bb.w >= ry0;
+      }
+      const unsigned m = __ballot_sync(kFull, rel);
+      __syncwarp();
+      if (rel) {
+        const int slot = __popc(m & lt);
+        const float4* src = recv + (long long)gj * kRecF4;
+#pragma unroll
+        for (int q = 0; q < kRecF4; ++q) st_rec[slot * kRecF4 + q] = src[q];
+        st_gid[slot] = gj;
+      }
+      __syncwarp();
+      const int nrel = __popc(m);
+      for (int e = 0; e < nrel; ++e) {
+        const float4* r = st_rec + e * kRecF4;
+        const int ge = st_gid[e];
+        if (K1 == 0 && K2 == 0) {
+          float al, t;
+          if (p.active && eval_full<STATS>(r, p, al, t)) ring3_push<STATS, BWD>(p, k3s, a3s, K3, lane, pack_key(t, ge), al, recv);
+        } else {
+          bool k = false;
+          if (p.active) {
+            float dx, dy, qw;
+            if (STATS) ++p.n_eval;
+            k = pair_test(r[0], r[1], r[2], r[3].x, p.px, p.py, dx, dy, qw);
+          }
+          const unsigned bal = __ballot_sync(kFull, k);
+          unsigned long long x1 = kEmptyKey;
+          if ((bal >> (lane & 16)) & 0xFFFFu) x1 = regwin_push<K1>(w1, pack_key(depth_at(r, c4x, c4y), ge));
+          if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1);
+        }
+      }
+    }
+    if (K1 > 0 || K2 > 0) {
+      for (int it = 0; it < K1; ++it) {
+        const unsigned long long x1 = regwin_pop<K1>(w1);
+        if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1);
+      }
+      for (int it = 0; it < K2; ++it) pop2(regwin_pop<K2>(w2));
+    }
+    while (p.n3 > 0) {
+      const unsigned long long m = k3s[p.h3 * 32 + lane];
+      const float am = a3s[p.h3 * 32 + lane];
+      p.h3 = p.h3 + 1 == K3 ? 0 : p.h3 + 1;
+      p.n3--;
+      blend<STATS, BWD>(p, am, (int)(m & 0xffffffffu), recv);
+    }
+    if (STATS) {
+      n_eval += p.n_eval;
+      n_kept += p.n_kept;
+      n_blend += p.n_blend;
+    }
+    if (BWD) continue;
+    // ---- outputs (same as the block kernel)
+    const float v0 = fmaf(p.T, a.bg[0], p.C0), v1 = fmaf(p.T, a.bg[1], p.C1), v2 = fmaf(p.T, a.bg[2], p.C2);
+    const long long HW = (long long)vp.H * vp.W;
+    const int W2 = vp.W / 2, H2 = vp.H / 2;
+    const long long HW2 = (long long)H2 * W2;
+    if (g.kind == kKindFull) {
+      float s0 = v0 + __shfl_xor_sync(kFull, v0, 1), s1 = v1 + __shfl_xor_sync(kFull, v1, 1),
+            s2 = v2 + __shfl_xor_sync(kFull, v2, 1);
+      s0 += __shfl_xor_sync(kFull, s0, 2);
+      s1 += __shfl_xor_sync(kFull, s1, 2);
+      s2 += __shfl_xor_sync(kFull, s2, 2);
+      const float a0 = 0.25f * s0, a1 = 0.25f * s1, a2 = 0.25f * s2;
+      if (valid) {
+        float o0 = v0, o1 = v1, o2 = v2;
+        if (a.fovea_mode != 0 && a.tile_class[g.tile] == kClassHybrid) {
+          const float dx = p.px - vp.gaze_x, dy = p.py - vp.gaze_y;
+          const float w = fminf(fmaxf((vp.radius + vp.band - sqrtf(dx * dx + dy * dy)) / vp.band, 0.f), 1.f);
+          o0 = w * v0 + (1.f - w) * a0;
+          o1 = w * v1 + (1.f - w) * a1;
+          o2 = w * v2 + (1.f - w) * a2;
+        }
+        float* out = a.out + (long long)g.view * 3 * HW + (long long)Y * vp.W + X;
+        out[0] = o0;
+        out[HW] = o1;
+        out[2 * HW] = o2;
+        if (a.s_full) a.s_full[(long long)g.view * HW + (long long)Y * vp.W + X] = make_float4(p.C0, p.C1, p.C2, p.T);
+        if (a.low && (lane & 3) == 0 && X / 2 < W2 && Y / 2 < H2) {
+          float* lo = a.low + (long long)g.view * 3 * HW2 + (long long)(Y / 2) * W2 + X / 2;
+          lo[0] = a0;
+          lo[HW2] = a1;
+          lo[2 * HW2] = a2;
+        }
+      }
+    } else if (valid) {
+      float* lo = a.low + (long long)g.view * 3 * HW2 + (long long)Y * W2 + X;
+      lo[0] = v0;
+      lo[HW2] = v1;
+      lo[2 * HW2] = v2;
+      if (a.s_low) a.s_low[(long long)g.view * HW2 + (long long)Y * W2 + X] = make_float4(p.C0, p.C1, p.C2, p.T);
+    }
+  }
+  if (STATS) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n_eval += __shfl_xor_sync(kFull, n_eval, o);
+      n_kept += __shfl_xor_sync(kFull, n_kept, o);
+      n_blend += __shfl_xor_sync(kFull, n_blend, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&a.stats[0], (unsigned long long)n_eval);
+      atomicAdd(&a.stats[1], (unsigned long long)n_kept);
+      atomicAdd(&a.stats[2], (unsigned long long)n_blend);
+    }
+  }
+}
+
+template <int K1, int K2, bool BWD, bool STATS>
+void launch_warp_t(const RenderArgs& a, cudaStream_t st) {
+  const size_t smem = warp_smem_bytes(a.k3) * kRegionWarps;
+  static size_t set_smem = 0;
+  static int per_sm_cached[kMaxWin + 1] = {0};
+  if (smem > set_smem) {
+    cudaFuncSetAttribute(warp_render_kernel<K1, K2, BWD, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_smem = smem;
+  }
+  int per_sm = per_sm_cached[a.k3];
+  if (per_sm <= 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_render_kernel<K1, K2, BWD, STATS>,
+                                                  kRegionWarps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    per_sm_cached[a.k3] = per_sm;
+  }
+  if (a.max_ctas_per_sm > 0) per_sm = std::min(per_sm, a.max_ctas_per_sm * (kBlock / (kRegionWarps * 32)));
+  warp_render_kernel<K1, K2, BWD, STATS><<<(unsigned)(device_sm_count() * per_sm), kRegionWarps * 32, smem, st>>>(a);
+}
+
+// fast path for the common window shapes; returns false when (k1, k2) is not compiled
+template <bool BWD, bool STATS>
+bool launch_warp(const RenderArgs& a, cudaStream_t st) {
+  const int k1 = a.sort_mode == 2 ? a.k1 : 0, k2 = a.sort_mode == 2 ? a.k2 : 0;
+  if (a.sort_mode == 0) return false;
+  if (k1 == 0 && k2 == 0) launch_warp_t<0, 0, BWD, STATS>(a, st);
+  else if (k1 == 4 && k2 == 8) launch_warp_t<4, 8, BWD, STATS>(a, st);
+  else if (k1 == 8 && k2 == 16) launch_warp_t<8, 16, BWD, STATS>(a, st);
+  else if (k1 == 1 && k2 == 1) launch_warp_t<1, 1, BWD, STATS>(a, st);
+  else return false;
+  return true;
+}
+
 // bilinear x2 upsampling of the half-resolution image into periphery tiles
 __global__ void composite_kernel(const ViewParams* __restrict__ views, int n_views, const uint8_t* __restrict__ tile_class,
                                  int tiles_per_view, int T, const float* __restrict__ low, float* __restrict__ out, int W,
@@ -701,6 +1081,7 @@ void launch_workitems(const ViewParams* d_views, int n_views, int fovea_mode, in
 
 void launch_render(const RenderArgs& a, long long max_items, cudaStream_t st) {
   const bool stats = a.stats != nullptr;
+  if (stats ? launch_warp<false, true>(a, st) : launch_warp<false, false>(a, st)) return;
   switch (a.sort_mode * 2 + (stats ? 1 : 0)) {
     case 0: launch_render_t<0, false, false>(a, max_items, st); break;
     case 1: launch_render_t<0, true, false>(a, max_items, st); break;
@@ -713,6 +1094,7 @@ void launch_render(const RenderArgs& a, long long max_items, cudaStream_t st) {
 
 // replays the forward's per-ray decisions and emits record gradients at every blend
 void launch_render_backward(const RenderArgs& a, long long max_items, cudaStream_t st) {
+  if (launch_warp<true, false>(a, st)) return;
   switch (a.sort_mode) {
     case 0: launch_render_t<0, false, true>(a, max_items, st); break;
     case 1: launch_render_t<1, false, true>(a, max_items, st); break;

@@ -164,8 +164,14 @@ vrs_status vrs_copy_instances(vrs_ctx* ctx, uint64_t* d_keys, uint32_t* d_vals, 
                               int64_t cap, int64_t* n, void* stream);
 
 /* Per-Gaussian Optimal-Projection records of one view (Sec. 4.2) for inspection:
- * d_out[N][24] float (layout documented in the design doc: projected-mean pixel, plane map,
- * conic, log2 opacity, depth form, rgb), d_bbox[N][4] float (xmin, ymin, xmax, ymax;
+ * d_out[N][24] float, six groups of four relative to the projected mean pm (pixels):
+ * (pm.x, pm.y, H00, H01), (H10, H11, H20, H21), (H22, a00, 2 a01, a11),
+ * (log2 opacity, n0, n1, n2), (m00, 2 m01, m11, 2 m02), (2 m12, r, g, b), where
+ * H = [E; u] K^-1 maps a pixel offset d from pm (homogeneous (d, 1)) to the tangent
+ * plane (s1, s2, w) with plane point s / w, a = 0.5 log2(e) A is the scaled conic,
+ * n and m the linear and quadratic forms of t* (numerator n.(d,1), denominator
+ * (d,1)^T M (d,1)), normalised so that t* at pm is the view depth of the mean;
+ * d_bbox[N][4] float (xmin, ymin, xmax, ymax;
  * all zero when culled), d_count[N] uint32 tiles kept after Eq. 4 culling with
  * key_tile-sized tiles. */
 vrs_status vrs_project(vrs_ctx* ctx, const vrs_gaussians* scene, const vrs_camera* h_cam, int key_tile,

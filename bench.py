@@ -393,6 +393,36 @@ def approximation_error(R, api, ds, frame, cfg_hier, torch):
             "pixels_over_2e-4_pct": float((d.amax(dim=1) > 2e-4).float().mean() * 100)}
 
 
+RENDER_SOURCES = ["paper_2505_10144_gb300/csrc/render.cu", "paper_2505_10144_gb300/csrc/common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "render_traffic_vr_stereo_500k.txt")
+
+
+def render_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in RENDER_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the render kernel from the committed ncu summary, or None
+    when the kernel's source changed since that capture (or there is none)."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != render_source_hash():
+            return None, "render source changed since the ncu capture"
+        return float(kv["dram_bytes_per_launch"]), kv.get("capture", "")
+    except (OSError, KeyError, ValueError):
+        return None, "no ncu traffic summary"
+
+
 def psnr(a, b):
     mse = float(((a - b) ** 2).mean())
     return float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
@@ -459,7 +489,7 @@ def main():
         if pg:
             pg.barrier()
 
-    def timed(cfg, steps, profile=False):
+    def timed_eager(cfg, steps, profile=False):
         for i in range(args.warmup):
             frame(i, cfg)
         R.check()
@@ -478,7 +508,36 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms, stages, ncalls
 
-    # foveated frames (the headline)
+    def graphed(cfg):
+        """A frame as one CUDA-graph replay (own context), its instance workspace sized
+        by the largest count over the camera path (an untimed eager pass)."""
+        Rg = api.Renderer()
+        most = 0
+        for fr in wl.frames:
+            Rg.render([ds], [0, 0], fr.cameras, fr.foveas, cfg, out=out)
+            most = max(most, Rg.stats()["instances"])
+        fr0 = wl.frames[0]
+        G = api.GraphedRender(Rg, [ds], [0, 0], fr0.cameras, fr0.foveas, cfg, instances=int(most * 1.02) + 4096)
+        return Rg, G
+
+    def timed_graph(G, Rg, steps):
+        for i in range(args.warmup):
+            fr = wl.frames[i % len(wl.frames)]
+            G.replay(fr.cameras, fr.foveas)
+        Rg.check()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            fr = wl.frames[(args.warmup + i) % len(wl.frames)]
+            flush.zero_()
+            ev[i][0].record()
+            G.replay(fr.cameras, fr.foveas)
+            ev[i][1].record()
+        barrier()
+        Rg.check()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    # foveated frames (the headline): one graph replay per stereo frame
     gpu_index = local
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -486,19 +545,25 @@ def main():
             gpu_index = int(vis.split(",")[local])
         except ValueError:
             pass
+    Rg, G = graphed(fov_cfg)
+    kernels_per_frame = Rg.stats()["kernels"]
     with ClockSampler(gpu_index) as clk:
         t_wall = time.perf_counter()
-        ms_fov, stages, ncalls = timed(fov_cfg, args.steps, profile=True)
+        ms_fov = timed_graph(G, Rg, args.steps)
         t_wall = time.perf_counter() - t_wall
-    kernels_per_frame = R.stats()["kernels"]
     total_ms = sum(ms_fov)
     if pg:
         t = torch.tensor([total_ms], device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         total_ms = float(t.item())
     value = ws * args.steps / (total_ms / 1e3)
-    # plain full-resolution render on the same GPU
-    ms_plain, _, _ = timed(plain_cfg, min(args.plain_steps, args.steps))
+    # the same frames issued eagerly (one vrs_render call each), with per-stage events
+    ms_eager, stages, ncalls = timed_eager(fov_cfg, min(args.plain_steps, args.steps), profile=True)
+    # plain full-resolution render on the same GPU, also one graph replay per frame
+    Rp, Gp = graphed(plain_cfg)
+    ms_plain = timed_graph(Gp, Rp, min(args.plain_steps, args.steps))
+    del Gp
+    Rp.close()
     # quality of the foveated frame against the plain render
     ps = []
     o2 = torch.empty_like(out)
@@ -524,27 +589,31 @@ def main():
     sm_mhz = clocks["sm_mhz"] or 2070.0
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / (render_ms / 1e3) / 1e12 if render_ms > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": "render_kernel<hier>", "achieved": achieved, "peak": peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tflops if peak_tflops else None, "traffic": None,
+    traffic, traffic_note = profiled_traffic()
+    roofline = {"bound": "alu", "kernel": "warp_render_kernel<4,8> (hierarchical 4/8/16)", "achieved": achieved,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops if peak_tflops else None,
+                "traffic": traffic, "traffic_note": traffic_note,
                 "peak_source": f"FP32 FMA peak: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                f"{sm_mhz:.0f} MHz (median SM clock under load)",
                 "work_per_launch": {"evaluated_pairs": cnt["evaluated"], "kept_pairs": cnt["kept"],
                                     "blended_pairs": cnt["blended"], "flops": flops},
                 "avg_launch_ms": render_ms}
-    # end to end through the public API: camera/gaze in, both images back to pinned host
+    # end to end through the public API: camera/gaze in (pinned staging -> device inside
+    # the replay), both images back to pinned host memory every frame
     host = torch.empty((2, 3, H_IMG, W_IMG), dtype=torch.float32, pin_memory=True)
     for i in range(args.warmup):
-        frame(i, fov_cfg)
-        host.copy_(out, non_blocking=True)
+        fr = wl.frames[i % len(wl.frames)]
+        host.copy_(G.replay(fr.cameras, fr.foveas), non_blocking=True)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n_e2e = min(40, args.steps)
     e0.record()
     for i in range(n_e2e):
-        frame(args.warmup + i, fov_cfg)
-        host.copy_(out, non_blocking=True)
+        fr = wl.frames[(args.warmup + i) % len(wl.frames)]
+        host.copy_(G.replay(fr.cameras, fr.foveas), non_blocking=True)
     e1.record()
     barrier()
+    Rg.check()
     e2e_fps = ws * n_e2e / (e0.elapsed_time(e1) / 1e3)
     import ctypes
     from paper_2505_10144_gb300 import _lib
@@ -558,19 +627,24 @@ def main():
                    "width": W_IMG, "height": H_IMG, "views": 2, "sh_degree": 3, "windows": list(WINDOWS),
                    "fovea": "circle r=0.15W, band 0.1r, periphery 1/2 res, bilinear",
                    "l2": "flushed between frames (256 MB write outside the timed events)",
-                   "timing": "CUDA events around each frame on the launching stream"},
+                   "timing": "CUDA events around each frame on the launching stream",
+                   "frame": "one CUDA graph replay of the whole stereo frame (vrs_update_views + replay)"},
         "p50_ms": float(np.percentile(ms_fov, 50)), "p99_ms": float(np.percentile(ms_fov, 99)),
         "plain": {"value": len(ms_plain) / (sum(ms_plain) / 1e3), "unit": "frames/s",
                   "ms_per_step": statistics.mean(ms_plain), "p99_ms": float(np.percentile(ms_plain, 99)),
                   "config": "full resolution, 16x16 tiles, hierarchical 4/8/16, same pipeline"},
         "speedup_vs_plain": statistics.mean(ms_plain) / statistics.mean(ms_fov),
+        "eager": {"value": len(ms_eager) / (sum(ms_eager) / 1e3), "unit": "frames/s",
+                  "ms_per_step": statistics.mean(ms_eager), "p99_ms": float(np.percentile(ms_eager, 99)),
+                  "config": "one vrs_render call per frame (host reads the instance count back)"},
         "psnr_vs_plain_db": statistics.mean(ps),
         "hier_vs_exact": approx,
         "stage_ms_per_frame": {k: v / max(ncalls, 1) for k, v in stages.items()},
         "counters_per_frame": cnt,
         "roofline": roofline,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "Renderer.render (vrs_render) + device-to-host copy of both eyes into pinned memory"},
+                "path": "GraphedRender.replay (vrs_update_views + graph replay) + device-to-host copy of both "
+                        "eyes into pinned memory"},
         "gpu_launches": kernels_per_frame * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,

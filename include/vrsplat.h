@@ -152,7 +152,10 @@ vrs_status vrs_check_status(vrs_ctx* ctx, void* stream, int64_t* required_instan
 
 /* Counters of the last render (host int64[8]): 0 instances, 1 work items, 2 evaluated
  * pairs, 3 kept pairs, 4 blended pairs, 5 views, 6 sort passes, 7 kernels launched.
- * Counters 2-4 are filled only when opts.stats was 1.  Synchronises the stream. */
+ * Counters 2-4 are filled only when opts.stats was 1: evaluated counts each (sample,
+ * Gaussian) pair tested once, kept the pairs that entered the per-sample window with
+ * alpha >= 1/255, blended the pairs composited before the transmittance stop.
+ * Synchronises the stream. */
 vrs_status vrs_get_stats(vrs_ctx* ctx, void* stream, int64_t* h_out8);
 
 /* Copy the sorted instances of the last render into caller buffers:

@@ -320,7 +320,9 @@ class GraphedRender:
     whose instances exceed it raises VRS_ERR_CAPACITY at the next check()."""
 
     def __init__(self, renderer: Renderer, scenes, view_scene, cams, foveas, cfg: RenderConfig,
-                 headroom: float = 1.3):
+                 headroom: float = 1.3, instances: int | None = None):
+        """instances: instance capacity to reserve (e.g. the largest count over a known
+        camera path); default: the count of this first render x headroom."""
         self.R, self.scenes, self.view_scene, self.cfg = renderer, scenes, list(view_scene), cfg
         n_views = len(cams)
         W, H = int(cams[0].width), int(cams[0].height)
@@ -329,7 +331,8 @@ class GraphedRender:
         renderer.check()
         need = renderer.stats()["instances"]
         total = sum(scenes[v].n for v in self.view_scene)
-        renderer.reserve(n_views, W, H, total, int(need * headroom) + (1 << 16))
+        cap = int(instances) if instances is not None else int(need * headroom) + (1 << 16)
+        renderer.reserve(n_views, W, H, total, max(cap, need))
         renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out)
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()

@@ -295,16 +295,32 @@ __device__ __forceinline__ float depth_at(const float4* r, float x, float y) {
   return pair_depth(f3, f4, m12x2, x - f0.x, y - f0.y);
 }
 
-// full evaluation of a record at the thread's sample: kept, alpha, depth
-template <bool STATS>
+// full evaluation of a record at the thread's sample: kept, alpha, depth.  COUNT_EVAL is
+// false where the pair was already counted when it entered the cascade.
+template <bool STATS, bool COUNT_EVAL = true>
 __device__ __forceinline__ bool eval_full(const float4* r, Px& p, float& alpha, float& t) {
   const float4 f0 = r[0], f1 = r[1], f2 = r[2], f3 = r[3];
   float dx, dy, qw;
-  if (STATS) ++p.n_eval;
+  if (STATS && COUNT_EVAL) ++p.n_eval;
   if (!pair_test(f0, f1, f2, f3.x, p.px, p.py, dx, dy, qw)) return false;
   if (STATS) ++p.n_kept;
   alpha = pair_alpha(f3.x, qw);
   t = pair_depth(f3, r[4], r[5].x, dx, dy);
+  return true;
+}
+
+// the same, also returning the pair's colour
+template <bool STATS, bool COUNT_EVAL = true>
+__device__ __forceinline__ bool eval_full(const float4* r, Px& p, float& alpha, float& t, float3& c) {
+  const float4 f0 = r[0], f1 = r[1], f2 = r[2], f3 = r[3];
+  float dx, dy, qw;
+  if (STATS && COUNT_EVAL) ++p.n_eval;
+  if (!pair_test(f0, f1, f2, f3.x, p.px, p.py, dx, dy, qw)) return false;
+  if (STATS) ++p.n_kept;
+  const float4 f5 = r[5];
+  alpha = pair_alpha(f3.x, qw);
+  t = pair_depth(f3, r[4], f5.x, dx, dy);
+  c = make_float3(f5.y, f5.z, f5.w);
   return true;
 }
 
@@ -461,7 +477,8 @@ __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
     auto pop2 = [&](int g2) {
       if (g2 >= 0 && p.active) {
         float al, t;
-        if (eval_full<STATS>(recv + (long long)g2 * kRecF4, p, al, t)) l3_push<STATS, BWD>(p, s, K3, t, g2, al, recv);
+        if (eval_full<STATS, false>(recv + (long long)g2 * kRecF4, p, al, t))
+          l3_push<STATS, BWD>(p, s, K3, t, g2, al, recv);
       }
     };
     // popped from a 4x4 window: 2x2-block membership, 2x2 window
@@ -470,7 +487,6 @@ __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
       const float4* r = recv + (long long)(g1 >= 0 ? g1 : 0) * kRecF4;
       if (g1 >= 0 && p.active) {
         float dx, dy, qw;
-        if (STATS) ++p.n_eval;
         k = pair_test(r[0], r[1], r[2], r[3].x, p.px, p.py, dx, dy, qw);
       }
       const unsigned bal = __ballot_sync(kFull, k);
@@ -651,86 +667,186 @@ __device__ __forceinline__ unsigned long long pack_key(float t, int g) {
   return ((unsigned long long)float_order_bits(t) << 32) | (unsigned)g;
 }
 
-template <int K>
-struct RegWin {
-  unsigned long long e[K > 0 ? K : 1];
+// Block windows distributed over the lanes of their block.  The 4x4-block window (K1
+// <= 16 entries) keeps slot s on lane 16 b + s of block b; the 2x2-block window (K2 <= 16)
+// keeps slot s on lane 4 c + (s & 3) of block c, register s >> 2.  Slots hold packed
+// (depth bits << 32 | index) keys in ascending order, empty slots kEmptyKey.  An
+// insertion counts the slots below the new key with one ballot and moves the others by
+// one slot with shuffles, so its cost does not grow with the window size.  Every lane of
+// the warp takes part in every call (full-mask shuffles); do_push and the key are uniform
+// over the block.
+
+template <int K1>
+struct Win16 {
+  unsigned long long e;  // this lane's slot (lane & 15)
+  unsigned pl;           // payload of the slot (the block's kept-sample mask at entry)
+  int n;                 // entries held by this lane's block
 };
 
-template <int K>
-__device__ __forceinline__ void regwin_clear(RegWin<K>& w) {
-#pragma unroll
-  for (int i = 0; i < (K > 0 ? K : 1); ++i) w.e[i] = kEmptyKey;
+__device__ __forceinline__ unsigned long long shfl64(unsigned long long v, int src, int width) {
+  const unsigned lo = __shfl_sync(kFull, (unsigned)v, src, width);
+  const unsigned hi = __shfl_sync(kFull, (unsigned)(v >> 32), src, width);
+  return ((unsigned long long)hi << 32) | lo;
 }
 
-// insert x, then pop the minimum when the window holds more than K; returns the popped
-// key or kEmptyKey (empty slots hold kEmptyKey and sort last)
-template <int K>
-__device__ __forceinline__ unsigned long long regwin_push(RegWin<K>& w, unsigned long long x) {
-  if (K == 0) return x;
-  if (w.e[K - 1] != kEmptyKey) {
-    if (x < w.e[0]) return x;
-    const unsigned long long popped = w.e[0];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      const unsigned long long nxt = (i + 1 < K) ? w.e[(i + 1) % K] : kEmptyKey;
-      const unsigned long long cur = w.e[i];
-      w.e[i] = (nxt < x) ? nxt : ((i == 0 || cur < x) ? x : cur);
+// insert (x, xpl) when do_push, then pop the minimum when the window holds more than
+// K1; returns the popped key (kEmptyKey if none) and its payload, uniform over the block
+template <int K1>
+__device__ __forceinline__ unsigned long long win16_push(Win16<K1>& w, unsigned long long x, unsigned xpl,
+                                                         bool do_push, int lane, unsigned& popl) {
+  const int slot = lane & 15;
+  const unsigned bal = __ballot_sync(kFull, w.e < x);
+  const int pos = __popc((bal >> (lane & 16)) & 0xFFFFu);
+  const int su = slot - 1 < 0 ? 0 : slot - 1, sd = slot + 1 > 15 ? 15 : slot + 1;
+  const unsigned long long up = shfl64(w.e, su, 16), dn = shfl64(w.e, sd, 16), e0 = shfl64(w.e, 0, 16);
+  const unsigned pup = __shfl_sync(kFull, w.pl, su, 16), pdn = __shfl_sync(kFull, w.pl, sd, 16),
+                 p0 = __shfl_sync(kFull, w.pl, 0, 16);
+  popl = xpl;
+  if (!do_push) return kEmptyKey;
+  if (w.n < K1) {
+    if (slot == pos) {
+      w.e = x;
+      w.pl = xpl;
+    } else if (slot > pos) {
+      w.e = up;
+      w.pl = pup;
     }
-    return popped;
+    ++w.n;
+    return kEmptyKey;
   }
-#pragma unroll
-  for (int i = K - 1; i >= 0; --i) {
-    const unsigned long long cur = w.e[i];
-    const unsigned long long prv = i > 0 ? w.e[i > 0 ? i - 1 : 0] : 0ull;
-    w.e[i] = (cur < x) ? cur : ((i == 0 || prv < x) ? x : prv);
+  if (pos == 0) return x;
+  if (slot < pos - 1) {
+    w.e = dn;
+    w.pl = pdn;
+  } else if (slot == pos - 1) {
+    w.e = x;
+    w.pl = xpl;
   }
-  return kEmptyKey;
+  popl = p0;
+  return e0;
 }
 
-template <int K>
-__device__ __forceinline__ unsigned long long regwin_pop(RegWin<K>& w) {
-  if (K == 0) return kEmptyKey;
-  const unsigned long long m = w.e[0];
+template <int K1>
+__device__ __forceinline__ unsigned long long win16_pop(Win16<K1>& w, int lane, unsigned& popl) {
+  const int slot = lane & 15;
+  const int sd = slot + 1 > 15 ? 15 : slot + 1;
+  const unsigned long long dn = shfl64(w.e, sd, 16), e0 = shfl64(w.e, 0, 16);
+  const unsigned pdn = __shfl_sync(kFull, w.pl, sd, 16);
+  popl = __shfl_sync(kFull, w.pl, 0, 16);
+  if (w.n == 0) return kEmptyKey;
+  w.e = (slot + 1 < w.n) ? dn : kEmptyKey;
+  w.pl = pdn;
+  --w.n;
+  return e0;
+}
+
+template <int K2>
+struct Win4 {
+  static constexpr int R = (K2 + 3) / 4 > 0 ? (K2 + 3) / 4 : 1;
+  unsigned long long f[R];  // slots 4 r + (lane & 3)
+  int n;
+};
+
+template <int K2>
+__device__ __forceinline__ unsigned long long win4_push(Win4<K2>& w, unsigned long long x, bool do_push, int lane) {
+  constexpr int R = Win4<K2>::R;
+  const int j = lane & 3, base = lane & ~3;
+  int pos = 0;
 #pragma unroll
-  for (int i = 0; i + 1 < K; ++i) w.e[i] = w.e[i + 1];
-  w.e[K - 1] = kEmptyKey;
-  return m;
+  for (int r = 0; r < R; ++r) pos += __popc((__ballot_sync(kFull, w.f[r] < x) >> base) & 0xFu);
+  unsigned long long left[R], right[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    left[r] = shfl64(w.f[r], base | ((j + 3) & 3), 32);
+    right[r] = shfl64(w.f[r], base | ((j + 1) & 3), 32);
+  }
+  const unsigned long long e0 = shfl64(w.f[0], base, 32);
+  if (!do_push) return kEmptyKey;
+  if (w.n < K2) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int s = 4 * r + j;
+      const unsigned long long up = j > 0 ? left[r] : (r > 0 ? left[r > 0 ? r - 1 : 0] : kEmptyKey);
+      w.f[r] = s < pos ? w.f[r] : (s == pos ? x : up);
+    }
+    ++w.n;
+    return kEmptyKey;
+  }
+  if (pos == 0) return x;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int s = 4 * r + j;
+    const unsigned long long dn = j < 3 ? right[r] : (r + 1 < R ? right[r + 1 < R ? r + 1 : 0] : kEmptyKey);
+    w.f[r] = s < pos - 1 ? dn : (s == pos - 1 ? x : w.f[r]);
+  }
+  return e0;
+}
+
+template <int K2>
+__device__ __forceinline__ unsigned long long win4_pop(Win4<K2>& w, int lane) {
+  constexpr int R = Win4<K2>::R;
+  const int j = lane & 3, base = lane & ~3;
+  unsigned long long right[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) right[r] = shfl64(w.f[r], base | ((j + 1) & 3), 32);
+  const unsigned long long e0 = shfl64(w.f[0], base, 32);
+  if (w.n == 0) return kEmptyKey;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int s = 4 * r + j;
+    const unsigned long long dn = j < 3 ? right[r] : (r + 1 < R ? right[r + 1 < R ? r + 1 : 0] : kEmptyKey);
+    w.f[r] = s + 1 < w.n ? dn : kEmptyKey;
+  }
+  --w.n;
+  return e0;
 }
 
 __host__ __device__ inline size_t warp_smem_bytes(int k3) { return 3200 + (size_t)k3 * 32 * 12; }
 
-// per-lane ring of the per-sample window: packed keys and alphas, [slot][lane]
+// blend of one pair whose colour c the caller holds; the backward replay reads the rest
+// of the record for the gradient
 template <bool STATS, bool BWD>
-__device__ __forceinline__ void ring3_push(Px& p, unsigned long long* kk, float* aa, int K3, int lane,
-                                           unsigned long long x, float alpha, const float4* __restrict__ recv) {
-  if (p.n3 == K3) {
-    const unsigned long long m = kk[p.h3 * 32 + lane];
+__device__ __forceinline__ void blend_c(Px& p, float alpha, int g, float3 c, const float4* __restrict__ recv) {
+  if (!p.active) return;
+  const float test = p.T * (1.f - alpha);
+  if (test < kTStop) {
+    p.active = false;
+    return;
+  }
+  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16);
+  const float aT = alpha * p.T;
+  p.C0 = fmaf(aT, c.x, p.C0);
+  p.C1 = fmaf(aT, c.y, p.C1);
+  p.C2 = fmaf(aT, c.z, p.C2);
+  p.T = test;
+  if (STATS) ++p.n_blend;
+}
+
+__device__ __forceinline__ float3 rec_colour(const float4* __restrict__ recv, int g) {
+  const float4 f5 = recv[(long long)g * kRecF4 + 5];
+  return make_float3(f5.y, f5.z, f5.w);
+}
+
+// Per-lane ring of the per-sample window: packed keys and alphas, [slot][lane], ascending
+// from the head h3.  hc holds the colour of the head entry: it is loaded when an entry
+// becomes the head, so the load is in flight while the lane works on later entries and
+// the blend of a popped head reads no memory.
+template <bool STATS, bool BWD>
+__device__ __forceinline__ void ring3_push(Px& p, float3& hc, unsigned long long* kk, float* aa, int K3, int lane,
+                                           unsigned long long x, float alpha, float3 c, const float4* __restrict__ recv) {
+  const bool full = p.n3 == K3;
+  unsigned long long m = 0;
+  float am = 0.f;
+  float3 mc = hc;
+  if (full) {
+    m = kk[p.h3 * 32 + lane];
     if (x < m) {
-      blend<STATS, BWD>(p, alpha, (int)(x & 0xffffffffu), recv);
+      blend_c<STATS, BWD>(p, alpha, (int)(x & 0xffffffffu), c, recv);
       return;
     }
-    const float am = aa[p.h3 * 32 + lane];
+    am = aa[p.h3 * 32 + lane];
     p.h3 = p.h3 + 1 == K3 ? 0 : p.h3 + 1;
     p.n3--;
-    int j = p.n3;
-    while (j > 0) {
-      int q = p.h3 + j - 1;
-      if (q >= K3) q -= K3;
-      const unsigned long long v = kk[q * 32 + lane];
-      if (!(x < v)) break;
-      int d = q + 1;
-      if (d >= K3) d -= K3;
-      kk[d * 32 + lane] = v;
-      aa[d * 32 + lane] = aa[q * 32 + lane];
-      --j;
-    }
-    int d = p.h3 + j;
-    if (d >= K3) d -= K3;
-    kk[d * 32 + lane] = x;
-    aa[d * 32 + lane] = alpha;
-    p.n3++;
-    blend<STATS, BWD>(p, am, (int)(m & 0xffffffffu), recv);
-    return;
   }
   int j = p.n3;
   while (j > 0) {
@@ -749,6 +865,22 @@ __device__ __forceinline__ void ring3_push(Px& p, unsigned long long* kk, float*
   kk[d * 32 + lane] = x;
   aa[d * 32 + lane] = alpha;
   p.n3++;
+  if (j == 0) hc = c;                                                        // x is the new head
+  else if (full) hc = rec_colour(recv, (int)(kk[p.h3 * 32 + lane] & 0xffffffffu));  // the next entry is
+  if (full) blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);
+}
+
+// pops the head of the per-sample window and blends it
+template <bool STATS, bool BWD>
+__device__ __forceinline__ void ring3_pop(Px& p, float3& hc, const unsigned long long* kk, const float* aa, int K3,
+                                          int lane, const float4* __restrict__ recv) {
+  const unsigned long long m = kk[p.h3 * 32 + lane];
+  const float am = aa[p.h3 * 32 + lane];
+  const float3 mc = hc;
+  p.h3 = p.h3 + 1 == K3 ? 0 : p.h3 + 1;
+  p.n3--;
+  if (p.n3 > 0) hc = rec_colour(recv, (int)(kk[p.h3 * 32 + lane] & 0xffffffffu));
+  blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);
 }
 
 template <int K1, int K2, bool BWD, bool STATS>
@@ -836,31 +968,35 @@ __global__ void __launch_bounds__(kRegionWarps * 32) warp_render_kernel(RenderAr
       c2x = bx2 + 1.f;
       c2y = by2 + 1.f;
     }
-    RegWin<K1> w1;
-    RegWin<K2> w2;
-    regwin_clear(w1);
-    regwin_clear(w2);
+    Win16<K1> w1;
+    Win4<K2> w2;
+    w1.e = kEmptyKey;
+    w1.pl = 0u;
+    w1.n = 0;
+    float3 hc = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < Win4<K2>::R; ++r) w2.f[r] = kEmptyKey;
+    w2.n = 0;
+    // popped from a 2x2 window: per-sample evaluation, into the per-sample window
     auto pop2 = [&](unsigned long long x2) {
       if (x2 != kEmptyKey && p.active) {
         const int g2 = (int)(x2 & 0xffffffffu);
+        const float4* r = recv + (long long)g2 * kRecF4;
         float al, t;
-        if (eval_full<STATS>(recv + (long long)g2 * kRecF4, p, al, t))
-          ring3_push<STATS, BWD>(p, k3s, a3s, K3, lane, pack_key(t, g2), al, recv);
+        float3 c;
+        if (eval_full<STATS, false>(r, p, al, t, c)) ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, g2), al, c, recv);
       }
     };
-    auto pop1 = [&](unsigned long long x1) {  // all lanes
-      const bool has = x1 != kEmptyKey;
-      const int g1 = has ? (int)(x1 & 0xffffffffu) : 0;
-      const float4* r = recv + (long long)g1 * kRecF4;
-      bool k = false;
-      if (has && p.active) {
-        float dx, dy, qw;
-        if (STATS) ++p.n_eval;
-        k = pair_test(r[0], r[1], r[2], r[3].x, p.px, p.py, dx, dy, qw);
-      }
+    // popped from a 4x4 window (all lanes; x1 and its kept-sample mask m1 are uniform
+    // over the 4x4 block): 2x2-block membership over the still-active samples, 2x2 window
+    auto pop1 = [&](unsigned long long x1, unsigned m1) {
+      const bool k = x1 != kEmptyKey && p.active && ((m1 >> (lane & 15)) & 1u);
       const unsigned bal = __ballot_sync(kFull, k);
-      unsigned long long x2 = kEmptyKey;
-      if ((bal >> (lane & ~3)) & 0xFu) x2 = regwin_push<K2>(w2, pack_key(depth_at(r, c2x, c2y), g1));
+      if (bal == 0u) return;
+      const int g1 = (int)(x1 & 0xffffffffu);
+      const float4* r = recv + (long long)(x1 != kEmptyKey ? g1 : 0) * kRecF4;
+      const unsigned long long x2 =
+          win4_push<K2>(w2, pack_key(depth_at(r, c2x, c2y), g1), ((bal >> (lane & ~3)) & 0xFu) != 0u, lane);
       pop2(x2);
     };
     const long long start = a.ranges[2 * (long long)g.tile], end = a.ranges[2 * (long long)g.tile + 1];
@@ -890,7 +1026,9 @@ __global__ void __launch_bounds__(kRegionWarps * 32) warp_render_kernel(RenderAr
         const int ge = st_gid[e];
         if (K1 == 0 && K2 == 0) {
           float al, t;
-          if (p.active && eval_full<STATS>(r, p, al, t)) ring3_push<STATS, BWD>(p, k3s, a3s, K3, lane, pack_key(t, ge), al, recv);
+          float3 c;
+          if (p.active && eval_full<STATS>(r, p, al, t, c))
+            ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
         } else {
           bool k = false;
           if (p.active) {
@@ -899,26 +1037,23 @@ __global__ void __launch_bounds__(kRegionWarps * 32) warp_render_kernel(RenderAr
             k = pair_test(r[0], r[1], r[2], r[3].x, p.px, p.py, dx, dy, qw);
           }
           const unsigned bal = __ballot_sync(kFull, k);
-          unsigned long long x1 = kEmptyKey;
-          if ((bal >> (lane & 16)) & 0xFFFFu) x1 = regwin_push<K1>(w1, pack_key(depth_at(r, c4x, c4y), ge));
-          if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1);
+          if (bal == 0u) continue;
+          const unsigned bm = (bal >> (lane & 16)) & 0xFFFFu;
+          unsigned m1;
+          const unsigned long long x1 = win16_push<K1>(w1, pack_key(depth_at(r, c4x, c4y), ge), bm, bm != 0u, lane, m1);
+          if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1, m1);
         }
       }
     }
     if (K1 > 0 || K2 > 0) {
       for (int it = 0; it < K1; ++it) {
-        const unsigned long long x1 = regwin_pop<K1>(w1);
-        if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1);
+        unsigned m1;
+        const unsigned long long x1 = win16_pop<K1>(w1, lane, m1);
+        if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1, m1);
       }
-      for (int it = 0; it < K2; ++it) pop2(regwin_pop<K2>(w2));
+      for (int it = 0; it < K2; ++it) pop2(win4_pop<K2>(w2, lane));
     }
-    while (p.n3 > 0) {
-      const unsigned long long m = k3s[p.h3 * 32 + lane];
-      const float am = a3s[p.h3 * 32 + lane];
-      p.h3 = p.h3 + 1 == K3 ? 0 : p.h3 + 1;
-      p.n3--;
-      blend<STATS, BWD>(p, am, (int)(m & 0xffffffffu), recv);
-    }
+    while (p.n3 > 0 && p.active) ring3_pop<STATS, BWD>(p, hc, k3s, a3s, K3, lane, recv);
     if (STATS) {
       n_eval += p.n_eval;
       n_kept += p.n_kept;

@@ -115,8 +115,9 @@ vrs_status vrs_create(vrs_ctx** ctx, size_t workspace_bytes_hint);
 vrs_status vrs_destroy(vrs_ctx* ctx);
 
 /* Pre-size the workspace for up to n_views views of width x height, total_gaussians
- * summed over the rendered views' scenes, and max_instances Gaussian/tile pairs.  Must
- * be called outside stream capture before capturing vrs_render into a CUDA graph. */
+ * summed over the rendered views' scenes, and max_instances Gaussian/tile pairs (at
+ * most 2^31 - 1 per render; a render needing more returns VRS_ERR_CAPACITY).  Must be
+ * called outside stream capture before capturing vrs_render into a CUDA graph. */
 vrs_status vrs_reserve(vrs_ctx* ctx, int n_views, int width, int height, int64_t total_gaussians,
                        int64_t max_instances);
 

@@ -328,7 +328,8 @@ vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes
     c->last_instances = need;
     c->max_needed = std::max(c->max_needed, need);
     if (need > c->key_cap || c->key_cap == 0) {
-      const long long cap = need + need / 4 + 4096;
+      const long long cap = std::min(need + need / 4 + 4096, kMaxInstances);
+      if (need > kMaxInstances) return fail(c, VRS_ERR_CAPACITY, "more than 2^31 - 1 instances");
       for (int b = 0; b < 2; ++b)
         if (!ensure(c, c->keys[b], sizeof(uint64_t) * cap, false, &s) || !ensure(c, c->vals[b], sizeof(uint32_t) * cap, false, &s))
           return s;
@@ -445,7 +446,8 @@ vrs_status vrs_destroy(vrs_ctx* c) {
 }
 
 vrs_status vrs_reserve(vrs_ctx* c, int n_views, int width, int height, int64_t total_gaussians, int64_t max_instances) {
-  if (!c || n_views <= 0 || width <= 0 || height <= 0 || total_gaussians < 0 || max_instances <= 0)
+  if (!c || n_views <= 0 || width <= 0 || height <= 0 || total_gaussians < 0 || max_instances <= 0 ||
+      max_instances > kMaxInstances)
     return fail(c, VRS_ERR_INVALID, "bad reserve arguments");
   vrs_status s = VRS_OK;
   const long long VT = (long long)n_views * ((width + 15) / 16) * ((height + 15) / 16);

@@ -38,6 +38,8 @@ constexpr uint32_t kStOverflow = 2u;
 
 constexpr int kMaxWin = 32;
 constexpr int kBlock = 256;
+// instances of one render (32-bit list indices in the render kernels)
+constexpr long long kMaxInstances = (1ll << 31) - 1;
 
 struct ViewParams {
   float R[9];

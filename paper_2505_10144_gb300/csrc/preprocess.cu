@@ -306,10 +306,14 @@ __device__ __forceinline__ float4 shfl4(const float4& v, int src) {
                      __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
 }
 
-// The warp walks its Gaussians one at a time; the 32 lanes test 32 tiles of the current
-// Gaussian's rectangle at once, so a Gaussian covering many tiles does not serialise a
-// thread.  Lane j of the warp ends up with the kept-tile count of its own Gaussian.
-__global__ void __launch_bounds__(256) preprocess_kernel(SceneDev s, const ViewParams* __restrict__ views,
+// Gaussians whose rectangle holds at most kLaneTiles tiles test them in their own lane
+// (most Gaussians: a few 32x32 tiles).  The warp then walks the larger ones one at a
+// time, its 32 lanes testing 32 tiles of the current Gaussian's rectangle at once, so a
+// Gaussian covering many tiles does not serialise a thread.  Both walks call the same
+// tile_keep, so the count and the emit pass make the same decisions.
+constexpr int kLaneTiles = 8;
+
+__global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const ViewParams* __restrict__ views,
                                                          const int* __restrict__ view_list, int nv, int T,
                                                          float4* __restrict__ rec, float4* __restrict__ bbox,
                                                          uint32_t* __restrict__ count) {
@@ -324,7 +328,14 @@ __global__ void __launch_bounds__(256) preprocess_kernel(SceneDev s, const ViewP
     if (!ok) bb = make_float4(0.f, 0.f, -1.f, -1.f);
     const Span sp = make_span(bb, vp, T, ok);
     uint32_t mine = 0;
-    unsigned todo = __ballot_sync(0xffffffffu, sp.nt > 0);
+    if (sp.nt <= kLaneTiles) {
+      for (int t = 0; t < sp.nt; ++t) {
+        float x0, y0, x1, y1;
+        tile_quad(sp.tx0 + t % sp.nx, sp.ty0 + t / sp.nx, T, vp, x0, y0, x1, y1);
+        mine += tile_keep(r[0], r[1], r[2], r[3], r[4], r[5].x, x0, y0, x1, y1).keep ? 1u : 0u;
+      }
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, sp.nt > kLaneTiles);
     while (todo) {
       const int j = __ffs(todo) - 1;
       todo &= todo - 1;
@@ -374,9 +385,33 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
   const ViewParams& vp = views[view];
   const long long vg = vp.base + i;
   const uint32_t cnt = i < nview ? count[vg] : 0u;
-  unsigned todo = __ballot_sync(0xffffffffu, cnt > 0);
   const uint64_t vbase = (uint64_t)view * (uint64_t)tiles_per_view;
   const uint32_t lt = (1u << lane) - 1u;
+  Span sp{0, 0, 0, 0};
+  if (cnt > 0) sp = make_span(bbox[vg], vp, T, true);
+  if (cnt > 0 && sp.nt <= kLaneTiles) {
+    const float4* r = rec + vg * kRecF4;
+    const float4 g0 = r[0], g1 = r[1], g2 = r[2], g3 = r[3], g4 = r[4];
+    const float g5x = r[5].x;
+    long long o = offsets[vg];
+    const uint32_t gid = (uint32_t)i;
+    for (int t = 0; t < sp.nt; ++t) {
+      float x0, y0, x1, y1;
+      const int tx = sp.tx0 + t % sp.nx, ty = sp.ty0 + t / sp.nx;
+      tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
+      const Keep kp = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1);
+      if (kp.keep) {
+        if (o < cap) {
+          keys[o] = ((vbase + (uint64_t)(ty * vp.ntx + tx)) << 32) | float_order_bits(kp.key);
+          vals[o] = gid;
+        } else {
+          atomicOr(status, kStOverflow);
+        }
+        ++o;
+      }
+    }
+  }
+  unsigned todo = __ballot_sync(0xffffffffu, cnt > 0 && sp.nt > kLaneTiles);
   while (todo) {
     const int j = __ffs(todo) - 1;
     todo &= todo - 1;
@@ -384,17 +419,17 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
     const float4* r = rec + vj * kRecF4;
     const float4 g0 = r[0], g1 = r[1], g2 = r[2], g3 = r[3], g4 = r[4];
     const float g5x = r[5].x;
-    const Span sp = make_span(bbox[vj], vp, T, true);
+    const Span spj = make_span(bbox[vj], vp, T, true);
     long long o = offsets[vj];
     const uint32_t gid = (uint32_t)(vj - vp.base);
-    for (int b = 0; b < sp.nt; b += 32) {
+    for (int b = 0; b < spj.nt; b += 32) {
       const int t = b + lane;
       Keep kp{false, 0.f};
       int tx = 0, ty = 0;
-      if (t < sp.nt) {
+      if (t < spj.nt) {
         float x0, y0, x1, y1;
-        tx = sp.tx0 + t % sp.nx;
-        ty = sp.ty0 + t / sp.nx;
+        tx = spj.tx0 + t % spj.nx;
+        ty = spj.ty0 + t / spj.nx;
         tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
         kp = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1);
       }

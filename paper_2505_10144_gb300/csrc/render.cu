@@ -801,7 +801,16 @@ __device__ __forceinline__ unsigned long long win4_pop(Win4<K2>& w, int lane) {
   return e0;
 }
 
-__host__ __device__ inline size_t warp_smem_bytes(int k3) { return 3200 + (size_t)k3 * 32 * 12; }
+// list entries a warp stages per batch (records of those meeting its region)
+// and the resident CTAs per SM its register budget is set for.  Measured on the VR
+// frame: occupancy decides (the kernel waits on memory), so the small block windows
+// take 8-entry batches and a 64-register budget (8 CTAs of 4 warps with K3 = 16), the
+// larger ones keep 16-entry batches and 72 registers (7 CTAs), where 64 would spill.
+template <int K2>
+constexpr int stage_of() { return K2 <= 8 ? 8 : 16; }
+template <int K2, bool BWD>
+constexpr int ctas_of() { return BWD ? 5 : (K2 <= 8 ? 8 : 7); }
+__host__ __device__ inline size_t warp_smem_bytes(int k3, int stage) { return (size_t)stage * 100 + (size_t)k3 * 32 * 12; }
 
 // blend of one pair whose colour c the caller holds; the backward replay reads the rest
 // of the record for the gradient
@@ -884,15 +893,16 @@ __device__ __forceinline__ void ring3_pop(Px& p, float3& hc, const unsigned long
 }
 
 template <int K1, int K2, bool BWD, bool STATS>
-__global__ void __launch_bounds__(kRegionWarps * 32) warp_render_kernel(RenderArgs a) {
+__global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_render_kernel(RenderArgs a) {
+  constexpr int kStage = stage_of<K2>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int K3 = a.k3;
-  unsigned char* ws = smem_raw + (size_t)wib * warp_smem_bytes(K3);
+  unsigned char* ws = smem_raw + (size_t)wib * warp_smem_bytes(K3, kStage);
   float4* st_rec = reinterpret_cast<float4*>(ws);
-  int* st_gid = reinterpret_cast<int*>(ws + 3072);
-  unsigned long long* k3s = reinterpret_cast<unsigned long long*>(ws + 3200);
-  float* a3s = reinterpret_cast<float*>(ws + 3200 + (size_t)K3 * 256);
+  int* st_gid = reinterpret_cast<int*>(ws + kStage * 96);
+  unsigned long long* k3s = reinterpret_cast<unsigned long long*>(ws + kStage * 100);
+  float* a3s = reinterpret_cast<float*>(ws + kStage * 100 + (size_t)K3 * 256);
   const int sx = (lane & 1) | ((lane >> 1) & 2) | ((lane >> 2) & 4);
   const int sy = ((lane >> 1) & 1) | ((lane >> 2) & 2);
   const unsigned lt = (1u << lane) - 1u;
@@ -999,10 +1009,13 @@ __global__ void __launch_bounds__(kRegionWarps * 32) warp_render_kernel(RenderAr
           win4_push<K2>(w2, pack_key(depth_at(r, c2x, c2y), g1), ((bal >> (lane & ~3)) & 0xFu) != 0u, lane);
       pop2(x2);
     };
-    const long long start = a.ranges[2 * (long long)g.tile], end = a.ranges[2 * (long long)g.tile + 1];
-    for (long long b0 = start; b0 < end; b0 += 32) {
+    // instance indices fit 32 bits (the instance capacity is below 2^31)
+    const unsigned start = a.ranges[2 * (long long)g.tile], end = a.ranges[2 * (long long)g.tile + 1];
+    // 32 list entries per round (one per lane: index and bounding-box test), staged
+    // kStage lanes at a time into the warp's record buffer
+    for (unsigned b0 = start; b0 < end; b0 += 32) {
       if (!__any_sync(kFull, p.active)) break;
-      const long long j = b0 + lane;
+      const unsigned j = b0 + lane;
       bool rel = false;
       int gj = 0;
       if (j < end) {
@@ -1010,38 +1023,44 @@ __global__ void __launch_bounds__(kRegionWarps * 32) warp_render_kernel(RenderAr
         const float4 bb = a.bbox[vp.base + gj];
         rel = bb.x <= rx1 && bb.z >= rx0 && bb.y <= ry1 && bb.w >= ry0;
       }
-      const unsigned m = __ballot_sync(kFull, rel);
-      __syncwarp();
-      if (rel) {
-        const int slot = __popc(m & lt);
-        const float4* src = recv + (long long)gj * kRecF4;
+      const unsigned mall = __ballot_sync(kFull, rel);
+      for (int q0 = 0; q0 < 32; q0 += kStage) {
+        const unsigned m = mall & ((kStage == 32 ? kFull : ((1u << kStage) - 1u)) << q0);
+        if (m == 0u) continue;
+        if (q0 > 0 && !__any_sync(kFull, p.active)) break;
+        __syncwarp();
+        if ((m >> lane) & 1u) {
+          const int slot = __popc(m & lt);
+          const float4* src = recv + (long long)gj * kRecF4;
 #pragma unroll
-        for (int q = 0; q < kRecF4; ++q) st_rec[slot * kRecF4 + q] = src[q];
-        st_gid[slot] = gj;
-      }
-      __syncwarp();
-      const int nrel = __popc(m);
-      for (int e = 0; e < nrel; ++e) {
-        const float4* r = st_rec + e * kRecF4;
-        const int ge = st_gid[e];
-        if (K1 == 0 && K2 == 0) {
-          float al, t;
-          float3 c;
-          if (p.active && eval_full<STATS>(r, p, al, t, c))
-            ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
-        } else {
-          bool k = false;
-          if (p.active) {
-            float dx, dy, qw;
-            if (STATS) ++p.n_eval;
-            k = pair_test(r[0], r[1], r[2], r[3].x, p.px, p.py, dx, dy, qw);
+          for (int q = 0; q < kRecF4; ++q) st_rec[slot * kRecF4 + q] = src[q];
+          st_gid[slot] = gj;
+        }
+        __syncwarp();
+        const int nrel = __popc(m);
+        for (int e = 0; e < nrel; ++e) {
+          const float4* r = st_rec + e * kRecF4;
+          const int ge = st_gid[e];
+          if (K1 == 0 && K2 == 0) {
+            float al, t;
+            float3 c;
+            if (p.active && eval_full<STATS>(r, p, al, t, c))
+              ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
+          } else {
+            bool k = false;
+            if (p.active) {
+              float dx, dy, qw;
+              if (STATS) ++p.n_eval;
+              k = pair_test(r[0], r[1], r[2], r[3].x, p.px, p.py, dx, dy, qw);
+            }
+            const unsigned bal = __ballot_sync(kFull, k);
+            if (bal == 0u) continue;
+            const unsigned bm = (bal >> (lane & 16)) & 0xFFFFu;
+            unsigned m1;
+            const unsigned long long x1 =
+                win16_push<K1>(w1, pack_key(depth_at(r, c4x, c4y), ge), bm, bm != 0u, lane, m1);
+            if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1, m1);
           }
-          const unsigned bal = __ballot_sync(kFull, k);
-          if (bal == 0u) continue;
-          const unsigned bm = (bal >> (lane & 16)) & 0xFFFFu;
-          unsigned m1;
-          const unsigned long long x1 = win16_push<K1>(w1, pack_key(depth_at(r, c4x, c4y), ge), bm, bm != 0u, lane, m1);
-          if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1, m1);
         }
       }
     }
@@ -1118,7 +1137,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32) warp_render_kernel(RenderAr
 
 template <int K1, int K2, bool BWD, bool STATS>
 void launch_warp_t(const RenderArgs& a, cudaStream_t st) {
-  const size_t smem = warp_smem_bytes(a.k3) * kRegionWarps;
+  const size_t smem = warp_smem_bytes(a.k3, stage_of<K2>()) * kRegionWarps;
   static size_t set_smem = 0;
   static int per_sm_cached[kMaxWin + 1] = {0};
   if (smem > set_smem) {

@@ -46,7 +46,8 @@ class _Opts(C.Structure):
                 ("key_tile", C.c_int), ("foveated", C.c_int), ("tile_cull", C.c_int),
                 ("brute", C.c_int), ("gaze_x", C.c_double), ("gaze_y", C.c_double),
                 ("radius", C.c_double), ("band", C.c_double), ("bg", C.c_double * 3),
-                ("margin_alpha", C.c_double), ("margin_stop", C.c_double), ("margin_tie", C.c_double)]
+                ("margin_alpha", C.c_double), ("margin_stop", C.c_double), ("margin_tie", C.c_double),
+                ("visible", C.c_void_p)]
 
 
 class _Out(C.Structure):
@@ -71,7 +72,7 @@ def lib():
         _lib.og_edge_max.argtypes = [dp, dp, dp, dp]
         _lib.og_sh_basis.argtypes = [C.c_int, dp, dp]
         _lib.og_tile_lists.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), C.c_int, C.c_int,
-                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
         _lib.og_tile_lists.restype = C.c_int64
         _lib.og_num_threads.restype = C.c_int
     return _lib
@@ -170,11 +171,19 @@ MODES = {"exact": 0, "window": 1, "hier": 2}
 
 def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 16, fovea=None,
            bg=(0.0, 0.0, 0.0), tile_cull: bool = True, brute: bool = False,
-           want_orders: bool = False, want_samples: bool = False, margins=(1e-5, 1e-5, 3e-7)) -> dict:
+           want_orders: bool = False, want_samples: bool = False, margins=(1e-5, 1e-5, 3e-7),
+           visible=None) -> dict:
     """Render one view.  fovea: None for the plain method, else an object with gaze_x,
-    gaze_y, radius_px, band_px (single-pass foveation, 32x32 key tiles)."""
+    gaze_y, radius_px, band_px (single-pass foveation, 32x32 key tiles).  visible: None,
+    or an [H, W] array, nonzero where the pixel is visible (visibility culling)."""
     W, H = int(cam.width), int(cam.height)
     o = _Opts()
+    vis = None
+    if visible is not None:
+        vis = np.ascontiguousarray(np.asarray(visible) != 0, dtype=np.uint8)
+        if vis.shape != (H, W):
+            raise ValueError("visible must be [H, W]")
+        o.visible = vis.ctypes.data
     o.mode = MODES[mode]
     o.k1, o.k2, o.k3 = (int(k) for k in windows)
     o.key_tile = int(key_tile)
@@ -218,17 +227,20 @@ def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 
                 lowimg=lowimg if fovea is not None else None, orders=orders, stats=stats)
 
 
-def tile_lists(scene, cam, key_tile: int = 16, tile_cull: bool = True):
+def tile_lists(scene, cam, key_tile: int = 16, tile_cull: bool = True, visible=None):
     """-> (counts[nty, ntx], gids, keys) of the oracle's sorted per-tile instance lists."""
     W, H, T = int(cam.width), int(cam.height), int(key_tile)
+    vis = None if visible is None else np.ascontiguousarray(np.asarray(visible) != 0, dtype=np.uint8)
+    vp = None if vis is None else C.c_void_p(vis.ctypes.data)
     ntx, nty = (W + T - 1) // T, (H + T - 1) // T
     counts = np.zeros(ntx * nty, np.int64)
     sr = _SceneRef(scene)
     camc = _cam(cam)
-    tot = lib().og_tile_lists(C.byref(sr.s), C.byref(camc), T, int(tile_cull), _ptr(counts), None, None, 0)
+    tot = lib().og_tile_lists(C.byref(sr.s), C.byref(camc), T, int(tile_cull), vp, _ptr(counts), None, None, 0)
     gids = np.zeros(max(tot, 1), np.int32)
     keys = np.zeros(max(tot, 1))
-    lib().og_tile_lists(C.byref(sr.s), C.byref(camc), T, int(tile_cull), _ptr(counts), _ptr(gids), _ptr(keys), len(gids))
+    lib().og_tile_lists(C.byref(sr.s), C.byref(camc), T, int(tile_cull), vp, _ptr(counts), _ptr(gids), _ptr(keys),
+                        len(gids))
     return counts.reshape(nty, ntx), gids[:tot], keys[:tot]
 
 

@@ -79,6 +79,10 @@ typedef struct {
   /* margins of the FP32-vs-FP64 comparison rule: a sample is marginal when a decision
    * falls within these relative distances of its threshold */
   double margin_alpha, margin_stop, margin_tie;
+  /* visibility culling (Sec. 4.3): [H][W] bytes, nonzero where the pixel is visible in
+   * the headset; NULL = every pixel visible.  A key tile with no visible pixel gets no
+   * Gaussian/tile instances, and its pixels output the background. */
+  const uint8_t* visible;
 } og_opts;
 
 typedef struct {
@@ -652,11 +656,30 @@ static int tentry_cmp(const void* a, const void* b) {
   return (x->gid > y->gid) - (x->gid < y->gid);
 }
 
+/* tile visibility: a key tile is visible when any of its pixels is (all tiles when the
+ * mask is NULL); returns a calloc'd [ntiles] array of 0/1 */
+static uint8_t* tile_visibility(const uint8_t* visible, int W, int H, int T) {
+  const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T;
+  uint8_t* tv = (uint8_t*)calloc((size_t)ntx * nty, 1);
+  for (int ty = 0; ty < nty; ++ty)
+    for (int tx = 0; tx < ntx; ++tx) {
+      int any = visible == NULL;
+      for (int y = ty * T; y < (ty + 1) * T && y < H && !any; ++y)
+        for (int x = tx * T; x < (tx + 1) * T && x < W; ++x)
+          if (visible[(int64_t)y * W + x]) {
+            any = 1;
+            break;
+          }
+      tv[ty * ntx + tx] = (uint8_t)any;
+    }
+  return tv;
+}
+
 /* Gaussian/tile instances after the bounding rectangle and (optionally) Eq. 4 culling,
- * sorted per tile by (key, gid): the stream every sample of the tile reads.  cnt gets
- * ntiles + 1 prefix offsets. */
+ * on visible tiles only (tvis NULL: all), sorted per tile by (key, gid): the stream every
+ * sample of the tile reads.  cnt gets ntiles + 1 prefix offsets. */
 static tentry* build_lists(const og_proj* P, int64_t n, const og_camera* cam, int T, int tile_cull,
-                           int64_t* cnt) {
+                           const uint8_t* tvis, int64_t* cnt) {
   const int W = cam->width, H = cam->height;
   const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
   tentry* lists = NULL;
@@ -674,6 +697,7 @@ static tentry* build_lists(const og_proj* P, int64_t n, const og_camera* cam, in
       for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
           double key = P[i].mu[2], qmin;
+          if (tvis && !tvis[ty * ntx + tx]) continue;
           if (tile_cull) {
             double x0 = tx * T + 0.5, y0 = ty * T + 0.5;
             double x1 = fmin((tx + 1) * T, W) - 0.5, y1 = fmin((ty + 1) * T, H) - 0.5;
@@ -783,6 +807,8 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
       for (int tx = 0; tx < ntx; ++tx) cls[ty * ntx + tx] = (uint8_t)classify_tile(o, cam, tx, ty, T);
   if (out->tile_class) memcpy(out->tile_class, cls, ntiles);
 
+  /* visibility culling: invisible key tiles get no instances */
+  uint8_t* tvis = tile_visibility(o->visible, W, H, T);
   /* tile lists sorted by (key, gid): the stream each sample reads */
   int64_t* cnt = (int64_t*)calloc(ntiles + 1, sizeof(int64_t));
   tentry* lists = NULL;
@@ -794,7 +820,7 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
       if (P[i].valid) brute_ids[m++] = (int32_t)i;
     nvalid = m;
   } else {
-    lists = build_lists(P, n, cam, T, o->tile_cull, cnt);
+    lists = build_lists(P, n, cam, T, o->tile_cull, tvis, cnt);
   }
   out->stats[1] = o->brute ? 0 : cnt[ntiles];
 
@@ -804,6 +830,7 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
   for (int y = 0; y < H; ++y)
     for (int x = 0; x < W; ++x) {
       int c = cls[(y / T) * ntx + x / T];
+      if (!tvis[(y / T) * ntx + x / T]) continue; /* no sample renders: C = 0, T = 1 */
       if (c != 2) S[(int64_t)y * W + x].active_sample = 1;
       else if (!(x & 1) && !(y & 1)) S[nfull + (int64_t)(y / 2) * W2 + x / 2].active_sample = 1;
     }
@@ -977,7 +1004,9 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
       int c = cls[(y / T) * ntx + x / T];
       int marg = 0;
       double v[3];
-      if (!o->foveated || c == 0) {
+      if (!tvis[(y / T) * ntx + x / T]) {
+        for (int ch = 0; ch < 3; ++ch) v[ch] = bg[ch];
+      } else if (!o->foveated || c == 0) {
         for (int ch = 0; ch < 3; ++ch) v[ch] = S[k].C[ch] + S[k].T * bg[ch];
         marg = S[k].marginal;
       } else if (c == 1) {
@@ -1031,6 +1060,7 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
   free(brute_ids);
   free(cnt);
   free(cls);
+  free(tvis);
   free(P);
   return 0;
 }
@@ -1038,8 +1068,8 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
 /* Tile lists as the oracle builds them, for list-level comparisons:
  * counts[ntiles] (always), and when gids/keys are given (sized >= total) the sorted
  * lists concatenated by tile. Returns the total number of instances. */
-int64_t og_tile_lists(const og_scene* sc, const og_camera* cam, int T, int tile_cull, int64_t* counts,
-                      int32_t* gids, double* keys, int64_t cap) {
+int64_t og_tile_lists(const og_scene* sc, const og_camera* cam, int T, int tile_cull, const uint8_t* visible,
+                      int64_t* counts, int32_t* gids, double* keys, int64_t cap) {
   const int W = cam->width, H = cam->height;
   const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
   const int64_t n = sc->n;
@@ -1047,7 +1077,9 @@ int64_t og_tile_lists(const og_scene* sc, const og_camera* cam, int T, int tile_
 #pragma omp parallel for schedule(dynamic, 1024)
   for (int64_t i = 0; i < n; ++i) og_project(sc, i, cam, &P[i]);
   int64_t* cnt = (int64_t*)calloc(ntiles + 1, sizeof(int64_t));
-  tentry* lists = build_lists(P, n, cam, T, tile_cull, cnt);
+  uint8_t* tvis = tile_visibility(visible, W, H, T);
+  tentry* lists = build_lists(P, n, cam, T, tile_cull, tvis, cnt);
+  free(tvis);
   for (int t = 0; t < ntiles; ++t) counts[t] = cnt[t + 1] - cnt[t];
   int64_t tot = cnt[ntiles];
   if (gids && keys && cap >= tot)

@@ -353,6 +353,80 @@ def test_foveated_focus_pixels_equal_plain_render():
     assert np.array_equal(r["image"][:, cls == 0], plain[:, cls == 0])
 
 
+def _partial_mask(H, W):
+    """Visible everywhere except the left 40 columns and the bottom-right corner, with one
+    tile kept by a single visible pixel (tile-level culling keeps it whole)."""
+    m = np.ones((H, W), np.uint8)
+    m[:, :40] = 0
+    m[H - 40:, W - 56:] = 0
+    m[5, 3] = 1
+    return m
+
+
+def test_visibility_all_visible_is_no_mask():
+    """Visibility culling with every pixel visible changes nothing (bitwise)."""
+    rng = np.random.default_rng(21)
+    sc = random_scene(500, rng, sh_degree=1)
+    c = cam(160, 128, 70.0)
+    ones = np.ones((128, 160), np.uint8)
+    fov = synth.Fovea(70.0, 60.0, 30.0, 6.0)
+    for kw in (dict(key_tile=16), dict(key_tile=32, fovea=fov)):
+        for mode in ("exact", "hier"):
+            a = on.render(sc, c, mode, **kw)
+            b = on.render(sc, c, mode, visible=ones, **kw)
+            assert np.array_equal(a["image"], b["image"]) and a["stats"] == b["stats"]
+
+
+def test_visibility_culls_exactly_the_invisible_tiles():
+    """Sec. 4.3 visibility culling: a tile with no visible pixel loses its instances and
+    outputs the background; every other tile keeps the same sorted list, and (plain
+    method: a pixel depends on its own tile only) the same pixels."""
+    rng = np.random.default_rng(22)
+    sc = random_scene(700, rng, sh_degree=1)
+    W, H, T = 160, 128, 16
+    c = cam(W, H, 70.0)
+    m = _partial_mask(H, W)
+    ty, tx = np.mgrid[0:H // T, 0:W // T]
+    tvis = m.reshape(H // T, T, W // T, T).any(axis=(1, 3))
+    assert (~tvis).sum() >= 10 and tvis[0, 0]  # the single-pixel tile stays
+    c0, g0, k0 = on.tile_lists(sc, c, key_tile=T)
+    c1, g1, k1 = on.tile_lists(sc, c, key_tile=T, visible=m)
+    assert c1[~tvis].sum() == 0 and np.array_equal(c1[tvis], c0[tvis])
+    off0 = np.concatenate([[0], np.cumsum(c0.ravel())])
+    off1 = np.concatenate([[0], np.cumsum(c1.ravel())])
+    for t in np.flatnonzero(tvis.ravel()):
+        assert np.array_equal(g0[off0[t]:off0[t + 1]], g1[off1[t]:off1[t + 1]])
+        assert np.array_equal(k0[off0[t]:off0[t + 1]], k1[off1[t]:off1[t + 1]])
+    bg = (0.2, 0.4, 0.6)
+    a = on.render(sc, c, "exact", key_tile=T, bg=bg)["image"]
+    b = on.render(sc, c, "exact", key_tile=T, bg=bg, visible=m)["image"]
+    pix_vis = np.repeat(np.repeat(tvis, T, 0), T, 1)
+    assert np.array_equal(b[:, pix_vis], a[:, pix_vis])
+    for ch in range(3):
+        assert np.all(b[ch][~pix_vis] == np.float32(bg[ch]))
+
+
+def test_visibility_foveated_periphery_reads_background():
+    """Foveated: invisible tiles output the background, and visible periphery pixels
+    whose bilinear taps stay in visible tiles are unchanged."""
+    rng = np.random.default_rng(23)
+    sc = random_scene(700, rng, sh_degree=1)
+    W, H, T = 192, 128, 32
+    c = cam(W, H, 80.0)
+    fov = synth.Fovea(140.0, 70.0, 26.0, 5.0)
+    m = np.ones((H, W), np.uint8)
+    m[:, :32] = 0  # the first tile column
+    bg = (0.1, 0.3, 0.5)
+    a = on.render(sc, c, "hier", key_tile=T, fovea=fov, bg=bg)
+    b = on.render(sc, c, "hier", key_tile=T, fovea=fov, bg=bg, visible=m)
+    assert (a["tile_class"][:, 0] == 2).all()
+    for ch in range(3):
+        assert np.all(b["image"][ch][:, :32] == np.float32(bg[ch]))
+    # bilinear taps of pixel x reach low-res column floor((x + 0.5) / 2 - 0.5) ... + 1,
+    # i.e. full-res columns >= 32 only for x >= 34
+    assert np.array_equal(b["image"][:, :, 34:], a["image"][:, :, 34:])
+
+
 def test_tile_census_from_paper():
     g = json.load(open(os.path.join(GOLDEN, "tile_census.json")))
     empty = make_scene(np.zeros((0, 3)))

@@ -440,6 +440,37 @@ def test_tile_census_from_paper():
         assert counts.sum() == n and counts.min() > 0
 
 
+def test_two_pass_baseline_composition():
+    """Appendix A two-pass baseline: the centre pass is the plain render cropped (same
+    rays); outside the band the image is the half-resolution render upsampled (checked
+    against torch's half-pixel bilinear resize); in the band it is the w-blend of the
+    two; where w = 1 it is the full-resolution pixel."""
+    import torch.nn.functional as F
+    from oracle import twopass as otp
+    rng = np.random.default_rng(25)
+    sc = random_scene(800, rng, sh_degree=2)
+    W, H = 192, 128
+    c = cam(W, H, 80.0)
+    fov = synth.Fovea(84.0, 60.0, 22.0, 5.0)
+    tp = otp.render(sc, c, fov, "exact")
+    x0, y0, sw, sh = tp["rect"]
+    assert sw == sh == 2 * (27 + 1) and 0 <= x0 <= W - sw and 0 <= y0 <= H - sh
+    plain = on.render(sc, c, "exact", key_tile=16)["image"]
+    assert np.allclose(tp["centre"], plain[:, y0:y0 + sh, x0:x0 + sw], rtol=0, atol=1e-12)
+    low = on.render(sc, otp.half_camera(c), "exact", key_tile=16)["image"]
+    assert np.array_equal(low, tp["low"])
+    up = F.interpolate(torch.tensor(low)[None], scale_factor=2, mode="bilinear", align_corners=False)[0].numpy()
+    w = otp.fovea_weight_image(W, H, fov)
+    assert (w == 0).mean() > 0.5 and (w == 1).any() and ((w > 0) & (w < 1)).any()
+    z = w == 0
+    assert np.allclose(tp["image"][:, z], up[:, z], rtol=0, atol=1e-12)
+    o = w == 1
+    assert np.allclose(tp["image"][:, o], plain[:, o], rtol=0, atol=1e-12)
+    b = (w > 0) & (w < 1)
+    blend = w[None] * plain + (1 - w[None]) * up
+    assert np.allclose(tp["image"][:, b], blend[:, b], rtol=0, atol=1e-12)
+
+
 # ---------------------------------------------------------------- gradients
 
 def _fd_scene(rng):
@@ -481,6 +512,44 @@ def test_gradient_matches_central_differences(fovea):
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, j, fd, an)
             checked += 1
     assert checked > 30
+
+
+def test_gradient_with_visibility_mask_matches_central_differences():
+    """Foveated render under a visibility mask (three 32x32 tiles: hybrid, periphery,
+    invisible): autograd of the restatement, whose invisible pixels are the constant
+    background and whose periphery reads background samples from the invisible tile, vs
+    central differences of the C oracle."""
+    rng = np.random.default_rng(24)
+    sc = _fd_scene(rng)
+    c = cam(96, 32, 40.0)
+    fov = synth.Fovea(14.0, 16.0, 8.0, 4.0)
+    vis = np.ones((32, 96), np.uint8)
+    vis[:, 64:] = 0
+    bg = (0.3, 0.2, 0.1)
+    base = on.render(sc, c, "exact", key_tile=32, fovea=fov, want_orders=True, visible=vis, bg=bg)
+    assert list(base["tile_class"][0]) == [1, 2, 6]
+    w = rng.normal(size=base["image"].shape)
+    g = og.image_grad(sc, c, base["orders"], w, base["tile_class"], fov, bg)
+    checked = 0
+    for name in ["mean", "log_scale", "opacity_logit", "sh"]:
+        flat = getattr(sc, name).reshape(-1)
+        for j in rng.choice(flat.size, size=min(10, flat.size), replace=False):
+            x0 = flat[j]
+            h = 1e-6 * max(1.0, abs(x0))
+            vals, same = [], True
+            for s in (+1, -1):
+                flat[j] = x0 + s * h
+                r = on.render(sc, c, "exact", key_tile=32, fovea=fov, want_orders=True, visible=vis, bg=bg)
+                same &= all(np.array_equal(a, b) for a, b in zip(r["orders"], base["orders"]))
+                vals.append((r["image"] * w).sum())
+            flat[j] = x0
+            if not same:
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = g[name].reshape(-1)[j]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, j, fd, an)
+            checked += 1
+    assert checked > 20
 
 
 # ---------------------------------------------------------------- loss and network

@@ -508,16 +508,18 @@ def main():
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms, stages, ncalls
 
-    def graphed(cfg):
+    def graphed(cfg, visible=None):
         """A frame as one CUDA-graph replay (own context), its instance workspace sized
         by the largest count over the camera path (an untimed eager pass)."""
         Rg = api.Renderer()
         most = 0
         for fr in wl.frames:
-            Rg.render([ds], [0, 0], fr.cameras, fr.foveas, cfg, out=out)
+            Rg.render([ds], [0, 0], fr.cameras, fr.foveas, cfg, out=out, visible=visible)
             most = max(most, Rg.stats()["instances"])
         fr0 = wl.frames[0]
-        G = api.GraphedRender(Rg, [ds], [0, 0], fr0.cameras, fr0.foveas, cfg, instances=int(most * 1.02) + 4096)
+        G = api.GraphedRender(Rg, [ds], [0, 0], fr0.cameras, fr0.foveas, cfg, instances=int(most * 1.02) + 4096,
+                              visible=visible)
+        Rg.most_instances = most
         return Rg, G
 
     def timed_graph(G, Rg, steps):
@@ -564,6 +566,58 @@ def main():
     ms_plain = timed_graph(Gp, Rp, min(args.plain_steps, args.steps))
     del Gp
     Rp.close()
+    # the same foveated frames with visibility culling (Sec. 4.3) under a synthetic lens
+    # mask per eye (an OpenXR hidden-area mask stands in): culled tiles hold the background
+    from paper_2505_10144_gb300 import synth
+    masks = [torch.from_numpy(synth.lens_mask(W_IMG, H_IMG, e)).cuda() for e in (-1, +1)]
+    Rv, Gv = graphed(fov_cfg, visible=masks)
+    ms_vis = timed_graph(Gv, Rv, min(args.plain_steps, args.steps))
+    fr1 = wl.frames[1]
+    Rv.render([ds], [0, 0], fr1.cameras, fr1.foveas, fov_cfg, out=out, visible=masks)
+    inst_vis = Rv.stats()["instances"]
+    Rv.render([ds], [0, 0], fr1.cameras, fr1.foveas, fov_cfg, out=out)
+    inst_all = Rv.stats()["instances"]
+    T = 32
+    ntx, nty = (W_IMG + T - 1) // T, (H_IMG + T - 1) // T
+    culled = 0
+    for m in masks:
+        pad = torch.zeros((nty * T, ntx * T), dtype=torch.bool, device="cuda")
+        pad[:H_IMG, :W_IMG] = m != 0
+        culled += int((~pad.reshape(nty, T, ntx, T).any(dim=3).any(dim=1)).sum())
+    visibility = {"value": len(ms_vis) / (sum(ms_vis) / 1e3), "unit": "frames/s",
+                  "ms_per_step": statistics.mean(ms_vis), "p99_ms": float(np.percentile(ms_vis, 99)),
+                  "tiles_culled_pct": 100.0 * culled / (2 * ntx * nty),
+                  "instances_frame1": inst_vis, "instances_frame1_unmasked": inst_all,
+                  "mask": "ellipse 0.535 W x 0.555 H per eye, centre 3% towards the nose (synthetic lens)"}
+    del Gv
+    Rv.close()
+    # the two-pass foveated baseline (Appendix A) on the same frames, eager calls like
+    # the "eager" single-pass line: full-resolution centre square + half-resolution view
+    n_tp = min(args.plain_steps, args.steps)
+    for i in range(args.warmup):
+        fr = wl.frames[i % len(wl.frames)]
+        R.render_two_pass([ds], [0, 0], fr.cameras, fr.foveas, fov_cfg, out=out)
+    R.check()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_tp)]
+    for i in range(n_tp):
+        fr = wl.frames[(args.warmup + i) % len(wl.frames)]
+        flush.zero_()
+        ev[i][0].record()
+        R.render_two_pass([ds], [0, 0], fr.cameras, fr.foveas, fov_cfg, out=out)
+        ev[i][1].record()
+    barrier()
+    R.check()
+    ms_tp = [a.elapsed_time(b) for a, b in ev]
+    fr1 = wl.frames[1]
+    tp_img = R.render_two_pass([ds], [0, 0], fr1.cameras, fr1.foveas, fov_cfg, out=out).clone()
+    sp_img = R.render([ds], [0, 0], fr1.cameras, fr1.foveas, fov_cfg).clone()
+    two_pass = {"value": len(ms_tp) / (sum(ms_tp) / 1e3), "unit": "frames/s", "ms_per_step": statistics.mean(ms_tp),
+                "p99_ms": float(np.percentile(ms_tp, 99)),
+                "single_pass_eager_ms": statistics.mean(ms_eager),
+                "single_pass_speedup": statistics.mean(ms_tp) / statistics.mean(ms_eager),
+                "psnr_vs_single_pass_db": psnr(tp_img, sp_img),
+                "config": "vrs_render_two_pass: centre square at full resolution + half-resolution view, eager"}
     # quality of the foveated frame against the plain render
     ps = []
     o2 = torch.empty_like(out)
@@ -634,6 +688,8 @@ def main():
                   "ms_per_step": statistics.mean(ms_plain), "p99_ms": float(np.percentile(ms_plain, 99)),
                   "config": "full resolution, 16x16 tiles, hierarchical 4/8/16, same pipeline"},
         "speedup_vs_plain": statistics.mean(ms_plain) / statistics.mean(ms_fov),
+        "visibility_culling": visibility,
+        "two_pass_baseline": two_pass,
         "eager": {"value": len(ms_eager) / (sum(ms_eager) / 1e3), "unit": "frames/s",
                   "ms_per_step": statistics.mean(ms_eager), "p99_ms": float(np.percentile(ms_eager, 99)),
                   "config": "one vrs_render call per frame (host reads the instance count back)"},

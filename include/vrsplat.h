@@ -86,11 +86,17 @@ typedef struct {
  *   mode 2: single-pass foveated, periphery pixels left to the periphery network:
  *           only the half-resolution image (d_low_rgb) is written for them
  * focus_tile (8 or 16) only changes how focus tiles are split into work, never the
- * image.  Foveated modes need even width and height. */
+ * image.  Foveated modes need even width and height.
+ * visible (visibility culling, Sec. 4.3): NULL, or a device [height][width] byte mask of
+ * the headset's visible area (nonzero = visible), caller-owned and read during the
+ * render.  A key tile with no visible pixel gets no Gaussian/tile instances and no
+ * render work; its pixels (and half-resolution samples) are set to bg.  It applies in
+ * every mode, and the backward pass gives those pixels no gradient. */
 typedef struct {
   float gaze_x, gaze_y, radius_px, band_px;
   int mode;
   int focus_tile;
+  const uint8_t* visible;
 } vrs_fovea;
 
 /* Per-ray ordering (Sec. 4.1):
@@ -135,6 +141,23 @@ vrs_status vrs_render(vrs_ctx* ctx, const vrs_gaussians* scenes, int n_scenes, c
                       const vrs_camera* h_cams, const vrs_fovea* h_fovea, int n_views,
                       const vrs_render_opts* opts, float* d_out_rgb, float* d_low_rgb,
                       int save_for_backward, void* stream);
+
+/* Two-pass foveated rendering, the paper's comparison baseline (Appendix A).  Pass 1
+ * renders, per view, a full-resolution square around the gaze through a tight frustum
+ * (the camera cropped to side 2 * (ceil(max(radius + band)) + 1), clamped to the image,
+ * placed at integer offsets inside the image).  Pass 2 renders the view at half
+ * resolution: half focal length, principal point and size.  It skips, by a visibility
+ * mask, the half-resolution pixels that no full-resolution pixel with w < 1 reads.  The
+ * output is w * centre + (1 - w) * bilinear(half) inside the square and the bilinear
+ * upsample elsewhere (w of vrs_fovea; w = 0 outside the square).
+ *   h_fovea: mode 1 for every view.  opts: sort mode and windows of both passes (their
+ *   key tiles are 16).  d_out_rgb: device float [n_views][3][height][width].
+ * Both passes use the context's workspace (its last render is the second pass).  Not
+ * capturable in a CUDA graph (VRS_ERR_UNSUPPORTED); at most 64 views; even width and
+ * height. */
+vrs_status vrs_render_two_pass(vrs_ctx* ctx, const vrs_gaussians* scenes, int n_scenes, const int* h_view_scene,
+                               const vrs_camera* h_cams, const vrs_fovea* h_fovea, int n_views,
+                               const vrs_render_opts* opts, float* d_out_rgb, void* stream);
 
 /* Backward of the last vrs_render called with save_for_backward = 1, with identical
  * scenes, cameras, foveas and options: accumulates d<d_dL_drgb, rgb>/d(params) into

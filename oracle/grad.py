@@ -149,16 +149,20 @@ def fovea_weight(px, py, fovea):
 
 
 def image_from_samples(C, T, cam, tile_class=None, fovea=None, bg=(0.0, 0.0, 0.0), key_tile=32):
-    """Compose the output image from sample colours (plain, or single-pass foveated)."""
+    """Compose the output image from sample colours (plain, or single-pass foveated).
+    A tile class with 4 added marks a tile without visible pixels (visibility culling,
+    Sec. 4.3): its samples render nothing and its pixels are the background constant."""
     W, H = int(cam.width), int(cam.height)
     bgt = torch.tensor([float(np.float32(b)) for b in bg], dtype=torch.float64)
     val = C + T[:, None] * bgt  # [S, 3]
     full = val[: W * H].T.reshape(3, H, W)
-    if fovea is None:
+    if fovea is None:  # samples of invisible tiles have empty orders: C = 0, T = 1, i.e. bg
         return full
     W2, H2 = W // 2, H // 2
     grp = val[W * H:].T.reshape(3, H2, W2)
-    cls = np.repeat(np.repeat(np.asarray(tile_class), key_tile, 0), key_tile, 1)[:H, :W]
+    cls_all = np.repeat(np.repeat(np.asarray(tile_class), key_tile, 0), key_tile, 1)[:H, :W]
+    invisible = (cls_all & 4) != 0
+    cls = cls_all & 3
     cls_g = cls[0::2, 0::2]
     avg = full.reshape(3, H2, 2, W2, 2).mean(dim=(2, 4))
     lowimg = torch.where(torch.tensor(cls_g == 2)[None], grp, avg)
@@ -168,7 +172,8 @@ def image_from_samples(C, T, cam, tile_class=None, fovea=None, bg=(0.0, 0.0, 0.0
     hybrid = w[None] * full + (1 - w[None]) * up_avg
     up = bilinear_up2(lowimg)
     c = torch.tensor(cls)[None]
-    return torch.where(c == 0, full, torch.where(c == 1, hybrid, up))
+    img = torch.where(c == 0, full, torch.where(c == 1, hybrid, up))
+    return torch.where(torch.tensor(invisible)[None], bgt[:, None, None].expand(3, H, W), img)
 
 
 def bilinear_up2(L: torch.Tensor) -> torch.Tensor:

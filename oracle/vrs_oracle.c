@@ -91,7 +91,7 @@ typedef struct {
   double *low;        /* [4][H/2][W/2]: C rgb and T of group samples (NaN elsewhere) */
   double *lowimg;     /* [3][H/2][W/2]: the half-resolution image that is upsampled */
   uint8_t *marginal;  /* [H][W]: 1 where an FP32 renderer may legitimately differ */
-  uint8_t *tile_class;/* [nty][ntx]: 0 focus/plain, 1 hybrid, 2 periphery */
+  uint8_t *tile_class;/* [nty][ntx]: 0 focus/plain, 1 hybrid, 2 periphery; + 4 when invisible */
   int32_t *order;     /* gids in blend order, samples concatenated */
   int64_t *order_off; /* [H*W + (H/2)*(W/2) + 1] */
   int64_t max_order;
@@ -805,10 +805,11 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
   if (o->foveated)
     for (int ty = 0; ty < nty; ++ty)
       for (int tx = 0; tx < ntx; ++tx) cls[ty * ntx + tx] = (uint8_t)classify_tile(o, cam, tx, ty, T);
-  if (out->tile_class) memcpy(out->tile_class, cls, ntiles);
 
   /* visibility culling: invisible key tiles get no instances */
   uint8_t* tvis = tile_visibility(o->visible, W, H, T);
+  if (out->tile_class) /* class, with 4 added for a tile without visible pixels */
+    for (int t = 0; t < ntiles; ++t) out->tile_class[t] = (uint8_t)(cls[t] | (tvis[t] ? 0 : 4));
   /* tile lists sorted by (key, gid): the stream each sample reads */
   int64_t* cnt = (int64_t*)calloc(ntiles + 1, sizeof(int64_t));
   tentry* lists = NULL;

@@ -28,7 +28,7 @@ class Camera(C.Structure):
 
 class Fovea(C.Structure):
     _fields_ = [("gaze_x", C.c_float), ("gaze_y", C.c_float), ("radius_px", C.c_float), ("band_px", C.c_float),
-                ("mode", C.c_int), ("focus_tile", C.c_int)]
+                ("mode", C.c_int), ("focus_tile", C.c_int), ("visible", C.c_void_p)]
 
 
 class RenderOpts(C.Structure):
@@ -40,7 +40,8 @@ class RenderOpts(C.Structure):
 EXPORTED = ["vrs_create", "vrs_destroy", "vrs_reserve", "vrs_render", "vrs_render_backward", "vrs_check_status",
             "vrs_get_stats", "vrs_copy_instances", "vrs_project", "vrs_sort_pairs", "vrs_loss_l1_ssim",
             "vrs_adam_step", "vrs_profile_begin", "vrs_profile_end", "vrs_sort_pairs_noalloc", "vrs_update_views", "vrs_set_tuning",
-            "vrs_net_forward", "vrs_net_backward", "vrs_net_periphery", "vrs_mse", "vrs_last_error"]
+            "vrs_net_forward", "vrs_net_backward", "vrs_net_periphery", "vrs_mse", "vrs_render_two_pass",
+            "vrs_last_error"]
 
 _lib = None
 
@@ -66,6 +67,7 @@ def load() -> C.CDLL:
     lib.vrs_destroy.argtypes = [vp]
     lib.vrs_reserve.argtypes = [vp, i32, i32, i32, i64, i64]
     lib.vrs_render.argtypes = [vp, P(Gaussians), i32, P(i32), P(Camera), P(Fovea), i32, P(RenderOpts), vp, vp, i32, vp]
+    lib.vrs_render_two_pass.argtypes = [vp, P(Gaussians), i32, P(i32), P(Camera), P(Fovea), i32, P(RenderOpts), vp, vp]
     lib.vrs_render_backward.argtypes = [vp, P(Gaussians), i32, P(i32), P(Camera), P(Fovea), i32, P(RenderOpts), vp,
                                         P(GaussianGrads), vp]
     lib.vrs_check_status.argtypes = [vp, vp, P(i64)]

@@ -71,7 +71,7 @@ def camera_c(cam) -> _lib.Camera:
     return c
 
 
-def fovea_c(fov, mode: int, focus_tile: int = 16) -> _lib.Fovea:
+def fovea_c(fov, mode: int, focus_tile: int = 16, visible=None) -> _lib.Fovea:
     f = _lib.Fovea()
     if fov is not None:
         f.gaze_x, f.gaze_y, f.radius_px, f.band_px = (float(fov.gaze_x), float(fov.gaze_y), float(fov.radius_px),
@@ -79,7 +79,22 @@ def fovea_c(fov, mode: int, focus_tile: int = 16) -> _lib.Fovea:
     else:
         f.band_px = 1.0
     f.mode, f.focus_tile = int(mode), int(focus_tile)
+    f.visible = _ptr(visible)
     return f
+
+
+def _check_masks(visible, cams):
+    """visible: None, or one entry per view: None or a contiguous CUDA uint8 [H, W] mask."""
+    if visible is None:
+        return [None] * len(cams)
+    if len(visible) != len(cams):
+        raise ValueError("one visibility mask (or None) per view")
+    for m, c in zip(visible, cams):
+        if m is None:
+            continue
+        if m.dtype != torch.uint8 or not m.is_cuda or not m.is_contiguous() or tuple(m.shape) != (int(c.height), int(c.width)):
+            raise ValueError("a visibility mask is a contiguous CUDA uint8 tensor [height, width]")
+    return list(visible)
 
 
 @dataclass
@@ -129,13 +144,14 @@ class Renderer:
         if st != 0:
             raise VrsError(st, self.lib.vrs_last_error(self.ctx).decode())
 
-    def _marshal(self, scenes, view_scene, cams, foveas, cfg: RenderConfig):
+    def _marshal(self, scenes, view_scene, cams, foveas, cfg: RenderConfig, visible=None):
         n_views = len(cams)
+        masks = _check_masks(visible, cams)
         sc = (_lib.Gaussians * len(scenes))(*[s.c() for s in scenes])
         vs = (C.c_int * n_views)(*[int(v) for v in view_scene])
         cm = (_lib.Camera * n_views)(*[camera_c(c) for c in cams])
         mode = FOVEA_MODES[cfg.fovea_mode]
-        fv = (_lib.Fovea * n_views)(*[fovea_c(foveas[k] if foveas else None, mode, cfg.focus_tile)
+        fv = (_lib.Fovea * n_views)(*[fovea_c(foveas[k] if foveas else None, mode, cfg.focus_tile, masks[k])
                                       for k in range(n_views)])
         o = cfg.opts()
         self._keep = (sc, vs, cm, fv, o)
@@ -145,20 +161,36 @@ class Renderer:
         self._check(self.lib.vrs_reserve(self.ctx, n_views, width, height, int(total_gaussians), int(max_instances)))
 
     def render(self, scenes, view_scene, cams, foveas=None, cfg: RenderConfig | None = None, out=None, low=None,
-               save: bool = False, stream=None) -> torch.Tensor:
+               save: bool = False, stream=None, visible=None) -> torch.Tensor:
+        """visible: None, or per view None or a CUDA uint8 [H, W] headset visibility mask
+        (visibility culling: tiles without a visible pixel are not rendered and hold bg)."""
         cfg = cfg or RenderConfig()
         n_views = len(cams)
         W, H = int(cams[0].width), int(cams[0].height)
         if out is None:
             out = torch.empty((n_views, 3, H, W), device="cuda", dtype=torch.float32)
-        sc, vs, cm, fv, o = self._marshal(scenes, view_scene, cams, foveas, cfg)
+        sc, vs, cm, fv, o = self._marshal(scenes, view_scene, cams, foveas, cfg, visible)
         self._check(self.lib.vrs_render(self.ctx, sc, len(scenes), vs, cm, fv, n_views, C.byref(o), _ptr(out),
                                         _ptr(low), int(save), _stream(stream)))
         return out
 
-    def backward(self, scenes, view_scene, cams, foveas, cfg: RenderConfig, dL_dout: torch.Tensor, grads,
-                 stream=None):
+    def render_two_pass(self, scenes, view_scene, cams, foveas, cfg: RenderConfig | None = None, out=None,
+                        stream=None) -> torch.Tensor:
+        """The two-pass foveated baseline (full-resolution centre square + half-resolution
+        view, blended), for comparison with the single-pass render."""
+        cfg = cfg or RenderConfig(fovea_mode="bilinear")
+        n_views = len(cams)
+        W, H = int(cams[0].width), int(cams[0].height)
+        if out is None:
+            out = torch.empty((n_views, 3, H, W), device="cuda", dtype=torch.float32)
         sc, vs, cm, fv, o = self._marshal(scenes, view_scene, cams, foveas, cfg)
+        self._check(self.lib.vrs_render_two_pass(self.ctx, sc, len(scenes), vs, cm, fv, n_views, C.byref(o), _ptr(out),
+                                                 _stream(stream)))
+        return out
+
+    def backward(self, scenes, view_scene, cams, foveas, cfg: RenderConfig, dL_dout: torch.Tensor, grads,
+                 stream=None, visible=None):
+        sc, vs, cm, fv, o = self._marshal(scenes, view_scene, cams, foveas, cfg, visible)
         gr = (_lib.GaussianGrads * len(grads))(*[_lib.GaussianGrads(*[_ptr(t) for t in g.tensors()]) for g in grads])
         self._check(self.lib.vrs_render_backward(self.ctx, sc, len(scenes), vs, cm, fv, len(cams), C.byref(o),
                                                  _ptr(dL_dout.contiguous()), gr, _stream(stream)))
@@ -185,13 +217,18 @@ class Renderer:
         m = int(n.value)
         return keys[:m], vals[:m], ranges
 
-    def update_views(self, cams, foveas=None, cfg: RenderConfig | None = None):
-        """New cameras / gaze for the next replay of a captured render (same view count)."""
+    def update_views(self, cams, foveas=None, cfg: RenderConfig | None = None, visible=None):
+        """New cameras / gaze for the next replay of a captured render (same view count;
+        visibility masks present exactly where the captured render had them)."""
         cfg = cfg or RenderConfig()
         n = len(cams)
+        masks = _check_masks(visible, cams)
         cm = (_lib.Camera * n)(*[camera_c(c) for c in cams])
         mode = FOVEA_MODES[cfg.fovea_mode]
-        fv = (_lib.Fovea * n)(*[fovea_c(foveas[k], mode, cfg.focus_tile) for k in range(n)]) if foveas else None
+        fv = None
+        if foveas or visible is not None:
+            fv = (_lib.Fovea * n)(*[fovea_c(foveas[k] if foveas else None, mode, cfg.focus_tile, masks[k])
+                                    for k in range(n)])
         self._check(self.lib.vrs_update_views(self.ctx, cm, fv, n))
 
     def set_tuning(self, max_render_ctas_per_sm: int = 0):
@@ -320,28 +357,30 @@ class GraphedRender:
     whose instances exceed it raises VRS_ERR_CAPACITY at the next check()."""
 
     def __init__(self, renderer: Renderer, scenes, view_scene, cams, foveas, cfg: RenderConfig,
-                 headroom: float = 1.3, instances: int | None = None):
+                 headroom: float = 1.3, instances: int | None = None, visible=None):
         """instances: instance capacity to reserve (e.g. the largest count over a known
         camera path); default: the count of this first render x headroom."""
         self.R, self.scenes, self.view_scene, self.cfg = renderer, scenes, list(view_scene), cfg
+        self.visible = visible  # fixed per eye: every replay reads the same masks
         n_views = len(cams)
         W, H = int(cams[0].width), int(cams[0].height)
         self.out = torch.empty((n_views, 3, H, W), device="cuda", dtype=torch.float32)
-        renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out)
+        renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out, visible=visible)
         renderer.check()
         need = renderer.stats()["instances"]
         total = sum(scenes[v].n for v in self.view_scene)
         cap = int(instances) if instances is not None else int(need * headroom) + (1 << 16)
         renderer.reserve(n_views, W, H, total, max(cap, need))
-        renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out)
+        renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out, visible=visible)
         torch.cuda.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         self.stream = torch.cuda.Stream()
         with torch.cuda.graph(self.graph, stream=self.stream):
-            renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out, stream=self.stream)
+            renderer.render(scenes, self.view_scene, cams, foveas, cfg, out=self.out, stream=self.stream,
+                            visible=visible)
 
     def replay(self, cams=None, foveas=None) -> torch.Tensor:
         if cams is not None:
-            self.R.update_views(cams, foveas, self.cfg)
+            self.R.update_views(cams, foveas, self.cfg, visible=self.visible)
         self.graph.replay()
         return self.out

@@ -40,6 +40,7 @@ struct Saved {
   bool valid = false;
   int n_views = 0, W = 0, H = 0, key_tile = 0, fovea_mode = 0, sort_mode = 0, tiles_per_view = 0;
   int k[3] = {0, 0, 0};
+  bool has_mask = false;
   long long total_nv = 0;
   int sorted_buf = 0;
 };
@@ -49,7 +50,8 @@ struct Saved {
 struct vrs_ctx {
   std::string err;
   DevBuf views, view_list, rec, bbox, count, offsets, partials, keys[2], vals[2], sort_scratch, ranges, tile_class,
-      items, counters, low, s_full, s_low, stats, grad_rec, dsamp_full, dsamp_low, loss_scratch, misc, net_tmp;
+      items, counters, low, s_full, s_low, stats, grad_rec, dsamp_full, dsamp_low, loss_scratch, misc, net_tmp,
+      tvis, sat, tp_centre, tp_low, tp_mask, kcache;
   ViewParams* h_views = nullptr;  // pinned staging
   int* h_view_list = nullptr;
   uint32_t* h_small = nullptr;    // pinned: [0] total instances, [1] status, [2] items
@@ -181,6 +183,14 @@ void fill_view(ViewParams& vp, const vrs_camera& c, const vrs_fovea* f, int T) {
   vp.gaze_y = f ? f->gaze_y : 0.f;
   vp.radius = f ? f->radius_px : 0.f;
   vp.band = f ? f->band_px : 1.f;
+  vp.visible = f ? f->visible : nullptr;
+}
+
+bool any_mask(const vrs_fovea* fov, int n_views) {
+  if (!fov) return false;
+  for (int v = 0; v < n_views; ++v)
+    if (fov[v].visible) return true;
+  return false;
 }
 
 vrs_status stage_views(vrs_ctx* c, int n_views, cudaStream_t st, bool cap_mode) {
@@ -216,6 +226,7 @@ vrs_status reserve_staging(vrs_ctx* c, int n_views, bool cap_mode = false) {
 
 struct Plan {
   int n_views, W, H, T, tiles_per_view, fovea_mode;
+  bool has_mask = false;
   long long total_nv;
   std::vector<long long> view_n;
   std::vector<int> scene_first, scene_count;  // into the view list grouped by scene
@@ -261,6 +272,7 @@ vrs_status plan_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, co
   pl.H = H;
   pl.T = T;
   pl.fovea_mode = fm;
+  pl.has_mask = any_mask(fov, n_views);
   pl.tiles_per_view = ((W + T - 1) / T) * ((H + T - 1) / T);
   if ((long long)pl.tiles_per_view * n_views >= (1ll << 31)) return fail(c, VRS_ERR_INVALID, "too many tiles");
   vrs_status st = reserve_staging(c, n_views, cap_mode);
@@ -297,23 +309,39 @@ vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes
   const long long VT = (long long)pl.n_views * pl.tiles_per_view;
   if (!ensure(c, c->rec, sizeof(float4) * kRecF4 * NV, cap_mode, &s) ||
       !ensure(c, c->bbox, sizeof(float4) * NV, cap_mode, &s) || !ensure(c, c->count, sizeof(uint32_t) * NV, cap_mode, &s) ||
+      !ensure(c, c->kcache, sizeof(unsigned long long) * kKeyCacheSlots * NV, cap_mode, &s) ||
       !ensure(c, c->offsets, sizeof(uint32_t) * NV, cap_mode, &s) ||
       !ensure(c, c->partials, scan_partials_bytes(NV), cap_mode, &s) ||
       !ensure(c, c->ranges, sizeof(uint32_t) * 2 * VT, cap_mode, &s) ||
       !ensure(c, c->tile_class, VT, cap_mode, &s) || !ensure(c, c->items, sizeof(WorkItem) * 4 * VT, cap_mode, &s) ||
       !ensure(c, c->counters, sizeof(uint32_t) * kCtrCount, cap_mode, &s))
     return s;
+  Visibility vis{nullptr, nullptr, pl.tiles_per_view, 0};
+  const int ntx = (pl.W + pl.T - 1) / pl.T, nty = (pl.H + pl.T - 1) / pl.T;
+  if (pl.has_mask) {
+    vis.sat_per_view = (ntx + 1) * (nty + 1);
+    if (!ensure(c, c->tvis, VT, cap_mode, &s) ||
+        !ensure(c, c->sat, sizeof(uint32_t) * (size_t)vis.sat_per_view * pl.n_views, cap_mode, &s))
+      return s;
+    vis.tvis = P<uint8_t>(c->tvis);
+    vis.sat = P<uint32_t>(c->sat);
+  }
   if ((s = stage_views(c, pl.n_views, st, cap_mode))) return s;
   uint32_t* ctr = P<uint32_t>(c->counters);
   cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * kCtrStatus, st);  // n_items, queue, total (status is sticky)
   cudaMemsetAsync(c->ranges.p, 0, sizeof(uint32_t) * 2 * VT, st);
   prof_mark(c, 0, st);
   int launches = 0;
+  if (pl.has_mask) {
+    launch_visibility(P<ViewParams>(c->views), pl.n_views, pl.T, ntx, nty, vis, st);
+    launches += 2;
+  }
   for (int sc = 0; sc < n_scenes; ++sc) {
     if (!pl.scene_count[sc]) continue;
     ++launches;
     launch_preprocess(to_dev(scenes[sc]), P<ViewParams>(c->views), P<int>(c->view_list) + pl.scene_first[sc],
-                      pl.scene_count[sc], pl.T, P<float4>(c->rec), P<float4>(c->bbox), P<uint32_t>(c->count), st);
+                      pl.scene_count[sc], pl.T, vis, P<float4>(c->rec), P<float4>(c->bbox), P<uint32_t>(c->count),
+                      P<unsigned long long>(c->kcache), st);
   }
   prof_mark(c, 1, st);
   launch_scan_u32(P<uint32_t>(c->count), P<uint32_t>(c->offsets), pl.total_nv, ctr + kCtrTotal,
@@ -341,7 +369,8 @@ vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes
   prof_mark(c, 2, st);
   for (int v = 0; v < pl.n_views; ++v) launches += pl.view_n[v] > 0 ? 1 : 0;
   launch_duplicate(P<ViewParams>(c->views), pl.n_views, P<float4>(c->rec), P<float4>(c->bbox), P<uint32_t>(c->count),
-                   P<uint32_t>(c->offsets), pl.view_n.data(), pl.T, pl.tiles_per_view, P<uint64_t>(c->keys[0]),
+                   P<uint32_t>(c->offsets), pl.view_n.data(), pl.T, pl.tiles_per_view, vis,
+                   P<unsigned long long>(c->kcache), P<uint64_t>(c->keys[0]),
                    P<uint32_t>(c->vals[0]), ctr + kCtrTotal, c->key_cap, ctr + kCtrStatus, st);
   clamp_n_kernel<<<1, 1, 0, st>>>(ctr + kCtrTotal, ctr + kCtrSortN, c->key_cap, ctr + kCtrStatus);
   prof_mark(c, 3, st);
@@ -357,8 +386,8 @@ vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes
   launches += 1 + 2 + c->last_passes;
   prof_mark(c, 4, st);
   launch_ranges(kb[cur], ctr + kCtrSortN, sort_n, P<uint32_t>(c->ranges), VT, st);
-  launch_workitems(P<ViewParams>(c->views), pl.n_views, pl.fovea_mode, pl.T, pl.tiles_per_view, P<WorkItem>(c->items),
-                   ctr + kCtrNItems, P<uint8_t>(c->tile_class), st);
+  launch_workitems(P<ViewParams>(c->views), pl.n_views, pl.fovea_mode, pl.T, pl.tiles_per_view, vis.tvis,
+                   P<WorkItem>(c->items), ctr + kCtrNItems, P<uint8_t>(c->tile_class), st);
   c->last_launches = launches + 2;
   return VRS_OK;
 }
@@ -433,7 +462,8 @@ vrs_status vrs_destroy(vrs_ctx* c) {
   DevBuf* all[] = {&c->views, &c->view_list, &c->rec, &c->bbox, &c->count, &c->offsets, &c->partials, &c->keys[0],
                    &c->keys[1], &c->vals[0], &c->vals[1], &c->sort_scratch, &c->ranges, &c->tile_class, &c->items,
                    &c->counters, &c->low, &c->s_full, &c->s_low, &c->stats, &c->grad_rec, &c->dsamp_full,
-                   &c->dsamp_low, &c->loss_scratch, &c->misc, &c->net_tmp};
+                   &c->dsamp_low, &c->loss_scratch, &c->misc, &c->net_tmp, &c->tvis, &c->sat, &c->tp_centre,
+                   &c->tp_low, &c->tp_mask, &c->kcache};
   for (DevBuf* b : all)
     if (b->p) cudaFree(b->p);
   if (c->h_views) cudaFreeHost(c->h_views);
@@ -456,10 +486,14 @@ vrs_status vrs_reserve(vrs_ctx* c, int n_views, int width, int height, int64_t t
   if (!ensure(c, c->views, sizeof(ViewParams) * n_views, false, &s) || !ensure(c, c->view_list, sizeof(int) * n_views, false, &s) ||
       !ensure(c, c->rec, sizeof(float4) * kRecF4 * NV, false, &s) || !ensure(c, c->bbox, sizeof(float4) * NV, false, &s) ||
       !ensure(c, c->count, sizeof(uint32_t) * NV, false, &s) || !ensure(c, c->offsets, sizeof(uint32_t) * NV, false, &s) ||
+      !ensure(c, c->kcache, sizeof(unsigned long long) * kKeyCacheSlots * NV, false, &s) ||
       !ensure(c, c->partials, scan_partials_bytes(NV), false, &s) ||
       !ensure(c, c->ranges, sizeof(uint32_t) * 2 * VT, false, &s) || !ensure(c, c->tile_class, VT, false, &s) ||
       !ensure(c, c->items, sizeof(WorkItem) * 4 * VT, false, &s) ||
-      !ensure(c, c->low, sizeof(float) * 3 * (size_t)n_views * (width / 2) * (height / 2) + 16, false, &s))
+      !ensure(c, c->low, sizeof(float) * 3 * (size_t)n_views * (width / 2) * (height / 2) + 16, false, &s) ||
+      !ensure(c, c->tvis, VT, false, &s) ||
+      !ensure(c, c->sat, sizeof(uint32_t) * (size_t)n_views * ((width + 15) / 16 + 1) * ((height + 15) / 16 + 1),
+              false, &s))
     return s;
   for (int b = 0; b < 2; ++b)
     if (!ensure(c, c->keys[b], sizeof(uint64_t) * max_instances, false, &s) ||
@@ -511,6 +545,11 @@ vrs_status vrs_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, con
     a.stats = P<unsigned long long>(c->stats);
   }
   const long long max_items = 4ll * n_views * pl.tiles_per_view;
+  if (pl.has_mask) {
+    launch_invisible_fill(P<ViewParams>(c->views), n_views, pl.T, pl.tiles_per_view, P<uint8_t>(c->tvis), o->bg,
+                          d_out_rgb, a.low, pl.W, pl.H, st);
+    c->last_launches += 1;
+  }
   prof_mark(c, 5, st);
   launch_render(a, max_items, st);
   prof_mark(c, 6, st);
@@ -530,8 +569,82 @@ vrs_status vrs_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, con
   sv.sort_mode = o->sort_mode;
   sv.tiles_per_view = pl.tiles_per_view;
   sv.total_nv = pl.total_nv;
+  sv.has_mask = pl.has_mask;
   for (int k = 0; k < 3; ++k) sv.k[k] = o->win[k];
   return VRS_OK;
+}
+
+vrs_status vrs_render_two_pass(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, const int* view_scene,
+                               const vrs_camera* cams, const vrs_fovea* fov, int n_views, const vrs_render_opts* o,
+                               float* d_out_rgb, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!d_out_rgb || !cams || !fov || !o || n_views <= 0) return fail(c, VRS_ERR_INVALID, "null or empty argument");
+  if (n_views > kTwoPassMaxViews) return fail(c, VRS_ERR_INVALID, "two-pass rendering takes at most 64 views");
+  const int W = cams[0].width, H = cams[0].height;
+  if (W <= 0 || H <= 0 || (W & 1) || (H & 1)) return fail(c, VRS_ERR_INVALID, "two-pass rendering needs even sizes");
+  int half = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (cams[v].width != W || cams[v].height != H) return fail(c, VRS_ERR_INVALID, "views must share the image size");
+    if (fov[v].mode != 1 || !std::isfinite(fov[v].gaze_x) || !std::isfinite(fov[v].gaze_y) ||
+        !(fov[v].radius_px >= 0) || !(fov[v].band_px > 0) || !std::isfinite(fov[v].radius_px + fov[v].band_px))
+      return fail(c, VRS_ERR_INVALID, "two-pass rendering needs fovea mode 1 and valid fovea parameters");
+    half = std::max(half, (int)std::ceil(fov[v].radius_px + fov[v].band_px) + 1);
+  }
+  // centre squares: the focus disc and band of every view (w = 0 outside), integer offsets
+  const int SW = std::min(2 * half, W), SH = std::min(2 * half, H);
+  TwoPassViews tp;
+  memset(&tp, 0, sizeof tp);
+  std::vector<vrs_camera> cc(cams, cams + n_views), lc(cams, cams + n_views);
+  std::vector<vrs_fovea> lf(n_views);
+  for (int v = 0; v < n_views; ++v) {
+    tp.gaze_x[v] = fov[v].gaze_x;
+    tp.gaze_y[v] = fov[v].gaze_y;
+    tp.radius[v] = fov[v].radius_px;
+    tp.band[v] = fov[v].band_px;
+    tp.x0[v] = std::min(std::max((int)std::floor(fov[v].gaze_x) - half, 0), W - SW);
+    tp.y0[v] = std::min(std::max((int)std::floor(fov[v].gaze_y) - half, 0), H - SH);
+    cc[v].cx -= tp.x0[v];
+    cc[v].cy -= tp.y0[v];
+    cc[v].width = SW;
+    cc[v].height = SH;
+    lc[v].fx *= 0.5f;
+    lc[v].fy *= 0.5f;
+    lc[v].cx *= 0.5f;
+    lc[v].cy *= 0.5f;
+    lc[v].width = W / 2;
+    lc[v].height = H / 2;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool cap_mode = capturing(st);
+  // both passes stage their views through the same pinned buffer, which a replay of a
+  // captured graph would read after the second pass rewrote it
+  if (cap_mode) return fail(c, VRS_ERR_UNSUPPORTED, "two-pass rendering cannot be captured in a graph");
+  vrs_status s = VRS_OK;
+  const size_t HW2 = (size_t)(W / 2) * (H / 2);
+  if (!ensure(c, c->tp_centre, sizeof(float) * 3 * (size_t)n_views * SW * SH, cap_mode, &s) ||
+      !ensure(c, c->tp_low, sizeof(float) * 3 * (size_t)n_views * HW2, cap_mode, &s) ||
+      !ensure(c, c->tp_mask, (size_t)n_views * HW2, cap_mode, &s))
+    return s;
+  for (int v = 0; v < n_views; ++v) {
+    lf[v] = vrs_fovea{0.f, 0.f, 0.f, 1.f, 0, 16, P<uint8_t>(c->tp_mask) + (size_t)v * HW2};
+  }
+  vrs_render_opts po = *o;
+  po.key_tile = 16;
+  // pass 1: the centre squares at full resolution (a tight frustum: the cropped camera)
+  if ((s = vrs_render(c, scenes, n_scenes, view_scene, cc.data(), nullptr, n_views, &po, P<float>(c->tp_centre),
+                      nullptr, 0, stream)))
+    return s;
+  const int launches1 = c->last_launches;
+  // pass 2: half resolution, only where some full-resolution pixel with w < 1 reads it
+  launch_lowmask(tp, n_views, W, H, P<uint8_t>(c->tp_mask), st);
+  if ((s = vrs_render(c, scenes, n_scenes, view_scene, lc.data(), lf.data(), n_views, &po, P<float>(c->tp_low),
+                      nullptr, 0, stream)))
+    return s;
+  launch_two_pass_composite(tp, n_views, W, H, SW, SH, P<float>(c->tp_centre), P<float>(c->tp_low), d_out_rgb, st);
+  c->last_launches += launches1 + 2;
+  c->saved.valid = false;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "two-pass composite");
 }
 
 vrs_status vrs_render_backward(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, const int* view_scene,
@@ -825,6 +938,8 @@ vrs_status vrs_update_views(vrs_ctx* c, const vrs_camera* cams, const vrs_fovea*
     if (cams[v].width != c->saved.W || cams[v].height != c->saved.H)
       return fail(c, VRS_ERR_INVALID, "update_views cannot change the image size");
   }
+  if (any_mask(fov, n_views) != c->saved.has_mask)
+    return fail(c, VRS_ERR_INVALID, "update_views cannot add or remove visibility masks");
   if (c->staging_done) cudaEventSynchronize(c->staging_done);  // the last copy of the staging has run
   for (int v = 0; v < n_views; ++v) {
     ViewParams& vp = c->h_views[v];

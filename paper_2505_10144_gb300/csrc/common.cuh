@@ -50,6 +50,7 @@ struct ViewParams {
   int ntx, nty;     // key tiles per row / column
   long long base;   // offset of this view in the per-(view, Gaussian) arrays
   float gaze_x, gaze_y, radius, band;
+  const uint8_t* visible;  // [H][W] headset visibility mask (nonzero = visible) or null
 };
 
 struct SceneDev {
@@ -65,6 +66,25 @@ struct WorkItem {
 
 enum { kKindFull = 0, kKindLow = 1 };
 enum { kClassFocus = 0, kClassHybrid = 1, kClassPeriphery = 2 };
+// flag or'ed into the class of a key tile with no visible pixel (visibility culling)
+constexpr uint8_t kClassInvisible = 4;
+
+// Visible key tiles per view and their summed-area table (visibility culling, Sec. 4.3):
+// tvis[view * tiles_per_view + tile] is 1 when a pixel of the tile is visible; sat[view]
+// holds (nty + 1) x (ntx + 1) counts, sat[y][x] = visible tiles in rows < y, columns < x.
+struct Visibility {
+  const uint8_t* tvis;
+  const uint32_t* sat;
+  int tiles_per_view;
+  int sat_per_view;
+};
+
+__device__ __forceinline__ uint32_t sat_count(const Visibility& v, int view, int ntx, int tx0, int ty0, int tx1,
+                                              int ty1) {
+  const uint32_t* S = v.sat + (long long)view * v.sat_per_view;
+  const int w = ntx + 1;
+  return S[(ty1 + 1) * w + tx1 + 1] - S[ty0 * w + tx1 + 1] - S[(ty1 + 1) * w + tx0] + S[ty0 * w + tx0];
+}
 
 __host__ __device__ inline uint32_t float_order_bits(float f) {
   uint32_t b;
@@ -111,15 +131,19 @@ __device__ __forceinline__ bool tie_less(float ta, int ga, float tb, int gb) {
 
 // ---- launchers implemented in the .cu files -----------------------------------------
 
+void launch_visibility(const ViewParams* d_views, int n_views, int key_tile, int ntx, int nty, const Visibility& v,
+                       cudaStream_t st);
 void launch_preprocess(const SceneDev& s, const ViewParams* d_views, const int* d_view_list, int n_views_scene,
-                       int key_tile, float4* rec, float4* bbox, uint32_t* count, cudaStream_t st);
+                       int key_tile, const Visibility& vis, float4* rec, float4* bbox, uint32_t* count,
+                       unsigned long long* kcache, cudaStream_t st);
+constexpr int kKeyCacheSlots = 8;  // kept-tile keys the count pass stores per (view, Gaussian)
 void launch_scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* d_total, uint32_t* partials,
                      cudaStream_t st);
 size_t scan_partials_bytes(long long n);
 void launch_duplicate(const ViewParams* d_views, int n_views, const float4* rec, const float4* bbox,
                       const uint32_t* count, const uint32_t* offsets, const long long* h_view_n, int key_tile,
-                      int tiles_per_view, uint64_t* keys, uint32_t* vals, const uint32_t* d_total, long long cap,
-                      uint32_t* status, cudaStream_t st);
+                      int tiles_per_view, const Visibility& vis, const unsigned long long* kcache, uint64_t* keys,
+                      uint32_t* vals, const uint32_t* d_total, long long cap, uint32_t* status, cudaStream_t st);
 
 struct SortScratch {
   uint32_t* hist;      // [8][256]
@@ -167,7 +191,11 @@ struct RenderArgs {
 };
 
 void launch_workitems(const ViewParams* d_views, int n_views, int fovea_mode, int key_tile, int tiles_per_view,
-                      WorkItem* items, uint32_t* n_items, uint8_t* tile_class, cudaStream_t st);
+                      const uint8_t* tvis, WorkItem* items, uint32_t* n_items, uint8_t* tile_class, cudaStream_t st);
+// background into the output pixels (and half-resolution samples) of invisible tiles
+void launch_invisible_fill(const ViewParams* d_views, int n_views, int key_tile, int tiles_per_view,
+                           const uint8_t* tvis, const float bg[3], float* out, float* low, int W, int H,
+                           cudaStream_t st);
 void launch_render(const RenderArgs& a, long long max_items, cudaStream_t st);
 void launch_composite(const RenderArgs& a, int W, int H, cudaStream_t st);
 void launch_render_backward(const RenderArgs& a, long long max_items, cudaStream_t st);
@@ -178,5 +206,15 @@ void launch_preprocess_backward(const SceneDev& s, const ViewParams* d_views, co
                                 int n_views_scene, const uint32_t* count, const float* grad_rec,
                                 const vrs_gaussian_grads& g, cudaStream_t st);
 int device_sm_count();
+
+// per-view parameters of the two-pass foveated baseline (passed by value)
+constexpr int kTwoPassMaxViews = 64;
+struct TwoPassViews {
+  float gaze_x[kTwoPassMaxViews], gaze_y[kTwoPassMaxViews], radius[kTwoPassMaxViews], band[kTwoPassMaxViews];
+  int x0[kTwoPassMaxViews], y0[kTwoPassMaxViews];  // centre square origin (full-resolution pixels)
+};
+void launch_lowmask(const TwoPassViews& tp, int n_views, int W, int H, uint8_t* mask, cudaStream_t st);
+void launch_two_pass_composite(const TwoPassViews& tp, int n_views, int W, int H, int SW, int SH, const float* centre,
+                               const float* low, float* out, cudaStream_t st);
 
 }  // namespace vrs

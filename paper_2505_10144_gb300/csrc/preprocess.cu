@@ -313,26 +313,49 @@ __device__ __forceinline__ float4 shfl4(const float4& v, int src) {
 // tile_keep, so the count and the emit pass make the same decisions.
 constexpr int kLaneTiles = 8;
 
+// The count pass also keeps the sort keys of a Gaussian's first kKeyCache kept tiles
+// (view-local tile << 32 | depth bits, row-major order of the rectangle), so the emit
+// pass copies them for every Gaussian with at most that many instances instead of
+// testing its tiles again.
+constexpr int kKeyCache = kKeyCacheSlots;
+__device__ __forceinline__ unsigned long long local_key(int tile, float key) {
+  return ((unsigned long long)(unsigned)tile << 32) | float_order_bits(key);
+}
+
 __global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const ViewParams* __restrict__ views,
-                                                         const int* __restrict__ view_list, int nv, int T,
-                                                         float4* __restrict__ rec, float4* __restrict__ bbox,
-                                                         uint32_t* __restrict__ count) {
+                                                            const int* __restrict__ view_list, int nv, int T,
+                                                            Visibility vis, float4* __restrict__ rec,
+                                                            float4* __restrict__ bbox, uint32_t* __restrict__ count,
+                                                            unsigned long long* __restrict__ kcache) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool in = i < s.n;
   for (int k = 0; k < nv; ++k) {
-    const ViewParams& vp = views[view_list[k]];
+    const int view = view_list[k];
+    const ViewParams& vp = views[view];
     const long long vg = vp.base + i;
     float4 r[6], bb;
     const bool ok = in && project_gaussian(s, i, vp, r, bb);
     if (!ok) bb = make_float4(0.f, 0.f, -1.f, -1.f);
-    const Span sp = make_span(bb, vp, T, ok);
+    Span sp = make_span(bb, vp, T, ok);
+    // no visible tile in the rectangle: nothing to test (summed-area table, Sec. 4.3)
+    if (vis.tvis && sp.nt > 0 &&
+        sat_count(vis, view, vp.ntx, sp.tx0, sp.ty0, sp.tx0 + sp.nx - 1, sp.ty0 + sp.nt / sp.nx - 1) == 0)
+      sp.nt = 0;
+    const uint8_t* tv = vis.tvis ? vis.tvis + (long long)view * vis.tiles_per_view : nullptr;
     uint32_t mine = 0;
+    unsigned long long* kc = kcache + vg * kKeyCache;
     if (sp.nt <= kLaneTiles) {
       for (int t = 0; t < sp.nt; ++t) {
         float x0, y0, x1, y1;
-        tile_quad(sp.tx0 + t % sp.nx, sp.ty0 + t / sp.nx, T, vp, x0, y0, x1, y1);
-        mine += tile_keep(r[0], r[1], r[2], r[3], r[4], r[5].x, x0, y0, x1, y1).keep ? 1u : 0u;
+        const int tx = sp.tx0 + t % sp.nx, ty = sp.ty0 + t / sp.nx;
+        if (tv && !tv[ty * vp.ntx + tx]) continue;
+        tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
+        const Keep kp = tile_keep(r[0], r[1], r[2], r[3], r[4], r[5].x, x0, y0, x1, y1);
+        if (kp.keep) {
+          if (mine < kKeyCache) kc[mine] = local_key(ty * vp.ntx + tx, kp.key);
+          ++mine;
+        }
       }
     }
     unsigned todo = __ballot_sync(0xffffffffu, sp.nt > kLaneTiles);
@@ -344,16 +367,25 @@ __global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const Vi
       const float g5x = __shfl_sync(0xffffffffu, r[5].x, j);
       const int tx0 = __shfl_sync(0xffffffffu, sp.tx0, j), ty0 = __shfl_sync(0xffffffffu, sp.ty0, j);
       const int nx = __shfl_sync(0xffffffffu, sp.nx, j), nt = __shfl_sync(0xffffffffu, sp.nt, j);
+      unsigned long long* kcj = kcache + (vp.base + (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31) + j) * kKeyCache;
       uint32_t c = 0;
       for (int b = 0; b < nt; b += 32) {
-        bool keep = false;
+        Keep kp{false, 0.f};
         const int t = b + lane;
+        int tile = 0;
         if (t < nt) {
           float x0, y0, x1, y1;
-          tile_quad(tx0 + t % nx, ty0 + t / nx, T, vp, x0, y0, x1, y1);
-          keep = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1).keep;
+          const int tx = tx0 + t % nx, ty = ty0 + t / nx;
+          tile = ty * vp.ntx + tx;
+          if (!tv || tv[tile]) {
+            tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
+            kp = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1);
+          }
         }
-        c += __popc(__ballot_sync(0xffffffffu, keep));
+        const unsigned bal = __ballot_sync(0xffffffffu, kp.keep);
+        const uint32_t slot = c + __popc(bal & ((1u << lane) - 1u));
+        if (kp.keep && slot < kKeyCache) kcj[slot] = local_key(tile, kp.key);
+        c += __popc(bal);
       }
       if (lane == j) mine = c;
     }
@@ -377,9 +409,10 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
                                                         const float4* __restrict__ bbox,
                                                         const uint32_t* __restrict__ count,
                                                         const uint32_t* __restrict__ offsets, long long nview, int T,
-                                                        int tiles_per_view, uint64_t* __restrict__ keys,
-                                                        uint32_t* __restrict__ vals, long long cap,
-                                                        uint32_t* status) {
+                                                        int tiles_per_view, const uint8_t* __restrict__ tvis,
+                                                        const unsigned long long* __restrict__ kcache,
+                                                        uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                        long long cap, uint32_t* status) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const ViewParams& vp = views[view];
@@ -387,9 +420,22 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
   const uint32_t cnt = i < nview ? count[vg] : 0u;
   const uint64_t vbase = (uint64_t)view * (uint64_t)tiles_per_view;
   const uint32_t lt = (1u << lane) - 1u;
+  const uint8_t* tv = tvis ? tvis + (long long)view * tiles_per_view : nullptr;
+  if (cnt > 0 && cnt <= kKeyCache) {  // the count pass kept these keys
+    const unsigned long long* kc = kcache + vg * kKeyCache;
+    const long long o = offsets[vg];
+    for (uint32_t q = 0; q < cnt; ++q) {
+      if (o + q < cap) {
+        keys[o + q] = kc[q] + (vbase << 32);
+        vals[o + q] = (uint32_t)i;
+      } else {
+        atomicOr(status, kStOverflow);
+      }
+    }
+  }
   Span sp{0, 0, 0, 0};
-  if (cnt > 0) sp = make_span(bbox[vg], vp, T, true);
-  if (cnt > 0 && sp.nt <= kLaneTiles) {
+  if (cnt > kKeyCache) sp = make_span(bbox[vg], vp, T, true);
+  if (cnt > kKeyCache && sp.nt <= kLaneTiles) {
     const float4* r = rec + vg * kRecF4;
     const float4 g0 = r[0], g1 = r[1], g2 = r[2], g3 = r[3], g4 = r[4];
     const float g5x = r[5].x;
@@ -398,6 +444,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
     for (int t = 0; t < sp.nt; ++t) {
       float x0, y0, x1, y1;
       const int tx = sp.tx0 + t % sp.nx, ty = sp.ty0 + t / sp.nx;
+      if (tv && !tv[ty * vp.ntx + tx]) continue;
       tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
       const Keep kp = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1);
       if (kp.keep) {
@@ -411,7 +458,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
       }
     }
   }
-  unsigned todo = __ballot_sync(0xffffffffu, cnt > 0 && sp.nt > kLaneTiles);
+  unsigned todo = __ballot_sync(0xffffffffu, cnt > kKeyCache && sp.nt > kLaneTiles);
   while (todo) {
     const int j = __ffs(todo) - 1;
     todo &= todo - 1;
@@ -430,8 +477,10 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
         float x0, y0, x1, y1;
         tx = spj.tx0 + t % spj.nx;
         ty = spj.ty0 + t / spj.nx;
-        tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
-        kp = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1);
+        if (!tv || tv[ty * vp.ntx + tx]) {
+          tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
+          kp = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1);
+        }
       }
       const unsigned bal = __ballot_sync(0xffffffffu, kp.keep);
       if (kp.keep) {
@@ -449,22 +498,74 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
 }
 
 void launch_preprocess(const SceneDev& s, const ViewParams* d_views, const int* d_view_list, int nv, int T,
-                       float4* rec, float4* bbox, uint32_t* count, cudaStream_t st) {
+                       const Visibility& vis, float4* rec, float4* bbox, uint32_t* count,
+                       unsigned long long* kcache, cudaStream_t st) {
   if (s.n <= 0 || nv <= 0) return;
   const unsigned grid = (unsigned)((s.n + 255) / 256);
-  preprocess_kernel<<<grid, 256, 0, st>>>(s, d_views, d_view_list, nv, T, rec, bbox, count);
+  preprocess_kernel<<<grid, 256, 0, st>>>(s, d_views, d_view_list, nv, T, vis, rec, bbox, count, kcache);
 }
 
 void launch_duplicate(const ViewParams* d_views, int n_views, const float4* rec, const float4* bbox,
                       const uint32_t* count, const uint32_t* offsets, const long long* h_view_n, int T,
-                      int tiles_per_view, uint64_t* keys, uint32_t* vals, const uint32_t* /*d_total*/, long long cap,
-                      uint32_t* status, cudaStream_t st) {
+                      int tiles_per_view, const Visibility& vis, const unsigned long long* kcache, uint64_t* keys,
+                      uint32_t* vals, const uint32_t* /*d_total*/, long long cap, uint32_t* status, cudaStream_t st) {
   for (int v = 0; v < n_views; ++v) {
     if (h_view_n[v] <= 0) continue;
     const unsigned grid = (unsigned)((h_view_n[v] + 255) / 256);
     duplicate_kernel<<<grid, 256, 0, st>>>(d_views, v, rec, bbox, count, offsets, h_view_n[v], T, tiles_per_view,
-                                           keys, vals, cap, status);
+                                           vis.tvis, kcache, keys, vals, cap, status);
   }
+}
+
+// ---- visibility culling (Sec. 4.3) ----------------------------------------------------
+
+// One block per (view, key tile): the tile is visible when any of its pixels is.
+__global__ void __launch_bounds__(256) tile_visibility_kernel(const ViewParams* __restrict__ views, int T,
+                                                              int tiles_per_view, uint8_t* __restrict__ tvis) {
+  const int view = blockIdx.x / tiles_per_view, t = blockIdx.x % tiles_per_view;
+  const ViewParams& vp = views[view];
+  const int tx = t % vp.ntx, ty = t / vp.ntx;
+  int any = 0;
+  if (!vp.visible) {
+    any = 1;
+  } else if (t < vp.ntx * vp.nty) {
+    for (int p = threadIdx.x; p < T * T && !any; p += blockDim.x) {
+      const int x = tx * T + p % T, y = ty * T + p / T;
+      if (x < vp.W && y < vp.H && vp.visible[(long long)y * vp.W + x]) any = 1;
+    }
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) tvis[blockIdx.x] = (uint8_t)(any != 0);
+}
+
+// One block per view: summed-area table of the visible tiles, (nty + 1) x (ntx + 1).
+__global__ void __launch_bounds__(256) sat_kernel(const uint8_t* __restrict__ tvis, int tiles_per_view, int ntx,
+                                                  int nty, int sat_per_view, uint32_t* __restrict__ sat) {
+  const int view = blockIdx.x;
+  const uint8_t* tv = tvis + (long long)view * tiles_per_view;
+  uint32_t* S = sat + (long long)view * sat_per_view;
+  const int w = ntx + 1;
+  for (int x = threadIdx.x; x < w; x += blockDim.x) S[x] = 0;
+  for (int y = threadIdx.x; y < nty; y += blockDim.x) {  // row prefix sums
+    uint32_t run = 0;
+    S[(y + 1) * w] = 0;
+    for (int x = 0; x < ntx; ++x) {
+      run += tv[y * ntx + x];
+      S[(y + 1) * w + x + 1] = run;
+    }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < w; x += blockDim.x)  // column prefix sums
+    for (int y = 1; y <= nty; ++y) S[y * w + x] += S[(y - 1) * w + x];
+}
+
+void launch_visibility(const ViewParams* d_views, int n_views, int T, int ntx, int nty, const Visibility& v,
+                       cudaStream_t st) {
+  if (n_views <= 0) return;
+  tile_visibility_kernel<<<(unsigned)(n_views * v.tiles_per_view), 256, 0, st>>>(d_views, T, v.tiles_per_view,
+                                                                                 const_cast<uint8_t*>(v.tvis));
+  sat_kernel<<<(unsigned)n_views, 256, 0, st>>>(v.tvis, v.tiles_per_view, ntx, nty, v.sat_per_view,
+                                                const_cast<uint32_t*>(v.sat));
 }
 
 // ---- inspection entry point support ----------------------------------------------

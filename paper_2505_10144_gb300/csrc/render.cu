@@ -29,8 +29,8 @@ __device__ __forceinline__ void sample_xy(int tid, int& x, int& y) {
 }
 
 __global__ void workitems_kernel(const ViewParams* __restrict__ views, int n_views, int fovea_mode, int T,
-                                 int tiles_per_view, WorkItem* __restrict__ items, uint32_t* n_items,
-                                 uint8_t* __restrict__ tile_class) {
+                                 int tiles_per_view, const uint8_t* __restrict__ tvis, WorkItem* __restrict__ items,
+                                 uint32_t* n_items, uint8_t* __restrict__ tile_class) {
   const long long gi = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gi >= (long long)n_views * tiles_per_view) return;
   const int view = (int)(gi / tiles_per_view), t = (int)(gi % tiles_per_view);
@@ -46,6 +46,10 @@ __global__ void workitems_kernel(const ViewParams* __restrict__ views, int n_vie
     const float fy = fmaxf(fabsf(y0 - vp.gaze_y), fabsf(y1 - vp.gaze_y));
     const float dmin = sqrtf(nx * nx + ny * ny), dmax = sqrtf(fx * fx + fy * fy);
     cls = dmax <= vp.radius ? kClassFocus : (dmin >= vp.radius + vp.band ? kClassPeriphery : kClassHybrid);
+  }
+  if (tvis && !tvis[gi]) {  // visibility culling: no work; invisible_fill writes the background
+    tile_class[gi] = (uint8_t)(cls | kClassInvisible);
+    return;
   }
   tile_class[gi] = (uint8_t)cls;
   const int tile = (int)gi;
@@ -1168,6 +1172,68 @@ bool launch_warp(const RenderArgs& a, cudaStream_t st) {
   return true;
 }
 
+// ---- two-pass foveated baseline (Appendix A) ------------------------------------------
+
+// Half-resolution pixels of the second pass whose upsampled value some full-resolution
+// pixel with w < 1 reads: pixel (i, j) is tapped by the pixels 2i - 1 .. 2i + 2 (columns)
+// and 2j - 1 .. 2j + 2 (rows); w < 1 where the pixel centre lies farther than radius from
+// the gaze.  Written as a visibility mask of the half-resolution render.
+__global__ void lowmask_kernel(TwoPassViews tp, int n_views, int W, int H, uint8_t* __restrict__ mask) {
+  const int W2 = W / 2, H2 = H / 2;
+  const long long HW2 = (long long)W2 * H2, total = HW2 * n_views;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(q / HW2);
+    const long long r = q % HW2;
+    const int i = (int)(r % W2), j = (int)(r / W2);
+    bool need = false;
+    for (int y = max(2 * j - 1, 0); y <= min(2 * j + 2, H - 1) && !need; ++y)
+      for (int x = max(2 * i - 1, 0); x <= min(2 * i + 2, W - 1); ++x) {
+        const float dx = x + 0.5f - tp.gaze_x[v], dy = y + 0.5f - tp.gaze_y[v];
+        if (sqrtf(dx * dx + dy * dy) > tp.radius[v]) {
+          need = true;
+          break;
+        }
+      }
+    mask[q] = need ? 1 : 0;
+  }
+}
+
+// out = w * centre + (1 - w) * bilinear(low) inside each view's centre square, the
+// upsampled half-resolution image elsewhere (w = 0 there)
+__global__ void two_pass_composite_kernel(TwoPassViews tp, int n_views, int W, int H, int SW, int SH,
+                                          const float* __restrict__ centre, const float* __restrict__ low,
+                                          float* __restrict__ out) {
+  const int W2 = W / 2, H2 = H / 2;
+  const long long HW = (long long)W * H, HW2 = (long long)W2 * H2, HWc = (long long)SW * SH, total = HW * n_views;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
+    const int v = (int)(q / HW);
+    const long long r = q % HW;
+    const int x = (int)(r % W), y = (int)(r / W);
+    const float ux = (x + 0.5f) * 0.5f - 0.5f, uy = (y + 0.5f) * 0.5f - 0.5f;
+    const int x0 = (int)floorf(ux), y0 = (int)floorf(uy);
+    const float fx = ux - x0, fy = uy - y0;
+    const int xa = min(max(x0, 0), W2 - 1), xb = min(max(x0 + 1, 0), W2 - 1);
+    const int ya = min(max(y0, 0), H2 - 1), yb = min(max(y0 + 1, 0), H2 - 1);
+    const int cx = x - tp.x0[v], cy = y - tp.y0[v];
+    const bool in = cx >= 0 && cx < SW && cy >= 0 && cy < SH;
+    float w = 0.f;
+    if (in) {
+      const float dx = x + 0.5f - tp.gaze_x[v], dy = y + 0.5f - tp.gaze_y[v];
+      w = fminf(fmaxf((tp.radius[v] + tp.band[v] - sqrtf(dx * dx + dy * dy)) / tp.band[v], 0.f), 1.f);
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      const float* L = low + ((long long)v * 3 + ch) * HW2;
+      const float top = (1.f - fx) * L[(long long)ya * W2 + xa] + fx * L[(long long)ya * W2 + xb];
+      const float bot = (1.f - fx) * L[(long long)yb * W2 + xa] + fx * L[(long long)yb * W2 + xb];
+      const float up = (1.f - fy) * top + fy * bot;
+      float o = up;
+      if (w > 0.f) o = w * centre[((long long)v * 3 + ch) * HWc + (long long)cy * SW + cx] + (1.f - w) * up;
+      out[((long long)v * 3 + ch) * HW + r] = o;
+    }
+  }
+}
+
 // bilinear x2 upsampling of the half-resolution image into periphery tiles
 __global__ void composite_kernel(const ViewParams* __restrict__ views, int n_views, const uint8_t* __restrict__ tile_class,
                                  int tiles_per_view, int T, const float* __restrict__ low, float* __restrict__ out, int W,
@@ -1226,11 +1292,53 @@ void launch_render_t(const RenderArgs& a, long long max_items, cudaStream_t st) 
 }  // namespace
 
 void launch_workitems(const ViewParams* d_views, int n_views, int fovea_mode, int T, int tiles_per_view,
-                      WorkItem* items, uint32_t* n_items, uint8_t* tile_class, cudaStream_t st) {
+                      const uint8_t* tvis, WorkItem* items, uint32_t* n_items, uint8_t* tile_class, cudaStream_t st) {
   const long long n = (long long)n_views * tiles_per_view;
   if (n <= 0) return;
   workitems_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_views, n_views, fovea_mode, T, tiles_per_view,
-                                                               items, n_items, tile_class);
+                                                               tvis, items, n_items, tile_class);
+}
+
+// One block per (view, key tile); invisible tiles get the background in every output
+// pixel and, when the half-resolution image exists, in every 2x2-group sample.
+__global__ void __launch_bounds__(256) invisible_fill_kernel(const ViewParams* __restrict__ views, int T,
+                                                             int tiles_per_view, const uint8_t* __restrict__ tvis,
+                                                             float b0, float b1, float b2, float* __restrict__ out,
+                                                             float* __restrict__ low, int W, int H) {
+  if (tvis[blockIdx.x]) return;
+  const int view = blockIdx.x / tiles_per_view, t = blockIdx.x % tiles_per_view;
+  const ViewParams& vp = views[view];
+  if (t >= vp.ntx * vp.nty) return;
+  const int tx = t % vp.ntx, ty = t / vp.ntx;
+  const long long HW = (long long)W * H;
+  float* o = out + (long long)view * 3 * HW;
+  for (int p = threadIdx.x; p < T * T; p += blockDim.x) {
+    const int x = tx * T + p % T, y = ty * T + p / T;
+    if (x >= W || y >= H) continue;
+    const long long q = (long long)y * W + x;
+    o[q] = b0;
+    o[HW + q] = b1;
+    o[2 * HW + q] = b2;
+  }
+  if (!low) return;
+  const int W2 = W / 2, H2 = H / 2, T2 = T / 2;
+  const long long HW2 = (long long)W2 * H2;
+  float* l = low + (long long)view * 3 * HW2;
+  for (int p = threadIdx.x; p < T2 * T2; p += blockDim.x) {
+    const int x = tx * T2 + p % T2, y = ty * T2 + p / T2;
+    if (x >= W2 || y >= H2) continue;
+    const long long q = (long long)y * W2 + x;
+    l[q] = b0;
+    l[HW2 + q] = b1;
+    l[2 * HW2 + q] = b2;
+  }
+}
+
+void launch_invisible_fill(const ViewParams* d_views, int n_views, int T, int tiles_per_view, const uint8_t* tvis,
+                           const float bg[3], float* out, float* low, int W, int H, cudaStream_t st) {
+  if (n_views <= 0 || !tvis) return;
+  invisible_fill_kernel<<<(unsigned)(n_views * tiles_per_view), 256, 0, st>>>(d_views, T, tiles_per_view, tvis, bg[0],
+                                                                              bg[1], bg[2], out, low, W, H);
 }
 
 void launch_render(const RenderArgs& a, long long max_items, cudaStream_t st) {
@@ -1254,6 +1362,20 @@ void launch_render_backward(const RenderArgs& a, long long max_items, cudaStream
     case 1: launch_render_t<1, false, true>(a, max_items, st); break;
     default: launch_render_t<2, false, true>(a, max_items, st); break;
   }
+}
+
+void launch_lowmask(const TwoPassViews& tp, int n_views, int W, int H, uint8_t* mask, cudaStream_t st) {
+  const long long n = (long long)n_views * (W / 2) * (H / 2);
+  if (n <= 0) return;
+  lowmask_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8192), 256, 0, st>>>(tp, n_views, W, H, mask);
+}
+
+void launch_two_pass_composite(const TwoPassViews& tp, int n_views, int W, int H, int SW, int SH, const float* centre,
+                               const float* low, float* out, cudaStream_t st) {
+  const long long n = (long long)n_views * W * H;
+  if (n <= 0) return;
+  two_pass_composite_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 16384), 256, 0, st>>>(
+      tp, n_views, W, H, SW, SH, centre, low, out);
 }
 
 void launch_composite(const RenderArgs& a, int W, int H, cudaStream_t st) {

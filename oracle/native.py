@@ -171,7 +171,7 @@ MODES = {"exact": 0, "window": 1, "hier": 2}
 
 def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 16, fovea=None,
            bg=(0.0, 0.0, 0.0), tile_cull: bool = True, brute: bool = False,
-           want_orders: bool = False, want_samples: bool = False, margins=(1e-5, 1e-5, 3e-7),
+           want_orders: bool = False, want_samples: bool = False, margins=(5e-5, 1e-5, 3e-7),
            visible=None) -> dict:
     """Render one view.  fovea: None for the plain method, else an object with gaze_x,
     gaze_y, radius_px, band_px (single-pass foveation, 32x32 key tiles).  visible: None,

@@ -166,7 +166,7 @@ def sh_basis(degree: int, direction) -> np.ndarray:
     return Y
 
 
-MODES = {"exact": 0, "window": 1, "hier": 2}
+MODES = {"exact": 0, "window": 1, "hier": 2, "global_z": 3, "global_dist": 4}
 
 
 def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 16, fovea=None,

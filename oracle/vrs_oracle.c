@@ -68,7 +68,9 @@ typedef struct {
 } og_camera;
 
 typedef struct {
-  int mode;      /* 0 exact, 1 window (k3), 2 hierarchical (k1, k2, k3) */
+  int mode;      /* 0 exact, 1 window (k3), 2 hierarchical (k1, k2, k3), 3 global sort by view-space z
+                  * of the mean, 4 global sort by distance |mu - o| (the popping orders of 3DGS
+                  * and Mini-Splatting, Sec. 3): blend every tile list in its order */
   int k1, k2, k3;
   int key_tile;  /* side of the square tiles the sort keys use: 16 or 32 */
   int foveated;  /* 0 plain (every pixel a sample), 1 single-pass foveated */
@@ -679,7 +681,7 @@ static uint8_t* tile_visibility(const uint8_t* visible, int W, int H, int T) {
  * on visible tiles only (tvis NULL: all), sorted per tile by (key, gid): the stream every
  * sample of the tile reads.  cnt gets ntiles + 1 prefix offsets. */
 static tentry* build_lists(const og_proj* P, int64_t n, const og_camera* cam, int T, int tile_cull,
-                           const uint8_t* tvis, int64_t* cnt) {
+                           const uint8_t* tvis, int key_mode, int64_t* cnt) {
   const int W = cam->width, H = cam->height;
   const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
   tentry* lists = NULL;
@@ -703,6 +705,9 @@ static tentry* build_lists(const og_proj* P, int64_t n, const og_camera* cam, in
             double x1 = fmin((tx + 1) * T, W) - 0.5, y1 = fmin((ty + 1) * T, H) - 0.5;
             if (!og_tile_keep(&P[i], cam, x0, y0, x1, y1, &key, &qmin)) continue;
           }
+          /* global orders: one key per Gaussian */
+          if (key_mode == 3) key = P[i].mu[2];
+          if (key_mode == 4) key = sqrt(P[i].mu[0] * P[i].mu[0] + P[i].mu[1] * P[i].mu[1] + P[i].mu[2] * P[i].mu[2]);
           int t = ty * ntx + tx;
           if (!pass)
             cnt[t + 1]++;
@@ -785,6 +790,7 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
   if (W <= 0 || H <= 0 || T <= 0 || T % 4) return -1;
   if (o->foveated && (T != 32 || W % 2 || H % 2)) return -1;
   if (o->brute && o->mode != 0) return -1;
+  if (o->mode < 0 || o->mode > 4) return -1;
   const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
   const int64_t n = sc->n;
   const int W2 = W / 2, H2 = H / 2;
@@ -821,7 +827,7 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
       if (P[i].valid) brute_ids[m++] = (int32_t)i;
     nvalid = m;
   } else {
-    lists = build_lists(P, n, cam, T, o->tile_cull, tvis, cnt);
+    lists = build_lists(P, n, cam, T, o->tile_cull, tvis, o->mode, cnt);
   }
   out->stats[1] = o->brute ? 0 : cnt[ntiles];
 
@@ -870,6 +876,40 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
       }
       render_exact(P, cam, cand, nc, px, py, &S[k], &evals, &kept);
       free(tmp);
+    }
+  } else if (o->mode == 3 || o->mode == 4) {
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : evals, kept)
+    for (int64_t k = 0; k < nsamp; ++k) {
+      if (!S[k].active_sample) continue;
+      int sx, sy;
+      double px, py;
+      if (k < nfull) {
+        sx = (int)(k % W);
+        sy = (int)(k / W);
+        px = sx + 0.5;
+        py = sy + 0.5;
+      } else {
+        int64_t g = k - nfull;
+        sx = (int)(g % W2) * 2;
+        sy = (int)(g / W2) * 2;
+        px = sx + 1.0;
+        py = sy + 1.0;
+      }
+      const int t = (sy / T) * ntx + sx / T;
+      double last_key = -INFINITY;
+      for (int64_t j = cnt[t]; j < cnt[t + 1] && !S[k].done; ++j) {
+        double a, ts, sg;
+        ++evals;
+        const int32_t gid = lists[j].gid;
+        const int keep = og_eval(&P[gid], cam, px, py, &a, &ts, &sg);
+        mark_threshold(&S[k], sg);
+        if (!keep) continue;
+        ++kept;
+        /* an FP32 key may order two near-equal keys the other way */
+        if (fabs(lists[j].key - last_key) <= g_margin_tie * fabs(lists[j].key)) S[k].marginal = 1;
+        last_key = lists[j].key;
+        blend(&S[k], a, P[gid].rgb, gid);
+      }
     }
   } else {
     int k1 = o->mode == 1 ? 0 : o->k1, k2 = o->mode == 1 ? 0 : o->k2, k3 = o->k3;
@@ -1079,7 +1119,7 @@ int64_t og_tile_lists(const og_scene* sc, const og_camera* cam, int T, int tile_
   for (int64_t i = 0; i < n; ++i) og_project(sc, i, cam, &P[i]);
   int64_t* cnt = (int64_t*)calloc(ntiles + 1, sizeof(int64_t));
   uint8_t* tvis = tile_visibility(visible, W, H, T);
-  tentry* lists = build_lists(P, n, cam, T, tile_cull, tvis, cnt);
+  tentry* lists = build_lists(P, n, cam, T, tile_cull, tvis, 0, cnt);
   free(tvis);
   for (int t = 0; t < ntiles; ++t) counts[t] = cnt[t + 1] - cnt[t];
   int64_t tot = cnt[ntiles];

@@ -471,6 +471,58 @@ def test_two_pass_baseline_composition():
     assert np.allclose(tp["image"][:, b], blend[:, b], rtol=0, atol=1e-12)
 
 
+def test_global_sort_orders_two_gaussians_closed_form():
+    """Global orders (Sec. 3: 3DGS sorts by view-space z, Mini-Splatting by distance):
+    B is nearer in z, A nearer in distance; where both cover a pixel the blend is
+    alpha_1 c_1 + (1 - alpha_1) alpha_2 c_2 in the respective order."""
+    W, H, f = 96, 64, 40.0
+    c = cam(W, H, f)
+    A = [0.0, 0.0, 2.0]
+    B = [1.5, 0.0, 1.9]
+    sc = make_scene([A, B], [[-1.2] * 3, [-1.2] * 3], [[1, 0, 0, 0], [1, 0, 0, 0]], [1.0, 1.0],
+                    [[1.5, -1.0, -1.0], [-1.0, -1.0, 1.5]])
+    gz = on.render(sc, c, "global_z", key_tile=16)["image"]
+    gd = on.render(sc, c, "global_dist", key_tile=16)["image"]
+    rgb = [0.5 + sc.sh[0, :, i].astype(np.float64) / (2 * SQRT_PI) for i in range(2)]
+    checked = 0
+    for py in range(H):
+        for px in range(W):
+            ka, aa, _, _ = on.eval_one(sc, 0, c, px + 0.5, py + 0.5)
+            kb, ab, _, _ = on.eval_one(sc, 1, c, px + 0.5, py + 0.5)
+            if not (ka and kb):
+                continue
+            z_first = ab * rgb[1] + (1 - ab) * aa * rgb[0]
+            d_first = aa * rgb[0] + (1 - aa) * ab * rgb[1]
+            assert np.allclose(gz[:, py, px], z_first, atol=1e-12)
+            assert np.allclose(gd[:, py, px], d_first, atol=1e-12)
+            checked += 1
+    assert checked > 20
+
+
+def test_global_sort_equals_exact_when_layers_are_separated():
+    """Isotropic Gaussians on fronto-parallel layers far apart in depth: the per-ray
+    order of maximum response, the z order and the distance order coincide."""
+    rng = np.random.default_rng(26)
+    pts = []
+    for z in (2.0, 3.0, 4.0):  # a grid per layer, spaced wider than a footprint, shifted per layer
+        off = rng.uniform(0, 0.3, 2)
+        for i in range(6):
+            for j in range(5):
+                pts.append([((i - 2.5) * 0.3 + off[0]) * z * 0.5, ((j - 2.0) * 0.3 + off[1]) * z * 0.5, z])
+    n = len(pts)
+    sc = make_scene(np.array(pts), np.full((n, 3), -3.0), np.tile([1.0, 0, 0, 0], (n, 1)),
+                    rng.normal(0, 1, n), rng.normal(0, 1, (n, 3)))
+    c = cam(80, 64, 40.0)
+    ex = on.render(sc, c, "exact", key_tile=16, want_orders=True)
+    order, off = ex["orders"]
+    assert (np.diff(off[:80 * 64]) >= 2).sum() > 200  # pixels where two layers blend
+    for mode in ("global_z", "global_dist"):
+        g = on.render(sc, c, mode, key_tile=16)
+        ok = ~(ex["marginal"] | g["marginal"])
+        assert ok.mean() > 0.9
+        assert np.allclose(g["image"][:, ok], ex["image"][:, ok], rtol=0, atol=1e-12)
+
+
 # ---------------------------------------------------------------- gradients
 
 def _fd_scene(rng):

@@ -612,6 +612,22 @@ def main():
     fr1 = wl.frames[1]
     tp_img = R.render_two_pass([ds], [0, 0], fr1.cameras, fr1.foveas, fov_cfg, out=out).clone()
     sp_img = R.render([ds], [0, 0], fr1.cameras, fr1.foveas, fov_cfg).clone()
+    # the popping global orders of 3DGS (view-space z) and Mini-Splatting (distance) on the
+    # same foveated frames (graph replays), with their error against the exact per-ray order
+    global_orders = {}
+    exact_cfg = api.RenderConfig(**{**fov_cfg.__dict__, "sort_mode": "exact"})
+    ex_img = R.render([ds], [0, 0], fr1.cameras, fr1.foveas, exact_cfg).clone()
+    for gm in ("global_z", "global_dist"):
+        gcfg = api.RenderConfig(**{**fov_cfg.__dict__, "sort_mode": gm})
+        Rq, Gq = graphed(gcfg)
+        ms_q = timed_graph(Gq, Rq, min(args.plain_steps, args.steps))
+        q_img = Rq.render([ds], [0, 0], fr1.cameras, fr1.foveas, gcfg).clone()
+        global_orders[gm] = {"value": len(ms_q) / (sum(ms_q) / 1e3), "unit": "frames/s",
+                             "ms_per_step": statistics.mean(ms_q), "psnr_vs_exact_db": psnr(q_img, ex_img)}
+        del Gq
+        Rq.close()
+    global_orders["hier_4_8_16_psnr_vs_exact_db"] = psnr(R.render([ds], [0, 0], fr1.cameras, fr1.foveas, fov_cfg),
+                                                          ex_img)
     two_pass = {"value": len(ms_tp) / (sum(ms_tp) / 1e3), "unit": "frames/s", "ms_per_step": statistics.mean(ms_tp),
                 "p99_ms": float(np.percentile(ms_tp, 99)),
                 "single_pass_eager_ms": statistics.mean(ms_eager),
@@ -690,6 +706,7 @@ def main():
         "speedup_vs_plain": statistics.mean(ms_plain) / statistics.mean(ms_fov),
         "visibility_culling": visibility,
         "two_pass_baseline": two_pass,
+        "global_orders": global_orders,
         "eager": {"value": len(ms_eager) / (sum(ms_eager) / 1e3), "unit": "frames/s",
                   "ms_per_step": statistics.mean(ms_eager), "p99_ms": float(np.percentile(ms_eager, 99)),
                   "config": "one vrs_render call per frame (host reads the instance count back)"},

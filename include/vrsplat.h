@@ -105,7 +105,11 @@ typedef struct {
  *               depth-sorted stream
  *   sort_mode 2 hierarchical: min-windows of win[0] (4x4-sample block), win[1]
  *               (2x2-sample block) and win[2] (per sample) entries in cascade
- * win[*] <= 32.  key_tile: 16 or 32, the tile size of the global sort (foveated modes
+ *   sort_mode 3 global by view-space z of the mean (the order of 3DGS, Sec. 3) and
+ *   sort_mode 4 global by distance of the mean from the camera centre (Mini-Splatting):
+ *               every tile list is blended in its order, no per-ray resort (these
+ *               orders pop; they are the paper's cheaper comparison orders)
+ * win[*] <= 32 (unused by modes 0, 3 and 4).  key_tile: 16 or 32, the tile size of the global sort (foveated modes
  * use 32).  bg: background colour.  stats: 1 to collect device counters. */
 typedef struct {
   int sort_mode;

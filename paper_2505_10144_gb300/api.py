@@ -16,7 +16,7 @@ import torch
 from . import _lib
 from ._lib import VrsError
 
-SORT_MODES = {"exact": 0, "window": 1, "hier": 2}
+SORT_MODES = {"exact": 0, "window": 1, "hier": 2, "global_z": 3, "global_dist": 4}
 FOVEA_MODES = {"plain": 0, "bilinear": 1, "net": 2}
 
 

@@ -226,6 +226,7 @@ vrs_status reserve_staging(vrs_ctx* c, int n_views, bool cap_mode = false) {
 
 struct Plan {
   int n_views, W, H, T, tiles_per_view, fovea_mode;
+  int key_mode = 0;  // 3, 4: global orders
   bool has_mask = false;
   long long total_nv;
   std::vector<long long> view_n;
@@ -241,8 +242,8 @@ vrs_status plan_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, co
     vrs_status st = check_scene(c, scenes[s]);
     if (st) return st;
   }
-  if (o->sort_mode < 0 || o->sort_mode > 2) return fail(c, VRS_ERR_INVALID, "sort_mode must be 0, 1 or 2");
-  if (o->sort_mode >= 1 && (o->win[2] < 1 || o->win[2] > kMaxWin))
+  if (o->sort_mode < 0 || o->sort_mode > 4) return fail(c, VRS_ERR_INVALID, "sort_mode must be 0 .. 4");
+  if ((o->sort_mode == 1 || o->sort_mode == 2) && (o->win[2] < 1 || o->win[2] > kMaxWin))
     return fail(c, VRS_ERR_INVALID, "per-sample window must be 1..32");
   if (o->sort_mode == 2 && (o->win[0] < 0 || o->win[0] > kMaxWin || o->win[1] < 0 || o->win[1] > kMaxWin))
     return fail(c, VRS_ERR_INVALID, "block windows must be 0..32");
@@ -272,6 +273,7 @@ vrs_status plan_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, co
   pl.H = H;
   pl.T = T;
   pl.fovea_mode = fm;
+  pl.key_mode = o->sort_mode >= 3 ? o->sort_mode : 0;
   pl.has_mask = any_mask(fov, n_views);
   pl.tiles_per_view = ((W + T - 1) / T) * ((H + T - 1) / T);
   if ((long long)pl.tiles_per_view * n_views >= (1ll << 31)) return fail(c, VRS_ERR_INVALID, "too many tiles");
@@ -340,7 +342,7 @@ vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes
     if (!pl.scene_count[sc]) continue;
     ++launches;
     launch_preprocess(to_dev(scenes[sc]), P<ViewParams>(c->views), P<int>(c->view_list) + pl.scene_first[sc],
-                      pl.scene_count[sc], pl.T, vis, P<float4>(c->rec), P<float4>(c->bbox), P<uint32_t>(c->count),
+                      pl.scene_count[sc], pl.T, pl.key_mode, vis, P<float4>(c->rec), P<float4>(c->bbox), P<uint32_t>(c->count),
                       P<unsigned long long>(c->kcache), st);
   }
   prof_mark(c, 1, st);
@@ -370,7 +372,7 @@ vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes
   for (int v = 0; v < pl.n_views; ++v) launches += pl.view_n[v] > 0 ? 1 : 0;
   launch_duplicate(P<ViewParams>(c->views), pl.n_views, P<float4>(c->rec), P<float4>(c->bbox), P<uint32_t>(c->count),
                    P<uint32_t>(c->offsets), pl.view_n.data(), pl.T, pl.tiles_per_view, vis,
-                   P<unsigned long long>(c->kcache), P<uint64_t>(c->keys[0]),
+                   P<unsigned long long>(c->kcache), pl.key_mode, P<uint64_t>(c->keys[0]),
                    P<uint32_t>(c->vals[0]), ctr + kCtrTotal, c->key_cap, ctr + kCtrStatus, st);
   clamp_n_kernel<<<1, 1, 0, st>>>(ctr + kCtrTotal, ctr + kCtrSortN, c->key_cap, ctr + kCtrStatus);
   prof_mark(c, 3, st);
@@ -412,7 +414,8 @@ RenderArgs make_args(vrs_ctx* c, const Plan& pl, const vrs_render_opts* o) {
   a.sort_mode = o->sort_mode;
   a.k1 = o->win[0];
   a.k2 = o->win[1];
-  a.k3 = o->win[2];
+  a.k3 = o->sort_mode >= 3 ? 0 : o->win[2];
+  a.stream_order = o->sort_mode >= 3 ? 1 : 0;
   for (int k = 0; k < 3; ++k) a.bg[k] = o->bg[k];
   a.status = ctr + kCtrStatus;
   return a;

@@ -133,8 +133,9 @@ __device__ __forceinline__ bool tie_less(float ta, int ga, float tb, int gb) {
 
 void launch_visibility(const ViewParams* d_views, int n_views, int key_tile, int ntx, int nty, const Visibility& v,
                        cudaStream_t st);
+// key_mode: 0 the Eq. 4 tile key; 3, 4 the global orders (view-space z, distance)
 void launch_preprocess(const SceneDev& s, const ViewParams* d_views, const int* d_view_list, int n_views_scene,
-                       int key_tile, const Visibility& vis, float4* rec, float4* bbox, uint32_t* count,
+                       int key_tile, int key_mode, const Visibility& vis, float4* rec, float4* bbox, uint32_t* count,
                        unsigned long long* kcache, cudaStream_t st);
 constexpr int kKeyCacheSlots = 8;  // kept-tile keys the count pass stores per (view, Gaussian)
 void launch_scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* d_total, uint32_t* partials,
@@ -142,8 +143,9 @@ void launch_scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* d
 size_t scan_partials_bytes(long long n);
 void launch_duplicate(const ViewParams* d_views, int n_views, const float4* rec, const float4* bbox,
                       const uint32_t* count, const uint32_t* offsets, const long long* h_view_n, int key_tile,
-                      int tiles_per_view, const Visibility& vis, const unsigned long long* kcache, uint64_t* keys,
-                      uint32_t* vals, const uint32_t* d_total, long long cap, uint32_t* status, cudaStream_t st);
+                      int tiles_per_view, const Visibility& vis, const unsigned long long* kcache, int key_mode,
+                      uint64_t* keys, uint32_t* vals, const uint32_t* d_total, long long cap, uint32_t* status,
+                      cudaStream_t st);
 
 struct SortScratch {
   uint32_t* hist;      // [8][256]
@@ -188,6 +190,7 @@ struct RenderArgs {
   const float* dL_dlow;
   float* grad_rec;  // [sum N][16] per-(view, Gaussian) record gradients
   int max_ctas_per_sm;  // tuning: cap on resident render CTAs per SM (0 = occupancy limit)
+  int stream_order;     // global orders: blend each tile list in its order (no per-ray resort)
 };
 
 void launch_workitems(const ViewParams* d_views, int n_views, int fovea_mode, int key_tile, int tiles_per_view,

@@ -322,9 +322,22 @@ __device__ __forceinline__ unsigned long long local_key(int tile, float key) {
   return ((unsigned long long)(unsigned)tile << 32) | float_order_bits(key);
 }
 
+// Sort key of the global orders (Sec. 3): key_mode 3 = view-space z of the mean (3DGS),
+// 4 = its distance from the camera centre (Mini-Splatting), recovered from the record's
+// projected mean and z; otherwise the Eq. 4 tile key.
+__device__ __forceinline__ float order_key(int key_mode, float tile_key, const float4& f0, const float4& f3,
+                                           const ViewParams& vp) {
+  if (key_mode == 3) return f3.w;
+  if (key_mode == 4) {
+    const float mz = f3.w, mx = (f0.x - vp.cx) * mz / vp.fx, my = (f0.y - vp.cy) * mz / vp.fy;
+    return sqrtf(mx * mx + my * my + mz * mz);
+  }
+  return tile_key;
+}
+
 __global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const ViewParams* __restrict__ views,
                                                             const int* __restrict__ view_list, int nv, int T,
-                                                            Visibility vis, float4* __restrict__ rec,
+                                                            int key_mode, Visibility vis, float4* __restrict__ rec,
                                                             float4* __restrict__ bbox, uint32_t* __restrict__ count,
                                                             unsigned long long* __restrict__ kcache) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -353,7 +366,7 @@ __global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const Vi
         tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
         const Keep kp = tile_keep(r[0], r[1], r[2], r[3], r[4], r[5].x, x0, y0, x1, y1);
         if (kp.keep) {
-          if (mine < kKeyCache) kc[mine] = local_key(ty * vp.ntx + tx, kp.key);
+          if (mine < kKeyCache) kc[mine] = local_key(ty * vp.ntx + tx, order_key(key_mode, kp.key, r[0], r[3], vp));
           ++mine;
         }
       }
@@ -384,7 +397,7 @@ __global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const Vi
         }
         const unsigned bal = __ballot_sync(0xffffffffu, kp.keep);
         const uint32_t slot = c + __popc(bal & ((1u << lane) - 1u));
-        if (kp.keep && slot < kKeyCache) kcj[slot] = local_key(tile, kp.key);
+        if (kp.keep && slot < kKeyCache) kcj[slot] = local_key(tile, order_key(key_mode, kp.key, g0, g3, vp));
         c += __popc(bal);
       }
       if (lane == j) mine = c;
@@ -410,7 +423,7 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
                                                         const uint32_t* __restrict__ count,
                                                         const uint32_t* __restrict__ offsets, long long nview, int T,
                                                         int tiles_per_view, const uint8_t* __restrict__ tvis,
-                                                        const unsigned long long* __restrict__ kcache,
+                                                        const unsigned long long* __restrict__ kcache, int key_mode,
                                                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                         long long cap, uint32_t* status) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -449,7 +462,8 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
       const Keep kp = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1);
       if (kp.keep) {
         if (o < cap) {
-          keys[o] = ((vbase + (uint64_t)(ty * vp.ntx + tx)) << 32) | float_order_bits(kp.key);
+          keys[o] = ((vbase + (uint64_t)(ty * vp.ntx + tx)) << 32) |
+                    float_order_bits(order_key(key_mode, kp.key, g0, g3, vp));
           vals[o] = gid;
         } else {
           atomicOr(status, kStOverflow);
@@ -486,7 +500,8 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
       if (kp.keep) {
         const long long slot = o + __popc(bal & lt);
         if (slot < cap) {
-          keys[slot] = ((vbase + (uint64_t)(ty * vp.ntx + tx)) << 32) | float_order_bits(kp.key);
+          keys[slot] = ((vbase + (uint64_t)(ty * vp.ntx + tx)) << 32) |
+                       float_order_bits(order_key(key_mode, kp.key, g0, g3, vp));
           vals[slot] = gid;
         } else {
           atomicOr(status, kStOverflow);
@@ -498,22 +513,23 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
 }
 
 void launch_preprocess(const SceneDev& s, const ViewParams* d_views, const int* d_view_list, int nv, int T,
-                       const Visibility& vis, float4* rec, float4* bbox, uint32_t* count,
+                       int key_mode, const Visibility& vis, float4* rec, float4* bbox, uint32_t* count,
                        unsigned long long* kcache, cudaStream_t st) {
   if (s.n <= 0 || nv <= 0) return;
   const unsigned grid = (unsigned)((s.n + 255) / 256);
-  preprocess_kernel<<<grid, 256, 0, st>>>(s, d_views, d_view_list, nv, T, vis, rec, bbox, count, kcache);
+  preprocess_kernel<<<grid, 256, 0, st>>>(s, d_views, d_view_list, nv, T, key_mode, vis, rec, bbox, count, kcache);
 }
 
 void launch_duplicate(const ViewParams* d_views, int n_views, const float4* rec, const float4* bbox,
                       const uint32_t* count, const uint32_t* offsets, const long long* h_view_n, int T,
-                      int tiles_per_view, const Visibility& vis, const unsigned long long* kcache, uint64_t* keys,
-                      uint32_t* vals, const uint32_t* /*d_total*/, long long cap, uint32_t* status, cudaStream_t st) {
+                      int tiles_per_view, const Visibility& vis, const unsigned long long* kcache, int key_mode,
+                      uint64_t* keys, uint32_t* vals, const uint32_t* /*d_total*/, long long cap, uint32_t* status,
+                      cudaStream_t st) {
   for (int v = 0; v < n_views; ++v) {
     if (h_view_n[v] <= 0) continue;
     const unsigned grid = (unsigned)((h_view_n[v] + 255) / 256);
     duplicate_kernel<<<grid, 256, 0, st>>>(d_views, v, rec, bbox, count, offsets, h_view_n[v], T, tiles_per_view,
-                                           vis.tvis, kcache, keys, vals, cap, status);
+                                           vis.tvis, kcache, key_mode, keys, vals, cap, status);
   }
 }
 

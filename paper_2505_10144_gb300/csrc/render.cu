@@ -1048,8 +1048,12 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
           if (K1 == 0 && K2 == 0) {
             float al, t;
             float3 c;
-            if (p.active && eval_full<STATS>(r, p, al, t, c))
-              ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
+            if (p.active && eval_full<STATS>(r, p, al, t, c)) {
+              if (a.stream_order)  // global orders: the list order is the blend order
+                blend_c<STATS, BWD>(p, al, ge, c, recv);
+              else
+                ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
+            }
           } else {
             bool k = false;
             if (p.active) {

@@ -197,6 +197,19 @@ def test_render_plain_stereo_shell(R, vr_small, mode):
         parity(gpu[v], ref["image"], ref["marginal"])
 
 
+@pytest.mark.parametrize("mode", ["global_z", "global_dist"])
+def test_render_global_orders(R, vr_small, mode):
+    """The global-sort orders of Sec. 3 (view-space z, distance), plain and foveated."""
+    scene, cams, fov = vr_small
+    gpu = render_gpu(R, scene, cams, sort_mode=mode, key_tile=16)
+    gpf = render_gpu(R, scene, cams, fov, sort_mode=mode, key_tile=32, fovea_mode="bilinear")
+    for v in range(2):
+        ref = on.render(scene, cams[v], mode, key_tile=16)
+        parity(gpu[v], ref["image"], ref["marginal"])
+        ref = on.render(scene, cams[v], mode, key_tile=32, fovea=fov[v])
+        parity(gpf[v], ref["image"], ref["marginal"])
+
+
 # ---------------------------------------------------------------- edge cases
 
 def test_empty_scene_gives_background(R):

@@ -130,45 +130,82 @@ struct Px {
 // T_final saved, every term is available in front-to-back order:
 //   dL/dc_i     = dL/dC alpha_i T_i
 //   dL/dalpha_i = T_i (dL/dC . c_i) - (dL/dC . (C_final - C_<=i) + dL/dT_final T_final) / (1 - alpha_i)
+// Adds v[16] to grad (the record gradient of Gaussian g) once per group of the lanes
+// executing together that hold the same g: the group's lowest lane gathers the others'
+// values by shuffles and alone issues the atomics.  Neighbouring samples tend to blend the
+// same Gaussian at the same step, so this divides the atomic traffic on L2.
+__device__ __forceinline__ void grad_add16(float* __restrict__ grad, int g, float v[16]) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, g);
+  const int lane = threadIdx.x & 31;
+  const bool leader = (__ffs(peers) - 1) == lane;
+  unsigned rest = leader ? (peers & (peers - 1u)) : 0u;  // the leader's peers, itself excluded
+  const int n = __popc(rest);
+  const int rounds = __reduce_max_sync(act, n);
+  for (int it = 0; it < rounds; ++it) {
+    const int src = rest ? __ffs(rest) - 1 : lane;
+    rest &= rest - 1u;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float o = __shfl_sync(act, v[k], src);
+      if (leader && it < n) v[k] += o;
+    }
+  }
+  if (leader) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if (v[k] != 0.f) atomicAdd(grad + k, v[k]);
+  }
+}
+
+// d(loss)/d(record) of one blended pair, accumulated into the record gradient (16
+// floats: pm_x, pm_y, h00, h01, h10, h11, h20, h21, h22, a00, a01x2, a11, log2 sigma, r,
+// g, b).  alpha_i, c_i, T_i and C_<i are the values the forward used; with C_final and
+// T_final saved, every term is available in front-to-back order:
+//   dL/dc_i     = dL/dC alpha_i T_i
+//   dL/dalpha_i = T_i (dL/dC . c_i) - (dL/dC . (C_final - C_<=i) + dL/dT_final T_final) / (1 - alpha_i)
 __device__ __forceinline__ void blend_grad(const Px& p, float alpha, const float4* r, float Tb, float Cb0, float Cb1,
-                                           float Cb2, float* __restrict__ grad) {
-  const float4 f0 = r[0], f1 = r[1], f2 = r[2], f3 = r[3], f5 = r[5];
+                                           float Cb2, float* __restrict__ grad, int g) {
+  const float4 f0 = r[0], f1 = r[1], f2 = r[2], f5 = r[5];
   const float aT = alpha * Tb;
   const float c0 = f5.y, c1 = f5.z, c2 = f5.w;
   const float le0 = fmaf(aT, c0, Cb0), le1 = fmaf(aT, c1, Cb1), le2 = fmaf(aT, c2, Cb2);
   const float cdot = p.G0 * c0 + p.G1 * c1 + p.G2 * c2;
   const float rest = p.G0 * (p.F0 - le0) + p.G1 * (p.F1 - le1) + p.G2 * (p.F2 - le2) + p.GT * p.TF;
   const float dLda = Tb * cdot - rest / (1.f - alpha);
-  atomicAdd(grad + 13, p.G0 * aT);
-  atomicAdd(grad + 14, p.G1 * aT);
-  atomicAdd(grad + 15, p.G2 * aT);
-  if (alpha >= kAlphaMax) return;  // clamped: alpha does not depend on the Gaussian
-  const float dx = p.px - f0.x, dy = p.py - f0.y;
-  const float a = fmaf(f0.z, dx, f0.w * dy);
-  const float b = fmaf(f1.x, dx, f1.y * dy);
-  const float w = fmaf(f1.z, dx, fmaf(f1.w, dy, f2.x));
-  const float iw2 = 1.f / (w * w);
-  const float qn = fmaf(a, fmaf(f2.y, a, f2.z * b), f2.w * b * b);
-  const float qw = qn * iw2;
-  const float gl = dLda * alpha * kLn2;  // dL/d(log2 sigma) = -dL/dq'
-  const float gqn = -gl * iw2;
-  const float gw = 2.f * gl * qw / w;
-  const float ga = gqn * (2.f * f2.y * a + f2.z * b), gb = gqn * (f2.z * a + 2.f * f2.w * b);
-  const float gdx = ga * f0.z + gb * f1.x + gw * f1.z, gdy = ga * f0.w + gb * f1.y + gw * f1.w;
-  atomicAdd(grad + 0, -gdx);
-  atomicAdd(grad + 1, -gdy);
-  atomicAdd(grad + 2, ga * dx);
-  atomicAdd(grad + 3, ga * dy);
-  atomicAdd(grad + 4, gb * dx);
-  atomicAdd(grad + 5, gb * dy);
-  atomicAdd(grad + 6, gw * dx);
-  atomicAdd(grad + 7, gw * dy);
-  atomicAdd(grad + 8, gw);
-  atomicAdd(grad + 9, gqn * a * a);
-  atomicAdd(grad + 10, gqn * a * b);
-  atomicAdd(grad + 11, gqn * b * b);
-  atomicAdd(grad + 12, gl);
-  (void)f3;
+  float v[16];
+#pragma unroll
+  for (int k = 0; k < 13; ++k) v[k] = 0.f;
+  v[13] = p.G0 * aT;
+  v[14] = p.G1 * aT;
+  v[15] = p.G2 * aT;
+  if (alpha < kAlphaMax) {  // clamped: alpha does not depend on the Gaussian
+    const float dx = p.px - f0.x, dy = p.py - f0.y;
+    const float a = fmaf(f0.z, dx, f0.w * dy);
+    const float b = fmaf(f1.x, dx, f1.y * dy);
+    const float w = fmaf(f1.z, dx, fmaf(f1.w, dy, f2.x));
+    const float iw2 = 1.f / (w * w);
+    const float qn = fmaf(a, fmaf(f2.y, a, f2.z * b), f2.w * b * b);
+    const float qw = qn * iw2;
+    const float gl = dLda * alpha * kLn2;  // dL/d(log2 sigma) = -dL/dq'
+    const float gqn = -gl * iw2;
+    const float gw = 2.f * gl * qw / w;
+    const float ga = gqn * (2.f * f2.y * a + f2.z * b), gb = gqn * (f2.z * a + 2.f * f2.w * b);
+    v[0] = -(ga * f0.z + gb * f1.x + gw * f1.z);
+    v[1] = -(ga * f0.w + gb * f1.y + gw * f1.w);
+    v[2] = ga * dx;
+    v[3] = ga * dy;
+    v[4] = gb * dx;
+    v[5] = gb * dy;
+    v[6] = gw * dx;
+    v[7] = gw * dy;
+    v[8] = gw;
+    v[9] = gqn * a * a;
+    v[10] = gqn * a * b;
+    v[11] = gqn * b * b;
+    v[12] = gl;
+  }
+  grad_add16(grad, g, v);
 }
 
 template <bool STATS, bool BWD = false>
@@ -179,7 +216,7 @@ __device__ __forceinline__ void blend(Px& p, float alpha, int g, const float4* _
     p.active = false;
     return;
   }
-  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16);
+  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16, g);
   const float4 c = recv[(long long)g * kRecF4 + 5];
   const float aT = alpha * p.T;
   p.C0 = fmaf(aT, c.y, p.C0);
@@ -826,7 +863,7 @@ __device__ __forceinline__ void blend_c(Px& p, float alpha, int g, float3 c, con
     p.active = false;
     return;
   }
-  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16);
+  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16, g);
   const float aT = alpha * p.T;
   p.C0 = fmaf(aT, c.x, p.C0);
   p.C1 = fmaf(aT, c.y, p.C1);

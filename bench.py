@@ -439,10 +439,11 @@ def profiled_traffic():
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
         if kv.get("source_sha256") != render_source_hash():
-            return None, "render source changed since the ncu capture"
-        return float(kv["dram_bytes_per_launch"]), kv.get("capture", "")
+            return None, "render source changed since the ncu capture", None
+        issue = float(kv["issue_slots_busy_pct"]) / 100.0 if "issue_slots_busy_pct" in kv else None
+        return float(kv["dram_bytes_per_launch"]), kv.get("capture", ""), issue
     except (OSError, KeyError, ValueError):
-        return None, "no ncu traffic summary"
+        return None, "no ncu traffic summary", None
 
 
 def psnr(a, b):
@@ -681,10 +682,13 @@ def main():
     sm_mhz = clocks["sm_mhz"] or 2070.0
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     achieved = flops / (render_ms / 1e3) / 1e12 if render_ms > 0 else 0.0
-    traffic, traffic_note = profiled_traffic()
+    traffic, traffic_note, issue_busy = profiled_traffic()
     roofline = {"bound": "alu", "kernel": "warp_render_kernel<4,8> (hierarchical 4/8/16)", "achieved": achieved,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops if peak_tflops else None,
                 "traffic": traffic, "traffic_note": traffic_note,
+                "issue_slots_busy_ncu": issue_busy,
+                "note": "the kernel is bound by instruction issue (window bookkeeping: shuffles, shared memory, "
+                        "compares), so its FP32-FLOP fraction is low while its issue slots are mostly busy",
                 "peak_source": f"FP32 FMA peak: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                f"{sm_mhz:.0f} MHz (median SM clock under load)",
                 "work_per_launch": {"evaluated_pairs": cnt["evaluated"], "kept_pairs": cnt["kept"],

@@ -45,7 +45,8 @@ def gpu_grads(R, scene, cams, foveas, cfg, dimg):
     return {k: t.cpu().numpy().astype(np.float64) for k, t in zip(names, g.tensors())}
 
 
-@pytest.mark.parametrize("mode,win", [("exact", (0, 0, 0)), ("window", (0, 0, 16)), ("hier", (4, 8, 16))])
+@pytest.mark.parametrize("mode,win", [("exact", (0, 0, 0)), ("window", (0, 0, 16)), ("hier", (4, 8, 16)),
+                                      ("global_z", (0, 0, 0))])
 def test_backward_plain_matches_oracle(R, mode, win):
     """1k Gaussians, 64x64, 110 deg FOV, SH degree 3 (the fine-tuning gradient subset)."""
     from paper_2505_10144_gb300 import api

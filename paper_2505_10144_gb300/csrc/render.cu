@@ -1219,13 +1219,13 @@ bool launch_warp(const RenderArgs& a, cudaStream_t st) {
 // pixel with w < 1 reads: pixel (i, j) is tapped by the pixels 2i - 1 .. 2i + 2 (columns)
 // and 2j - 1 .. 2j + 2 (rows); w < 1 where the pixel centre lies farther than radius from
 // the gaze.  Written as a visibility mask of the half-resolution render.
-__global__ void lowmask_kernel(TwoPassViews tp, int n_views, int W, int H, uint8_t* __restrict__ mask) {
+__global__ void lowmask_kernel(TwoPassViews tp, int W, int H, uint8_t* __restrict__ mask) {
   const int W2 = W / 2, H2 = H / 2;
-  const long long HW2 = (long long)W2 * H2, total = HW2 * n_views;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(q / HW2);
-    const long long r = q % HW2;
-    const int i = (int)(r % W2), j = (int)(r / W2);
+  const long long HW2 = (long long)W2 * H2;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.z;
+  if (i >= W2) return;
+  for (int j = blockIdx.y; j < H2; j += gridDim.y) {
+    const long long q = (long long)v * HW2 + (long long)j * W2 + i;
     bool need = false;
     for (int y = max(2 * j - 1, 0); y <= min(2 * j + 2, H - 1) && !need; ++y)
       for (int x = max(2 * i - 1, 0); x <= min(2 * i + 2, W - 1); ++x) {
@@ -1241,15 +1241,15 @@ __global__ void lowmask_kernel(TwoPassViews tp, int n_views, int W, int H, uint8
 
 // out = w * centre + (1 - w) * bilinear(low) inside each view's centre square, the
 // upsampled half-resolution image elsewhere (w = 0 there)
-__global__ void two_pass_composite_kernel(TwoPassViews tp, int n_views, int W, int H, int SW, int SH,
+__global__ void two_pass_composite_kernel(TwoPassViews tp, int W, int H, int SW, int SH,
                                           const float* __restrict__ centre, const float* __restrict__ low,
                                           float* __restrict__ out) {
   const int W2 = W / 2, H2 = H / 2;
-  const long long HW = (long long)W * H, HW2 = (long long)W2 * H2, HWc = (long long)SW * SH, total = HW * n_views;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(q / HW);
-    const long long r = q % HW;
-    const int x = (int)(r % W), y = (int)(r / W);
+  const long long HW = (long long)W * H, HW2 = (long long)W2 * H2, HWc = (long long)SW * SH;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, v = blockIdx.z;
+  if (x >= W) return;
+  for (int y = blockIdx.y; y < H; y += gridDim.y) {
+    const long long r = (long long)y * W + x;
     const float ux = (x + 0.5f) * 0.5f - 0.5f, uy = (y + 0.5f) * 0.5f - 0.5f;
     const int x0 = (int)floorf(ux), y0 = (int)floorf(uy);
     const float fx = ux - x0, fy = uy - y0;
@@ -1275,27 +1275,27 @@ __global__ void two_pass_composite_kernel(TwoPassViews tp, int n_views, int W, i
   }
 }
 
-// bilinear x2 upsampling of the half-resolution image into periphery tiles
-__global__ void composite_kernel(const ViewParams* __restrict__ views, int n_views, const uint8_t* __restrict__ tile_class,
-                                 int tiles_per_view, int T, const float* __restrict__ low, float* __restrict__ out, int W,
-                                 int H) {
-  const long long HW = (long long)W * H;
-  const int W2 = W / 2, H2 = H / 2;
-  const long long HW2 = (long long)W2 * H2;
-  const long long total = HW * n_views;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-    const int view = (int)(i / HW);
-    const long long r = i % HW;
-    const int y = (int)(r / W), x = (int)(r % W);
-    const ViewParams& vp = views[view];
+// Bilinear x2 upsampling of the half-resolution image into periphery tiles: one thread
+// per output pixel, grid (row chunks of 256 pixels, rows, views), so no index division.
+__global__ void __launch_bounds__(256) composite_kernel(const ViewParams* __restrict__ views,
+                                                        const uint8_t* __restrict__ tile_class, int tiles_per_view,
+                                                        int T, const float* __restrict__ low, float* __restrict__ out,
+                                                        int W, int H) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, view = blockIdx.z;
+  if (x >= W) return;
+  const ViewParams& vp = views[view];
+  for (int y = blockIdx.y; y < H; y += gridDim.y) {
     if (tile_class[(long long)view * tiles_per_view + (y / T) * vp.ntx + x / T] != kClassPeriphery) continue;
+    const long long HW = (long long)W * H;
+    const int W2 = W / 2, H2 = H / 2;
+    const long long HW2 = (long long)W2 * H2;
     const float ux = (x + 0.5f) * 0.5f - 0.5f, uy = (y + 0.5f) * 0.5f - 0.5f;
     const int x0 = (int)floorf(ux), y0 = (int)floorf(uy);
     const float fx = ux - x0, fy = uy - y0;
     const int xa = min(max(x0, 0), W2 - 1), xb = min(max(x0 + 1, 0), W2 - 1);
     const int ya = min(max(y0, 0), H2 - 1), yb = min(max(y0 + 1, 0), H2 - 1);
     const float* L = low + (long long)view * 3 * HW2;
-    float* o = out + (long long)view * 3 * HW + r;
+    float* o = out + (long long)view * 3 * HW + (long long)y * W + x;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float* Lc = L + c * HW2;
@@ -1406,24 +1406,22 @@ void launch_render_backward(const RenderArgs& a, long long max_items, cudaStream
 }
 
 void launch_lowmask(const TwoPassViews& tp, int n_views, int W, int H, uint8_t* mask, cudaStream_t st) {
-  const long long n = (long long)n_views * (W / 2) * (H / 2);
-  if (n <= 0) return;
-  lowmask_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 8192), 256, 0, st>>>(tp, n_views, W, H, mask);
+  if (n_views <= 0 || W < 2 || H < 2) return;
+  const dim3 grid((unsigned)((W / 2 + 255) / 256), (unsigned)std::min(H / 2, 65535), (unsigned)n_views);
+  lowmask_kernel<<<grid, 256, 0, st>>>(tp, W, H, mask);
 }
 
 void launch_two_pass_composite(const TwoPassViews& tp, int n_views, int W, int H, int SW, int SH, const float* centre,
                                const float* low, float* out, cudaStream_t st) {
-  const long long n = (long long)n_views * W * H;
-  if (n <= 0) return;
-  two_pass_composite_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 16384), 256, 0, st>>>(
-      tp, n_views, W, H, SW, SH, centre, low, out);
+  if (n_views <= 0 || W <= 0 || H <= 0) return;
+  const dim3 grid((unsigned)((W + 255) / 256), (unsigned)std::min(H, 65535), (unsigned)n_views);
+  two_pass_composite_kernel<<<grid, 256, 0, st>>>(tp, W, H, SW, SH, centre, low, out);
 }
 
 void launch_composite(const RenderArgs& a, int W, int H, cudaStream_t st) {
-  const long long total = (long long)W * H * a.n_views;
-  const unsigned grid = (unsigned)std::min<long long>((total + 255) / 256, (long long)device_sm_count() * 16);
-  composite_kernel<<<grid, 256, 0, st>>>(a.views, a.n_views, a.tile_class, a.tiles_per_view, a.key_tile, a.low, a.out,
-                                         W, H);
+  if (W <= 0 || H <= 0 || a.n_views <= 0) return;
+  const dim3 grid((unsigned)((W + 255) / 256), (unsigned)std::min(H, 65535), (unsigned)a.n_views);
+  composite_kernel<<<grid, 256, 0, st>>>(a.views, a.tile_class, a.tiles_per_view, a.key_tile, a.low, a.out, W, H);
 }
 
 }  // namespace vrs

@@ -844,14 +844,18 @@ __device__ __forceinline__ unsigned long long win4_pop(Win4<K2>& w, int lane) {
 
 // list entries a warp stages per batch (records of those meeting its region)
 // and the resident CTAs per SM its register budget is set for.  Measured on the VR
-// frame: occupancy decides (the kernel waits on memory), so the small block windows
-// take 8-entry batches and a 64-register budget (8 CTAs of 4 warps with K3 = 16), the
-// larger ones keep 16-entry batches and 72 registers (7 CTAs), where 64 would spill.
+// frame: occupancy decides (the kernel waits on memory and on the issue of window
+// bookkeeping), and with the tournament-tree window 16-entry batches and a 72-register
+// budget (7 CTAs of 4 warps per SM, K3 = 16) beat 8 CTAs at 64 registers, which spill.
 template <int K2>
-constexpr int stage_of() { return K2 <= 8 ? 8 : 16; }
+constexpr int stage_of() { return 16; }
 template <int K2, bool BWD>
-constexpr int ctas_of() { return BWD ? 5 : (K2 <= 8 ? 8 : 7); }
-__host__ __device__ inline size_t warp_smem_bytes(int k3, int stage) { return (size_t)stage * 100 + (size_t)k3 * 32 * 12; }
+constexpr int ctas_of() { return BWD ? 5 : 7; }
+// key slots of the per-sample window: the tournament tree (k3 <= 16) always has 16
+__host__ __device__ inline int window_key_slots(int k3) { return k3 <= 16 ? 16 : k3; }
+__host__ __device__ inline size_t warp_smem_bytes(int k3, int stage) {
+  return (size_t)stage * 100 + (size_t)window_key_slots(k3) * 32 * 8 + (size_t)k3 * 32 * 4;
+}
 
 // blend of one pair whose colour c the caller holds; the backward replay reads the rest
 // of the record for the gradient
@@ -875,6 +879,85 @@ __device__ __forceinline__ void blend_c(Px& p, float alpha, int g, float3 c, con
 __device__ __forceinline__ float3 rec_colour(const float4* __restrict__ recv, int g) {
   const float4 f5 = recv[(long long)g * kRecF4 + 5];
   return make_float3(f5.y, f5.z, f5.w);
+}
+
+// Per-sample window as a tournament tree over 16 slots (K3 <= 16).  The keys and alphas
+// sit in shared memory, [slot][lane]; the winners (smallest key) of the 15 internal nodes
+// are 4-bit slot numbers in one 64-bit register (node n = 1 .. 15 at bits 4 (n - 1),
+// children 2n and 2n + 1, slot s at node 16 + s).  Putting a key into a slot replays the
+// four matches on the slot's path to the root, so every insertion costs the same: no
+// data-dependent shifting and no divergence.  Unused slots hold kEmptyKey.  hc is the
+// colour of the root winner, loaded when the winner changes.
+// every internal node starts with the leftmost slot of its subtree (all slots empty)
+constexpr unsigned long long kTreeInit = 0x0eca86420c840800ull;
+__device__ __forceinline__ int tree_get(unsigned long long t, int node) { return (int)((t >> (4 * (node - 1))) & 0xFull); }
+__device__ __forceinline__ unsigned long long tree_set(unsigned long long t, int node, int slot) {
+  const int sh = 4 * (node - 1);
+  return (t & ~(0xFull << sh)) | ((unsigned long long)slot << sh);
+}
+
+// key x now sits in slot s: replay s's path; returns the root winner's key
+__device__ __forceinline__ unsigned long long tree_replay(unsigned long long& t, const unsigned long long* kk, int lane,
+                                                         int s, unsigned long long x) {
+  int node = 16 + s, cs = s;
+  unsigned long long ck = x;
+#pragma unroll
+  for (int lv = 0; lv < 4; ++lv) {
+    const int sib = node ^ 1;
+    const int ss = sib >= 16 ? sib - 16 : tree_get(t, sib);
+    const unsigned long long sk = kk[ss * 32 + lane];
+    if (sk < ck) {
+      ck = sk;
+      cs = ss;
+    }
+    node >>= 1;
+    t = tree_set(t, node, cs);
+  }
+  return ck;
+}
+
+template <bool STATS, bool BWD>
+__device__ __forceinline__ void tree3_push(Px& p, unsigned long long& t, float3& hc, unsigned long long* kk, float* aa,
+                                           int K3, int lane, unsigned long long x, float alpha, float3 c,
+                                           const float4* __restrict__ recv) {
+  if (p.n3 < K3) {  // filling: the next free slot
+    const int s = p.n3++;
+    kk[s * 32 + lane] = x;
+    aa[s * 32 + lane] = alpha;
+    const int w0 = tree_get(t, 1);
+    tree_replay(t, kk, lane, s, x);
+    if (tree_get(t, 1) != w0 || s == 0) hc = c;
+    return;
+  }
+  const int w = tree_get(t, 1);
+  const unsigned long long m = kk[w * 32 + lane];
+  if (x < m) {  // x is the smallest: out at once
+    blend_c<STATS, BWD>(p, alpha, (int)(x & 0xffffffffu), c, recv);
+    return;
+  }
+  const float am = aa[w * 32 + lane];
+  const float3 mc = hc;
+  kk[w * 32 + lane] = x;
+  aa[w * 32 + lane] = alpha;
+  const unsigned long long nk = tree_replay(t, kk, lane, w, x);
+  const int nw = tree_get(t, 1);
+  hc = nw == w ? c : rec_colour(recv, (int)(nk & 0xffffffffu));
+  blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);
+}
+
+// pops the root winner and blends it
+template <bool STATS, bool BWD>
+__device__ __forceinline__ void tree3_pop(Px& p, unsigned long long& t, float3& hc, unsigned long long* kk,
+                                          const float* aa, int lane, const float4* __restrict__ recv) {
+  const int w = tree_get(t, 1);
+  const unsigned long long m = kk[w * 32 + lane];
+  const float am = aa[w * 32 + lane];
+  const float3 mc = hc;
+  kk[w * 32 + lane] = kEmptyKey;
+  const unsigned long long nk = tree_replay(t, kk, lane, w, kEmptyKey);
+  p.n3--;
+  if (p.n3 > 0) hc = rec_colour(recv, (int)(nk & 0xffffffffu));
+  blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);
 }
 
 // Per-lane ring of the per-sample window: packed keys and alphas, [slot][lane], ascending
@@ -943,7 +1026,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
   float4* st_rec = reinterpret_cast<float4*>(ws);
   int* st_gid = reinterpret_cast<int*>(ws + kStage * 96);
   unsigned long long* k3s = reinterpret_cast<unsigned long long*>(ws + kStage * 100);
-  float* a3s = reinterpret_cast<float*>(ws + kStage * 100 + (size_t)K3 * 256);
+  float* a3s = reinterpret_cast<float*>(ws + kStage * 100 + (size_t)window_key_slots(K3) * 256);
   const int sx = (lane & 1) | ((lane >> 1) & 2) | ((lane >> 2) & 4);
   const int sy = ((lane >> 1) & 1) | ((lane >> 2) & 2);
   const unsigned lt = (1u << lane) - 1u;
@@ -1025,6 +1108,11 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
     w1.pl = 0u;
     w1.n = 0;
     float3 hc = make_float3(0.f, 0.f, 0.f);
+    // per-sample window: tournament tree when K3 <= 16 (every slot starts empty), else ring
+    const bool use_tree = K3 <= 16;
+    unsigned long long tree = kTreeInit;
+    if (use_tree)
+      for (int s3 = 0; s3 < 16; ++s3) k3s[s3 * 32 + lane] = kEmptyKey;
 #pragma unroll
     for (int r = 0; r < Win4<K2>::R; ++r) w2.f[r] = kEmptyKey;
     w2.n = 0;
@@ -1035,7 +1123,12 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
         const float4* r = recv + (long long)g2 * kRecF4;
         float al, t;
         float3 c;
-        if (eval_full<STATS, false>(r, p, al, t, c)) ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, g2), al, c, recv);
+        if (eval_full<STATS, false>(r, p, al, t, c)) {
+          if (use_tree)
+            tree3_push<STATS, BWD>(p, tree, hc, k3s, a3s, K3, lane, pack_key(t, g2), al, c, recv);
+          else
+            ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, g2), al, c, recv);
+        }
       }
     };
     // popped from a 4x4 window (all lanes; x1 and its kept-sample mask m1 are uniform
@@ -1089,7 +1182,10 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
               if (a.stream_order)  // global orders: the list order is the blend order
                 blend_c<STATS, BWD>(p, al, ge, c, recv);
               else
-                ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
+                if (use_tree)
+                  tree3_push<STATS, BWD>(p, tree, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
+                else
+                  ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
             }
           } else {
             bool k = false;
@@ -1117,7 +1213,10 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
       }
       for (int it = 0; it < K2; ++it) pop2(win4_pop<K2>(w2, lane));
     }
-    while (p.n3 > 0 && p.active) ring3_pop<STATS, BWD>(p, hc, k3s, a3s, K3, lane, recv);
+    if (use_tree)
+      while (p.n3 > 0 && p.active) tree3_pop<STATS, BWD>(p, tree, hc, k3s, a3s, lane, recv);
+    else
+      while (p.n3 > 0 && p.active) ring3_pop<STATS, BWD>(p, hc, k3s, a3s, K3, lane, recv);
     if (STATS) {
       n_eval += p.n_eval;
       n_kept += p.n_kept;

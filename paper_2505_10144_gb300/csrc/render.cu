@@ -883,53 +883,84 @@ __device__ __forceinline__ float3 rec_colour(const float4* __restrict__ recv, in
 
 // Per-sample window as a tournament tree over 16 slots (K3 <= 16).  The keys and alphas
 // sit in shared memory, [slot][lane]; the winners (smallest key) of the 15 internal nodes
-// are 4-bit slot numbers in one 64-bit register (node n = 1 .. 15 at bits 4 (n - 1),
-// children 2n and 2n + 1, slot s at node 16 + s).  Putting a key into a slot replays the
-// four matches on the slot's path to the root, so every insertion costs the same: no
-// data-dependent shifting and no divergence.  Unused slots hold kEmptyKey.  hc is the
-// colour of the root winner, loaded when the winner changes.
+// (node n = 1 .. 15, children 2n and 2n + 1, slot s at node 16 + s) are 4-bit slot
+// numbers in two 32-bit registers: nodes 8 .. 15 in lo (nibble n - 8), nodes 1 .. 7 in hi
+// (nibble n - 1), so each level of a replay touches one word with 32-bit shifts.
+// Putting a key into a slot replays the four matches on the slot's path to the root, so
+// every insertion costs the same: no data-dependent shifting and no divergence.  Unused
+// slots hold kEmptyKey.  hc is the colour of the root winner, loaded when it changes.
+struct Tree16 {
+  unsigned lo, hi;
+};
 // every internal node starts with the leftmost slot of its subtree (all slots empty)
-constexpr unsigned long long kTreeInit = 0x0eca86420c840800ull;
-__device__ __forceinline__ int tree_get(unsigned long long t, int node) { return (int)((t >> (4 * (node - 1))) & 0xFull); }
-__device__ __forceinline__ unsigned long long tree_set(unsigned long long t, int node, int slot) {
-  const int sh = 4 * (node - 1);
-  return (t & ~(0xFull << sh)) | ((unsigned long long)slot << sh);
-}
+constexpr unsigned kTreeInitLo = 0xeca86420u, kTreeInitHi = 0x0c840800u;
+__device__ __forceinline__ int tree_root(const Tree16& t) { return (int)(t.hi & 0xFu); }
 
 // key x now sits in slot s: replay s's path; returns the root winner's key
-__device__ __forceinline__ unsigned long long tree_replay(unsigned long long& t, const unsigned long long* kk, int lane,
-                                                         int s, unsigned long long x) {
-  int node = 16 + s, cs = s;
+__device__ __forceinline__ unsigned long long tree_replay(Tree16& t, const unsigned long long* kk, int lane, int s,
+                                                         unsigned long long x) {
+  int cs = s;
   unsigned long long ck = x;
-#pragma unroll
-  for (int lv = 0; lv < 4; ++lv) {
-    const int sib = node ^ 1;
-    const int ss = sib >= 16 ? sib - 16 : tree_get(t, sib);
+  // level 0: leaf s against leaf s ^ 1; the winner goes to node 8 + s / 2 (lo)
+  {
+    const int ss = s ^ 1;
     const unsigned long long sk = kk[ss * 32 + lane];
     if (sk < ck) {
       ck = sk;
       cs = ss;
     }
-    node >>= 1;
-    t = tree_set(t, node, cs);
+    const int sh = 4 * (s >> 1);
+    t.lo = (t.lo & ~(0xFu << sh)) | ((unsigned)cs << sh);
+  }
+  // level 1: node 8 + s / 2 against its sibling (lo); the winner to node 4 + s / 4 (hi)
+  {
+    const int ss = (int)((t.lo >> (4 * ((s >> 1) ^ 1))) & 0xFu);
+    const unsigned long long sk = kk[ss * 32 + lane];
+    if (sk < ck) {
+      ck = sk;
+      cs = ss;
+    }
+    const int sh = 4 * (3 + (s >> 2));
+    t.hi = (t.hi & ~(0xFu << sh)) | ((unsigned)cs << sh);
+  }
+  // level 2: node 4 + s / 4 against its sibling (hi); the winner to node 2 + s / 8 (hi)
+  {
+    const int ss = (int)((t.hi >> (4 * (3 + ((s >> 2) ^ 1)))) & 0xFu);
+    const unsigned long long sk = kk[ss * 32 + lane];
+    if (sk < ck) {
+      ck = sk;
+      cs = ss;
+    }
+    const int sh = 4 * (1 + (s >> 3));
+    t.hi = (t.hi & ~(0xFu << sh)) | ((unsigned)cs << sh);
+  }
+  // level 3: node 2 + s / 8 against its sibling (hi); the winner to the root (hi)
+  {
+    const int ss = (int)((t.hi >> (4 * (1 + ((s >> 3) ^ 1)))) & 0xFu);
+    const unsigned long long sk = kk[ss * 32 + lane];
+    if (sk < ck) {
+      ck = sk;
+      cs = ss;
+    }
+    t.hi = (t.hi & ~0xFu) | (unsigned)cs;
   }
   return ck;
 }
 
 template <bool STATS, bool BWD>
-__device__ __forceinline__ void tree3_push(Px& p, unsigned long long& t, float3& hc, unsigned long long* kk, float* aa,
+__device__ __forceinline__ void tree3_push(Px& p, Tree16& t, float3& hc, unsigned long long* kk, float* aa,
                                            int K3, int lane, unsigned long long x, float alpha, float3 c,
                                            const float4* __restrict__ recv) {
   if (p.n3 < K3) {  // filling: the next free slot
     const int s = p.n3++;
     kk[s * 32 + lane] = x;
     aa[s * 32 + lane] = alpha;
-    const int w0 = tree_get(t, 1);
+    const int w0 = tree_root(t);
     tree_replay(t, kk, lane, s, x);
-    if (tree_get(t, 1) != w0 || s == 0) hc = c;
+    if (tree_root(t) != w0 || s == 0) hc = c;
     return;
   }
-  const int w = tree_get(t, 1);
+  const int w = tree_root(t);
   const unsigned long long m = kk[w * 32 + lane];
   if (x < m) {  // x is the smallest: out at once
     blend_c<STATS, BWD>(p, alpha, (int)(x & 0xffffffffu), c, recv);
@@ -940,16 +971,16 @@ __device__ __forceinline__ void tree3_push(Px& p, unsigned long long& t, float3&
   kk[w * 32 + lane] = x;
   aa[w * 32 + lane] = alpha;
   const unsigned long long nk = tree_replay(t, kk, lane, w, x);
-  const int nw = tree_get(t, 1);
+  const int nw = tree_root(t);
   hc = nw == w ? c : rec_colour(recv, (int)(nk & 0xffffffffu));
   blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);
 }
 
 // pops the root winner and blends it
 template <bool STATS, bool BWD>
-__device__ __forceinline__ void tree3_pop(Px& p, unsigned long long& t, float3& hc, unsigned long long* kk,
+__device__ __forceinline__ void tree3_pop(Px& p, Tree16& t, float3& hc, unsigned long long* kk,
                                           const float* aa, int lane, const float4* __restrict__ recv) {
-  const int w = tree_get(t, 1);
+  const int w = tree_root(t);
   const unsigned long long m = kk[w * 32 + lane];
   const float am = aa[w * 32 + lane];
   const float3 mc = hc;
@@ -1110,7 +1141,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
     float3 hc = make_float3(0.f, 0.f, 0.f);
     // per-sample window: tournament tree when K3 <= 16 (every slot starts empty), else ring
     const bool use_tree = K3 <= 16;
-    unsigned long long tree = kTreeInit;
+    Tree16 tree{kTreeInitLo, kTreeInitHi};
     if (use_tree)
       for (int s3 = 0; s3 < 16; ++s3) k3s[s3 * 32 + lane] = kEmptyKey;
 #pragma unroll

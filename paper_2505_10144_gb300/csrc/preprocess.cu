@@ -301,16 +301,8 @@ __device__ __forceinline__ Span make_span(const float4& bb, const ViewParams& vp
   return sp;
 }
 
-__device__ __forceinline__ float4 shfl4(const float4& v, int src) {
-  return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-                     __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
-}
-
-// Gaussians whose rectangle holds at most kLaneTiles tiles test them in their own lane
-// (most Gaussians: a few 32x32 tiles).  The warp then walks the larger ones one at a
-// time, its 32 lanes testing 32 tiles of the current Gaussian's rectangle at once, so a
-// Gaussian covering many tiles does not serialise a thread.  Both walks call the same
-// tile_keep, so the count and the emit pass make the same decisions.
+// The emit pass tests the tiles of a Gaussian in its own lane when its rectangle holds
+// at most kLaneTiles tiles, and with the whole warp otherwise.
 constexpr int kLaneTiles = 8;
 
 // The count pass also keeps the sort keys of a Gaussian's first kKeyCache kept tiles
@@ -335,13 +327,24 @@ __device__ __forceinline__ float order_key(int key_mode, float tile_key, const f
   return tile_key;
 }
 
+// The count pass works in two phases per view.  Each thread projects its Gaussian (record,
+// rectangle, span of key tiles).  Then the warp flattens the (Gaussian, tile) pairs of its
+// 32 Gaussians into one list and tests 32 of them per step, one per lane: a lane finds
+// its pair's Gaussian by a binary search over the warp's running tile counts and reads
+// that Gaussian's record (written in the first phase) from memory.  Every lane works
+// whatever the tile counts of the Gaussians, so few and many tiles, and culled
+// Gaussians, cost no idle lanes.  Kept tiles are counted per Gaussian in shared memory,
+// and ranked within their Gaussian in tile order for the key cache.
 __global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const ViewParams* __restrict__ views,
                                                             const int* __restrict__ view_list, int nv, int T,
                                                             int key_mode, Visibility vis, float4* __restrict__ rec,
                                                             float4* __restrict__ bbox, uint32_t* __restrict__ count,
                                                             unsigned long long* __restrict__ kcache) {
+  __shared__ uint32_t s_cnt[256];
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
+  uint32_t* wc = s_cnt + (threadIdx.x & ~31);  // this warp's 32 counters
+  const long long warp_i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
   const bool in = i < s.n;
   for (int k = 0; k < nv; ++k) {
     const int view = view_list[k];
@@ -356,61 +359,69 @@ __global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const Vi
         sat_count(vis, view, vp.ntx, sp.tx0, sp.ty0, sp.tx0 + sp.nx - 1, sp.ty0 + sp.nt / sp.nx - 1) == 0)
       sp.nt = 0;
     const uint8_t* tv = vis.tvis ? vis.tvis + (long long)view * vis.tiles_per_view : nullptr;
-    uint32_t mine = 0;
-    unsigned long long* kc = kcache + vg * kKeyCache;
-    if (sp.nt <= kLaneTiles) {
-      for (int t = 0; t < sp.nt; ++t) {
-        float x0, y0, x1, y1;
-        const int tx = sp.tx0 + t % sp.nx, ty = sp.ty0 + t / sp.nx;
-        if (tv && !tv[ty * vp.ntx + tx]) continue;
-        tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
-        const Keep kp = tile_keep(r[0], r[1], r[2], r[3], r[4], r[5].x, x0, y0, x1, y1);
-        if (kp.keep) {
-          if (mine < kKeyCache) kc[mine] = local_key(ty * vp.ntx + tx, order_key(key_mode, kp.key, r[0], r[3], vp));
-          ++mine;
-        }
-      }
-    }
-    unsigned todo = __ballot_sync(0xffffffffu, sp.nt > kLaneTiles);
-    while (todo) {
-      const int j = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const float4 g0 = shfl4(r[0], j), g1 = shfl4(r[1], j), g2 = shfl4(r[2], j), g3 = shfl4(r[3], j),
-                   g4 = shfl4(r[4], j);
-      const float g5x = __shfl_sync(0xffffffffu, r[5].x, j);
-      const int tx0 = __shfl_sync(0xffffffffu, sp.tx0, j), ty0 = __shfl_sync(0xffffffffu, sp.ty0, j);
-      const int nx = __shfl_sync(0xffffffffu, sp.nx, j), nt = __shfl_sync(0xffffffffu, sp.nt, j);
-      unsigned long long* kcj = kcache + (vp.base + (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31) + j) * kKeyCache;
-      uint32_t c = 0;
-      for (int b = 0; b < nt; b += 32) {
-        Keep kp{false, 0.f};
-        const int t = b + lane;
-        int tile = 0;
-        if (t < nt) {
-          float x0, y0, x1, y1;
-          const int tx = tx0 + t % nx, ty = ty0 + t / nx;
-          tile = ty * vp.ntx + tx;
-          if (!tv || tv[tile]) {
-            tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
-            kp = tile_keep(g0, g1, g2, g3, g4, g5x, x0, y0, x1, y1);
-          }
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, kp.keep);
-        const uint32_t slot = c + __popc(bal & ((1u << lane) - 1u));
-        if (kp.keep && slot < kKeyCache) kcj[slot] = local_key(tile, order_key(key_mode, kp.key, g0, g3, vp));
-        c += __popc(bal);
-      }
-      if (lane == j) mine = c;
-    }
     if (in) {
-      if (mine) {
+      bbox[vg] = bb;
+      if (sp.nt > 0) {
         float4* dst = rec + vg * kRecF4;
 #pragma unroll
         for (int q = 0; q < kRecF4; ++q) dst[q] = r[q];
       }
-      bbox[vg] = bb;
-      count[vg] = mine;
     }
+    // running tile counts of the warp's Gaussians (inclusive scan)
+    unsigned endc = (unsigned)sp.nt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, endc, o);
+      if (lane >= o) endc += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, endc, 31);
+    wc[lane] = 0u;
+    __syncwarp();  // records and counters visible to the warp
+    for (unsigned b = 0; b < total; b += 32) {
+      const unsigned t = b + lane;
+      // owner: the number of Gaussians whose tiles end at or before t
+      int own = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const unsigned e = __shfl_sync(0xffffffffu, endc, own + step - 1);
+        if (e <= t) own += step;
+      }
+      own = t < total ? own : 0;
+      const int nt_o = __shfl_sync(0xffffffffu, sp.nt, own), tx0 = __shfl_sync(0xffffffffu, sp.tx0, own),
+                ty0 = __shfl_sync(0xffffffffu, sp.ty0, own), nx = __shfl_sync(0xffffffffu, sp.nx, own);
+      const unsigned end_o = __shfl_sync(0xffffffffu, endc, own);
+      Keep kp{false, 0.f};
+      int tile = 0;
+      float4 f0, f3;
+      if (t < total) {
+        const int kk = (int)(t - (end_o - (unsigned)nt_o));
+        const int tx = tx0 + kk % nx, ty = ty0 + kk / nx;
+        tile = ty * vp.ntx + tx;
+        if (!tv || tv[tile]) {
+          const float4* ro = rec + (vp.base + warp_i0 + own) * kRecF4;
+          f0 = ro[0];
+          f3 = ro[3];
+          float x0, y0, x1, y1;
+          tile_quad(tx, ty, T, vp, x0, y0, x1, y1);
+          kp = tile_keep(f0, ro[1], ro[2], f3, ro[4], ro[5].x, x0, y0, x1, y1);
+        }
+      }
+      // rank among this step's kept tiles of the same Gaussian (tile order)
+      const unsigned bal = __ballot_sync(0xffffffffu, kp.keep);
+      const unsigned peers = __match_any_sync(0xffffffffu, t < total ? own : 32 + lane);
+      const unsigned mine_kept = bal & peers;
+      const uint32_t base = wc[own];
+      __syncwarp();
+      if (kp.keep) {
+        const uint32_t slot = base + __popc(mine_kept & ((1u << lane) - 1u));
+        if (slot < kKeyCache)
+          kcache[(vp.base + warp_i0 + own) * kKeyCache + slot] = local_key(tile, order_key(key_mode, kp.key, f0, f3, vp));
+        if ((mine_kept & ((1u << lane) - 1u)) == 0u) wc[own] = base + __popc(mine_kept);
+      }
+      __syncwarp();
+    }
+    if (in) count[vg] = wc[lane];
+    __syncwarp();
   }
 }
 

@@ -445,15 +445,40 @@ __global__ void __launch_bounds__(256) duplicate_kernel(const ViewParams* __rest
   const uint64_t vbase = (uint64_t)view * (uint64_t)tiles_per_view;
   const uint32_t lt = (1u << lane) - 1u;
   const uint8_t* tv = tvis ? tvis + (long long)view * tiles_per_view : nullptr;
-  if (cnt > 0 && cnt <= kKeyCache) {  // the count pass kept these keys
-    const unsigned long long* kc = kcache + vg * kKeyCache;
-    const long long o = offsets[vg];
-    for (uint32_t q = 0; q < cnt; ++q) {
-      if (o + q < cap) {
-        keys[o + q] = kc[q] + (vbase << 32);
-        vals[o + q] = (uint32_t)i;
-      } else {
-        atomicOr(status, kStOverflow);
+  // Gaussians with at most kKeyCache instances: the count pass kept their keys.  The
+  // warp copies them as one flattened list, one instance per lane (owner by binary
+  // search over the running counts), so the writes of consecutive Gaussians coalesce.
+  {
+    const long long warp_i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    const unsigned c = cnt <= kKeyCache ? cnt : 0u;
+    unsigned endc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, endc, o);
+      if (lane >= o) endc += y;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, endc, 31);
+    const long long myoff = c ? (long long)offsets[vg] : 0;
+    for (unsigned b = 0; b < total; b += 32) {
+      const unsigned t = b + lane;
+      int own = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const unsigned e = __shfl_sync(0xffffffffu, endc, own + step - 1);
+        if (e <= t) own += step;
+      }
+      own = t < total ? own : 0;
+      const unsigned end_o = __shfl_sync(0xffffffffu, endc, own), c_o = __shfl_sync(0xffffffffu, c, own);
+      const long long off_o = __shfl_sync(0xffffffffu, myoff, own);
+      if (t < total) {
+        const unsigned q = t - (end_o - c_o);
+        const long long o = off_o + q;
+        if (o < cap) {
+          keys[o] = kcache[(vp.base + warp_i0 + own) * kKeyCache + q] + (vbase << 32);
+          vals[o] = (uint32_t)(warp_i0 + own);
+        } else {
+          atomicOr(status, kStOverflow);
+        }
       }
     }
   }

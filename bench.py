@@ -17,6 +17,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -116,34 +117,33 @@ def crop_camera(cam, x0, y0, w, h):
     return synth.Camera(cam.world_to_cam, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, w, h, cam.near_z)
 
 
-def oracle_frame_estimate(scene64, frame, budget_s=20.0, bands=None):
-    """Seconds per stereo frame of the FP64 oracle, from a bounded sample of the same
-    foveated, hierarchical frame: full-width bands of 64 rows of eye 0 (one through the
-    gaze point, others in the periphery), each rendered by the oracle as it stands (the
-    band is the frame with the principal point shifted, so every sample is the frame's).
-    The per-row cost scales to the image height; the per-view fixed cost (projection of
-    every Gaussian) is measured on a 32-row band and counted once per eye.
-    Returns (seconds_per_frame, description, threads)."""
+def oracle_view_estimate(scene64, cam, fv, mode, key_tile, budget_s, bands):
+    """Seconds per view of the FP64 oracle, from a bounded sample of the view: full-width
+    bands of 64 rows, each rendered by the oracle as it stands (the band is the view with
+    the principal point shifted, so every sample is the view's).  The per-row cost scales
+    to the image height; the per-view fixed cost (projection of every Gaussian) is
+    measured on a 32-row band and counted once.  fv None renders plain (no fovea).
+    Returns (seconds_per_view, bands used, samples)."""
     from oracle import native as on
     from paper_2505_10144_gb300 import synth
     on.build()
-    cam, fv = frame.cameras[0], frame.foveas[0]
+    W, H = int(cam.width), int(cam.height)
 
     def band(y0, h):
-        c = crop_camera(cam, 0, y0, W_IMG, h)
-        f = synth.Fovea(fv.gaze_x, fv.gaze_y - y0, fv.radius_px, fv.band_px)
+        c = crop_camera(cam, 0, y0, W, h)
+        f = None if fv is None else synth.Fovea(fv.gaze_x, fv.gaze_y - y0, fv.radius_px, fv.band_px)
         t = time.perf_counter()
-        r = on.render(scene64, c, "hier", WINDOWS, 32, f)
+        r = on.render(scene64, c, mode, WINDOWS, key_tile, f)
         return time.perf_counter() - t, r["stats"]["samples"]
 
     # fixed cost from two heights of the same band: t(h) = fixed + h * per_row
-    yg = min(max(int(fv.gaze_y) - 32, 0), H_IMG - 64) // 32 * 32
+    yc = H // 2 if fv is None else int(fv.gaze_y)
+    yg = min(max(yc - 32, 0), H - 64) // 32 * 32
     t32, t64 = band(yg, 32)[0], band(yg, 64)[0]
     t_fixed = max(t32 - (t64 - t32), 0.0)
-    ys = bands or [int(fv.gaze_y), 256, 1792, 1024]
     rows, t_rows, samples, used = 0, 0.0, 0, 0
-    for y in ys:
-        y = min(max(y, 0), H_IMG - 64) // 32 * 32
+    for y in bands:
+        y = min(max(y, 0), H - 64) // 32 * 32
         dt, ns = band(y, 64)
         t_rows += max(dt - t_fixed, 0.0)
         rows += 64
@@ -151,10 +151,56 @@ def oracle_frame_estimate(scene64, frame, budget_s=20.0, bands=None):
         used += 1
         if t_rows + used * t_fixed > budget_s:
             break
-    sec = 2 * (t_fixed + t_rows / rows * H_IMG)
+    return t_fixed + t_rows / rows * H, used, samples
+
+
+def oracle_frame_estimate(scene64, frame, budget_s=20.0, bands=None):
+    """Seconds per stereo frame of the FP64 oracle on the foveated, hierarchical frame:
+    bands of eye 0 (one through the gaze point, others in the periphery), x 2 eyes.
+    Returns (seconds_per_frame, description, threads)."""
+    from oracle import native as on
+    cam, fv = frame.cameras[0], frame.foveas[0]
+    sec, used, samples = oracle_view_estimate(scene64, cam, fv, "hier", 32, budget_s,
+                                              bands or [int(fv.gaze_y), 256, 1792, 1024])
     desc = (f"FP64 oracle, hierarchical 4/8/16, foveated: {used} full-width bands of 64 rows ({samples} samples) "
             f"of eye 0, per-row cost scaled to {H_IMG} rows, plus the per-view fixed cost, x 2 eyes")
-    return sec, desc, on.num_threads()
+    return 2 * sec, desc, on.num_threads()
+
+
+def oracle_other_workloads(scene64, frame, budget_s=8.0):
+    """The oracle on the other workloads, each from a bounded sample like the headline
+    estimate: the plain stereo frame (full resolution, 16x16 tiles), the 256^2 10k-Gaussian
+    single view in exact order (rendered whole), and one 1280^2 view of the 500k-Gaussian
+    fine-tuning scene (forward render only, x 4 views)."""
+    from oracle import native as on
+    from paper_2505_10144_gb300 import synth
+    out = {}
+    sec, used, _ = oracle_view_estimate(scene64, frame.cameras[0], None, "hier", 16, budget_s, [256, 1024, 1792])
+    out["plain_stereo_frame_s"] = 2 * sec
+    out["plain_sample"] = f"{used} bands of 64 rows of eye 0, x 2 eyes"
+    sc = synth.tiny_scene(10_000, synth.rng_for(0))
+    sc64 = synth.Scene(*[np.ascontiguousarray(a, dtype=np.float64) for a in sc.arrays()], sc.sh_degree)
+    t = time.perf_counter()
+    on.render(sc64, synth.identity_camera(256, 256, 90.0), "exact", key_tile=16)
+    out["single_view_256_10k_exact_s"] = time.perf_counter() - t
+    ft = synth.shell_scene(N_GAUSS, synth.rng_for(3), sh_degree=3)
+    ft64 = synth.Scene(*[np.ascontiguousarray(a, dtype=np.float64) for a in ft.arrays()], ft.sh_degree)
+    cam = synth.ring_views(4, 1280, 1280, 110.0, synth.rng_for(3, salt=1))[0]
+    sec, used, _ = oracle_view_estimate(ft64, cam, None, "hier", 16, budget_s, [128, 640, 1088])
+    out["finetune_4x1280_forward_s"] = 4 * sec
+    out["finetune_sample"] = f"{used} bands of 64 rows of view 0, x 4 views (forward render only)"
+    return out
+
+
+def cpu_model() -> str:
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
 
 
 def run_reference(args, ws, rank):
@@ -446,6 +492,89 @@ def profiled_traffic():
         return None, "no ncu traffic summary", None
 
 
+def order_flips(ids_a, len_a, ids_b, len_b, torch, batch=256):
+    """Frame-to-frame order flips of probe rays: for each probe, the pairs of Gaussians
+    blended in both frames whose front-to-back order differs (the Kendall distance of the
+    two blend orders restricted to their common Gaussians).  ids [P, L] int32 padded,
+    len [P].  Returns (total flips, probes with a flip, common pairs)."""
+    P, L = ids_a.shape
+    ar = torch.arange(L, device=ids_a.device)
+    flips = flipped = common = 0
+    upper = ar[:, None] < ar[None, :]
+    for s0 in range(0, P, batch):
+        a, b = ids_a[s0:s0 + batch].long(), ids_b[s0:s0 + batch].long()
+        va = ar[None, :] < len_a[s0:s0 + batch, None].clamp(max=L)
+        vb = ar[None, :] < len_b[s0:s0 + batch, None].clamp(max=L)
+        m = (a[:, :, None] == b[:, None, :]) & va[:, :, None] & vb[:, None, :]
+        has = m.any(-1)
+        pos = torch.where(has, m.float().argmax(-1), torch.full_like(a, -1))
+        both = has[:, :, None] & has[:, None, :] & upper[None]
+        inv = both & (pos[:, :, None] > pos[:, None, :])
+        per = inv.sum((1, 2))
+        flips += int(per.sum())
+        flipped += int((per > 0).sum())
+        common += int(both.sum())
+    return flips, flipped, common
+
+
+def popping(api, ds, wl, cfg, torch, n_steps=12, grid=16, max_len=512):
+    """Popping of an order as order flips on unchanged world rays.  Each step takes eye
+    0 of a trajectory frame (camera A) and the next frame's viewing rotation about the
+    same eye position (camera B).  Rays through the pixel centres of a grid of A are
+    probed in A and, at the image points where the same world rays land, in B
+    (vrs_probe_orders); a flip is a pair of Gaussians the ray blends in both in the
+    opposite order.  A per-ray order depends on the ray alone, so it cannot flip here
+    (up to FP32 near-ties); an order keyed per Gaussian by the viewing direction can."""
+    from paper_2505_10144_gb300 import synth
+    ys, xs = np.mgrid[grid // 2:H_IMG:grid, grid // 2:W_IMG:grid]
+    px, py = xs.ravel() + 0.5, ys.ravel() + 0.5
+    steps = []
+    for f in range(n_steps):
+        ca, nxt = wl.frames[f].cameras[0], wl.frames[f + 1].cameras[0]
+        Ra = ca.world_to_cam[:, :3].astype(np.float64)
+        cb = synth.camera_from_pose(nxt.world_to_cam[:, :3].astype(np.float64).T, ca.center(), ca.width, ca.height,
+                                    ca.fx, ca.fy, ca.near_z, ca.cx, ca.cy)
+        Rb = cb.world_to_cam[:, :3].astype(np.float64)
+        d = np.stack([(px - ca.cx) / ca.fx, (py - ca.cy) / ca.fy, np.ones_like(px)])
+        db = Rb @ (Ra.T @ d)
+        z = np.where(db[2] > 1e-6, db[2], 1.0)
+        qx, qy = ca.fx * db[0] / z + ca.cx, ca.fy * db[1] / z + ca.cy
+        inside = (db[2] > 1e-6) & (qx >= 0) & (qx < W_IMG) & (qy >= 0) & (qy < H_IMG)
+        pa = np.stack([np.zeros(inside.sum()), px[inside], py[inside]], 1)
+        pb = np.stack([np.zeros(inside.sum()), qx[inside], qy[inside]], 1)
+        ang = np.degrees(np.arccos(np.clip((np.trace(Rb @ Ra.T) - 1) / 2, -1, 1)))
+        steps.append((ca, cb, wl.frames[f].foveas[0], torch.tensor(pa, dtype=torch.float32, device="cuda"),
+                      torch.tensor(pb, dtype=torch.float32, device="cuda"), ang))
+    R = api.Renderer()
+    out = {}
+    for mode in ("exact", "global_z", "global_dist"):
+        mcfg = api.RenderConfig(**{**cfg.__dict__, "sort_mode": mode})
+        tot = {"flips": 0, "flipped": 0, "common": 0, "blended": 0, "truncated": 0, "rays": 0}
+        for ca, cb, fv, pa, pb, _ in steps:
+            R.render([ds], [0], [ca], [fv], mcfg)
+            ids_a, _, la = R.probe_orders(pa, max_len)
+            R.render([ds], [0], [cb], [fv], mcfg)
+            ids_b, _, lb = R.probe_orders(pb, max_len)
+            R.check()
+            fl, fp, cm = order_flips(ids_a, la, ids_b, lb, torch)
+            tot["flips"] += fl
+            tot["flipped"] += fp
+            tot["common"] += cm
+            tot["blended"] += int(la.clamp(min=0).sum())
+            tot["truncated"] += int((la > max_len).sum() + (lb > max_len).sum())
+            tot["rays"] += pa.shape[0]
+        n = max(tot["rays"], 1)
+        out[mode] = {"flips_per_ray_per_step": tot["flips"] / n, "rays_with_flip_pct": 100.0 * tot["flipped"] / n,
+                     "flipped_pairs_pct": 100.0 * tot["flips"] / max(tot["common"], 1),
+                     "blended_per_ray": tot["blended"] / n, "truncated_rays": tot["truncated"]}
+    R.close()
+    out["config"] = (f"{n_steps} steps of the trajectory (72 Hz), each the next frame's viewing rotation about the "
+                     f"same eye position (mean {np.mean([s[5] for s in steps]):.2f} deg); rays through the pixel "
+                     f"centres of a {grid}-pixel grid of eye 0 that stay in view ({tot['rays'] // n_steps} per step), "
+                     f"foveated frames")
+    return out
+
+
 def psnr(a, b):
     mse = float(((a - b) ** 2).mean())
     return float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
@@ -494,6 +623,8 @@ def main():
     if args.workload == "net":
         run_net(args, api, torch, ws, rank)
         return
+    # measured denominators of the render roofline (microbenchmarks, a few ms each)
+    peaks = api.measure_peaks()
     n_frames = args.warmup + args.steps
     scene, wl = make_workload(n_frames, rank)
     ds = api.DeviceScene.from_host(scene)
@@ -649,6 +780,7 @@ def main():
                              "ms_per_step": statistics.mean(ms_q), "psnr_vs_exact_db": psnr(q_img, ex_img)}
         del Gq
         Rq.close()
+    global_orders["popping"] = popping(api, ds, wl, fov_cfg, torch)
     global_orders["hier_4_8_16_psnr_vs_exact_db"] = psnr(R.render([ds], [0, 0], fr1.cameras, fr1.foveas, fov_cfg),
                                                           ex_img)
     two_pass = {"value": len(ms_tp) / (sum(ms_tp) / 1e3), "unit": "frames/s", "ms_per_step": statistics.mean(ms_tp),
@@ -680,8 +812,10 @@ def main():
     clocks = clk.summary()
     props = torch.cuda.get_device_properties(local)
     sm_mhz = clocks["sm_mhz"] or 2070.0
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    derived_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    peak_tflops = peaks["fp32_tflops"]
     achieved = flops / (render_ms / 1e3) / 1e12 if render_ms > 0 else 0.0
+    exp2_rate = cnt["kept"] / (render_ms / 1e3) / 1e9 if render_ms > 0 else 0.0
     traffic, traffic_note, issue_busy = profiled_traffic()
     roofline = {"bound": "alu", "kernel": "warp_render_kernel<4,8> (hierarchical 4/8/16)", "achieved": achieved,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops if peak_tflops else None,
@@ -689,8 +823,12 @@ def main():
                 "issue_slots_busy_ncu": issue_busy,
                 "note": "the kernel is bound by instruction issue (window bookkeeping: shuffles, shared memory, "
                         "compares), so its FP32-FLOP fraction is low while its issue slots are mostly busy",
-                "peak_source": f"FP32 FMA peak: {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{sm_mhz:.0f} MHz (median SM clock under load)",
+                "peak_source": "of measured: FFMA microbenchmark (vrs_measure_peaks, 64 warps per SM, best of 5); "
+                               f"derived {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                               f"{sm_mhz:.0f} MHz = {derived_tflops:.1f} TFLOP/s",
+                "exp2": {"achieved_gops": exp2_rate, "peak_gops": peaks["exp2_gops"],
+                         "frac": exp2_rate / peaks["exp2_gops"] if peaks["exp2_gops"] else None,
+                         "per_launch": cnt["kept"], "note": "one exp2f per kept pair (the pair opacity)"},
                 "work_per_launch": {"evaluated_pairs": cnt["evaluated"], "kept_pairs": cnt["kept"],
                                     "blended_pairs": cnt["blended"], "flops": flops},
                 "avg_launch_ms": render_ms}
@@ -746,6 +884,7 @@ def main():
                         "eyes into pinned memory"},
         "gpu_launches": kernels_per_frame * args.steps,
         "clocks": clocks,
+        "measured_peaks": peaks,
         "wall_s_timed_region": t_wall,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -753,7 +892,8 @@ def main():
         scene64 = synth.Scene(*[np.ascontiguousarray(a, dtype=np.float64) for a in scene.arrays()], scene.sh_degree)
         sec, desc, thr = oracle_frame_estimate(scene64, wl.frames[0])
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "frames/s", "cores": thr, "kind": "oracle",
-                                "sample": desc, "host_cpus": os.cpu_count()}
+                                "sample": desc, "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
+                                "other_workloads": oracle_other_workloads(scene64, wl.frames[0])}
     if rank == 0:
         print(json.dumps(line), flush=True)
     R.close()

@@ -300,6 +300,50 @@ vrs_status vrs_adam_step(float* d_param, const float* d_grad, float* d_m, float*
 vrs_status vrs_profile_begin(vrs_ctx* ctx, int max_calls);
 vrs_status vrs_profile_end(vrs_ctx* ctx, void* stream, double* h_stage_ms, int64_t* n_calls);
 
+/* Blend order of single rays of the last vrs_render of this context (its views, sort
+ * mode, records and tile lists must be unchanged since).  d_probes is a device array
+ * [n_probes][3] of (view, x, y) floats: the ray through image point (x, y) of that view,
+ * in pixels (pixel (i, j) has its centre at (i + 0.5, j + 0.5); a half-resolution
+ * periphery sample of the foveated render sits at (2i + 1, 2j + 1)).  For each probe
+ * the Gaussians the ray blends, front to back, are written to d_ids[probe][max_len]
+ * (indices into the view's scene) and their depths t* (Sec. 4.1) to
+ * d_depth[probe][max_len] (d_depth may be NULL); d_len[probe] receives the number of
+ * blended pairs (entries past max_len are counted but not written) or -1 for a probe
+ * outside its view.  The pairs and their values are the render's own (same evaluation);
+ * the order is the render's sort mode: 0 exact (ascending depth, then index) or 3 / 4
+ * (global orders: tile-list order).  Blending stops before the pair that would take the
+ * transmittance below 1e-4.  Sort modes 1 and 2 return VRS_ERR_UNSUPPORTED: their
+ * windows order a ray by the pairs of its neighbours too.  Asynchronous on `stream`;
+ * all arrays are caller-owned device memory. */
+vrs_status vrs_probe_orders(vrs_ctx* ctx, const float* d_probes, int n_probes, int max_len, int32_t* d_ids,
+                            float* d_depth, int32_t* d_len, void* stream);
+
+/* Measured throughput peaks of the current device, the denominators of the render
+ * kernel's roofline (the render is bound by instruction issue on plain FP32, integer and
+ * special-function work, and reads its records from L2).  Runs microbenchmarks of a few
+ * milliseconds each on `stream` and synchronises it; allocates and frees about 2 GiB of
+ * scratch; needs no context.  Every rate is the best of five timed launches after one
+ * untimed launch, with 64 warps per SM and eight independent chains per thread:
+ *   fp32_tflops   FFMA throughput, 2 flop per FMA (1e12 flop/s)
+ *   exp2_gops     exp2f(c - x) throughput, the pair-opacity exponent (1e9 per s)
+ *   logic_gops    32-bit three-input logic throughput (1e9 operations per s)
+ *   l2_read_gbs   read bandwidth of a buffer of a quarter of the L2, read 256 times
+ *                 with L2-only loads (1e9 B/s)
+ *   dram_read_gbs read bandwidth of 2 GiB streamed once from HBM (1e9 B/s)
+ * sm_count, max_sm_clock_khz and l2_bytes are the runtime's device attributes.
+ * Returns VRS_ERR_INVALID for a NULL `out`, VRS_ERR_CUDA on any runtime error. */
+typedef struct {
+  int sm_count;
+  int max_sm_clock_khz;
+  int64_t l2_bytes;
+  double fp32_tflops;
+  double exp2_gops;
+  double logic_gops;
+  double l2_read_gbs;
+  double dram_read_gbs;
+} vrs_peaks;
+vrs_status vrs_measure_peaks(vrs_peaks* out, void* stream);
+
 const char* vrs_last_error(vrs_ctx* ctx);
 
 #ifdef __cplusplus

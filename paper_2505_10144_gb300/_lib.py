@@ -36,12 +36,18 @@ class RenderOpts(C.Structure):
                 ("stats", C.c_int)]
 
 
+class Peaks(C.Structure):
+    _fields_ = [("sm_count", C.c_int), ("max_sm_clock_khz", C.c_int), ("l2_bytes", C.c_int64),
+                ("fp32_tflops", C.c_double), ("exp2_gops", C.c_double), ("logic_gops", C.c_double),
+                ("l2_read_gbs", C.c_double), ("dram_read_gbs", C.c_double)]
+
+
 # every symbol include/vrsplat.h declares
 EXPORTED = ["vrs_create", "vrs_destroy", "vrs_reserve", "vrs_render", "vrs_render_backward", "vrs_check_status",
             "vrs_get_stats", "vrs_copy_instances", "vrs_project", "vrs_sort_pairs", "vrs_loss_l1_ssim",
             "vrs_adam_step", "vrs_profile_begin", "vrs_profile_end", "vrs_sort_pairs_noalloc", "vrs_update_views", "vrs_set_tuning",
             "vrs_net_forward", "vrs_net_backward", "vrs_net_periphery", "vrs_mse", "vrs_render_two_pass",
-            "vrs_last_error"]
+            "vrs_measure_peaks", "vrs_probe_orders", "vrs_last_error"]
 
 _lib = None
 
@@ -86,6 +92,8 @@ def load() -> C.CDLL:
     lib.vrs_mse.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.vrs_profile_begin.argtypes = [vp, i32]
     lib.vrs_profile_end.argtypes = [vp, vp, P(C.c_double), P(i64)]
+    lib.vrs_measure_peaks.argtypes = [P(Peaks), vp]
+    lib.vrs_probe_orders.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
     lib.vrs_last_error.argtypes = [vp]
     lib.vrs_last_error.restype = C.c_char_p
     for name in EXPORTED:

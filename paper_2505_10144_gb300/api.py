@@ -217,6 +217,19 @@ class Renderer:
         m = int(n.value)
         return keys[:m], vals[:m], ranges
 
+    def probe_orders(self, probes: torch.Tensor, max_len: int = 256, stream=None):
+        """Blend order of single rays of the last render (exact or global sort modes):
+        probes [n, 3] float32 (view, x, y) on the device -> (ids [n, max_len] int32,
+        depth [n, max_len] float32, length [n] int32; -1 for a probe outside its view)."""
+        probes = probes.to(torch.float32).contiguous()
+        n = probes.shape[0]
+        ids = torch.full((n, max_len), -1, dtype=torch.int32, device=probes.device)
+        depth = torch.zeros((n, max_len), dtype=torch.float32, device=probes.device)
+        length = torch.zeros(n, dtype=torch.int32, device=probes.device)
+        self._check(self.lib.vrs_probe_orders(self.ctx, _ptr(probes), n, max_len, _ptr(ids), _ptr(depth),
+                                              _ptr(length), _stream(stream)))
+        return ids, depth, length
+
     def update_views(self, cams, foveas=None, cfg: RenderConfig | None = None, visible=None):
         """New cameras / gaze for the next replay of a captured render (same view count;
         visibility masks present exactly where the captured render had them)."""
@@ -280,6 +293,17 @@ def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch
                            _stream(stream))
     if st != 0:
         raise VrsError(st, "vrs_adam_step failed")
+
+
+def measure_peaks(stream=None) -> dict:
+    """Measured FP32 FMA, exp2f and logic throughputs and L2 / HBM read bandwidths of the
+    current device (vrs_measure_peaks), with its SM count, maximum SM clock and L2 size."""
+    lib = _lib.load()
+    p = _lib.Peaks()
+    st = lib.vrs_measure_peaks(C.byref(p), _stream(stream))
+    if st != 0:
+        raise VrsError(st, "vrs_measure_peaks failed")
+    return {name: getattr(p, name) for name, _ in p._fields_}
 
 
 class RenderFunction(torch.autograd.Function):

@@ -27,6 +27,10 @@ void net_periphery(const float* params, const float* low, float* out, const uint
 vrs_status loss_l1_ssim_impl(const float* img, const float* tgt, int n, int H, int W, float* loss, float* grad,
                              void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t loss_scratch_bytes(int n, int H, int W);
+void launch_probe_orders(const ViewParams* views, int n_views, const float4* rec, const uint32_t* vals,
+                         const uint32_t* ranges, int key_tile, int tiles_per_view, int list_order,
+                         const float* probes, int n, int max_len, int* ids, float* depth, int* len,
+                         cudaStream_t st);
 }  // namespace vrs
 
 namespace {
@@ -781,6 +785,24 @@ vrs_status vrs_copy_instances(vrs_ctx* c, uint64_t* d_keys, uint32_t* d_vals, ui
                     cudaMemcpyDeviceToDevice, st);
   e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "copy instances");
+}
+
+vrs_status vrs_probe_orders(vrs_ctx* c, const float* d_probes, int n_probes, int max_len, int32_t* d_ids,
+                            float* d_depth, int32_t* d_len, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (n_probes < 0 || max_len < 0 || (n_probes > 0 && (!d_probes || !d_ids || !d_len)))
+    return fail(c, VRS_ERR_INVALID, "bad probe arguments");
+  const Saved& sv = c->saved;
+  if (sv.n_views <= 0 || !c->rec.p || !c->ranges.p) return fail(c, VRS_ERR_INVALID, "no render to probe");
+  if (sv.sort_mode != 0 && sv.sort_mode != 3 && sv.sort_mode != 4)
+    return fail(c, VRS_ERR_UNSUPPORTED, "probes follow the exact and global orders only");
+  if (n_probes == 0) return VRS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_probe_orders(P<ViewParams>(c->views), sv.n_views, P<float4>(c->rec), P<uint32_t>(c->vals[sv.sorted_buf]),
+                      P<uint32_t>(c->ranges), sv.key_tile, sv.tiles_per_view, sv.sort_mode >= 3 ? 1 : 0, d_probes,
+                      n_probes, max_len, d_ids, d_depth, d_len, st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "probe launch");
 }
 
 vrs_status vrs_project(vrs_ctx* c, const vrs_gaussians* scene, const vrs_camera* cam, int key_tile, float* d_out,

@@ -39,7 +39,7 @@ def test_binding_structs_match_header_sizes(tmp_path):
     the header's structs."""
     from paper_2505_10144_gb300 import _lib
     pairs = {"vrs_gaussians": _lib.Gaussians, "vrs_gaussian_grads": _lib.GaussianGrads,
-             "vrs_camera": _lib.Camera, "vrs_fovea": _lib.Fovea, "vrs_render_opts": _lib.RenderOpts}
+             "vrs_camera": _lib.Camera, "vrs_fovea": _lib.Fovea, "vrs_render_opts": _lib.RenderOpts, "vrs_peaks": _lib.Peaks}
     lines = ['#include <stdio.h>', '#include "vrsplat.h"', "int main(void) {"]
     for cname, cls in pairs.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')

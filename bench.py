@@ -261,11 +261,21 @@ def ncu_case(args, api, torch):
     R = api.Renderer()
     cfg = api.RenderConfig(sort_mode=args.mode, windows=WINDOWS, key_tile=32, fovea_mode="bilinear")
     out = torch.empty((2, 3, H, W), device="cuda")
+    grads = ds.zeros_like() if args.backward else None
+    dout = torch.randn((2, 3, H, W), device="cuda", generator=torch.Generator("cuda").manual_seed(7)) * 1e-3 \
+        if args.backward else None
     for fr in wl.frames:
-        R.render([ds], [0, 0], fr.cameras, fr.foveas, cfg, out=out)
+        R.render([ds], [0, 0], fr.cameras, fr.foveas, cfg, out=out, save=args.backward)
+        if args.backward:  # the replay of the same frame, one backward launch per forward launch
+            R.backward([ds], [0, 0], fr.cameras, fr.foveas, cfg, dout, [grads])
     R.check()
     torch.cuda.synchronize()
-    print(json.dumps({"ncu_case": True, "width": W, "height": H, "frames": len(wl.frames), **R.stats()}))
+    st = R.stats()
+    if args.stats:  # device counters of the last frame, from one more render with counters on
+        fr = wl.frames[-1]
+        R.render([ds], [0, 0], fr.cameras, fr.foveas, api.RenderConfig(**{**cfg.__dict__, "stats": True}), out=out)
+        st = R.stats()
+    print(json.dumps({"ncu_case": True, "width": W, "height": H, "frames": len(wl.frames), **st}))
     R.close()
 
 
@@ -592,6 +602,8 @@ def main():
                     help="only render warmup + steps foveated frames (for profiler captures)")
     ap.add_argument("--scale", type=float, default=1.0, help="resolution scale of --ncu-case")
     ap.add_argument("--mode", default="hier", choices=["exact", "window", "hier"], help="sort mode of --ncu-case")
+    ap.add_argument("--backward", action="store_true", help="--ncu-case: also run the backward pass of every frame")
+    ap.add_argument("--stats", action="store_true", help="--ncu-case: print the device counters of the last frame")
     ap.add_argument("--workload", default="vr", choices=["vr", "batched", "finetune", "net"],
                     help="vr: the headline stereo frame; batched: 3 scenes x 8 poses x 2 eyes in one graph "
                          "replay; finetune: 4 views at 1280^2, render + loss + backward + Adam")

@@ -151,10 +151,10 @@ __device__ __forceinline__ void grad_add16(float* __restrict__ grad, int g, floa
       if (leader && it < n) v[k] += o;
     }
   }
-  if (leader) {
+  if (leader) {  // four 16-byte vector atomics (grad is 64-byte aligned per Gaussian)
+    float4* g4 = reinterpret_cast<float4*>(grad);
 #pragma unroll
-    for (int k = 0; k < 16; ++k)
-      if (v[k] != 0.f) atomicAdd(grad + k, v[k]);
+    for (int k = 0; k < 4; ++k) atomicAdd(g4 + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
   }
 }
 

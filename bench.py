@@ -259,13 +259,21 @@ def ncu_case(args, api, torch):
     wl = synth.vr_trajectory(args.warmup + args.steps, synth.rng_for(1, salt=100), W, H)
     ds = api.DeviceScene.from_host(scene)
     R = api.Renderer()
-    cfg = api.RenderConfig(sort_mode=args.mode, windows=WINDOWS, key_tile=32, fovea_mode="bilinear")
+    cfg = api.RenderConfig(sort_mode=args.mode, windows=WINDOWS, key_tile=32,
+                           fovea_mode="net" if args.net else "bilinear")
     out = torch.empty((2, 3, H, W), device="cuda")
+    low = torch.empty((2, 3, H // 2, W // 2), device="cuda") if args.net else None
+    net = None
+    if args.net:  # the periphery network (random weights: the same work as trained ones)
+        from paper_2505_10144_gb300 import periphery
+        net = periphery.PeripheryNet(R, seed=4)
     grads = ds.zeros_like() if args.backward else None
     dout = torch.randn((2, 3, H, W), device="cuda", generator=torch.Generator("cuda").manual_seed(7)) * 1e-3 \
         if args.backward else None
     for fr in wl.frames:
-        R.render([ds], [0, 0], fr.cameras, fr.foveas, cfg, out=out, save=args.backward)
+        R.render([ds], [0, 0], fr.cameras, fr.foveas, cfg, out=out, low=low, save=args.backward)
+        if net is not None:
+            net.apply_periphery(low, out)
         if args.backward:  # the replay of the same frame, one backward launch per forward launch
             R.backward([ds], [0, 0], fr.cameras, fr.foveas, cfg, dout, [grads])
     R.check()
@@ -273,7 +281,7 @@ def ncu_case(args, api, torch):
     st = R.stats()
     if args.stats:  # device counters of the last frame, from one more render with counters on
         fr = wl.frames[-1]
-        R.render([ds], [0, 0], fr.cameras, fr.foveas, api.RenderConfig(**{**cfg.__dict__, "stats": True}), out=out)
+        R.render([ds], [0, 0], fr.cameras, fr.foveas, api.RenderConfig(**{**cfg.__dict__, "stats": True}), out=out, low=low)
         st = R.stats()
     print(json.dumps({"ncu_case": True, "width": W, "height": H, "frames": len(wl.frames), **st}))
     R.close()
@@ -604,6 +612,7 @@ def main():
     ap.add_argument("--mode", default="hier", choices=["exact", "window", "hier"], help="sort mode of --ncu-case")
     ap.add_argument("--backward", action="store_true", help="--ncu-case: also run the backward pass of every frame")
     ap.add_argument("--stats", action="store_true", help="--ncu-case: print the device counters of the last frame")
+    ap.add_argument("--net", action="store_true", help="--ncu-case: learned periphery (network on the periphery)")
     ap.add_argument("--workload", default="vr", choices=["vr", "batched", "finetune", "net"],
                     help="vr: the headline stereo frame; batched: 3 scenes x 8 poses x 2 eyes in one graph "
                          "replay; finetune: 4 views at 1280^2, render + loss + backward + Adam")
@@ -727,6 +736,27 @@ def main():
     value = ws * args.steps / (total_ms / 1e3)
     # the same frames issued eagerly (one vrs_render call each), with per-stage events
     ms_eager, stages, ncalls = timed_eager(fov_cfg, min(args.plain_steps, args.steps), profile=True)
+    # the same frames as two monocular passes (one vrs_render per eye): what the fused
+    # stereo pass (one preprocess reading every Gaussian once for both eyes, one sort,
+    # one render launch over both eyes' work) saves
+    n_mono = min(args.plain_steps, args.steps)
+    for i in range(args.warmup):
+        fr = wl.frames[i % len(wl.frames)]
+        for e in range(2):
+            R.render([ds], [0], [fr.cameras[e]], [fr.foveas[e]], fov_cfg, out=out[e:e + 1])
+    R.check()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_mono)]
+    for i in range(n_mono):
+        fr = wl.frames[(args.warmup + i) % len(wl.frames)]
+        flush.zero_()
+        ev[i][0].record()
+        for e in range(2):
+            R.render([ds], [0], [fr.cameras[e]], [fr.foveas[e]], fov_cfg, out=out[e:e + 1])
+        ev[i][1].record()
+    barrier()
+    R.check()
+    ms_mono = [a.elapsed_time(b) for a, b in ev]
     # plain full-resolution render on the same GPU, also one graph replay per frame
     Rp, Gp = graphed(plain_cfg)
     ms_plain = timed_graph(Gp, Rp, min(args.plain_steps, args.steps))
@@ -883,6 +913,9 @@ def main():
         "visibility_culling": visibility,
         "two_pass_baseline": two_pass,
         "global_orders": global_orders,
+        "stereo_fusion": {"fused_eager_ms": statistics.mean(ms_eager), "two_monocular_passes_ms": statistics.mean(ms_mono),
+                          "speedup": statistics.mean(ms_mono) / statistics.mean(ms_eager),
+                          "config": "the same foveated frames, eager: one vrs_render of both eyes vs one per eye"},
         "eager": {"value": len(ms_eager) / (sum(ms_eager) / 1e3), "unit": "frames/s",
                   "ms_per_step": statistics.mean(ms_eager), "p99_ms": float(np.percentile(ms_eager, 99)),
                   "config": "one vrs_render call per frame (host reads the instance count back)"},

@@ -846,11 +846,14 @@ __device__ __forceinline__ unsigned long long win4_pop(Win4<K2>& w, int lane) {
 // and the resident CTAs per SM its register budget is set for.  Measured on the VR
 // frame: occupancy decides (the kernel waits on memory and on the issue of window
 // bookkeeping), and with the tournament-tree window 16-entry batches and a 72-register
-// budget (7 CTAs of 4 warps per SM, K3 = 16) beat 8 CTAs at 64 registers, which spill.
+// budget (7 CTAs of 4 warps per SM, K3 = 16) beat 6 CTAs at 80 registers and 8 CTAs at
+// 64 registers (5.64 / 5.86 / 6.06 ms).  The backward replay holds the gradient terms
+// as well: 4 CTAs at 128 registers, with no spill, beat 5 CTAs at 96 registers, which
+// spill (28.2 / 32.0 ms on four 1280^2 views).
 template <int K2>
 constexpr int stage_of() { return 16; }
 template <int K2, bool BWD>
-constexpr int ctas_of() { return BWD ? 5 : 7; }
+constexpr int ctas_of() { return BWD ? 4 : 7; }
 // key slots of the per-sample window: the tournament tree (k3 <= 16) always has 16
 __host__ __device__ inline int window_key_slots(int k3) { return k3 <= 16 ? 16 : k3; }
 __host__ __device__ inline size_t warp_smem_bytes(int k3, int stage) {

@@ -23,7 +23,8 @@ void net_backward_train(const float* params, const float* x, const uint16_t* act
                         int W, float* dparams, float* dz2, float* dz1, cudaStream_t st);
 void net_mse(const float* y, const float* t, long long n, float* loss, float* dy, double* scratch, cudaStream_t st);
 void net_periphery(const float* params, const float* low, float* out, const uint8_t* tile_class,
-                   const ViewParams* views, int n_views, int tiles_per_view, int W, int H, cudaStream_t st);
+                   const ViewParams* views, int n_views, int tiles_per_view, int W, int H, uint32_t* status,
+                   cudaStream_t st);
 vrs_status loss_l1_ssim_impl(const float* img, const float* tgt, int n, int H, int W, float* loss, float* grad,
                              void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t loss_scratch_bytes(int n, int H, int W);
@@ -904,7 +905,7 @@ vrs_status vrs_net_periphery(vrs_ctx* c, const float* d_params, const float* d_l
   if (sv.n_views <= 0 || sv.fovea_mode == 0 || sv.key_tile != 32)
     return fail(c, VRS_ERR_INVALID, "vrs_net_periphery follows a foveated vrs_render");
   net_periphery(d_params, d_low, d_out, P<uint8_t>(c->tile_class), P<ViewParams>(c->views), sv.n_views,
-                sv.tiles_per_view, sv.W, sv.H, (cudaStream_t)stream);
+                sv.tiles_per_view, sv.W, sv.H, P<uint32_t>(c->counters) + kCtrStatus, (cudaStream_t)stream);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "net periphery");
 }

@@ -13,9 +13,10 @@
 //  - training (any image size, activations saved for the backward): direct 3x3
 //    convolutions in FP32 SIMT arithmetic on BF16 values, plus the data and weight
 //    gradients;
-//  - inference on the periphery tiles of a rendered frame: one fused tensor-core kernel
-//    per 32x32 tile (mma.sync m16n8k16 bf16 -> f32, ldmatrix, swizzled shared memory),
-//    all three layers in shared memory, reading the half-resolution image directly.
+//  - inference on the periphery tiles of a rendered frame: one fused kernel, all three
+//    layers of a 32x32 tile in shared memory as implicit GEMMs on the tensor cores
+//    (tcgen05.mma, BF16 -> FP32 accumulators in tensor memory), reading the
+//    half-resolution image directly.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -26,6 +27,9 @@ namespace vrs {
 
 constexpr int kNetCh = 32;
 constexpr int kW1 = 0, kB1 = 864, kW2 = 896, kB2 = 10112, kW3 = 10144, kB3 = 11008, kNetParams = 11011;
+static_assert(kB1 == kW1 + kNetCh * 3 * 9 && kW2 == kB1 + kNetCh && kB2 == kW2 + kNetCh * kNetCh * 9 &&
+                  kW3 == kB2 + kNetCh && kB3 == kW3 + 3 * kNetCh * 9 && kNetParams == kB3 + 3,
+              "parameter offsets (OIHW)");
 
 namespace {
 
@@ -211,217 +215,440 @@ __global__ void mse_kernel(const float* __restrict__ y, const float* __restrict_
 __global__ void mse_finalize_kernel(const double* sum, long long n, float* loss) { *loss = (float)(*sum / (double)n); }
 
 // ------------------------------------------------------------------ fused tensor-core inference
+//
+// One CTA of 128 threads per SM walks the periphery tiles of the frame.  Per 32x32 output
+// tile, the three convolutions run as implicit GEMMs on the 5th-generation tensor cores:
+// tcgen05.mma (BF16 x BF16 -> FP32, M = 128 output positions, N = 32 or 16 channels,
+// K = 16 per instruction), operands in shared memory, accumulators in tensor memory.
+//
+// Activations are the A operand, K-major, one row per grid position: 64-byte rows (32
+// channels) with the 64-byte swizzle for the conv2 and conv3 inputs, 32-byte rows with the
+// 32-byte swizzle for the conv1 input, whose row p holds x(p) and x(p + 1) (8 channels
+// each, 3 used).  A 3x3 tap (dy, dx) is a shift of the A start by dy * grid_width + dx
+// rows, and the swizzle keeps every row an aligned, conflict-free read.  Each layer
+// computes its outputs on the rows of its input grid (row width = input width): the
+// rightmost outputs of a row wrap around and are discarded, and in exchange every tap is
+// one uniform shift.  Weights are the B operand, K-major without swizzle: planes of 8 input
+// channels x N output channels, 16 bytes per output channel.  conv1 has one instruction
+// per tap pair (dy, 2j), (dy, 2j + 1); tap (dy, 3) has zero weights.
+//
+// Warp roles.  Warps 16-19 issue: lane 0 of MMA warp k starts the MMAs of the M tiles
+// numbered k mod 4 (in issue order) and commits each tile to its accumulator's "full"
+// mbarrier.  A single issuing thread waits out each tcgen05.mma before the next, which
+// left the tensor cores idle most of the time; four issuers keep several M tiles in
+// flight (measured on the VR stereo frame: 1.57 / 1.08 / 0.98 ms for 1 / 2 / 4 issuers,
+// 1.97 ms for the mma.sync kernel this one replaced).  Warps 0-15 load the input tile
+// and run the epilogues in four groups of four warps: group g takes the M tiles numbered
+// g mod 4, and warp w reads tensor-memory lanes 32 (w & 3) .. + 31, the rows of its
+// quarter, all 32 channels.  kAcc tensor-memory accumulators of 32 columns rotate, so the
+// issuers run up to kAcc M tiles ahead of the epilogues.  Handshakes, all on mbarriers (no
+// block-wide barrier inside the tile loop):
+//   full[b]  the MMAs into accumulator b completed (tcgen05.commit);
+//   empty[b] the four warps of the group that took its last tile have read accumulator b;
+//   ready    the sixteen epilogue warps have written a layer's input (x, conv1 output or
+//            conv2 output) and fenced it for the tensor cores.
+// Every wait is bounded.  A thread that gives up sets kStTimeout in *status and a flag in
+// shared memory that ends every other wait at once, so the block leaves together.
 
-constexpr int kT = 32;                 // output tile
-constexpr int kGx = kT + 6;            // input grid (halo 3)
-constexpr int kG1 = kT + 4;            // conv1 output grid
-constexpr int kG2 = kT + 2;            // conv2 output grid
-constexpr int kW1Stride = 88;          // conv1 K = 9 taps x 8 channels = 72, padded to 80 (+8 pad)
-constexpr int kWStride = 296;          // conv2 / conv3 K = 288 (+8 pad, conflict-free ldmatrix rows)
-constexpr int kSmW1 = 32 * kW1Stride * 2;
-constexpr int kSmW2 = 32 * kWStride * 2;
-constexpr int kSmW3 = 8 * kWStride * 2;
-constexpr int kSmBias = 80 * 4;
-constexpr int kSmA = kG2 * kG2 * 64;   // x tile (38^2 x 16 B) then conv2 output (34^2 x 64 B)
-constexpr int kSmB = kG1 * kG1 * 64;   // conv1 output
-constexpr int kOffW1 = 0, kOffW2 = kOffW1 + kSmW1, kOffW3 = kOffW2 + kSmW2, kOffBias = kOffW3 + kSmW3;
-constexpr int kOffA = kOffBias + kSmBias, kOffB = kOffA + kSmA;
-constexpr int kNetSmem = kOffB + kSmB;
+constexpr int kT = 32;                    // output tile
+constexpr int kGx = kT + 6;               // conv1 input grid (halo 3): 38 x 38
+constexpr int kG1 = kT + 4;               // conv1 output / conv2 input grid: 36 x 36
+constexpr int kG2 = kT + 2;               // conv2 output / conv3 input grid: 34 x 34
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = kEpiWarps * 32;      // warps 0-15
+constexpr int kIssuers = 4;                      // MMA warps (a divisor of kAcc)
+constexpr int kNetThreads = kEpiThreads + 32 * kIssuers;
+constexpr int kMt1 = (kG1 * kGx + 127) / 128;  // 11 M tiles of conv1 (36 rows of 38)
+constexpr int kMt2 = (kG2 * kG1 + 127) / 128;  // 10 M tiles of conv2 (34 rows of 36)
+constexpr int kMt3 = (kT * kG2 + 127) / 128;   // 9 M tiles of conv3 (32 rows of 34)
+// positions a plane must hold: the last M tile's rows plus the largest tap shift
+constexpr int kPosX = kMt1 * 128 + 2 * kGx + 3;   // 1487 (dx up to 3: zero-weight tap)
+constexpr int kPos1 = kMt2 * 128 + 2 * kG1 + 2;   // 1354
+constexpr int kPos2 = kMt3 * 128 + 2 * kG2 + 2;   // 1222
+constexpr int kRowsX = (kPosX + 7) / 8 * 8;  // conv1 input rows of 32 bytes
+constexpr int kRows1 = (kPos1 + 7) / 8 * 8;  // conv2 input rows of 64 bytes
+constexpr int kRows2 = (kPos2 + 7) / 8 * 8;  // conv3 input rows of 64 bytes
+constexpr int kSmW1 = 12 * 32 * 16;       // 6 MMAs x 2 K halves x [32 n][16 B]
+constexpr int kSmW2 = 36 * 32 * 16;       // 9 taps x 4 channel slices x [32 n][16 B]
+constexpr int kSmW3 = 36 * 16 * 16;       // 9 taps x 4 slices x [16 n][16 B] (3 real outputs)
+constexpr int kSmR0 = ((kRows2 * 64 > kRowsX * 32 ? kRows2 * 64 : kRowsX * 32) + 1023) / 1024 * 1024;  // x rows, then conv2 output
+constexpr int kSmR1 = kRows1 * 64;        // conv1 output
+constexpr int kOffW1 = 0, kOffW2 = kOffW1 + kSmW1, kOffW3 = kOffW2 + kSmW2, kOffR0 = kOffW3 + kSmW3;
+// kOffXres: float bilinear input of the 32 x 32 outputs; kOffLow: the half-resolution
+// patch (21 x 21 pixels, 3 channels, clamped to the image) the tile's bilinear input reads
+constexpr int kLowP = 21;
+constexpr int kOffR1 = kOffR0 + kSmR0, kOffXres = kOffR1 + kSmR1, kOffLow = kOffXres + kT * kT * 12;
+constexpr int kOffBias = kOffLow + 3 * kLowP * kLowP * 4 + 4, kOffBar = kOffBias + 80 * 4;
+constexpr int kAcc = 8;  // tensor-memory accumulators of 32 columns (a multiple of 4, a power of two)
+constexpr int kEpiGroups = kEpiWarps / 4;  // epilogue groups of four warps (one per lane quarter)
+static_assert(kAcc % kIssuers == 0 && kAcc % kEpiGroups == 0, "accumulators per MMA warp and epilogue group");
+// barrier area: full[kAcc], empty[kAcc], ready, then the abort flag and the TMEM address
+constexpr int kBarReady = 16 * kAcc, kBarAbort = kBarReady + 8, kBarTslot = kBarReady + 12;
+constexpr int kNetSmem = kOffBar + kBarReady + 16;
+static_assert(kNetSmem <= 227 * 1024, "net tile does not fit in shared memory");
+static_assert((kOffR0 | kOffR1) % 1024 == 0 && (kOffW2 | kOffW3) % 16 == 0, "operand alignment");
+constexpr long long kWaitLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(addr));
+// shared-memory matrix descriptor: no swizzle, K-core stride lbo, 8-row-group stride 128 B
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
 }
 
-__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+// shared-memory matrix descriptor, K-major with a 32-byte (layout 6) or 64-byte (layout
+// 4) swizzle: rows of 32 or 64 bytes, 8-row groups sbo bytes apart; the swizzle acts on
+// absolute address bits (XOR of bits 7 (.. 8) into bits 4 (.. 5)), so a start shifted by
+// whole rows, or by 32 bytes along K inside a 64-byte row, needs no base offset
+__device__ __forceinline__ uint64_t umma_desc_sw(uint32_t addr, uint32_t sbo, uint32_t layout) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
+         (1ull << 46) | ((uint64_t)layout << 61);
 }
 
-__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1) {
+// instruction descriptor: BF16 A and B (K-major), FP32 accumulator, M x N
+__device__ __forceinline__ uint32_t umma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-// 64-byte activation rows, 16-byte chunks swizzled so that eight consecutive positions
-// hit eight different bank groups
-__device__ __forceinline__ int act_off(int pos, int chunk) { return pos * 64 + ((chunk ^ ((pos >> 1) & 3)) << 4); }
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
+}
 
-__device__ __forceinline__ void bilinear_x(const float* __restrict__ L, int W2, int H2, long long HW2, int x, int y,
-                                           float v[3]) {
+// waits for the phase of the given parity; false when the wait gave up or another thread
+// of the block did (*abort)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile uint32_t* abort) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kWaitLimit && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity));
+    if (!done && *abort) return false;
+  }
+  if (!done) *abort = 1u;
+  return done != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  __syncwarp();
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float v[4]) {
+  uint32_t r[4];
+  __syncwarp();
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int c = 0; c < 4; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// bilinear x2 upsample (half-pixel aligned, clamped to the edge) at full-resolution pixel
+// (x, y), read from the shared half-resolution patch P: patch column j, row i hold the
+// image's column clamp(px0 + j), row clamp(py0 + i), so the taps x0 - px0 and x0 - px0 + 1
+// are the clamped taps x0 and x0 + 1
+__device__ __forceinline__ void bilinear_patch(const float* __restrict__ P, int px0, int py0, int x, int y,
+                                               float v[3]) {
   const float ux = (x + 0.5f) * 0.5f - 0.5f, uy = (y + 0.5f) * 0.5f - 0.5f;
   const int x0 = (int)floorf(ux), y0 = (int)floorf(uy);
   const float fx = ux - x0, fy = uy - y0;
-  const int xa = min(max(x0, 0), W2 - 1), xb = min(max(x0 + 1, 0), W2 - 1);
-  const int ya = min(max(y0, 0), H2 - 1), yb = min(max(y0 + 1, 0), H2 - 1);
+  const int xa = x0 - px0, ya = y0 - py0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const float* Lc = L + c * HW2;
-    const float top = (1.f - fx) * Lc[ya * W2 + xa] + fx * Lc[ya * W2 + xb];
-    const float bot = (1.f - fx) * Lc[yb * W2 + xa] + fx * Lc[yb * W2 + xb];
+    const float* Pc = P + c * kLowP * kLowP;
+    const float top = (1.f - fx) * Pc[ya * kLowP + xa] + fx * Pc[ya * kLowP + xa + 1];
+    const float bot = (1.f - fx) * Pc[(ya + 1) * kLowP + xa] + fx * Pc[(ya + 1) * kLowP + xa + 1];
     v[c] = (1.f - fy) * top + fy * bot;
   }
 }
 
-// implicit-GEMM 3x3 conv, 32 input channels in swizzled 64-byte rows (grid gin wide),
-// outputs on a gout x gout grid, NT n8 tiles; epilogue functor per (m, channel pair)
-template <int NT, class Epi>
-__device__ __forceinline__ void conv32_mma(uint32_t in_base, int gin, int gout, uint32_t w_base, Epi epi) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int M = gout * gout, mtiles = (M + 15) / 16;
-  for (int mt = warp; mt < mtiles; mt += kBlock / 32) {
-    float acc[NT][4];
+// the MMAs of one M tile of one layer into accumulator d (issued by one thread).  A tap
+// or a channel slice moves an operand's start by whole 16-byte units, so each MMA's
+// descriptors are the layer's base descriptors plus an offset in the start-address field
+// (every shared-memory address here is below 2^18, so the 14-bit field cannot carry).
+__device__ __forceinline__ void issue_tile(int layer, int mt, uint32_t d, uint32_t sm0) {
+  if (layer == 1) {
+    const uint32_t id = umma_idesc(128, 32);
+    // rows of 32 bytes: row p holds x(p) and x(p + 1), so one instruction covers taps
+    // (dy, 2j) and (dy, 2j + 1) from row p + dy * kGx + 2j
+    const uint64_t a0 = umma_desc_sw(sm0 + kOffR0, 256, 6) + (uint64_t)(mt * 128 * 2);
+    const uint64_t b0 = umma_desc(sm0 + kOffW1, 512);
 #pragma unroll
-    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    int m = mt * 16 + (lane & 15);
-    if (m >= M) m = M - 1;
-    const int oi = m / gout, oj = m % gout;
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-      const int pos = (oi + tap / 3) * gin + oj + tap % 3;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        uint32_t a0, a1, a2, a3;
-        ldsm_x4(in_base + act_off(pos, 2 * h + (lane >> 4)), a0, a1, a2, a3);
-        const int k0 = tap * 32 + h * 16;
-#pragma unroll
-        for (int n = 0; n < NT; ++n) {
-          uint32_t b0, b1;
-          const int nrow = n * 8 + (lane & 7), kk = k0 + ((lane >> 3) & 1) * 8;
-          ldsm_x2(w_base + (nrow * kWStride + kk) * 2, b0, b1);
-          mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
-        }
-      }
+    for (int q = 0; q < 6; ++q) {  // q = 2 dy + j
+      const int dy = q >> 1, j = q & 1;
+      umma(d, a0 + (uint64_t)((dy * kGx + 2 * j) * 2), b0 + (uint64_t)(q * 64), id, q > 0);
     }
-    const int r0 = mt * 16 + (lane >> 2), c0 = 2 * (lane & 3);
+  } else {
+    const int gin = layer == 2 ? kG1 : kG2;
+    const uint32_t bplane = layer == 2 ? 512u : 256u;
+    const uint32_t id = umma_idesc(128, layer == 2 ? 32 : 16);
+    // rows of 64 bytes (32 channels); tap (dy, dx) starts dy * gin + dx rows further, and
+    // the second K half 32 bytes into the row
+    const uint64_t a0 = umma_desc_sw(sm0 + (layer == 2 ? kOffR1 : kOffR0), 512, 4) + (uint64_t)(mt * 128 * 4);
+    const uint64_t b0 = umma_desc(sm0 + (layer == 2 ? kOffW2 : kOffW3), bplane);
 #pragma unroll
-    for (int n = 0; n < NT; ++n) {
-      epi(r0, n * 8 + c0, acc[n][0], acc[n][1]);
-      epi(r0 + 8, n * 8 + c0, acc[n][2], acc[n][3]);
+    for (int t = 0; t < 9; ++t) {
+      const int dy = t / 3, dx = t % 3;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        umma(d, a0 + (uint64_t)((dy * gin + dx) * 4 + 2 * h),
+             b0 + (uint64_t)((t * 4 + 2 * h) * (int)(bplane >> 4)), id, (t | h) != 0);
     }
   }
 }
 
-__global__ void __launch_bounds__(kBlock, 1) net_periphery_kernel(const float* __restrict__ params,
-                                                                  const float* __restrict__ low,
-                                                                  float* __restrict__ out,
-                                                                  const uint8_t* __restrict__ tile_class,
-                                                                  const ViewParams* __restrict__ views, int n_views,
-                                                                  int tiles_per_view, int W, int H) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  uint16_t* w1s = reinterpret_cast<uint16_t*>(sm + kOffW1);
-  uint16_t* w2s = reinterpret_cast<uint16_t*>(sm + kOffW2);
-  uint16_t* w3s = reinterpret_cast<uint16_t*>(sm + kOffW3);
+// 8 BF16 values of one 16-byte plane slot
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  uint4 q;
+  q.x = (uint32_t)bf16bits(v[0]) | ((uint32_t)bf16bits(v[1]) << 16);
+  q.y = (uint32_t)bf16bits(v[2]) | ((uint32_t)bf16bits(v[3]) << 16);
+  q.z = (uint32_t)bf16bits(v[4]) | ((uint32_t)bf16bits(v[5]) << 16);
+  q.w = (uint32_t)bf16bits(v[6]) | ((uint32_t)bf16bits(v[7]) << 16);
+  return q;
+}
+
+__global__ void __launch_bounds__(kNetThreads, 1) net_periphery_kernel(const float* __restrict__ params,
+                                                                       const float* __restrict__ low,
+                                                                       float* __restrict__ out,
+                                                                       const uint8_t* __restrict__ tile_class,
+                                                                       const ViewParams* __restrict__ views,
+                                                                       int n_views, int tiles_per_view, int W, int H,
+                                                                       uint32_t* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char sm[];
   float* bias = reinterpret_cast<float*>(sm + kOffBias);
-  unsigned char* A = sm + kOffA;
-  unsigned char* B = sm + kOffB;
-  // weights to BF16, K-major rows: conv1 k = tap * 8 + c, conv2/3 k = tap * 32 + c
-  for (int k = threadIdx.x; k < 32 * kW1Stride; k += kBlock) {
-    const int n = k / kW1Stride, kk = k % kW1Stride, tap = kk / 8, c = kk % 8;
-    w1s[k] = (tap < 9 && c < 3) ? bf16bits(params[kW1 + (n * 3 + c) * 9 + tap]) : (uint16_t)0;
+  float* xres = reinterpret_cast<float*>(sm + kOffXres);
+  volatile uint32_t* abort = reinterpret_cast<volatile uint32_t*>(sm + kOffBar + kBarAbort);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + kOffBar + kBarTslot);
+  const uint32_t sm0 = smem_u32(sm);
+  const uint32_t bar_full = sm0 + kOffBar, bar_empty = bar_full + 8 * kAcc, bar_ready = sm0 + kOffBar + kBarReady;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // every operand byte starts defined (plane tails are read by discarded rows only)
+  for (int i = tid; i < (kOffBias - kOffR0) / 16; i += kNetThreads)
+    reinterpret_cast<uint4*>(sm + kOffR0)[i] = make_uint4(0u, 0u, 0u, 0u);
+  // weights to BF16 planes [slice][n][8 channels]
+  for (int i = tid; i < 12 * 32 * 8; i += kNetThreads) {  // conv1: plane 2q + half, q = 2 dy + j
+    const int e = i & 7, n = (i >> 3) & 31, pl = i >> 8;
+    const int q = pl >> 1, dy = q >> 1, dx = 2 * (q & 1) + (pl & 1);
+    const float w = (dx < 3 && e < 3) ? params[kW1 + (n * 3 + e) * 9 + dy * 3 + dx] : 0.f;
+    reinterpret_cast<uint16_t*>(sm + kOffW1)[i] = bf16bits(w);
   }
-  for (int k = threadIdx.x; k < 32 * kWStride; k += kBlock) {
-    const int n = k / kWStride, kk = k % kWStride, tap = kk / 32, c = kk % 32;
-    w2s[k] = kk < 288 ? bf16bits(params[kW2 + (n * 32 + c) * 9 + tap]) : (uint16_t)0;
+  for (int i = tid; i < 36 * 32 * 8; i += kNetThreads) {  // conv2: plane 4 t + slice
+    const int e = i & 7, n = (i >> 3) & 31, pl = i >> 8;
+    const int t = pl >> 2, c = (pl & 3) * 8 + e;
+    reinterpret_cast<uint16_t*>(sm + kOffW2)[i] = bf16bits(params[kW2 + (n * 32 + c) * 9 + t]);
   }
-  for (int k = threadIdx.x; k < 8 * kWStride; k += kBlock) {
-    const int n = k / kWStride, kk = k % kWStride, tap = kk / 32, c = kk % 32;
-    w3s[k] = (n < 3 && kk < 288) ? bf16bits(params[kW3 + (n * 32 + c) * 9 + tap]) : (uint16_t)0;
+  for (int i = tid; i < 36 * 16 * 8; i += kNetThreads) {  // conv3: 16 output rows, 3 real
+    const int e = i & 7, n = (i >> 3) & 15, pl = i >> 7;
+    const int t = pl >> 2, c = (pl & 3) * 8 + e;
+    reinterpret_cast<uint16_t*>(sm + kOffW3)[i] = bf16bits(n < 3 ? params[kW3 + (n * 32 + c) * 9 + t] : 0.f);
   }
-  if (threadIdx.x < 32) bias[threadIdx.x] = params[kB1 + threadIdx.x];
-  if (threadIdx.x < 32) bias[32 + threadIdx.x] = params[kB2 + threadIdx.x];
-  if (threadIdx.x < 3) bias[64 + threadIdx.x] = params[kB3 + threadIdx.x];
+  if (tid < 32) bias[tid] = params[kB1 + tid];
+  if (tid < 32) bias[32 + tid] = params[kB2 + tid];
+  if (tid < 3) bias[64 + tid] = params[kB3 + tid];
+  if (tid == 0) {
+    for (int b = 0; b < kAcc; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_full + 8u * b), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_empty + 8u * b), "r"(4));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_ready), "r"(kEpiWarps));
+    *abort = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == kEpiWarps) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(32 * kAcc));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
   const int W2 = W / 2, H2 = H / 2;
   const long long HW = (long long)W * H, HW2 = (long long)W2 * H2;
   const long long n_tiles = (long long)n_views * tiles_per_view;
-  const int lane = threadIdx.x & 31;
-  for (long long tg = blockIdx.x; tg < n_tiles; tg += gridDim.x) {
-    if (tile_class[tg] != kClassPeriphery) continue;
-    const int view = (int)(tg / tiles_per_view), t = (int)(tg % tiles_per_view);
-    const ViewParams& vp = views[view];
-    const int ox = (t % vp.ntx) * kT, oy = (t / vp.ntx) * kT;
-    const float* L = low + (long long)view * 3 * HW2;
-    __syncthreads();  // previous tile done with A / B
-    // x tile (halo 3), BF16, 8 channels per position (3 used)
-    for (int p = threadIdx.x; p < kGx * kGx; p += kBlock) {
-      const int gx = ox - 3 + p % kGx, gy = oy - 3 + p / kGx;
-      float v[3] = {0.f, 0.f, 0.f};
-      if (gx >= 0 && gx < W && gy >= 0 && gy < H) bilinear_x(L, W2, H2, HW2, gx, gy, v);
-      uint4 q;
-      q.x = (uint32_t)bf16bits(v[0]) | ((uint32_t)bf16bits(v[1]) << 16);
-      q.y = (uint32_t)bf16bits(v[2]);
-      q.z = q.w = 0u;
-      *reinterpret_cast<uint4*>(A + p * 16) = q;
-    }
-    __syncthreads();
-    // conv1 (K = 80: taps t = 2 step + {0, 1}, 8 channels each) -> B, 36 x 36
-    {
-      const int warp = threadIdx.x >> 5;
-      const int M = kG1 * kG1, mtiles = M / 16;
-      const uint32_t abase = smem_u32(A), wbase = smem_u32(w1s);
-      for (int mt = warp; mt < mtiles; mt += kBlock / 32) {
-        float acc[4][4];
+  bool ok = true;
+  if (warp >= kEpiWarps) {
+    // ---- MMA warps: lane 0 of MMA warp k issues the M tiles numbered k mod kIssuers, in
+    // the epilogue warps' tile order (each accumulator is always fed by the same warp)
+    const uint32_t k = (uint32_t)(warp - kEpiWarps);
+    if ((tid & 31) == 0) {
+      uint32_t cnt = 0, ph_empty = 0, ph_ready = 0;
+      uint32_t nc[kAcc];  // commits into each accumulator
 #pragma unroll
-        for (int n = 0; n < 4; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-        const int m = mt * 16 + (lane & 15), oi = m / kG1, oj = m % kG1;
+      for (int b = 0; b < kAcc; ++b) nc[b] = 0u;
+      for (long long tg = blockIdx.x; tg < n_tiles && ok; tg += gridDim.x) {
+        if (tile_class[tg] != kClassPeriphery) continue;
+        for (int layer = 1; layer <= 3 && ok; ++layer) {
+          ok = mbar_wait(bar_ready, ph_ready, abort);  // the layer's input is in shared memory
+          ph_ready ^= 1u;
+          tc_fence_after();
+          const int nt = layer == 1 ? kMt1 : (layer == 2 ? kMt2 : kMt3);
+          for (int mt = 0; mt < nt && ok; ++mt, ++cnt) {
+            if (cnt % kIssuers != k) continue;
+            const uint32_t b = cnt & (kAcc - 1u);
+            // accumulator b is free once its previous tile was read (the first use of each
+            // accumulator waits on the phase before the first, which counts as complete)
+            ok = mbar_wait(bar_empty + 8u * b, ((ph_empty >> b) & 1u) ^ 1u, abort);
+            ph_empty ^= 1u << b;
+            tc_fence_after();
+            if (ok) {
+              issue_tile(layer, mt, tmem + 32u * b, sm0);
+              umma_commit(bar_full + 8u * b);
 #pragma unroll
-        for (int step = 0; step < 5; ++step) {
-          const int tap = min(2 * step + (lane >> 4), 8);
-          const int pos = (oi + tap / 3) * kGx + oj + tap % 3;
-          uint32_t a0, a1, a2, a3;
-          ldsm_x4(abase + pos * 16, a0, a1, a2, a3);
-#pragma unroll
-          for (int n = 0; n < 4; ++n) {
-            uint32_t b0, b1;
-            const int nrow = n * 8 + (lane & 7), kk = step * 16 + ((lane >> 3) & 1) * 8;
-            ldsm_x2(wbase + (nrow * kW1Stride + kk) * 2, b0, b1);
-            mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+              for (int a = 0; a < kAcc; ++a) nc[a] += (uint32_t)a == b ? 1u : 0u;
+            }
           }
         }
-        const int r0 = mt * 16 + (lane >> 2), c0 = 2 * (lane & 3);
+      }
+      if (!ok || *abort) {
+        // the block gave up: the MMAs already committed finish (bounded waits that ignore
+        // the abort flag) before their accumulators are released
+        uint32_t none = 0u;
 #pragma unroll
-        for (int n = 0; n < 4; ++n)
-#pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            const int mm = r0 + 8 * hh, ch = n * 8 + c0;
-            const int gx = ox - 2 + mm % kG1, gy = oy - 2 + mm / kG1;
-            const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            const float v0 = in ? fmaxf(acc[n][2 * hh] + bias[ch], 0.f) : 0.f;
-            const float v1 = in ? fmaxf(acc[n][2 * hh + 1] + bias[ch + 1], 0.f) : 0.f;
-            *reinterpret_cast<uint32_t*>(B + act_off(mm, ch >> 3) + (ch & 7) * 2) =
-                (uint32_t)bf16bits(v0) | ((uint32_t)bf16bits(v1) << 16);
-          }
+        for (int b = 0; b < kAcc; ++b)
+          if (nc[b]) mbar_wait(bar_full + 8u * b, (nc[b] - 1u) & 1u, &none);
       }
     }
-    __syncthreads();
-    // conv2 -> A (34 x 34)
-    conv32_mma<4>(smem_u32(B), kG1, kG2, smem_u32(w2s), [&](int mm, int ch, float c0v, float c1v) {
-      if (mm >= kG2 * kG2) return;
-      const int gx = ox - 1 + mm % kG2, gy = oy - 1 + mm / kG2;
-      const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
-      const float v0 = in ? fmaxf(c0v + bias[32 + ch], 0.f) : 0.f;
-      const float v1 = in ? fmaxf(c1v + bias[32 + ch + 1], 0.f) : 0.f;
-      *reinterpret_cast<uint32_t*>(A + act_off(mm, ch >> 3) + (ch & 7) * 2) =
-          (uint32_t)bf16bits(v0) | ((uint32_t)bf16bits(v1) << 16);
-    });
-    __syncthreads();
-    // conv3 -> out (32 x 32): residual on the float bilinear input
-    conv32_mma<1>(smem_u32(A), kG2, kT, smem_u32(w3s), [&](int mm, int ch, float c0v, float c1v) {
-      const int gx = ox + mm % kT, gy = oy + mm / kT;
-      if (gx >= W || gy >= H || ch >= 3) return;
-      float v[3];
-      bilinear_x(L, W2, H2, HW2, gx, gy, v);
-      float* o = out + (long long)view * 3 * HW + (long long)gy * W + gx;
-      o[(long long)ch * HW] = v[ch] + c0v + bias[64 + ch];
-      if (ch + 1 < 3) o[(long long)(ch + 1) * HW] = v[ch + 1] + c1v + bias[64 + ch + 1];
-    });
+  } else {
+    // ---- epilogue warps 0-15
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const int group = warp >> 2;  // takes the M tiles numbered group mod kEpiGroups
+    float* patch = reinterpret_cast<float*>(sm + kOffLow);
+    uint32_t cnt = 0, ph_full = 0;
+    for (long long tg = blockIdx.x; tg < n_tiles && ok; tg += gridDim.x) {
+      if (tile_class[tg] != kClassPeriphery) continue;
+      const int view = (int)(tg / tiles_per_view), t = (int)(tg % tiles_per_view);
+      const ViewParams& vp = views[view];
+      const int ox = (t % vp.ntx) * kT, oy = (t / vp.ntx) * kT;
+      const float* L = low + (long long)view * 3 * HW2;
+      // the half-resolution patch under the tile and its halo, one load per value
+      const int px0 = ox / 2 - 2, py0 = oy / 2 - 2;
+      for (int i = tid; i < 3 * kLowP * kLowP; i += kEpiThreads) {
+        const int c = i / (kLowP * kLowP), r = (i / kLowP) % kLowP, j = i % kLowP;
+        const int gy = min(max(py0 + r, 0), H2 - 1), gx = min(max(px0 + j, 0), W2 - 1);
+        patch[i] = L[c * HW2 + (long long)gy * W2 + gx];
+      }
+      asm volatile("bar.sync 2, %0;" ::"n"(kEpiThreads));
+      // x plane (halo 3): BF16 bilinear input, channels 3..7 zero; the float input of the
+      // 32 x 32 outputs is kept for the residual
+      for (int p = tid; p < kGx * kGx; p += kEpiThreads) {
+        const int gx = ox - 3 + p % kGx, gy = oy - 3 + p / kGx;
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (gx >= 0 && gx < W && gy >= 0 && gy < H) bilinear_patch(patch, px0, py0, gx, gy, v);
+        // x(p) is the first half of row p and the second half of row p - 1 (32-byte
+        // swizzle: the halves swap where address bit 7 is set)
+        const uint4 xq = pack8(v);
+        const uint32_t sw0 = ((sm0 + kOffR0 + (uint32_t)p * 32u) >> 7) & 1u;
+        *reinterpret_cast<uint4*>(sm + kOffR0 + p * 32 + (sw0 << 4)) = xq;
+        if (p > 0) {
+          const uint32_t sw1 = ((sm0 + kOffR0 + (uint32_t)(p - 1) * 32u) >> 7) & 1u;
+          *reinterpret_cast<uint4*>(sm + kOffR0 + (p - 1) * 32 + ((1u ^ sw1) << 4)) = xq;
+        }
+        const int i = p / kGx - 3, j = p % kGx - 3;
+        if (i >= 0 && i < kT && j >= 0 && j < kT) {
+          float* xr = xres + (i * kT + j) * 3;
+          xr[0] = v[0];
+          xr[1] = v[1];
+          xr[2] = v[2];
+        }
+      }
+      for (int layer = 1; layer <= 3 && ok; ++layer) {
+        fence_async_smem();  // this warp's writes of the layer's input, to the tensor cores
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(bar_ready);
+        const int nt = layer == 1 ? kMt1 : (layer == 2 ? kMt2 : kMt3);
+        const int gin = layer == 1 ? kGx : (layer == 2 ? kG1 : kG2);
+        const int gout = layer == 1 ? kG1 : (layer == 2 ? kG2 : kT);
+        for (int mt = 0; mt < nt && ok; ++mt, ++cnt) {
+          if ((int)(cnt % kEpiGroups) != group) continue;  // another group's M tile
+          const uint32_t b = cnt & (kAcc - 1u);
+          ok = mbar_wait(bar_full + 8u * b, (ph_full >> b) & 1u, abort);
+          ph_full ^= 1u << b;
+          if (!__all_sync(0xffffffffu, ok)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int m = mt * 128 + (warp & 3) * 32 + (tid & 31);
+          const int oi = m / gin, oj = m - oi * gin;
+          const uint32_t taddr = tmem + lane_base + 32u * b;
+          if (layer < 3) {
+            float v[32];
+            tmem_ld32(taddr, v);
+            tc_fence_before();
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(bar_empty + 8u * b);
+            if (oi < gout && oj < gout) {
+              const int off = layer == 1 ? 2 : 1;
+              const int gx = ox - off + oj, gy = oy - off + oi;
+              const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+              const float* bb = bias + (layer == 1 ? 0 : 32);
+#pragma unroll
+              for (int c = 0; c < 32; ++c) v[c] = in ? fmaxf(v[c] + bb[c], 0.f) : 0.f;
+              const uint32_t row = (uint32_t)(layer == 1 ? kOffR1 : kOffR0) + (uint32_t)(oi * gout + oj) * 64u;
+              const uint32_t sw = ((sm0 + row) >> 7) & 3u;  // 64-byte swizzle of this row
+#pragma unroll
+              for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(sm + row + ((q ^ sw) << 4)) = pack8(v + 8 * q);
+            }
+          } else {  // three output channels
+            float v[4];
+            tmem_ld4(taddr, v);
+            tc_fence_before();
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(bar_empty + 8u * b);
+            const int gx = ox + oj, gy = oy + oi;
+            if (oi < kT && oj < kT && gx < W && gy < H) {
+              const float* xr = xres + (oi * kT + oj) * 3;
+              float* o = out + (long long)view * 3 * HW + (long long)gy * W + gx;
+#pragma unroll
+              for (int c = 0; c < 3; ++c) o[(long long)c * HW] = xr[c] + v[c] + bias[64 + c];
+            }
+          }
+        }
+      }
+      // the next tile's patch, x plane and residual input overwrite shared memory: conv3's
+      // MMAs (which read R0) have all completed, and every epilogue warp is past its reads
+      asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads));
+    }
   }
+  if (!ok) atomicOr(status, kStTimeout);
+  // every committed MMA has completed here: the epilogue warps awaited each one, or, when
+  // the block gave up, the issuing lane did
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kEpiWarps)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32 * kAcc));
 }
 
 unsigned grid_for(long long n) {
@@ -500,7 +727,8 @@ void net_mse(const float* y, const float* t, long long n, float* loss, float* dy
 }
 
 void net_periphery(const float* params, const float* low, float* out, const uint8_t* tile_class,
-                   const ViewParams* views, int n_views, int tiles_per_view, int W, int H, cudaStream_t st) {
+                   const ViewParams* views, int n_views, int tiles_per_view, int W, int H, uint32_t* status,
+                   cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(net_periphery_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmem);
@@ -508,8 +736,8 @@ void net_periphery(const float* params, const float* low, float* out, const uint
   }
   const long long n = (long long)n_views * tiles_per_view;
   const unsigned grid = (unsigned)std::min<long long>(n, (long long)device_sm_count());
-  net_periphery_kernel<<<grid, kBlock, kNetSmem, st>>>(params, low, out, tile_class, views, n_views, tiles_per_view, W,
-                                                       H);
+  net_periphery_kernel<<<grid, kNetThreads, kNetSmem, st>>>(params, low, out, tile_class, views, n_views,
+                                                            tiles_per_view, W, H, status);
 }
 
 int net_smem_bytes() { return kNetSmem; }

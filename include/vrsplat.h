@@ -300,6 +300,15 @@ vrs_status vrs_adam_step(float* d_param, const float* d_grad, float* d_m, float*
 vrs_status vrs_profile_begin(vrs_ctx* ctx, int max_calls);
 vrs_status vrs_profile_end(vrs_ctx* ctx, void* stream, double* h_stage_ms, int64_t* n_calls);
 
+/* Failure-detection check of the library's bounded device waits.  Runs one of them
+ * against a flag that nothing sets, with a short limit (1000 polls): which = 0 the radix
+ * sort's decoupled look-back wait, which = 1 the mbarrier wait of the periphery-network
+ * kernel.  The wait gives up, the kernel raises the timeout status and returns, so the
+ * next vrs_check_status on this stream reports VRS_ERR_TIMEOUT (and clears it); the
+ * context stays usable.  Nothing faults, traps or hangs.  Not allowed during stream
+ * capture; VRS_ERR_INVALID for another `which`. */
+vrs_status vrs_test_bounded_wait(vrs_ctx* ctx, int which, void* stream);
+
 /* Blend order of single rays of the last vrs_render of this context (its views, sort
  * mode, records and tile lists must be unchanged since).  d_probes is a device array
  * [n_probes][3] of (view, x, y) floats: the ray through image point (x, y) of that view,

@@ -47,7 +47,7 @@ EXPORTED = ["vrs_create", "vrs_destroy", "vrs_reserve", "vrs_render", "vrs_rende
             "vrs_get_stats", "vrs_copy_instances", "vrs_project", "vrs_sort_pairs", "vrs_loss_l1_ssim",
             "vrs_adam_step", "vrs_profile_begin", "vrs_profile_end", "vrs_sort_pairs_noalloc", "vrs_update_views", "vrs_set_tuning",
             "vrs_net_forward", "vrs_net_backward", "vrs_net_periphery", "vrs_mse", "vrs_render_two_pass",
-            "vrs_measure_peaks", "vrs_probe_orders", "vrs_last_error"]
+            "vrs_measure_peaks", "vrs_probe_orders", "vrs_test_bounded_wait", "vrs_last_error"]
 
 _lib = None
 
@@ -94,6 +94,7 @@ def load() -> C.CDLL:
     lib.vrs_profile_end.argtypes = [vp, vp, P(C.c_double), P(i64)]
     lib.vrs_measure_peaks.argtypes = [P(Peaks), vp]
     lib.vrs_probe_orders.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp]
+    lib.vrs_test_bounded_wait.argtypes = [vp, i32, vp]
     lib.vrs_last_error.argtypes = [vp]
     lib.vrs_last_error.restype = C.c_char_p
     for name in EXPORTED:

@@ -217,6 +217,11 @@ class Renderer:
         m = int(n.value)
         return keys[:m], vals[:m], ranges
 
+    def test_bounded_wait(self, which: int, stream=None):
+        """Runs a bounded device wait (0: sort look-back, 1: network mbarrier) against a
+        flag nothing sets; the next check() raises the timeout status."""
+        self._check(self.lib.vrs_test_bounded_wait(self.ctx, int(which), _stream(stream)))
+
     def probe_orders(self, probes: torch.Tensor, max_len: int = 256, stream=None):
         """Blend order of single rays of the last render (exact or global sort modes):
         probes [n, 3] float32 (view, x, y) on the device -> (ids [n, max_len] int32,

@@ -28,6 +28,8 @@ void net_periphery(const float* params, const float* low, float* out, const uint
 vrs_status loss_l1_ssim_impl(const float* img, const float* tgt, int n, int H, int W, float* loss, float* grad,
                              void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t loss_scratch_bytes(int n, int H, int W);
+void launch_lookback_timeout_test(uint32_t* zeroed_look, uint32_t* status, cudaStream_t st);
+void launch_mbar_timeout_test(uint32_t* status, cudaStream_t st);
 void launch_probe_orders(const ViewParams* views, int n_views, const float4* rec, const uint32_t* vals,
                          const uint32_t* ranges, int key_tile, int tiles_per_view, int list_order,
                          const float* probes, int n, int max_len, int* ids, float* depth, int* len,
@@ -786,6 +788,25 @@ vrs_status vrs_copy_instances(vrs_ctx* c, uint64_t* d_keys, uint32_t* d_vals, ui
                     cudaMemcpyDeviceToDevice, st);
   e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "copy instances");
+}
+
+vrs_status vrs_test_bounded_wait(vrs_ctx* c, int which, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (which != 0 && which != 1) return fail(c, VRS_ERR_INVALID, "which: 0 look-back, 1 mbarrier");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (capturing(st)) return fail(c, VRS_ERR_INVALID, "not during stream capture");
+  vrs_status s = VRS_OK;
+  if (!ensure(c, c->misc, 2048, false, &s)) return s;
+  uint32_t* status = P<uint32_t>(c->counters) + kCtrStatus;
+  if (which == 0) {
+    uint32_t* look = reinterpret_cast<uint32_t*>(P<char>(c->misc) + 1024);  // 256 words nothing publishes
+    cudaMemsetAsync(look, 0, 1024, st);
+    launch_lookback_timeout_test(look, status, st);
+  } else {
+    launch_mbar_timeout_test(status, st);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "bounded-wait check");
 }
 
 vrs_status vrs_probe_orders(vrs_ctx* c, const float* d_probes, int n_probes, int max_len, int32_t* d_ids,

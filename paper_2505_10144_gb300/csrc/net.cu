@@ -324,9 +324,10 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar) {
 
 // waits for the phase of the given parity; false when the wait gave up or another thread
 // of the block did (*abort)
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile uint32_t* abort) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile uint32_t* abort,
+                                          long long limit = kWaitLimit) {
   uint32_t done = 0;
-  for (long long it = 0; it < kWaitLimit && !done; ++it) {
+  for (long long it = 0; it < limit && !done; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -424,6 +425,20 @@ __device__ __forceinline__ void issue_tile(int layer, int mt, uint32_t d, uint32
              b0 + (uint64_t)((t * 4 + 2 * h) * (int)(bplane >> 4)), id, (t | h) != 0);
     }
   }
+}
+
+// failure-detection check: phase 0 of a fresh mbarrier never completes (nothing arrives),
+// so the kernel's bounded wait gives up after `limit` polls and raises kStTimeout
+__global__ void mbar_timeout_kernel(uint32_t* status, int limit) {
+  __shared__ uint64_t bar;
+  __shared__ uint32_t abort;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+    abort = 0u;
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(smem_u32(&bar), 0u, &abort, limit);
+  if (!ok && threadIdx.x == 0) atomicOr(status, kStTimeout);
 }
 
 // 8 BF16 values of one 16-byte plane slot
@@ -739,6 +754,8 @@ void net_periphery(const float* params, const float* low, float* out, const uint
   net_periphery_kernel<<<grid, kNetThreads, kNetSmem, st>>>(params, low, out, tile_class, views, n_views,
                                                             tiles_per_view, W, H, status);
 }
+
+void launch_mbar_timeout_test(uint32_t* status, cudaStream_t st) { mbar_timeout_kernel<<<1, 128, 0, st>>>(status, 1000); }
 
 int net_smem_bytes() { return kNetSmem; }
 

@@ -28,6 +28,40 @@ constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1u;
 constexpr int kSpinLimit = 1 << 22;
 
+// Decoupled look-back: the sum of digit d's counts over the tiles before `tile`, read from
+// their published (flag | count) words, walking back until a tile that holds its full
+// prefix.  A word not yet published is polled again; after spin_limit such polls the wait
+// gives up, raises kStTimeout and returns false (excl then holds a partial sum).
+__device__ __forceinline__ bool lookback_prefix(uint32_t* look, long long tile, int d, int spin_limit,
+                                                uint32_t* status, uint32_t& excl) {
+  excl = 0;
+  long long j = tile - 1;
+  int spins = 0;
+  while (j >= 0) {
+    const uint32_t lv = atomicAdd(look + j * 256 + d, 0u);
+    const uint32_t flag = lv & ~kCountMask;
+    if (flag == 0u) {
+      if (++spins > spin_limit) {
+        atomicOr(status, kStTimeout);
+        return false;
+      }
+      __nanosleep(20);
+      continue;
+    }
+    excl += lv & kCountMask;
+    if (flag == kFlagPrefix) break;
+    --j;
+  }
+  return true;
+}
+
+// failure-detection check: tile 1 waits on tile 0's words, which nothing publishes (the
+// caller zeroes them), so every thread's wait gives up after spin_limit polls
+__global__ void lookback_timeout_kernel(uint32_t* look, uint32_t* status, int spin_limit) {
+  uint32_t excl;
+  lookback_prefix(look, 1, (int)threadIdx.x, spin_limit, status, excl);
+}
+
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   uint32_t x = v;
@@ -208,23 +242,7 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const uint64_t* __rest
     }
     uint32_t excl = 0;
     if (tile > 0) {
-      long long j = (long long)tile - 1;
-      int spins = 0;
-      while (j >= 0) {
-        const uint32_t lv = atomicAdd(look + j * 256 + d, 0u);
-        const uint32_t flag = lv & ~kCountMask;
-        if (flag == 0u) {
-          if (++spins > kSpinLimit) {
-            atomicOr(status, kStTimeout);
-            break;
-          }
-          __nanosleep(20);
-          continue;
-        }
-        excl += lv & kCountMask;
-        if (flag == kFlagPrefix) break;
-        --j;
-      }
+      lookback_prefix(look, tile, d, kSpinLimit, status, excl);
       atomicExch(my_look, kFlagPrefix | (excl + cnt));
     }
     S.global_base[d] = digit_offsets[d] + excl;
@@ -346,6 +364,10 @@ void launch_ranges(const uint64_t* keys, const uint32_t* d_n, long long cap, uin
   if (cap <= 0) return;
   const unsigned grid = (unsigned)std::min<long long>((cap + 255) / 256, (long long)device_sm_count() * 8);
   ranges_kernel<<<grid, 256, 0, st>>>(keys, d_n, ranges, n_tiles);
+}
+
+void launch_lookback_timeout_test(uint32_t* zeroed_look, uint32_t* status, cudaStream_t st) {
+  lookback_timeout_kernel<<<1, 256, 0, st>>>(zeroed_look, status, 1000);
 }
 
 }  // namespace vrs

@@ -875,22 +875,55 @@ def main():
                                     "blended_pairs": cnt["blended"], "flops": flops},
                 "avg_launch_ms": render_ms}
     # end to end through the public API: camera/gaze in (pinned staging -> device inside
-    # the replay), both images back to pinned host memory every frame
+    # the replay), both images back to pinned host memory every frame.  Serialized: the
+    # read-back follows the replay on one stream.  Pipelined, as a frame loop runs it: the
+    # image of frame i goes device-to-device into one of two staging buffers, then
+    # device-to-host on a copy stream while frame i + 1 renders.
     host = torch.empty((2, 3, H_IMG, W_IMG), dtype=torch.float32, pin_memory=True)
-    for i in range(args.warmup):
+    n_e2e = min(40, args.steps)
+
+    def serialized(i):
         fr = wl.frames[i % len(wl.frames)]
         host.copy_(G.replay(fr.cameras, fr.foveas), non_blocking=True)
-    barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_e2e = min(40, args.steps)
-    e0.record()
-    for i in range(n_e2e):
-        fr = wl.frames[(args.warmup + i) % len(wl.frames)]
-        host.copy_(G.replay(fr.cameras, fr.foveas), non_blocking=True)
-    e1.record()
-    barrier()
-    Rg.check()
-    e2e_fps = ws * n_e2e / (e0.elapsed_time(e1) / 1e3)
+
+    cur, cs = torch.cuda.current_stream(), torch.cuda.Stream()
+    stage = [torch.empty_like(out) for _ in range(2)]
+    hosts = [host, torch.empty((2, 3, H_IMG, W_IMG), dtype=torch.float32, pin_memory=True)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    staged = [torch.cuda.Event() for _ in range(2)]
+    used = [False, False]
+
+    def pipelined(i):
+        fr = wl.frames[i % len(wl.frames)]
+        img = G.replay(fr.cameras, fr.foveas)
+        k = i % 2
+        if used[k]:
+            cur.wait_event(copied[k])  # staging buffer k was read out two frames ago
+        stage[k].copy_(img, non_blocking=True)
+        staged[k].record(cur)
+        cs.wait_event(staged[k])
+        with torch.cuda.stream(cs):
+            hosts[k].copy_(stage[k], non_blocking=True)
+            copied[k].record(cs)
+        used[k] = True
+
+    def timed_e2e(step):
+        for i in range(args.warmup):
+            step(i)
+        cur.wait_stream(cs)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(n_e2e):
+            step(args.warmup + i)
+        cur.wait_stream(cs)  # the last read-back is inside the timed region
+        e1.record()
+        barrier()
+        Rg.check()
+        return ws * n_e2e / (e0.elapsed_time(e1) / 1e3)
+
+    e2e_serial = timed_e2e(serialized)
+    e2e_fps = timed_e2e(pipelined)
     import ctypes
     from paper_2505_10144_gb300 import _lib
     h2d = 2 * (ctypes.sizeof(_lib.Camera) + ctypes.sizeof(_lib.Fovea))
@@ -925,8 +958,12 @@ def main():
         "counters_per_frame": cnt,
         "roofline": roofline,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "path": "GraphedRender.replay (vrs_update_views + graph replay) + device-to-host copy of both "
-                        "eyes into pinned memory"},
+                "path": "GraphedRender.replay (vrs_update_views + graph replay), then both eyes to pinned host "
+                        "memory every frame: device-to-device into one of two staging buffers and device-to-host "
+                        "on a copy stream, overlapping the next frame's render",
+                "serialized_value": e2e_serial,
+                "serialized_path": "the same calls with the device-to-host copy on the render stream after each "
+                                   "replay"},
         "gpu_launches": kernels_per_frame * args.steps,
         "clocks": clocks,
         "measured_peaks": peaks,

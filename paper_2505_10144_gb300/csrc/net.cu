@@ -560,19 +560,46 @@ __global__ void __launch_bounds__(kNetThreads, 1) net_periphery_kernel(const flo
     const int group = warp >> 2;  // takes the M tiles numbered group mod kEpiGroups
     float* patch = reinterpret_cast<float*>(sm + kOffLow);
     uint32_t cnt = 0, ph_full = 0;
-    for (long long tg = blockIdx.x; tg < n_tiles && ok; tg += gridDim.x) {
-      if (tile_class[tg] != kClassPeriphery) continue;
+    // the next periphery tile of this block at or after tg
+    auto next_tile = [&](long long tg) {
+      while (tg < n_tiles && tile_class[tg] != kClassPeriphery) tg += gridDim.x;
+      return tg;
+    };
+    // the half-resolution patch under tile tg and its halo, this thread's values of it
+    // (loads issued now, consumed when the tile starts)
+    constexpr int kPatchPer = (3 * kLowP * kLowP + kEpiThreads - 1) / kEpiThreads;
+    auto load_patch = [&](long long tg, float pf[kPatchPer]) {
+      if (tg >= n_tiles) return;
+      const int view = (int)(tg / tiles_per_view), t = (int)(tg % tiles_per_view);
+      const int ntx = views[view].ntx;
+      const int px0 = (t % ntx) * (kT / 2) - 2, py0 = (t / ntx) * (kT / 2) - 2;
+      const float* L = low + (long long)view * 3 * HW2;
+#pragma unroll
+      for (int u = 0; u < kPatchPer; ++u) {
+        const int i = tid + u * kEpiThreads;
+        if (i < 3 * kLowP * kLowP) {
+          const int c = i / (kLowP * kLowP), r = (i / kLowP) % kLowP, j = i % kLowP;
+          const int gy = min(max(py0 + r, 0), H2 - 1), gx = min(max(px0 + j, 0), W2 - 1);
+          pf[u] = L[c * HW2 + (long long)gy * W2 + gx];
+        }
+      }
+    };
+    float pf[kPatchPer];
+    long long tg = next_tile(blockIdx.x);
+    load_patch(tg, pf);
+    for (; tg < n_tiles && ok;) {
       const int view = (int)(tg / tiles_per_view), t = (int)(tg % tiles_per_view);
       const ViewParams& vp = views[view];
       const int ox = (t % vp.ntx) * kT, oy = (t / vp.ntx) * kT;
-      const float* L = low + (long long)view * 3 * HW2;
-      // the half-resolution patch under the tile and its halo, one load per value
       const int px0 = ox / 2 - 2, py0 = oy / 2 - 2;
-      for (int i = tid; i < 3 * kLowP * kLowP; i += kEpiThreads) {
-        const int c = i / (kLowP * kLowP), r = (i / kLowP) % kLowP, j = i % kLowP;
-        const int gy = min(max(py0 + r, 0), H2 - 1), gx = min(max(px0 + j, 0), W2 - 1);
-        patch[i] = L[c * HW2 + (long long)gy * W2 + gx];
+#pragma unroll
+      for (int u = 0; u < kPatchPer; ++u) {
+        const int i = tid + u * kEpiThreads;
+        if (i < 3 * kLowP * kLowP) patch[i] = pf[u];
       }
+      // the following tile and its patch, loading while this tile is computed
+      const long long tg_next = next_tile(tg + gridDim.x);
+      load_patch(tg_next, pf);
       asm volatile("bar.sync 2, %0;" ::"n"(kEpiThreads));
       // x plane (halo 3): BF16 bilinear input, channels 3..7 zero; the float input of the
       // 32 x 32 outputs is kept for the residual
@@ -654,6 +681,7 @@ __global__ void __launch_bounds__(kNetThreads, 1) net_periphery_kernel(const flo
       // the next tile's patch, x plane and residual input overwrite shared memory: conv3's
       // MMAs (which read R0) have all completed, and every epilogue warp is past its reads
       asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads));
+      tg = tg_next;
     }
   }
   if (!ok) atomicOr(status, kStTimeout);

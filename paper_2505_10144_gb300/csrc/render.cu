@@ -899,54 +899,50 @@ struct Tree16 {
 constexpr unsigned kTreeInitLo = 0xeca86420u, kTreeInitHi = 0x0c840800u;
 __device__ __forceinline__ int tree_root(const Tree16& t) { return (int)(t.hi & 0xFu); }
 
-// key x now sits in slot s: replay s's path; returns the root winner's key
+// key x now sits in slot s: replay s's path; returns the root winner's key.  The four
+// opponents (the winners of the siblings of the path's nodes) are off the path, so they
+// are read from the tree words before any update and their keys loaded together; the
+// matches then run as a chain of compares only.
 __device__ __forceinline__ unsigned long long tree_replay(Tree16& t, const unsigned long long* kk, int lane, int s,
                                                          unsigned long long x) {
+  const int s1 = (int)((t.lo >> (4 * ((s >> 1) ^ 1))) & 0xFu);
+  const int s2 = (int)((t.hi >> (4 * (3 + ((s >> 2) ^ 1)))) & 0xFu);
+  const int s3 = (int)((t.hi >> (4 * (1 + ((s >> 3) ^ 1)))) & 0xFu);
+  const int s0 = s ^ 1;
+  const unsigned long long k0 = kk[s0 * 32 + lane], k1 = kk[s1 * 32 + lane], k2 = kk[s2 * 32 + lane],
+                           k3 = kk[s3 * 32 + lane];
   int cs = s;
   unsigned long long ck = x;
-  // level 0: leaf s against leaf s ^ 1; the winner goes to node 8 + s / 2 (lo)
+  if (k0 < ck) {
+    ck = k0;
+    cs = s0;
+  }
   {
-    const int ss = s ^ 1;
-    const unsigned long long sk = kk[ss * 32 + lane];
-    if (sk < ck) {
-      ck = sk;
-      cs = ss;
-    }
     const int sh = 4 * (s >> 1);
     t.lo = (t.lo & ~(0xFu << sh)) | ((unsigned)cs << sh);
   }
-  // level 1: node 8 + s / 2 against its sibling (lo); the winner to node 4 + s / 4 (hi)
+  if (k1 < ck) {
+    ck = k1;
+    cs = s1;
+  }
+  unsigned hi = t.hi;
   {
-    const int ss = (int)((t.lo >> (4 * ((s >> 1) ^ 1))) & 0xFu);
-    const unsigned long long sk = kk[ss * 32 + lane];
-    if (sk < ck) {
-      ck = sk;
-      cs = ss;
-    }
     const int sh = 4 * (3 + (s >> 2));
-    t.hi = (t.hi & ~(0xFu << sh)) | ((unsigned)cs << sh);
+    hi = (hi & ~(0xFu << sh)) | ((unsigned)cs << sh);
   }
-  // level 2: node 4 + s / 4 against its sibling (hi); the winner to node 2 + s / 8 (hi)
+  if (k2 < ck) {
+    ck = k2;
+    cs = s2;
+  }
   {
-    const int ss = (int)((t.hi >> (4 * (3 + ((s >> 2) ^ 1)))) & 0xFu);
-    const unsigned long long sk = kk[ss * 32 + lane];
-    if (sk < ck) {
-      ck = sk;
-      cs = ss;
-    }
     const int sh = 4 * (1 + (s >> 3));
-    t.hi = (t.hi & ~(0xFu << sh)) | ((unsigned)cs << sh);
+    hi = (hi & ~(0xFu << sh)) | ((unsigned)cs << sh);
   }
-  // level 3: node 2 + s / 8 against its sibling (hi); the winner to the root (hi)
-  {
-    const int ss = (int)((t.hi >> (4 * (1 + ((s >> 3) ^ 1)))) & 0xFu);
-    const unsigned long long sk = kk[ss * 32 + lane];
-    if (sk < ck) {
-      ck = sk;
-      cs = ss;
-    }
-    t.hi = (t.hi & ~0xFu) | (unsigned)cs;
+  if (k3 < ck) {
+    ck = k3;
+    cs = s3;
   }
+  t.hi = (hi & ~0xFu) | (unsigned)cs;
   return ck;
 }
 

@@ -899,48 +899,58 @@ struct Tree16 {
 constexpr unsigned kTreeInitLo = 0xeca86420u, kTreeInitHi = 0x0c840800u;
 __device__ __forceinline__ int tree_root(const Tree16& t) { return (int)(t.hi & 0xFu); }
 
-// key x now sits in slot s: replay s's path; returns the root winner's key.  The four
-// opponents (the winners of the siblings of the path's nodes) are off the path, so they
-// are read from the tree words before any update and their keys loaded together; the
-// matches then run as a chain of compares only.
-__device__ __forceinline__ unsigned long long tree_replay(Tree16& t, const unsigned long long* kk, int lane, int s,
-                                                         unsigned long long x) {
-  const int s1 = (int)((t.lo >> (4 * ((s >> 1) ^ 1))) & 0xFu);
-  const int s2 = (int)((t.hi >> (4 * (3 + ((s >> 2) ^ 1)))) & 0xFu);
-  const int s3 = (int)((t.hi >> (4 * (1 + ((s >> 3) ^ 1)))) & 0xFu);
-  const int s0 = s ^ 1;
-  const unsigned long long k0 = kk[s0 * 32 + lane], k1 = kk[s1 * 32 + lane], k2 = kk[s2 * 32 + lane],
-                           k3 = kk[s3 * 32 + lane];
+// The opponents of a replay of slot s: the winners of the siblings of the path's nodes,
+// which the replay does not change, with their keys (loaded together)
+struct TreeOpp {
+  int s0, s1, s2, s3;
+  unsigned long long k0, k1, k2, k3;
+};
+__device__ __forceinline__ TreeOpp tree_opponents(const Tree16& t, const unsigned long long* kk, int lane, int s) {
+  TreeOpp o;
+  o.s0 = s ^ 1;
+  o.s1 = (int)((t.lo >> (4 * ((s >> 1) ^ 1))) & 0xFu);
+  o.s2 = (int)((t.hi >> (4 * (3 + ((s >> 2) ^ 1)))) & 0xFu);
+  o.s3 = (int)((t.hi >> (4 * (1 + ((s >> 3) ^ 1)))) & 0xFu);
+  o.k0 = kk[o.s0 * 32 + lane];
+  o.k1 = kk[o.s1 * 32 + lane];
+  o.k2 = kk[o.s2 * 32 + lane];
+  o.k3 = kk[o.s3 * 32 + lane];
+  return o;
+}
+
+// key x now sits in slot s: the four matches of s's path against the opponents, as a
+// chain of compares; returns the root winner's key
+__device__ __forceinline__ unsigned long long tree_play(Tree16& t, int s, unsigned long long x, const TreeOpp& o) {
   int cs = s;
   unsigned long long ck = x;
-  if (k0 < ck) {
-    ck = k0;
-    cs = s0;
+  if (o.k0 < ck) {
+    ck = o.k0;
+    cs = o.s0;
   }
   {
     const int sh = 4 * (s >> 1);
     t.lo = (t.lo & ~(0xFu << sh)) | ((unsigned)cs << sh);
   }
-  if (k1 < ck) {
-    ck = k1;
-    cs = s1;
+  if (o.k1 < ck) {
+    ck = o.k1;
+    cs = o.s1;
   }
   unsigned hi = t.hi;
   {
     const int sh = 4 * (3 + (s >> 2));
     hi = (hi & ~(0xFu << sh)) | ((unsigned)cs << sh);
   }
-  if (k2 < ck) {
-    ck = k2;
-    cs = s2;
+  if (o.k2 < ck) {
+    ck = o.k2;
+    cs = o.s2;
   }
   {
     const int sh = 4 * (1 + (s >> 3));
     hi = (hi & ~(0xFu << sh)) | ((unsigned)cs << sh);
   }
-  if (k3 < ck) {
-    ck = k3;
-    cs = s3;
+  if (o.k3 < ck) {
+    ck = o.k3;
+    cs = o.s3;
   }
   t.hi = (hi & ~0xFu) | (unsigned)cs;
   return ck;
@@ -952,24 +962,27 @@ __device__ __forceinline__ void tree3_push(Px& p, Tree16& t, float3& hc, unsigne
                                            const float4* __restrict__ recv) {
   if (p.n3 < K3) {  // filling: the next free slot
     const int s = p.n3++;
+    const TreeOpp o = tree_opponents(t, kk, lane, s);
     kk[s * 32 + lane] = x;
     aa[s * 32 + lane] = alpha;
     const int w0 = tree_root(t);
-    tree_replay(t, kk, lane, s, x);
+    tree_play(t, s, x, o);
     if (tree_root(t) != w0 || s == 0) hc = c;
     return;
   }
+  // the root's key and alpha and the opponents of its slot, loaded together
   const int w = tree_root(t);
+  const TreeOpp o = tree_opponents(t, kk, lane, w);
   const unsigned long long m = kk[w * 32 + lane];
+  const float am = aa[w * 32 + lane];
   if (x < m) {  // x is the smallest: out at once
     blend_c<STATS, BWD>(p, alpha, (int)(x & 0xffffffffu), c, recv);
     return;
   }
-  const float am = aa[w * 32 + lane];
   const float3 mc = hc;
   kk[w * 32 + lane] = x;
   aa[w * 32 + lane] = alpha;
-  const unsigned long long nk = tree_replay(t, kk, lane, w, x);
+  const unsigned long long nk = tree_play(t, w, x, o);
   const int nw = tree_root(t);
   hc = nw == w ? c : rec_colour(recv, (int)(nk & 0xffffffffu));
   blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);
@@ -980,11 +993,12 @@ template <bool STATS, bool BWD>
 __device__ __forceinline__ void tree3_pop(Px& p, Tree16& t, float3& hc, unsigned long long* kk,
                                           const float* aa, int lane, const float4* __restrict__ recv) {
   const int w = tree_root(t);
+  const TreeOpp o = tree_opponents(t, kk, lane, w);
   const unsigned long long m = kk[w * 32 + lane];
   const float am = aa[w * 32 + lane];
   const float3 mc = hc;
   kk[w * 32 + lane] = kEmptyKey;
-  const unsigned long long nk = tree_replay(t, kk, lane, w, kEmptyKey);
+  const unsigned long long nk = tree_play(t, w, kEmptyKey, o);
   p.n3--;
   if (p.n3 > 0) hc = rec_colour(recv, (int)(nk & 0xffffffffu));
   blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);

@@ -51,6 +51,22 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest value of x over the ranks of the process group (a job's time is its
+    slowest rank's); x itself without a group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws: int, units_per_rank: float, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return ws * units_per_rank / (max_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -105,11 +121,17 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_trajectory(n_frames, rank=0):
+    """The head trajectory of one rank: every rank renders its own frames of the same
+    scene (weak scaling), each from its own seed."""
+    from paper_2505_10144_gb300 import synth
+    return synth.vr_trajectory(n_frames, synth.rng_for(1, salt=100 + rank), W_IMG, H_IMG)
+
+
 def make_workload(n_frames, rank=0):
     from paper_2505_10144_gb300 import synth
     scene = synth.shell_scene(N_GAUSS, synth.rng_for(1), sh_degree=3)
-    wl = synth.vr_trajectory(n_frames, synth.rng_for(1, salt=100 + rank), W_IMG, H_IMG)
-    return scene, wl
+    return scene, rank_trajectory(n_frames, rank)
 
 
 def crop_camera(cam, x0, y0, w, h):
@@ -287,7 +309,7 @@ def ncu_case(args, api, torch):
     R.close()
 
 
-def run_batched(args, api, torch, ws, rank):
+def run_batched(args, api, torch, ws, rank, pg=None):
     """Three scenes (200k, 1M, 3M Gaussians) x 8 head poses x 2 eyes = 48 views of
     2064x2208, foveated, in one vrs_render (one sort, one persistent render launch)
     captured in a CUDA graph; the autotuner picks the windows and CTA cap."""
@@ -331,7 +353,8 @@ def run_batched(args, api, torch, ws, rank):
     R.check()
     st = R.stats()
     line = {"metric": "batched views/s (3 scenes x 8 poses x 2 eyes, 2064x2208, one graph replay)",
-            "value": 48 * len(ms) / (sum(ms) / 1e3), "unit": "views/s", "n_gpus": ws, "steps": len(ms),
+            "value": job_rate(ws, 48 * len(ms), max_over_ranks(sum(ms), pg)), "unit": "views/s", "n_gpus": ws,
+            "steps": len(ms),
             "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched_3_scenes_200k_1M_3M_48_views_foveated", "views": 48,
@@ -344,7 +367,7 @@ def run_batched(args, api, torch, ws, rank):
     R.close()
 
 
-def run_finetune(args, api, torch, ws, rank):
+def run_finetune(args, api, torch, ws, rank, pg=None):
     """Fine-tuning step through the rasterizer: 500k Gaussians, 4 views of 1280x1280,
     110 deg FOV, 0.8 L1 + 0.2 (1 - SSIM), gradients for every parameter, Adam.  The
     targets are renders of a perturbed copy of the scene (means + N(0, 0.01), log-scales +
@@ -387,7 +410,8 @@ def run_finetune(args, api, torch, ws, rank):
     ms = e0.elapsed_time(e1) / steps
     R.check()
     line = {"metric": "fine-tuning steps/s (4 views 1280x1280, 500k Gaussians, render+loss+backward+Adam)",
-            "value": 1e3 / ms, "unit": "steps/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
+            "value": job_rate(ws, steps, max_over_ranks(ms * steps, pg)), "unit": "steps/s", "n_gpus": ws,
+            "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": "finetune_500k_4x1280", "windows": list(WINDOWS)},
             "loss_first": losses[0], "loss_last": losses[-1]}
@@ -396,7 +420,7 @@ def run_finetune(args, api, torch, ws, rank):
     R.close()
 
 
-def run_net(args, api, torch, ws, rank):
+def run_net(args, api, torch, ws, rank, pg=None):
     """Learned periphery: 1M Gaussians (room shell, SH degree 3), stereo 2064x2208,
     periphery at 1/4 of the pixels.  The network is trained on the GPU (library kernels)
     on 2000 seeded pose pairs (256x256 crops of random head poses: half-resolution
@@ -452,7 +476,8 @@ def run_net(args, api, torch, ws, rank):
     ms_net, ms_plain = timed(fnet, n), timed(fplain, n)
     R.check()
     line = {"metric": "stereo frames/s with the learned periphery (1M Gaussians, 2x2064x2208) and its PSNR vs plain",
-            "value": len(ms_net) / (sum(ms_net) / 1e3), "unit": "frames/s", "n_gpus": ws, "steps": len(ms_net),
+            "value": job_rate(ws, len(ms_net), max_over_ranks(sum(ms_net), pg)), "unit": "frames/s",
+            "n_gpus": ws, "steps": len(ms_net),
             "warmup": 3, "ms_per_step": statistics.mean(ms_net), "p99_ms": float(np.percentile(ms_net, 99)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32 render",
             "data": "synthetic", "config": {"workload": "learned_periphery_1M_stereo", "train_pairs": 2000,
@@ -636,13 +661,13 @@ def main():
         ncu_case(args, api, torch)
         return
     if args.workload == "batched":
-        run_batched(args, api, torch, ws, rank)
+        run_batched(args, api, torch, ws, rank, pg)
         return
     if args.workload == "finetune":
-        run_finetune(args, api, torch, ws, rank)
+        run_finetune(args, api, torch, ws, rank, pg)
         return
     if args.workload == "net":
-        run_net(args, api, torch, ws, rank)
+        run_net(args, api, torch, ws, rank, pg)
         return
     # measured denominators of the render roofline (microbenchmarks, a few ms each)
     peaks = api.measure_peaks()
@@ -728,12 +753,8 @@ def main():
         t_wall = time.perf_counter()
         ms_fov = timed_graph(G, Rg, args.steps)
         t_wall = time.perf_counter() - t_wall
-    total_ms = sum(ms_fov)
-    if pg:
-        t = torch.tensor([total_ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(ms_fov), pg)
+    value = job_rate(ws, args.steps, total_ms)
     # the same frames issued eagerly (one vrs_render call each), with per-stage events
     ms_eager, stages, ncalls = timed_eager(fov_cfg, min(args.plain_steps, args.steps), profile=True)
     # the same frames as two monocular passes (one vrs_render per eye): what the fused
@@ -922,7 +943,7 @@ def main():
         e1.record()
         barrier()
         Rg.check()
-        return ws * n_e2e / (e0.elapsed_time(e1) / 1e3)
+        return job_rate(ws, n_e2e, max_over_ranks(e0.elapsed_time(e1), pg))
 
     e2e_serial = timed_e2e(serialized)
     e2e_fps = timed_e2e(pipelined)

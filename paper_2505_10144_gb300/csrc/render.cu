@@ -130,32 +130,14 @@ struct Px {
 // T_final saved, every term is available in front-to-back order:
 //   dL/dc_i     = dL/dC alpha_i T_i
 //   dL/dalpha_i = T_i (dL/dC . c_i) - (dL/dC . (C_final - C_<=i) + dL/dT_final T_final) / (1 - alpha_i)
-// Adds v[16] to grad (the record gradient of Gaussian g) once per group of the lanes
-// executing together that hold the same g: the group's lowest lane gathers the others'
-// values by shuffles and alone issues the atomics.  Neighbouring samples tend to blend the
-// same Gaussian at the same step, so this divides the atomic traffic on L2.
-__device__ __forceinline__ void grad_add16(float* __restrict__ grad, int g, float v[16]) {
-  const unsigned act = __activemask();
-  const unsigned peers = __match_any_sync(act, g);
-  const int lane = threadIdx.x & 31;
-  const bool leader = (__ffs(peers) - 1) == lane;
-  unsigned rest = leader ? (peers & (peers - 1u)) : 0u;  // the leader's peers, itself excluded
-  const int n = __popc(rest);
-  const int rounds = __reduce_max_sync(act, n);
-  for (int it = 0; it < rounds; ++it) {
-    const int src = rest ? __ffs(rest) - 1 : lane;
-    rest &= rest - 1u;
+// Adds v[16] to grad (the record gradient of one Gaussian) with four 16-byte vector
+// atomics (grad is 64-byte aligned per Gaussian).  Gathering the lanes that blend the same
+// Gaussian in the same step by shuffles, with one lane issuing the atomics, ran slower
+// once the atomics were vectors: 27.5 against 22.1 ms on four 1280^2 views.
+__device__ __forceinline__ void grad_add16(float* __restrict__ grad, float v[16]) {
+  float4* g4 = reinterpret_cast<float4*>(grad);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const float o = __shfl_sync(act, v[k], src);
-      if (leader && it < n) v[k] += o;
-    }
-  }
-  if (leader) {  // four 16-byte vector atomics (grad is 64-byte aligned per Gaussian)
-    float4* g4 = reinterpret_cast<float4*>(grad);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) atomicAdd(g4 + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
-  }
+  for (int k = 0; k < 4; ++k) atomicAdd(g4 + k, make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]));
 }
 
 // d(loss)/d(record) of one blended pair, accumulated into the record gradient (16
@@ -165,7 +147,7 @@ __device__ __forceinline__ void grad_add16(float* __restrict__ grad, int g, floa
 //   dL/dc_i     = dL/dC alpha_i T_i
 //   dL/dalpha_i = T_i (dL/dC . c_i) - (dL/dC . (C_final - C_<=i) + dL/dT_final T_final) / (1 - alpha_i)
 __device__ __forceinline__ void blend_grad(const Px& p, float alpha, const float4* r, float Tb, float Cb0, float Cb1,
-                                           float Cb2, float* __restrict__ grad, int g) {
+                                           float Cb2, float* __restrict__ grad) {
   const float4 f0 = r[0], f1 = r[1], f2 = r[2], f5 = r[5];
   const float aT = alpha * Tb;
   const float c0 = f5.y, c1 = f5.z, c2 = f5.w;
@@ -205,7 +187,7 @@ __device__ __forceinline__ void blend_grad(const Px& p, float alpha, const float
     v[11] = gqn * b * b;
     v[12] = gl;
   }
-  grad_add16(grad, g, v);
+  grad_add16(grad, v);
 }
 
 template <bool STATS, bool BWD = false>
@@ -216,7 +198,7 @@ __device__ __forceinline__ void blend(Px& p, float alpha, int g, const float4* _
     p.active = false;
     return;
   }
-  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16, g);
+  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16);
   const float4 c = recv[(long long)g * kRecF4 + 5];
   const float aT = alpha * p.T;
   p.C0 = fmaf(aT, c.y, p.C0);
@@ -870,7 +852,7 @@ __device__ __forceinline__ void blend_c(Px& p, float alpha, int g, float3 c, con
     p.active = false;
     return;
   }
-  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16, g);
+  if (BWD) blend_grad(p, alpha, recv + (long long)g * kRecF4, p.T, p.C0, p.C1, p.C2, p.grad + (long long)g * 16);
   const float aT = alpha * p.T;
   p.C0 = fmaf(aT, c.x, p.C0);
   p.C1 = fmaf(aT, c.y, p.C1);

@@ -330,7 +330,7 @@ def run_batched(args, api, torch, ws, rank, pg=None):
     cams, fovs, vs = views(0)
     R = api.Renderer()
     base = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=32, fovea_mode="bilinear")
-    cache = args.tune_cache or os.path.join(ROOT, "gpurun_out", "autotune.json")
+    cache = args.tune_cache or os.path.join(ROOT, "_build", "autotune.json")
     best, cands = autotune.autotune(R, scenes, vs, cams, fovs, base, cache_path=cache, reps=2)
     R.set_tuning(best["max_ctas_per_sm"])
     cfg = api.RenderConfig(sort_mode="hier", windows=tuple(best["windows"]), key_tile=32, fovea_mode="bilinear")

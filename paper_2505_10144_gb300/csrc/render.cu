@@ -721,6 +721,26 @@ __device__ __forceinline__ unsigned long long win16_push(Win16<K1>& w, unsigned 
   const unsigned bal = __ballot_sync(kFull, w.e < x);
   const int pos = __popc((bal >> (lane & 16)) & 0xFFFFu);
   const int su = slot - 1 < 0 ? 0 : slot - 1, sd = slot + 1 > 15 ? 15 : slot + 1;
+  // Both blocks of the warp full (the common case on long lists): the insertion only moves
+  // entries towards the head, so the shuffles of the upward move are skipped.  Measured on
+  // the VR stereo frame: 5.43 against 5.53 ms.  The same split of the 2x2 window ran slower
+  // (5.59 ms; its extra registers spill).
+  if (__all_sync(kFull, w.n >= K1)) {
+    const unsigned long long fdn = shfl64(w.e, sd, 16), fe0 = shfl64(w.e, 0, 16);
+    const unsigned fpdn = __shfl_sync(kFull, w.pl, sd, 16), fp0 = __shfl_sync(kFull, w.pl, 0, 16);
+    popl = xpl;
+    if (!do_push) return kEmptyKey;
+    if (pos == 0) return x;
+    if (slot < pos - 1) {
+      w.e = fdn;
+      w.pl = fpdn;
+    } else if (slot == pos - 1) {
+      w.e = x;
+      w.pl = xpl;
+    }
+    popl = fp0;
+    return fe0;
+  }
   const unsigned long long up = shfl64(w.e, su, 16), dn = shfl64(w.e, sd, 16), e0 = shfl64(w.e, 0, 16);
   const unsigned pup = __shfl_sync(kFull, w.pl, su, 16), pdn = __shfl_sync(kFull, w.pl, sd, 16),
                  p0 = __shfl_sync(kFull, w.pl, 0, 16);

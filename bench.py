@@ -371,10 +371,13 @@ def run_finetune(args, api, torch, ws, rank, pg=None):
     """Fine-tuning step through the rasterizer: 500k Gaussians, 4 views of 1280x1280,
     110 deg FOV, 0.8 L1 + 0.2 (1 - SSIM), gradients for every parameter, Adam.  The
     targets are renders of a perturbed copy of the scene (means + N(0, 0.01), log-scales +
-    N(0, 0.1)) made by this renderer; the oracle pins the gradients in the tests."""
+    N(0, 0.1)) made by this renderer; the oracle pins the gradients in the tests.
+    With N ranks the step is data-parallel over views: each rank renders 4 views of its
+    own, and one all-reduce of the flat gradient buffer averages the gradients before
+    every rank takes the same Adam step."""
     from paper_2505_10144_gb300 import synth
     scene = synth.shell_scene(N_GAUSS, synth.rng_for(3), sh_degree=3)
-    cams = synth.ring_views(4, 1280, 1280, 110.0, synth.rng_for(3, salt=1))
+    cams = synth.ring_views(4, 1280, 1280, 110.0, synth.rng_for(3, salt=1 + 1000 * rank))
     target_scene = synth.perturbed(scene, synth.rng_for(3, salt=2))
     R = api.Renderer()
     cfg = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=16)
@@ -384,14 +387,14 @@ def run_finetune(args, api, torch, ws, rank, pg=None):
     lrs = {"mean": 1.6e-4, "log_scale": 5e-3, "quat": 1e-3, "opacity_logit": 5e-2, "sh": 2.5e-3}
     opt = api.Adam(params, lrs)
     ds = api.DeviceScene(*[params[k] for k in names], 3)
-    grads = ds.zeros_like()
+    grads, gflat = ds.flat_zeros_like()
 
     def step():
         img = R.render([ds], [0] * 4, cams, None, cfg, save=True)
         loss, dimg = R.loss(img, target)
-        for t in grads.tensors():
-            t.zero_()
+        gflat.zero_()
         R.backward([ds], [0] * 4, cams, None, cfg, dimg, [grads])
+        api.average_gradients(gflat, pg)
         opt.step(dict(zip(names, grads.tensors())))
         return loss
 
@@ -413,7 +416,9 @@ def run_finetune(args, api, torch, ws, rank, pg=None):
             "value": job_rate(ws, steps, max_over_ranks(ms * steps, pg)), "unit": "steps/s", "n_gpus": ws,
             "steps": steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": "finetune_500k_4x1280", "windows": list(WINDOWS)},
+            "data": "synthetic", "config": {"workload": "finetune_500k_4x1280", "windows": list(WINDOWS),
+                                            "parallelism": f"dp{ws} over views" + (
+                                                ", one gradient all-reduce per step" if ws > 1 else "")},
             "loss_first": losses[0], "loss_last": losses[-1]}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -60,6 +60,19 @@ class DeviceScene:
     def zeros_like(self) -> "DeviceScene":
         return DeviceScene(*[torch.zeros_like(t) for t in self.tensors()], self.sh_degree)
 
+    def flat_zeros_like(self) -> tuple["DeviceScene", torch.Tensor]:
+        """Zeroed buffers shaped like these parameters, as views of one flat float32
+        buffer (each part starts on a 64-float boundary), and that buffer: gradients laid
+        out this way are cleared with one fill and reduced with one collective."""
+        sizes = [t.numel() for t in self.tensors()]
+        offs, o = [], 0
+        for n in sizes:
+            offs.append(o)
+            o += (n + 63) // 64 * 64
+        flat = torch.zeros(o, dtype=torch.float32, device=self.mean.device)
+        parts = [flat[a:a + n].view(t.shape) for a, n, t in zip(offs, sizes, self.tensors())]
+        return DeviceScene(*parts, self.sh_degree), flat
+
 
 def camera_c(cam) -> _lib.Camera:
     c = _lib.Camera()
@@ -357,6 +370,17 @@ class LossFunction(torch.autograd.Function):
 
 def l1_ssim_loss(renderer: Renderer, img: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
     return LossFunction.apply(renderer, img, target)
+
+
+def average_gradients(flat: torch.Tensor, dist) -> None:
+    """Data-parallel fine-tuning over views: every rank renders its own views of the same
+    scene, and the mean of the ranks' gradients (one all-reduce of the flat gradient
+    buffer, then a scale by 1 / world size) is the gradient of the loss averaged over all
+    the views, so every rank's Adam step stays identical.  No-op without a group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM)
+    flat.mul_(1.0 / dist.get_world_size())
 
 
 class Adam:

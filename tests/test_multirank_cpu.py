@@ -1,7 +1,8 @@
 """The benchmark's multi-rank logic on CPU with gloo, world size 2: every rank renders its
 own trajectory of the same scene, the job's time is the slowest rank's (all-reduce max)
-and the job's rate counts every rank's frames.  The GPU path is replicas only (the render
-shards by view with no exchange), so this host logic is all there is to the N > 1 path."""
+and the job's rate counts every rank's frames.  The render shards by view with no
+exchange (replicas); fine-tuning is data-parallel over views, and its one exchange, the
+all-reduce that averages the flat gradient buffer, is checked here with gloo ranks."""
 import json
 import os
 import socket
@@ -70,3 +71,53 @@ def test_reference_arm_prints_on_rank_zero_only(capsys):
 
     assert bench.run_reference(Args(), 2, 1) is None
     assert capsys.readouterr().out == ""
+
+
+def _grad_worker(rank, ws, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(ws), RANK=str(rank))
+    import torch
+    import torch.distributed as dist
+    sys.path.insert(0, str(ROOT))
+    from paper_2505_10144_gb300 import api, synth
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        scene = api.DeviceScene.from_host(synth.shell_scene(1000, synth.rng_for(3), sh_degree=3), device="cpu")
+        grads, flat = scene.flat_zeros_like()
+        g = torch.Generator().manual_seed(100 + rank)
+        for t in grads.tensors():  # this rank's gradients, written through the views
+            t.copy_(torch.randn(t.shape, generator=g))
+        mine = [t.clone() for t in grads.tensors()]
+        api.average_gradients(flat, dist)
+        torch.save({"mine": mine, "avg": [t.clone() for t in grads.tensors()]}, Path(out_dir, f"g{rank}.pt"))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_flat_gradient_buffer_is_one_allocation_of_aligned_views():
+    import torch
+    sys.path.insert(0, str(ROOT))
+    from paper_2505_10144_gb300 import api, synth
+    scene = api.DeviceScene.from_host(synth.shell_scene(1001, synth.rng_for(3), sh_degree=3), device="cpu")
+    grads, flat = scene.flat_zeros_like()
+    base = flat.data_ptr()
+    for t, p in zip(grads.tensors(), scene.tensors()):
+        assert t.shape == p.shape and t.is_contiguous() and t.dtype == torch.float32
+        off = (t.data_ptr() - base) // 4
+        assert off % 64 == 0 and off + t.numel() <= flat.numel()
+        t.fill_(1.0)
+    assert float(flat.sum()) == sum(p.numel() for p in scene.tensors())  # parts are disjoint
+    flat.zero_()
+    assert all(float(t.abs().sum()) == 0.0 for t in grads.tensors())
+    api.average_gradients(flat, None)  # no group: nothing to do
+
+
+def test_two_gloo_ranks_average_the_flat_gradient_buffer(tmp_path):
+    import torch
+    ws = 2
+    mp.start_processes(_grad_worker, args=(ws, _free_port(), str(tmp_path)), nprocs=ws, start_method="spawn")
+    r = [torch.load(Path(tmp_path, f"g{k}.pt")) for k in range(ws)]
+    for i in range(5):
+        want = (r[0]["mine"][i] + r[1]["mine"][i]) / 2
+        assert torch.allclose(r[0]["avg"][i], want, rtol=1e-6, atol=1e-7)
+        assert torch.equal(r[0]["avg"][i], r[1]["avg"][i])  # every rank takes the same step

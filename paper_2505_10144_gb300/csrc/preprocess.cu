@@ -335,23 +335,49 @@ __device__ __forceinline__ float order_key(int key_mode, float tile_key, const f
 // whatever the tile counts of the Gaussians, so few and many tiles, and culled
 // Gaussians, cost no idle lanes.  Kept tiles are counted per Gaussian in shared memory,
 // and ranked within their Gaussian in tile order for the key cache.
+// parameter rows a Gaussian's projection reads: mean 3, log-scale 3, quaternion 4,
+// opacity logit 1, and 3 per SH coefficient of the scene's degree
+__host__ __device__ inline int param_rows(int deg) { return 11 + 3 * (deg + 1) * (deg + 1); }
+
+__device__ __forceinline__ const float* param_row(const SceneDev& s, int r) {
+  if (r < 3) return s.mean + r * s.n;
+  if (r < 6) return s.ls + (r - 3) * s.n;
+  if (r < 10) return s.quat + (r - 6) * s.n;
+  if (r == 10) return s.logit;
+  return s.sh + (r - 11) * s.n;
+}
+
 __global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const ViewParams* __restrict__ views,
                                                             const int* __restrict__ view_list, int nv, int T,
                                                             int key_mode, Visibility vis, float4* __restrict__ rec,
                                                             float4* __restrict__ bbox, uint32_t* __restrict__ count,
                                                             unsigned long long* __restrict__ kcache) {
   __shared__ uint32_t s_cnt[256];
+  extern __shared__ float s_par[];  // [param_rows(deg)][256]: the block's parameters
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   uint32_t* wc = s_cnt + (threadIdx.x & ~31);  // this warp's 32 counters
   const long long warp_i0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
   const bool in = i < s.n;
+  // The block's parameters go to shared memory with asynchronous 4-byte copies, all in
+  // flight at once (coalesced rows of the SoA arrays); every view then projects from
+  // there.  Reading them with plain loads left the kernel waiting on one load at a time.
+  const int rows = param_rows(s.deg);
+  if (in) {
+    for (int r = 0; r < rows; ++r) {
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_par + r * 256 + threadIdx.x);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(param_row(s, r) + i) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const SceneDev sb{s_par, s_par + 3 * 256, s_par + 6 * 256, s_par + 10 * 256, s_par + 11 * 256, 256, s.deg};
   for (int k = 0; k < nv; ++k) {
     const int view = view_list[k];
     const ViewParams& vp = views[view];
     const long long vg = vp.base + i;
     float4 r[6], bb;
-    const bool ok = in && project_gaussian(s, i, vp, r, bb);
+    const bool ok = in && project_gaussian(sb, threadIdx.x, vp, r, bb);
     if (!ok) bb = make_float4(0.f, 0.f, -1.f, -1.f);
     Span sp = make_span(bb, vp, T, ok);
     // no visible tile in the rectangle: nothing to test (summed-area table, Sec. 4.3)
@@ -554,7 +580,9 @@ void launch_preprocess(const SceneDev& s, const ViewParams* d_views, const int* 
                        unsigned long long* kcache, cudaStream_t st) {
   if (s.n <= 0 || nv <= 0) return;
   const unsigned grid = (unsigned)((s.n + 255) / 256);
-  preprocess_kernel<<<grid, 256, 0, st>>>(s, d_views, d_view_list, nv, T, key_mode, vis, rec, bbox, count, kcache);
+  const int smem = param_rows(s.deg) * 256 * (int)sizeof(float);
+  cudaFuncSetAttribute(preprocess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  preprocess_kernel<<<grid, 256, smem, st>>>(s, d_views, d_view_list, nv, T, key_mode, vis, rec, bbox, count, kcache);
 }
 
 void launch_duplicate(const ViewParams* d_views, int n_views, const float4* rec, const float4* bbox,

@@ -70,3 +70,52 @@ def test_autotuner_picks_a_candidate_and_caches_it(setup, tmp_path):
     R.set_tuning(0)
     b = R.render(scenes, vs, cams, fovs, cfg)
     assert torch.equal(a, b)
+
+
+def test_full_size_batched_views_sampled_crops():
+    """The batched workload at full size, as the benchmark launches it: scenes of 200k, 1M
+    and 3M Gaussians x 8 head poses x 2 eyes = 48 views of 2064x2208, foveated, hierarchical
+    4/8/16, in one captured graph.  Crops of one view per scene (32-aligned, at the gaze
+    point and in the periphery) against oracle renders of the same rays, interior pixels."""
+    from oracle import native as on
+    from paper_2505_10144_gb300 import api, build
+    build.build()
+    W, H = 2064, 2208
+    hosts = [synth.shell_scene(n, synth.rng_for(2, salt=k), sh_degree=3)
+             for k, n in enumerate([200_000, 1_000_000, 3_000_000])]
+    cams, fovs, vs = [], [], []
+    for k in range(3):
+        for fr in synth.batched_poses(8, synth.rng_for(2, salt=10 + k), W, H):
+            cams += fr.cameras
+            fovs += fr.foveas
+            vs += [k, k]
+    R = api.Renderer()
+    try:
+        scenes = [api.DeviceScene.from_host(h) for h in hosts]
+        cfg = api.RenderConfig(sort_mode="hier", windows=(4, 8, 16), key_tile=32, fovea_mode="bilinear")
+        gr = api.GraphedRender(R, scenes, vs, cams, fovs, cfg)
+        out = gr.replay()
+        R.check()
+        tol = 2e-4
+        checked = 0
+        for k in range(3):
+            v = 16 * k + 2 * (3 + k) + (k & 1)  # pose 3 + k, left or right eye
+            cam, fv = cams[v], fovs[v]
+            for sx, sy in [(fv.gaze_x, fv.gaze_y), (300.0 + 500.0 * k, 1900.0 - 400.0 * k)]:
+                x0 = int(min(max(sx - 32, 0), W - 64)) // 32 * 32
+                y0 = int(min(max(sy - 32, 0), H - 64)) // 32 * 32
+                c2 = synth.Camera(cam.world_to_cam, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, 64, 64, cam.near_z)
+                f2 = synth.Fovea(fv.gaze_x - x0, fv.gaze_y - y0, fv.radius_px, fv.band_px)
+                ref = on.render(hosts[k], c2, "hier", windows=(4, 8, 16), key_tile=32, fovea=f2)
+                sub = out[v][:, y0:y0 + 64, x0:x0 + 64].cpu().numpy().astype(np.float64)
+                m = ref["marginal"].copy()
+                m[:2, :] = m[-2:, :] = True  # bilinear reads across the crop edge
+                m[:, :2] = m[:, -2:] = True
+                assert (~m).sum() > 1000, (k, sx, sy, m.mean())
+                d = np.abs(sub - ref["image"]).max(axis=0)
+                bad = (d > tol) & ~m
+                assert not bad.any(), (k, sx, sy, int(bad.sum()), float(d[~m].max()))
+                checked += 1
+        assert checked == 6
+    finally:
+        R.close()

@@ -140,3 +140,41 @@ def test_training_beats_bilinear_on_held_out_crops(R):
     after = float(((y - tv) ** 2).mean())
     assert losses[-40:].mean() < losses[:40].mean()
     assert after < 0.99 * before, (after, before)
+
+
+def test_full_size_vr_frame_network_sampled_crops(R):
+    """1M Gaussians, stereo 2064x2208, foveated with the network (the learned-periphery
+    workload's frame): the fused tensor-core kernel runs once over every periphery tile of
+    both eyes.  Crops of its output against the float64 network applied to the float64
+    bilinear upsample of the GPU's half-resolution image (the network's input): the top-left
+    and bottom-right corners (zero padding, the ragged last tile column) and an interior
+    crop, each compared where the crop's 3-pixel halo is complete."""
+    from oracle import grad as ograd
+    from paper_2505_10144_gb300 import api, periphery
+    W, H = 2064, 2208
+    scene = api.DeviceScene.from_host(synth.shell_scene(1_000_000, synth.rng_for(4), sh_degree=3))
+    fr = synth.vr_trajectory(3, synth.rng_for(4, salt=200), W, H).frames[2]
+    net = periphery.PeripheryNet(R, seed=4, last_scale=1.0)
+    low = torch.empty((2, 3, H // 2, W // 2), device="cuda")
+    cfg = api.RenderConfig(sort_mode="hier", windows=(4, 8, 16), key_tile=32, fovea_mode="net")
+    out = R.render([scene], [0, 0], fr.cameras, fr.foveas, cfg, low=low)
+    net.apply_periphery(low, out)
+    R.check()
+    mask = periphery.periphery_mask(fr, W, H).numpy()
+    outs = out.cpu().numpy().astype(np.float64)
+    lows = low.cpu().numpy().astype(np.float64)
+    checked = 0
+    for v in range(2):
+        x = ograd.bilinear_up2(torch.tensor(lows[v]))  # [3, H, W]
+        # (crop origin, input window origin): outputs [y0, y0 + 64) x [x0, x0 + 64)
+        for y0, x0 in [(0, 0), (64, W - 128), (H - 64, W - 64)]:
+            wy0, wx0 = max(y0 - 3, 0), max(x0 - 3, 0)
+            wy1, wx1 = min(y0 + 67, H), min(x0 + 67, W)
+            assert mask[v, y0:y0 + 64, x0:x0 + 64].all()
+            y, _ = onet.forward(x[None, :, wy0:wy1, wx0:wx1], net.numpy_weights())
+            ref = y[0, :, y0 - wy0:y0 - wy0 + 64, x0 - wx0:x0 - wx0 + 64].numpy()
+            d = np.abs(outs[v][:, y0:y0 + 64, x0:x0 + 64] - ref)
+            assert np.quantile(d, 0.99) < 1e-3 and d.max() < 3e-2, (v, y0, x0, np.quantile(d, 0.99), d.max())
+            assert np.abs(ref - x[:, y0:y0 + 64, x0:x0 + 64].numpy()).max() > 1e-3  # the network acts here
+            checked += 1
+    assert checked == 6

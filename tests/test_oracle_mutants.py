@@ -1,0 +1,114 @@
+"""Planted mistakes in the float64 gradient oracle (``oracle/grad.py``), on the CPU.
+
+The gradient oracle is pinned by central differences of the C forward oracle, which
+re-sorts and re-culls at every evaluation and shares no code with it.  These tests show
+that this pin is sharp enough: each plausible slip below (a sign in the real SH basis,
+the 1/2 in the Gaussian's exponent, the direction of the focus/periphery blend
+weight of Sec. 4.3, the bilinear weights of the upsampled periphery) makes the
+autograd gradient disagree with the differences.  The mistakes are planted by patching
+the oracle module inside the test only.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import grad as og
+from oracle import native as on
+from paper_2505_10144_gb300 import synth
+from scenes import random_scene
+
+TOL = 1e-6  # the central-difference pin's bound, relative to max(1, |gradient|)
+
+
+@pytest.fixture(scope="module")
+def case():
+    """A 96x96 foveated view in 32-pixel tiles: the centre tile holds the focus circle's
+    blend band (hybrid), the eight others are periphery; 12 Gaussians at SH degree 3."""
+    rng = np.random.default_rng(404)
+    sc = random_scene(12, rng, sh_degree=3, z=(1.5, 2.5), xy=0.9, ls_mu=-1.6, ls_sd=0.3)
+    sc = synth.Scene(*[np.ascontiguousarray(a, dtype=np.float64) for a in sc.arrays()], sc.sh_degree)
+    c = synth.camera_from_pose(np.eye(3), (0, 0, 0), 96, 96, 84.0)
+    fov = synth.Fovea(48.0, 48.0, 10.0, 5.0)
+    base = on.render(sc, c, "exact", key_tile=32, fovea=fov, want_orders=True)
+    cls = np.asarray(base["tile_class"]) & 3
+    assert (cls == 1).any() and (cls == 2).any()
+    w = rng.normal(size=base["image"].shape)
+    fd = {}
+    for name in ["mean", "log_scale", "quat", "opacity_logit", "sh"]:
+        flat = getattr(sc, name).reshape(-1)
+        for j in rng.choice(flat.size, size=min(16, flat.size), replace=False):
+            x0 = flat[j]
+            h = 1e-6 * max(1.0, abs(x0))
+            vals, same = [], True
+            for s in (+1, -1):
+                flat[j] = x0 + s * h
+                r = on.render(sc, c, "exact", key_tile=32, fovea=fov, want_orders=True)
+                same &= all(np.array_equal(r["orders"][k], base["orders"][k]) for k in (0, 1))
+                vals.append((r["image"] * w).sum())
+            flat[j] = x0
+            if same:  # otherwise a sort, cull or stop decision moved: not differentiable there
+                fd[(name, int(j))] = (vals[0] - vals[1]) / (2 * h)
+    assert len(fd) > 50
+    return sc, c, fov, base, w, fd
+
+
+def _worst(case):
+    """Largest disagreement of the oracle's autograd gradient with the differences."""
+    sc, c, fov, base, w, fd = case
+    g = og.image_grad(sc, c, base["orders"], w, base["tile_class"], fov)
+    return max(abs(v - g[n].reshape(-1)[j]) / max(1.0, abs(g[n].reshape(-1)[j])) for (n, j), v in fd.items())
+
+
+def test_unmodified_gradient_oracle_meets_the_pin(case):
+    assert _worst(case) <= TOL
+
+
+def _sh_sign_slip(degree, d):
+    b = _sh_basis(degree, d).clone()
+    b[1] = -b[1]  # the l=1, m=-1 term with the wrong sign
+    return b
+
+
+def _blend_weight_reversed(px, py, fovea):
+    return 1.0 - _fovea_weight(px, py, fovea)
+
+
+def _bilinear_weights_swapped(L):
+    """x2 bilinear upsampling with the two neighbours' fractions exchanged."""
+    Cc, h, wd = L.shape
+
+    def axis(n):
+        u = (np.arange(2 * n) + 0.5) / 2 - 0.5
+        i0 = np.floor(u).astype(np.int64)
+        return np.clip(i0, 0, n - 1), np.clip(i0 + 1, 0, n - 1), 1.0 - (u - i0)
+
+    ya, yb, fy = axis(h)
+    xa, xb, fx = axis(wd)
+    fx = torch.tensor(fx)[None, None, :]
+    fy = torch.tensor(fy)[None, :, None]
+    top = (1 - fx) * L[:, ya][:, :, xa] + fx * L[:, ya][:, :, xb]
+    bot = (1 - fx) * L[:, yb][:, :, xa] + fx * L[:, yb][:, :, xb]
+    return (1 - fy) * top + fy * bot
+
+
+_sh_basis = og.sh_basis
+_fovea_weight = og.fovea_weight
+
+
+def _alpha_exponent_without_half(pr, j, px, py):
+    v = torch.stack([(px - pr["cx"]) / pr["fx"], (py - pr["cy"]) / pr["fy"], torch.ones_like(px)], 1)
+    u, E, A = pr["u"][j], pr["E"][j], pr["A"][j]
+    s = torch.einsum("mak,mk->ma", E, v) / (u * v).sum(1)[:, None]
+    q = torch.einsum("ma,mab,mb->m", s, A, s)
+    return torch.clamp_max(pr["sigma"][j] * torch.exp(-q), og.ALPHA_MAX)
+
+
+@pytest.mark.parametrize("target, mutant", [
+    ("sh_basis", _sh_sign_slip),
+    ("alpha_at", _alpha_exponent_without_half),
+    ("fovea_weight", _blend_weight_reversed),
+    ("bilinear_up2", _bilinear_weights_swapped),
+], ids=["sh-sign", "exponent-half", "blend-weight", "bilinear-weights"])
+def test_planted_mistake_fails_the_pin(case, monkeypatch, target, mutant):
+    monkeypatch.setattr(og, target, mutant)
+    assert _worst(case) > 100 * TOL, target

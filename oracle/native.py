@@ -14,12 +14,17 @@ import numpy as np
 
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "vrs_oracle.c"
-_LIB = _HERE / "lib" / "libvrs_oracle.so"
+# VRS_ORACLE_LIB names a prebuilt variant of the library to load instead: the tests that
+# plant a mistake in a copy of the C source and check that a pin fails use it.
+_VARIANT = os.environ.get("VRS_ORACLE_LIB")
+_LIB = Path(_VARIANT) if _VARIANT else _HERE / "lib" / "libvrs_oracle.so"
 _lib = None
 
 
 def build(force: bool = False) -> Path:
     """Compile the oracle with the host compiler (portable C, OpenMP)."""
+    if _VARIANT:
+        return _LIB
     if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
         _LIB.parent.mkdir(parents=True, exist_ok=True)
         tmp = _LIB.with_suffix(f".tmp{os.getpid()}.so")

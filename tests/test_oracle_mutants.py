@@ -112,3 +112,39 @@ def _alpha_exponent_without_half(pr, j, px, py):
 def test_planted_mistake_fails_the_pin(case, monkeypatch, target, mutant):
     monkeypatch.setattr(og, target, mutant)
     assert _worst(case) > 100 * TOL, target
+
+
+# ---------------------------------------------------------------- the C forward oracle
+
+_C_SLIPS = {
+    # the l=1, m=-1 harmonic with the wrong sign
+    "sh-sign": ("Y[1] = -c1 * y;", "Y[1] = c1 * y;"),
+    # the 1/2 dropped from the plane Gaussian's exponent
+    "exponent-half": ("*sg = p->sigma * exp(-0.5 * q);", "*sg = p->sigma * exp(-1.0 * q);"),
+    # front-to-back blending (Eq. 2) without the transmittance factor
+    "blend-transmittance": ("s->C[c] += alpha * s->T * rgb[c];", "s->C[c] += alpha * rgb[c];"),
+    # the inverse 2x2 covariance with the off-diagonal sign lost
+    "conic-sign": ("p->A[0][1] = p->A[1][0] = -p->Sp[0][1] / det;", "p->A[0][1] = p->A[1][0] = p->Sp[0][1] / det;"),
+}
+
+
+@pytest.mark.parametrize("slip", sorted(_C_SLIPS))
+def test_planted_mistake_in_the_c_oracle_fails_a_pin(slip, tmp_path):
+    """A copy of the C oracle with one slip, built beside the test, fails the pins."""
+    import os
+    import subprocess
+    import sys
+    from pathlib import Path
+
+    root = Path(__file__).resolve().parent.parent
+    src = (root / "oracle" / "vrs_oracle.c").read_text()
+    old, new = _C_SLIPS[slip]
+    assert src.count(old) == 1
+    (tmp_path / "mutant.c").write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(lib),
+                           str(tmp_path / "mutant.c"), "-lm"])
+    env = dict(os.environ, VRS_ORACLE_LIB=str(lib), OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", str(root / "tests" / "test_oracle_pins.py"), "-x", "-q",
+                        "-p", "no:cacheprovider"], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1 and " failed" in r.stdout, r.stdout[-2000:]

@@ -47,6 +47,24 @@ def test_sh_basis_orthonormal():
     assert np.abs(G - np.eye(16)).max() < 1e-12
 
 
+def test_sh_basis_signs_match_scipy_complex_harmonics():
+    """The 3DGS sign convention, pinned against scipy's complex harmonics (Condon-Shortley
+    phase included): Y_l0 = Y_l^0, Y_lm = sqrt(2) Re Y_l^m and Y_l,-m = sqrt(2) Im Y_l^m
+    for m > 0.  Orthonormality alone leaves every sign free."""
+    from scipy.special import sph_harm_y
+    rng = np.random.default_rng(5)
+    for _ in range(16):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        th, ph = math.acos(d[2]), math.atan2(d[1], d[0])
+        ref = []
+        for l in range(4):
+            for m in range(-l, l + 1):
+                y = sph_harm_y(l, abs(m), th, ph)
+                ref.append(y.real if m == 0 else math.sqrt(2) * (y.real if m > 0 else y.imag))
+        assert np.abs(on.sh_basis(3, d) - np.array(ref)).max() < 1e-13
+
+
 def test_sh_degree_truncation():
     d = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
     Y3 = on.sh_basis(3, d)

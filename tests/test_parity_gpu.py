@@ -244,6 +244,28 @@ def test_single_pixel_and_single_tile_images(R):
         parity(gpu, ref["image"], ref["marginal"])
 
 
+def test_large_and_near_gaussians_span_many_tiles(R):
+    """Gaussians much larger than a tile, some just beyond the near plane: nine in ten of
+    those in view cover more than eight 16x16 tiles (past the sort keys the duplication
+    pass caches per Gaussian), the largest nearly the whole image.  Exact and
+    hierarchical orders, plain and single-pass foveated."""
+    rng = np.random.default_rng(77)
+    scene = random_scene(400, rng, sh_degree=1, z=(0.25, 3.0), xy=1.5, ls_mu=-1.6, ls_sd=0.5)
+    cam = synth.identity_camera(192, 160, 90.0)
+    counts, gids, _ = on.tile_lists(scene, cam, key_tile=16)
+    per = np.bincount(gids, minlength=400)
+    assert (per > 8).sum() > 0.8 * (per > 0).sum() and per.max() > 0.8 * counts.size
+    fov = synth.fovea_for(192, (90.0, 70.0), radius_frac=0.2)
+    for mode, win in (("exact", (0, 0, 0)), ("hier", (4, 8, 16))):
+        ref = on.render(scene, cam, mode, windows=win, key_tile=16)
+        gpu = render_gpu(R, scene, [cam], sort_mode=mode, windows=win, key_tile=16)[0]
+        parity(gpu, ref["image"], ref["marginal"])
+        ref = on.render(scene, cam, mode, windows=win, key_tile=32, fovea=fov)
+        assert (ref["tile_class"] == 2).any()
+        gpu = render_gpu(R, scene, [cam], [fov], sort_mode=mode, windows=win, key_tile=32, fovea_mode="bilinear")[0]
+        parity(gpu, ref["image"], ref["marginal"])
+
+
 def test_invalid_arguments_are_rejected(R):
     a = api()
     scene = a.DeviceScene.from_host(random_scene(10, np.random.default_rng(0)))

@@ -63,6 +63,24 @@ def test_backward_plain_matches_oracle(R, mode, win):
 
 
 @pytest.mark.parametrize("mode,win", [("exact", (0, 0, 0)), ("hier", (4, 8, 16))])
+def test_backward_large_gaussians_matches_oracle(R, mode, win):
+    """400 Gaussians much larger than a tile, some just beyond the near plane, 96x80: a
+    pixel blends about 40 of them, so thousands of lanes add into the same Gaussian's
+    gradient."""
+    from paper_2505_10144_gb300 import api
+    rng = np.random.default_rng(78)
+    scene = random_scene(400, rng, sh_degree=1, z=(0.25, 3.0), xy=1.5, ls_mu=-1.6, ls_sd=0.5)
+    cam = synth.identity_camera(96, 80, 90.0)
+    ref = on.render(scene, cam, mode, windows=win, key_tile=16, want_orders=True)
+    assert len(ref["orders"][0]) > 30 * 96 * 80
+    dimg = rng.normal(size=(1, 3, 80, 96)) * ~ref["marginal"][None, None]
+    g_ref = og.image_grad(scene, cam, ref["orders"], dimg[0])
+    g = gpu_grads(R, scene, [cam], None, api.RenderConfig(sort_mode=mode, windows=win, key_tile=16), dimg)
+    errs = {k: rel_l2(g[k], g_ref[k]) for k in g_ref}
+    assert max(errs.values()) < GRAD_RTOL, errs
+
+
+@pytest.mark.parametrize("mode,win", [("exact", (0, 0, 0)), ("hier", (4, 8, 16))])
 def test_backward_foveated_stereo_matches_oracle(R, mode, win):
     from paper_2505_10144_gb300 import api
     rng = np.random.default_rng(32)

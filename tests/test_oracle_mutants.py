@@ -125,6 +125,9 @@ _C_SLIPS = {
     "blend-transmittance": ("s->C[c] += alpha * s->T * rgb[c];", "s->C[c] += alpha * rgb[c];"),
     # the inverse 2x2 covariance with the off-diagonal sign lost
     "conic-sign": ("p->A[0][1] = p->A[1][0] = -p->Sp[0][1] / det;", "p->A[0][1] = p->A[1][0] = p->Sp[0][1] / det;"),
+    # the focus/periphery blend weight (Sec. 4.3) without the band's offset
+    "fovea-weight": ("double w = (o->radius + o->band - sqrt(dx * dx + dy * dy)) / o->band;",
+                     "double w = (o->radius - sqrt(dx * dx + dy * dy)) / o->band;"),
 }
 
 

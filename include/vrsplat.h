@@ -269,9 +269,12 @@ vrs_status vrs_mse(vrs_ctx* ctx, const float* d_y, const float* d_t, int64_t n, 
  * inputs are not modified; in and out may be the same buffers) and no context.  The
  * scratch is a fixed device array of about 14 MiB built into the library; every GPU
  * that loads the library holds it until the process exits.  n above
- * VRS_SORT_NOALLOC_MAX_PAIRS returns VRS_ERR_INVALID and launches nothing.  The first call
- * on a device looks up the array's device address (host-side set-up, once per device,
- * on the current device): make that first call before any stream capture.  All calls
+ * VRS_SORT_NOALLOC_MAX_PAIRS returns VRS_ERR_INVALID and launches nothing.  Each call
+ * looks up the array's device address on the current device (a host-side call, made on
+ * every call so that no address outlives a reset context); the first call on a device
+ * also loads the module there, so make it before any stream capture.  A runtime error
+ * left by an earlier unrelated call is cleared on entry; VRS_ERR_CUDA then means that
+ * one of this call's own copies or launches failed.  All calls
  * share the one array and each clears what must start at zero, so calls that overlap on
  * the GPU (other streams, other host threads) race and must be serialised by the
  * caller.  d_status (device uint32, may be NULL) receives the sort's device status bits

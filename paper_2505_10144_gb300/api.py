@@ -141,6 +141,10 @@ class Renderer:
         if st != 0:
             raise VrsError(st, "vrs_create failed")
         self._keep = None
+        # incremented by every call that overwrites the context's lists and saved state
+        # (render, two-pass render, graph replay); a differentiable render checks it
+        # before its backward replays that state
+        self.generation = 0
 
     def close(self):
         if self.ctx:
@@ -183,6 +187,7 @@ class Renderer:
         if out is None:
             out = torch.empty((n_views, 3, H, W), device="cuda", dtype=torch.float32)
         sc, vs, cm, fv, o = self._marshal(scenes, view_scene, cams, foveas, cfg, visible)
+        self.generation += 1
         self._check(self.lib.vrs_render(self.ctx, sc, len(scenes), vs, cm, fv, n_views, C.byref(o), _ptr(out),
                                         _ptr(low), int(save), _stream(stream)))
         return out
@@ -197,6 +202,7 @@ class Renderer:
         if out is None:
             out = torch.empty((n_views, 3, H, W), device="cuda", dtype=torch.float32)
         sc, vs, cm, fv, o = self._marshal(scenes, view_scene, cams, foveas, cfg)
+        self.generation += 1
         self._check(self.lib.vrs_render_two_pass(self.ctx, sc, len(scenes), vs, cm, fv, n_views, C.byref(o), _ptr(out),
                                                  _stream(stream)))
         return out
@@ -328,8 +334,11 @@ class RenderFunction(torch.autograd.Function):
     """Differentiable render of one scene (fine-tuning through the rasterizer).
 
     Forward calls vrs_render with save_for_backward; backward calls vrs_render_backward
-    on the same Renderer, so the backward must run before that renderer renders again
-    (the usual forward -> loss -> backward order)."""
+    on the same Renderer, which replays the lists and samples the context saved.  So the
+    backward must run before that renderer renders again (the usual forward -> loss ->
+    backward order); a backward after another render on the same Renderer raises instead
+    of returning the gradients of the other render.  Use one Renderer per differentiable
+    render that must stay live (e.g. several loss terms before one backward)."""
 
     @staticmethod
     def forward(ctx, renderer, cfg, cams, foveas, sh_degree, mean, log_scale, quat, opacity_logit, sh):
@@ -337,10 +346,14 @@ class RenderFunction(torch.autograd.Function):
                          opacity_logit.detach().contiguous(), sh.detach().contiguous(), sh_degree)
         out = renderer.render([ds], [0] * len(cams), cams, foveas, cfg, save=True)
         ctx.renderer, ctx.cfg, ctx.cams, ctx.foveas, ctx.ds = renderer, cfg, cams, foveas, ds
+        ctx.generation = renderer.generation
         return out
 
     @staticmethod
     def backward(ctx, gout):
+        if ctx.renderer.generation != ctx.generation:
+            raise RuntimeError("the Renderer rendered again after this differentiable render: its saved lists and "
+                               "samples now belong to another frame (use one Renderer per live render)")
         g = ctx.ds.zeros_like()
         ctx.renderer.backward([ctx.ds], [0] * len(ctx.cams), ctx.cams, ctx.foveas, ctx.cfg, gout.contiguous(), [g])
         return (None, None, None, None, None, *g.tensors())
@@ -435,5 +448,6 @@ class GraphedRender:
     def replay(self, cams=None, foveas=None) -> torch.Tensor:
         if cams is not None:
             self.R.update_views(cams, foveas, self.cfg, visible=self.visible)
+        self.R.generation += 1
         self.graph.replay()
         return self.out

@@ -19,6 +19,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "../../include/vrsplat.h"
 
 namespace vrs {
@@ -209,6 +212,40 @@ void launch_preprocess_backward(const SceneDev& s, const ViewParams* d_views, co
                                 int n_views_scene, const uint32_t* count, const float* grad_rec,
                                 const vrs_gaussian_grads& g, cudaStream_t st);
 int device_sm_count();
+
+// Launch properties that depend on the device (SM count, occupancy, the dynamic shared
+// memory attribute of a kernel) are memoised per device: a table of kMemoDevices
+// entries, indexed by the current device, 0 meaning "not known yet".  Entries are
+// atomics, so host threads may race to fill one; they store the same value.
+constexpr int kMemoDevices = 64;
+inline int current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMemoDevices) return -1;
+  return dev;
+}
+template <typename F>
+int per_device_memo(std::atomic<int>* table, F compute) {
+  const int dev = current_device();
+  if (dev < 0) return compute();
+  int v = table[dev].load(std::memory_order_relaxed);
+  if (v <= 0) {
+    v = compute();
+    table[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+// Raises a kernel's dynamic shared memory limit to at least `bytes` on the current
+// device; `table` remembers per device the largest limit set so far.
+template <typename K>
+void ensure_dynamic_smem(std::atomic<int>* table, K kernel, int bytes) {
+  const int dev = current_device();
+  if (dev >= 0 && table[dev].load(std::memory_order_acquire) >= bytes) return;
+  static std::mutex m;  // one per kernel: the attribute only ever grows
+  std::lock_guard<std::mutex> lock(m);
+  if (dev >= 0 && table[dev].load(std::memory_order_relaxed) >= bytes) return;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (dev >= 0) table[dev].store(bytes, std::memory_order_release);
+}
 
 // per-view parameters of the two-pass foveated baseline (passed by value)
 constexpr int kTwoPassMaxViews = 64;

@@ -704,11 +704,8 @@ template <int CIN, int COUT, int LAYER>
 void launch_conv_fwd(dim3 grid, const float* params, const float* x, const uint16_t* ain, uint16_t* aout, float* y,
                      int H, int W, cudaStream_t st) {
   const int smem = (CIN * 324 + COUT * CIN * 9 + COUT) * 4;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(conv_fwd_kernel<CIN, COUT, LAYER>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  static std::atomic<int> smem_set[kMemoDevices];
+  ensure_dynamic_smem(smem_set, conv_fwd_kernel<CIN, COUT, LAYER>, smem);
   conv_fwd_kernel<CIN, COUT, LAYER><<<grid, 256, smem, st>>>(params, x, ain, aout, y, H, W);
 }
 
@@ -716,11 +713,8 @@ template <int CIN, int COUT>
 void launch_conv_bwd_data(dim3 grid, const float* params, int woff, const float* dout, const uint16_t* ain, float* din,
                           int H, int W, cudaStream_t st) {
   const int smem = (COUT * 324 + COUT * CIN * 9) * 4;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(conv_bwd_data_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  static std::atomic<int> smem_set[kMemoDevices];
+  ensure_dynamic_smem(smem_set, conv_bwd_data_kernel<CIN, COUT>, smem);
   conv_bwd_data_kernel<CIN, COUT><<<grid, 256, smem, st>>>(params, woff, dout, ain, din, H, W);
 }
 
@@ -728,11 +722,8 @@ template <int CIN, int COUT, int LAYER>
 void launch_conv_bwd_weight(unsigned grid, const float* x, const uint16_t* ain, const float* dout, int B, int H, int W,
                             float* dparams, cudaStream_t st) {
   const int smem = (CIN * 324 + COUT * 256 + COUT * CIN * 9 + COUT) * 4;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(conv_bwd_weight_kernel<CIN, COUT, LAYER>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
+  static std::atomic<int> smem_set[kMemoDevices];
+  ensure_dynamic_smem(smem_set, conv_bwd_weight_kernel<CIN, COUT, LAYER>, smem);
   conv_bwd_weight_kernel<CIN, COUT, LAYER><<<grid, 256, smem, st>>>(x, ain, dout, B, H, W, dparams);
 }
 
@@ -772,11 +763,8 @@ void net_mse(const float* y, const float* t, long long n, float* loss, float* dy
 void net_periphery(const float* params, const float* low, float* out, const uint8_t* tile_class,
                    const ViewParams* views, int n_views, int tiles_per_view, int W, int H, uint32_t* status,
                    cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(net_periphery_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kNetSmem);
-    attr = true;
-  }
+  static std::atomic<int> smem_set[kMemoDevices];
+  ensure_dynamic_smem(smem_set, net_periphery_kernel, kNetSmem);
   const long long n = (long long)n_views * tiles_per_view;
   const unsigned grid = (unsigned)std::min<long long>(n, (long long)device_sm_count());
   net_periphery_kernel<<<grid, kNetThreads, kNetSmem, st>>>(params, low, out, tile_class, views, n_views,

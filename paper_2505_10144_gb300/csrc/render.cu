@@ -1328,19 +1328,16 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
 template <int K1, int K2, bool BWD, bool STATS>
 void launch_warp_t(const RenderArgs& a, cudaStream_t st) {
   const size_t smem = warp_smem_bytes(a.k3, stage_of<K2>()) * kRegionWarps;
-  static size_t set_smem = 0;
-  static int per_sm_cached[kMaxWin + 1] = {0};
-  if (smem > set_smem) {
-    cudaFuncSetAttribute(warp_render_kernel<K1, K2, BWD, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    set_smem = smem;
-  }
-  int per_sm = per_sm_cached[a.k3];
-  if (per_sm <= 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, warp_render_kernel<K1, K2, BWD, STATS>,
-                                                  kRegionWarps * 32, smem);
-    if (per_sm < 1) per_sm = 1;
-    per_sm_cached[a.k3] = per_sm;
-  }
+  // attribute and occupancy per device and per window size k3 (set outside stream capture
+  // by the first eager call)
+  static std::atomic<int> smem_set[kMemoDevices];
+  static std::atomic<int> occupancy[kMaxWin + 1][kMemoDevices];
+  ensure_dynamic_smem(smem_set, warp_render_kernel<K1, K2, BWD, STATS>, (int)smem);
+  int per_sm = per_device_memo(occupancy[a.k3], [smem] {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, warp_render_kernel<K1, K2, BWD, STATS>, kRegionWarps * 32, smem);
+    return b > 0 ? b : 1;
+  });
   if (a.max_ctas_per_sm > 0) per_sm = std::min(per_sm, a.max_ctas_per_sm * (kBlock / (kRegionWarps * 32)));
   warp_render_kernel<K1, K2, BWD, STATS><<<(unsigned)(device_sm_count() * per_sm), kRegionWarps * 32, smem, st>>>(a);
 }
@@ -1455,20 +1452,17 @@ template <int MODE, bool STATS, bool BWD>
 void launch_render_t(const RenderArgs& a, long long max_items, cudaStream_t st) {
   const int K1 = MODE == 2 ? a.k1 : 0, K2 = MODE == 2 ? a.k2 : 0, K3 = MODE == 0 ? 0 : a.k3;
   const size_t smem = render_smem_bytes(K1, K2, K3);
-  // attribute and occupancy per shared-memory size, set once (outside any stream capture)
-  static size_t set_smem = 0;
-  static int per_sm_cached[kMaxWin * 3 + 1] = {0};
+  // attribute and occupancy per device and per shared-memory size (set outside stream
+  // capture by the first eager call)
+  static std::atomic<int> smem_set[kMemoDevices];
+  static std::atomic<int> occupancy[kMaxWin * 3 + 1][kMemoDevices];
   const int key = (int)std::min<size_t>(smem / 4096, (size_t)kMaxWin * 3);
-  if (smem > set_smem) {
-    cudaFuncSetAttribute(render_kernel<MODE, STATS, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    set_smem = smem;
-  }
-  int per_sm = per_sm_cached[key];
-  if (per_sm <= 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_kernel<MODE, STATS, BWD>, kBlock, smem);
-    if (per_sm < 1) per_sm = 1;
-    per_sm_cached[key] = per_sm;
-  }
+  ensure_dynamic_smem(smem_set, render_kernel<MODE, STATS, BWD>, (int)smem);
+  int per_sm = per_device_memo(occupancy[key], [smem] {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, render_kernel<MODE, STATS, BWD>, kBlock, smem);
+    return b > 0 ? b : 1;
+  });
   if (a.max_ctas_per_sm > 0) per_sm = std::min(per_sm, a.max_ctas_per_sm);
   const long long grid = std::min<long long>(max_items, (long long)device_sm_count() * per_sm);
   if (grid <= 0) return;

@@ -314,14 +314,14 @@ void sort_scratch_carve(void* base, long long cap, SortScratch* s) {
 }
 
 int device_sm_count() {
-  static int sms = 0;
-  if (!sms) {
+  static std::atomic<int> sms[kMemoDevices];
+  return per_device_memo(sms, [] {
+    int n = 0;
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  return sms;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  });
 }
 
 int launch_radix_sort(uint64_t* keys[2], uint32_t* vals[2], const uint32_t* d_n, long long cap, int bits,
@@ -335,17 +335,14 @@ int launch_radix_sort(uint64_t* keys[2], uint32_t* vals[2], const uint32_t* d_n,
   const unsigned hgrid = (unsigned)std::min<long long>((cap + kBlock * 8 - 1) / (kBlock * 8), (long long)sms * 8);
   histogram_kernel<<<hgrid, kBlock, 0, st>>>(keys[0], d_n, passes, bits, s.hist);
   histogram_scan_kernel<<<1, kBlock, 0, st>>>(s.hist, passes);
-  static bool attr = false;
   const int smem = (int)sizeof(SortSmem);
-  if (!attr) {
-    cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    attr = true;
-  }
-  static int per_sm = 0;
-  if (per_sm <= 0) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kBlock, smem);
-    if (per_sm < 1) per_sm = 1;
-  }
+  static std::atomic<int> smem_set[kMemoDevices], occupancy[kMemoDevices];
+  ensure_dynamic_smem(smem_set, onesweep_kernel, smem);
+  const int per_sm = per_device_memo(occupancy, [smem] {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, onesweep_kernel, kBlock, smem);
+    return b > 0 ? b : 1;
+  });
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)sms * per_sm);
   int cur = 0;
   for (int p = 0; p < passes; ++p) {

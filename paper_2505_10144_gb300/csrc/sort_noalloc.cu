@@ -15,8 +15,6 @@
 // that must start at zero (histograms, flags, counters) on its stream before it sorts.
 // Calls whose work overlaps on the GPU (on different streams, or from several host
 // threads) race on this one array and give undefined results: serialise them.
-#include <mutex>
-
 #include "common.cuh"
 
 namespace vrs {
@@ -35,27 +33,18 @@ constexpr size_t kNoallocBytes = kMiscOff + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_setup_mutex;
-
 __global__ void noalloc_set_n_kernel(uint32_t* p, uint32_t v) { *p = v; }
 
 __global__ void noalloc_status_kernel(const uint32_t* status, uint32_t* out) { *out = *status; }
 
-// Host-side address of the scratch array on the current device.  The array's name in
-// host code is only a stand-in, so the address comes from cudaGetSymbolAddress, once per
-// device, with that device current.
+// Device address of the scratch array on the current device.  In host code the array's
+// name is only a stand-in, so the address comes from cudaGetSymbolAddress, with the
+// device current.  The lookup is a host-side call and runs on every call: a cached
+// address would go stale if the device's primary context were reset and re-created.
 vrs_status scratch_for_current_device(unsigned char** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VRS_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VRS_ERR_CUDA;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return VRS_ERR_CUDA;
+  *out = static_cast<unsigned char*>(p);
   return VRS_OK;
 }
 
@@ -72,6 +61,9 @@ extern "C" vrs_status vrs_sort_pairs_noalloc(const uint64_t* d_keys_in, const ui
   if (sort_scratch_bytes(kNoallocMax) > kSortScratchBytes) return VRS_ERR_UNSUPPORTED;
   if (n == 0) return VRS_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  // an error left by an earlier, unrelated runtime call is not this call's: clear it so
+  // that the check at the end reports only what this call launched
+  (void)cudaGetLastError();
   unsigned char* base = nullptr;
   vrs_status s = scratch_for_current_device(&base);
   if (s != VRS_OK) return s;
@@ -80,19 +72,25 @@ extern "C" vrs_status vrs_sort_pairs_noalloc(const uint64_t* d_keys_in, const ui
   uint32_t* misc = reinterpret_cast<uint32_t*>(base + kMiscOff);  // [0] item count, [1] status
   SortScratch ss;
   sort_scratch_carve(base + kSortOff, kNoallocMax, &ss);
-  cudaMemsetAsync(misc, 0, 2 * sizeof(uint32_t), st);
-  if (d_keys_out != d_keys_in)
-    cudaMemcpyAsync(d_keys_out, d_keys_in, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
-  if (d_vals_out != d_vals_in)
-    cudaMemcpyAsync(d_vals_out, d_vals_in, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+  if (cudaMemsetAsync(misc, 0, 2 * sizeof(uint32_t), st) != cudaSuccess) return VRS_ERR_CUDA;
+  if (d_keys_out != d_keys_in &&
+      cudaMemcpyAsync(d_keys_out, d_keys_in, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return VRS_ERR_CUDA;
+  if (d_vals_out != d_vals_in &&
+      cudaMemcpyAsync(d_vals_out, d_vals_in, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return VRS_ERR_CUDA;
   noalloc_set_n_kernel<<<1, 1, 0, st>>>(misc, (uint32_t)n);
   uint64_t* kb[2] = {d_keys_out, alt_keys};
   uint32_t* vb[2] = {d_vals_out, alt_vals};
   // launch_radix_sort clears the histograms, counters and look-back flags it uses
   const int cur = launch_radix_sort(kb, vb, misc, n, bits, ss, misc + 1, st);
+  // a failed launch or clear inside the sort leaves the alternate buffer stale: stop
+  // before copying it out
+  if (cudaGetLastError() != cudaSuccess) return VRS_ERR_CUDA;
   if (cur == 1) {
-    cudaMemcpyAsync(d_keys_out, alt_keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(d_vals_out, alt_vals, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st);
+    if (cudaMemcpyAsync(d_keys_out, alt_keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_vals_out, alt_vals, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return VRS_ERR_CUDA;
   }
   if (d_status) noalloc_status_kernel<<<1, 1, 0, st>>>(misc + 1, d_status);
   return cudaGetLastError() == cudaSuccess ? VRS_OK : VRS_ERR_CUDA;

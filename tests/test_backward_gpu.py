@@ -136,6 +136,26 @@ def test_autograd_function_and_loss(R):
         assert torch.allclose(p.grad, t, rtol=1e-5, atol=1e-9)
 
 
+def test_backward_of_a_superseded_render_raises(R):
+    """Two differentiable renders on one Renderer: the backward of the second is that
+    render's gradient; the backward of the first, whose saved lists the second render
+    replaced, raises instead of returning the second render's gradient."""
+    from paper_2505_10144_gb300 import api
+    rng = np.random.default_rng(36)
+    scene = random_scene(300, rng, sh_degree=0, z=(1.0, 3.0), xy=2.0, ls_mu=-2.5)
+    params = {k: torch.tensor(np.asarray(v), device="cuda", requires_grad=True)
+              for k, v in zip(["mean", "log_scale", "quat", "opacity_logit", "sh"], scene.arrays())}
+    cfg = api.RenderConfig(sort_mode="hier", key_tile=16)
+    cam_a = synth.identity_camera(40, 32, 90.0)
+    cam_b = synth.camera_from_pose(synth.head_rotation(0.1), (0.05, 0, 0), 40, 32, synth.focal_for_hfov(40, 90.0))
+    img_a = api.render_differentiable(R, params, 0, [cam_a], None, cfg)
+    img_b = api.render_differentiable(R, params, 0, [cam_b], None, cfg)
+    img_b.sum().backward()
+    assert float(params["mean"].grad.abs().sum()) > 0
+    with pytest.raises(RuntimeError, match="rendered again"):
+        img_a.sum().backward()
+
+
 def test_loss_kernel_matches_oracle_on_several_images(R):
     rng = np.random.default_rng(34)
     x = rng.uniform(size=(3, 3, 37, 53)).astype(np.float32)

@@ -53,6 +53,38 @@ def test_noalloc_sort_matches_the_context_sort_on_two_calls(lib):
     R.close()
 
 
+def test_noalloc_sort_in_place_partial_digit_and_no_allocation(lib):
+    """In place (out = in), with a last digit of fewer than 8 bits (bits = 5, 13), and
+    without allocating: after a first call, which loads the library's module on this
+    device, further calls leave the device's free memory and torch's allocator as they
+    were."""
+    from paper_2505_10144_gb300 import api
+    R = api.Renderer()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    cases = []
+    for call, (n, bits) in enumerate([(4097, 5), (200_003, 13), (65_536, 64)]):
+        k, v = _keys(np.random.default_rng(100 + call), n)
+        ref_k, ref_v = R.sort_pairs(k, v, bits)
+        cases.append((k.clone(), v.clone(), ref_k, ref_v, n, bits))
+    status = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    warm_k, warm_v = cases[0][0].clone(), cases[0][1].clone()
+    assert lib.vrs_sort_pairs_noalloc(_p(warm_k), _p(warm_v), _p(warm_k), _p(warm_v), cases[0][4], cases[0][5],
+                                      _p(status), stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for k, v, ref_k, ref_v, n, bits in cases:
+        rc = lib.vrs_sort_pairs_noalloc(_p(k), _p(v), _p(k), _p(v), n, bits, _p(status), stream)
+        assert rc == 0
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert torch.equal(k, ref_k) and torch.equal(v, ref_v), (n, bits)
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0 and torch.cuda.memory_allocated() == alloc0
+    R.close()
+
+
 def test_noalloc_sort_rejects_more_than_its_maximum(lib):
     k = torch.zeros(4, dtype=torch.int64, device="cuda")
     v = torch.zeros(4, dtype=torch.int32, device="cuda")

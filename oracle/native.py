@@ -52,14 +52,15 @@ class _Opts(C.Structure):
                 ("brute", C.c_int), ("gaze_x", C.c_double), ("gaze_y", C.c_double),
                 ("radius", C.c_double), ("band", C.c_double), ("bg", C.c_double * 3),
                 ("margin_alpha", C.c_double), ("margin_stop", C.c_double), ("margin_tie", C.c_double),
-                ("visible", C.c_void_p)]
+                ("visible", C.c_void_p), ("outcomes", C.c_int)]
 
 
 class _Out(C.Structure):
     _fields_ = [("image", C.c_void_p), ("full", C.c_void_p), ("low", C.c_void_p),
                 ("lowimg", C.c_void_p), ("marginal", C.c_void_p), ("tile_class", C.c_void_p),
                 ("order", C.c_void_p), ("order_off", C.c_void_p), ("max_order", C.c_int64),
-                ("n_order", C.c_int64), ("stats", C.c_int64 * 8)]
+                ("n_order", C.c_int64), ("stats", C.c_int64 * 8), ("unchecked", C.c_void_p),
+                ("alt_off", C.POINTER(C.c_int64)), ("alt", C.POINTER(C.c_double)), ("n_alt", C.c_int64)]
 
 
 def lib():
@@ -77,7 +78,9 @@ def lib():
         _lib.og_edge_max.argtypes = [dp, dp, dp, dp]
         _lib.og_sh_basis.argtypes = [C.c_int, dp, dp]
         _lib.og_tile_lists.argtypes = [C.POINTER(_Scene), C.POINTER(_Camera), C.c_int, C.c_int,
-                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]
+                                       C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_int64]
+        _lib.og_free.argtypes = [C.c_void_p]
         _lib.og_tile_lists.restype = C.c_int64
         _lib.og_num_threads.restype = C.c_int
     return _lib
@@ -172,15 +175,24 @@ def sh_basis(degree: int, direction) -> np.ndarray:
 
 
 MODES = {"exact": 0, "window": 1, "hier": 2, "global_z": 3, "global_dist": 4}
+# relative margins of the FP32-vs-FP64 comparison rule: sigma G against 1/255, the
+# transmittance test against 1e-4, and near-equal depths or keys
+MARGINS = (5e-5, 1e-5, 3e-7)
 
 
 def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 16, fovea=None,
            bg=(0.0, 0.0, 0.0), tile_cull: bool = True, brute: bool = False,
-           want_orders: bool = False, want_samples: bool = False, margins=(5e-5, 1e-5, 3e-7),
-           visible=None) -> dict:
+           want_orders: bool = False, want_samples: bool = False, margins=MARGINS,
+           visible=None, outcomes: bool = False) -> dict:
     """Render one view.  fovea: None for the plain method, else an object with gaze_x,
     gaze_y, radius_px, band_px (single-pass foveation, 32x32 key tiles).  visible: None,
-    or an [H, W] array, nonzero where the pixel is visible (visibility culling)."""
+    or an [H, W] array, nonzero where the pixel is visible (visibility culling).
+
+    outcomes: also enumerate, per pixel, every composited value that the decisions of
+    its samples within the margins allow (keep against 1/255, stop against 1e-4, order
+    of near-tied depths or keys, hierarchical window and stream ties): the result gets
+    "alt" = (offsets [H*W + 1], values [n, 3]) of the values other than "image" and
+    "unchecked" [H, W], true where there are too many to enumerate."""
     W, H = int(cam.width), int(cam.height)
     o = _Opts()
     vis = None
@@ -201,6 +213,7 @@ def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 
     for k in range(3):
         o.bg[k] = float(np.float32(bg[k]))
     o.margin_alpha, o.margin_stop, o.margin_tie = (float(m) for m in margins)
+    o.outcomes = int(outcomes)
     T = int(key_tile)
     ntx, nty = (W + T - 1) // T, (H + T - 1) // T
     W2, H2 = W // 2, H // 2
@@ -215,25 +228,40 @@ def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 
     out = _Out()
     out.image, out.full, out.low, out.lowimg = _ptr(image), _ptr(full), _ptr(low), _ptr(lowimg)
     out.marginal, out.tile_class, out.order_off = _ptr(marginal), _ptr(tcls), _ptr(off)
+    unchecked = np.zeros((H, W), np.uint8) if outcomes else None
+    out.unchecked = _ptr(unchecked)
     sr = _SceneRef(scene)
     camc = _cam(cam)
     rc = lib().og_render(C.byref(sr.s), C.byref(camc), C.byref(o), C.byref(out))
     if rc != 0:
         raise ValueError("oracle render rejected its arguments")
+    alt = None
+    if outcomes:
+        n_alt = int(out.n_alt)
+        aoff = np.ctypeslib.as_array(out.alt_off, shape=(W * H + 1,)).copy()
+        vals = np.ctypeslib.as_array(out.alt, shape=(n_alt * 3,)).reshape(n_alt, 3).copy() if n_alt else np.zeros((0, 3))
+        lib().og_free(C.cast(out.alt_off, C.c_void_p))
+        lib().og_free(C.cast(out.alt, C.c_void_p))
+        alt = (aoff, vals)
     orders = None
     if want_orders:
         order = np.zeros(max(int(out.n_order), 1), np.int32)
         out.order, out.max_order = _ptr(order), len(order)
+        o.outcomes = 0
         rc = lib().og_render(C.byref(sr.s), C.byref(camc), C.byref(o), C.byref(out))
         orders = (order[:int(out.n_order)], off.copy())
-    stats = dict(zip(["valid", "instances", "evaluated", "kept", "blended", "marginal_px", "samples"],
-                     [int(v) for v in out.stats[:7]]))
+    stats = dict(zip(["valid", "instances", "evaluated", "kept", "blended", "marginal_px", "samples",
+                      "unchecked_px"], [int(v) for v in out.stats[:8]]))
     return dict(image=image, marginal=marginal.astype(bool), tile_class=tcls, full=full, low=low,
-                lowimg=lowimg if fovea is not None else None, orders=orders, stats=stats)
+                lowimg=lowimg if fovea is not None else None, orders=orders, stats=stats,
+                alt=alt, unchecked=None if unchecked is None else unchecked.astype(bool))
 
 
-def tile_lists(scene, cam, key_tile: int = 16, tile_cull: bool = True, visible=None):
-    """-> (counts[nty, ntx], gids, keys) of the oracle's sorted per-tile instance lists."""
+def tile_lists(scene, cam, key_tile: int = 16, tile_cull: bool = True, visible=None, relax: float = 0.0,
+               want_slack: bool = False):
+    """-> (counts[nty, ntx], gids, keys) of the oracle's sorted per-tile instance lists,
+    plus slack (qmin - r2 of each entry's Eq. 4 test) when want_slack.  relax > 0 adds the
+    entries with 0 < qmin - r2 <= relax."""
     W, H, T = int(cam.width), int(cam.height), int(key_tile)
     vis = None if visible is None else np.ascontiguousarray(np.asarray(visible) != 0, dtype=np.uint8)
     vp = None if vis is None else C.c_void_p(vis.ctypes.data)
@@ -241,12 +269,22 @@ def tile_lists(scene, cam, key_tile: int = 16, tile_cull: bool = True, visible=N
     counts = np.zeros(ntx * nty, np.int64)
     sr = _SceneRef(scene)
     camc = _cam(cam)
-    tot = lib().og_tile_lists(C.byref(sr.s), C.byref(camc), T, int(tile_cull), vp, _ptr(counts), None, None, 0)
+    tot = lib().og_tile_lists(C.byref(sr.s), C.byref(camc), T, int(tile_cull), vp, float(relax), _ptr(counts), None,
+                              None, None, 0)
     gids = np.zeros(max(tot, 1), np.int32)
     keys = np.zeros(max(tot, 1))
-    lib().og_tile_lists(C.byref(sr.s), C.byref(camc), T, int(tile_cull), vp, _ptr(counts), _ptr(gids), _ptr(keys),
-                        len(gids))
+    slack = np.zeros(max(tot, 1))
+    lib().og_tile_lists(C.byref(sr.s), C.byref(camc), T, int(tile_cull), vp, float(relax), _ptr(counts), _ptr(gids),
+                        _ptr(keys), _ptr(slack), len(gids))
+    if want_slack:
+        return counts.reshape(nty, ntx), gids[:tot], keys[:tot], slack[:tot]
     return counts.reshape(nty, ntx), gids[:tot], keys[:tot]
+
+
+def alpha_relax(margin_alpha: float = None) -> float:
+    """Eq. 4 exponent slack of the alpha margin: sigma G > (1 - m) / 255 <=> q < r2 - 2 ln(1 - m)."""
+    m = MARGINS[0] if margin_alpha is None else margin_alpha
+    return -2.0 * float(np.log1p(-m))
 
 
 def num_threads() -> int:

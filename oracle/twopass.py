@@ -57,12 +57,25 @@ def fovea_weight_image(width: int, height: int, fovea) -> np.ndarray:
     return np.clip((r + b - d) / b, 0.0, 1.0)
 
 
-def render(scene, cam, fovea, mode: str = "hier", windows=(4, 8, 16), bg=(0.0, 0.0, 0.0)) -> dict:
-    """-> dict(image [3, H, W], centre, low, rect, marginal [H, W])."""
+def _alts(ref, k):
+    """The values of pixel k of a plain render: its own, then its alternatives."""
+    off, vals = ref["alt"]
+    H, W = ref["image"].shape[1:]
+    y, x = divmod(k, W)
+    return [ref["image"][:, y, x]] + [vals[j] for j in range(off[k], off[k + 1])]
+
+
+def render(scene, cam, fovea, mode: str = "hier", windows=(4, 8, 16), bg=(0.0, 0.0, 0.0),
+           outcomes: bool = False) -> dict:
+    """-> dict(image [3, H, W], centre, low, rect, marginal [H, W]); with outcomes, also
+    the outcome sets of the composed image ("alt", "unchecked", as native.render): every
+    combination of the valid values of the centre pixel and of the four half-resolution
+    pixels it reads, through the same blend."""
     W, H = int(cam.width), int(cam.height)
     x0, y0, sw, sh = centre_rect(W, H, fovea)
-    c = on.render(scene, crop_camera(cam, x0, y0, sw, sh), mode, windows=windows, key_tile=16, bg=bg)
-    lo = on.render(scene, half_camera(cam), mode, windows=windows, key_tile=16, bg=bg)
+    c = on.render(scene, crop_camera(cam, x0, y0, sw, sh), mode, windows=windows, key_tile=16, bg=bg,
+                  outcomes=outcomes)
+    lo = on.render(scene, half_camera(cam), mode, windows=windows, key_tile=16, bg=bg, outcomes=outcomes)
     up = bilinear_up2(torch.tensor(lo["image"])).numpy()
     w = fovea_weight_image(W, H, fovea)
     img = up.copy()
@@ -78,4 +91,50 @@ def render(scene, cam, fovea, mode: str = "hier", windows=(4, 8, 16), bg=(0.0, 0
     marg = lm[ya][:, xa] | lm[ya][:, xb] | lm[yb][:, xa] | lm[yb][:, xb]
     marg = marg & (w < 1.0)
     marg[y0:y0 + sh, x0:x0 + sw] |= c["marginal"] & (wc > 0.0)
-    return dict(image=img, centre=c["image"], low=lo["image"], rect=(x0, y0, sw, sh), marginal=marg)
+    out = dict(image=img, centre=c["image"], low=lo["image"], rect=(x0, y0, sw, sh), marginal=marg)
+    if outcomes:
+        W2 = W // 2
+        ncen = np.diff(c["alt"][0]).reshape(sh, sw)
+        nlow = np.diff(lo["alt"][0]).reshape(H // 2, W2)
+        unchecked = np.zeros((H, W), bool)
+        alt_lists = {}
+        for y in range(H):
+            for x in range(W):
+                wv = w[y, x]
+                inside = x0 <= x < x0 + sw and y0 <= y < y0 + sh
+                taps = [(ya[y], xa[x]), (ya[y], xb[x]), (yb[y], xa[x]), (yb[y], xb[x])]
+                fx = (x + 0.5) / 2 - 0.5 - ux[x]
+                fy = (y + 0.5) / 2 - 0.5 - uy[y]
+                bw = [(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy]
+                need_c = inside and wv > 0 and ncen[y - y0, x - x0] > 0
+                need_l = wv < 1 and any(nlow[t] > 0 for t in taps)
+                if not (need_c or need_l):
+                    continue
+                if (inside and wv > 0 and c["unchecked"][y - y0, x - x0]) or \
+                        (wv < 1 and any(lo["unchecked"][t] for t in taps)):
+                    unchecked[y, x] = True
+                    continue
+                cs = _alts(c, (y - y0) * sw + (x - x0)) if inside and wv > 0 else [np.zeros(3)]
+                ls = [_alts(lo, t[0] * W2 + t[1]) if wv < 1 else [np.zeros(3)] for t in taps]
+                if len(cs) * np.prod([len(l) for l in ls]) > 4096:
+                    unchecked[y, x] = True
+                    continue
+                vals = []
+                for cv in cs:
+                    for l0 in ls[0]:
+                        for l1 in ls[1]:
+                            for l2 in ls[2]:
+                                for l3 in ls[3]:
+                                    upv = bw[0] * l0 + bw[1] * l1 + bw[2] * l2 + bw[3] * l3
+                                    v = wv * cv + (1.0 - wv) * upv if inside else upv
+                                    if np.abs(v - img[:, y, x]).max() > 0:
+                                        vals.append(v)
+                alt_lists[y * W + x] = vals
+        off = np.zeros(W * H + 1, np.int64)
+        for k, v in alt_lists.items():
+            off[k + 1] = len(v)
+        off = np.cumsum(off)
+        vals = [v for k in sorted(alt_lists) for v in alt_lists[k]]
+        out["alt"] = (off, np.array(vals).reshape(-1, 3))
+        out["unchecked"] = unchecked
+    return out

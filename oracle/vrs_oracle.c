@@ -85,6 +85,9 @@ typedef struct {
    * the headset; NULL = every pixel visible.  A key tile with no visible pixel gets no
    * Gaussian/tile instances, and its pixels output the background. */
   const uint8_t* visible;
+  /* 1: also enumerate the outcome sets (og_out.alt, og_out.unchecked): every result that
+   * the marginal decisions of a pixel's samples allow, for the FP32-vs-FP64 comparison */
+  int outcomes;
 } og_opts;
 
 typedef struct {
@@ -98,7 +101,16 @@ typedef struct {
   int64_t *order_off; /* [H*W + (H/2)*(W/2) + 1] */
   int64_t max_order;
   int64_t n_order;    /* out */
-  int64_t stats[8];   /* out: valid, instances, evaluated, kept, blended, marginal px, samples */
+  int64_t stats[8];   /* out: valid, instances, evaluated, kept, blended, marginal px, samples,
+                       * unchecked px */
+  /* outcome sets (og_opts.outcomes): for each pixel, the other valid composited values
+   * alt[alt_off[k] .. alt_off[k + 1]) (rgb triples), and unchecked[k] = 1 where the
+   * valid values are too many to enumerate.  alt_off and alt are malloc'd by og_render
+   * and released with og_free. */
+  uint8_t* unchecked; /* [H][W], caller-owned, may be NULL */
+  int64_t* alt_off;   /* out: [H*W + 1] */
+  double* alt;        /* out: [n_alt][3] */
+  int64_t n_alt;
 } og_out;
 
 /* ------------------------------------------------------------------ projection ---- */
@@ -218,8 +230,16 @@ static void conic_bbox(og_proj* p, const og_camera* c) {
   }
 }
 
-/* Optimal-Projection preprocessing of Gaussian i for camera c (Sec. 4.2, Eq. 1). */
+/* Optimal-Projection preprocessing of Gaussian i for camera c (Sec. 4.2, Eq. 1).
+ * Gaussians with opacity below sigma_min are culled (1/255 by definition: no alpha can
+ * reach the cut; a little lower when the outcome sets need those within the margin). */
+static int og_project_min(const og_scene* sc, int64_t i, const og_camera* c, og_proj* p, double sigma_min);
+
 int og_project(const og_scene* sc, int64_t i, const og_camera* c, og_proj* p) {
+  return og_project_min(sc, i, c, p, OG_ALPHA_MIN);
+}
+
+static int og_project_min(const og_scene* sc, int64_t i, const og_camera* c, og_proj* p, double sigma_min) {
   memset(p, 0, sizeof *p);
   const int64_t n = sc->n;
   double m[3] = {sc->mean[i], sc->mean[n + i], sc->mean[2 * n + i]};
@@ -259,7 +279,7 @@ int og_project(const og_scene* sc, int64_t i, const og_camera* c, og_proj* p) {
     }
   if (!all_finite(&p->Sc[0][0], 9) || !all_finite(&p->Sci[0][0], 9)) return 0;
   p->sigma = 1.0 / (1.0 + exp(-logit));
-  if (!(p->sigma >= OG_ALPHA_MIN)) return 0;
+  if (!(p->sigma >= sigma_min)) return 0;
   p->r2 = 2.0 * log(255.0 * p->sigma);
   p->d = sqrt(p->mu[0] * p->mu[0] + p->mu[1] * p->mu[1] + p->mu[2] * p->mu[2]);
   for (int k = 0; k < 3; ++k) p->u[k] = p->mu[k] / p->d;
@@ -340,8 +360,17 @@ void og_edge_max(const double A4[4], const double P[2], const double D[2], doubl
 /* Tile culling on the optimal plane (Sec. 4.2, Eq. 4).  The quad spans the sample
  * positions [x0, x1] x [y0, y1].  Returns 1 when the pair is kept; *key = t* on the ray
  * through the maximum point projected back to the image. */
+static int og_tile_keep_r(const og_proj* p, const og_camera* c, double x0, double y0, double x1, double y1,
+                          double relax, double* key, double* qmin_out);
+
 static int og_tile_keep(const og_proj* p, const og_camera* c, double x0, double y0, double x1,
                         double y1, double* key, double* qmin_out) {
+  return og_tile_keep_r(p, c, x0, y0, x1, y1, 0.0, key, qmin_out);
+}
+
+/* og_tile_keep with the cut moved up by relax: keeps the pair while qmin <= r2 + relax */
+static int og_tile_keep_r(const og_proj* p, const og_camera* c, double x0, double y0, double x1, double y1,
+                          double relax, double* key, double* qmin_out) {
   const double cx[4] = {x0, x1, x1, x0}, cy[4] = {y0, y0, y1, y1};
   double S[4][2];
   *key = p->mu[2];
@@ -374,7 +403,7 @@ static int og_tile_keep(const og_proj* p, const og_camera* c, double x0, double 
     }
   }
   *qmin_out = qmin;
-  if (!(qmin <= p->r2)) return 0;
+  if (!(qmin <= p->r2 + relax)) return 0;
   double y[3];
   for (int k = 0; k < 3; ++k) y[k] = p->u[k] + p->E[0][k] * X[0] + p->E[1][k] * X[1];
   if (y[2] > 0) {
@@ -479,27 +508,82 @@ typedef struct {
   int n, cap;
 } window;
 
-static void win_push(window* w, went x, int* tie) {
-  if (w->n == w->cap) {
-    w->cap = w->cap ? 2 * w->cap : 16;
-    w->e = (went*)realloc(w->e, sizeof(went) * w->cap);
-  }
-  int j = w->n++;
-  while (j > 0 && went_less(x, w->e[j - 1])) {
-    w->e[j] = w->e[j - 1];
-    --j;
-  }
-  w->e[j] = x;
-  double tol = g_margin_tie * fabs(x.key);
-  if ((j > 0 && fabs(w->e[j - 1].key - x.key) <= tol) || (j + 1 < w->n && fabs(w->e[j + 1].key - x.key) <= tol))
-    *tie = 1;
+/* ---- decisions within the comparison margins ------------------------------------
+ * An FP32 renderer may legitimately take a decision the other way when its FP64 value
+ * lies within the comparison rule's margin of the threshold.  Each such decision gets
+ * an identity, so that a run can record it and a re-run can be told to flip it:
+ *   OG_DEC_KEEP  alpha of (sample idx, Gaussian g1) against 1/255
+ *   OG_DEC_STOP  transmittance test of (sample idx, Gaussian g1) against 1e-4
+ *   OG_DEC_WTIE  order of Gaussians g1 < g2 in window idx of a hierarchical block
+ *   OG_DEC_STIE  order of Gaussians g1 < g2 in the tile's sorted stream
+ * The alpha clamp at 0.99 is continuous in sigma G, so it decides nothing here. */
+enum { OG_DEC_KEEP = 0, OG_DEC_STOP = 1, OG_DEC_WTIE = 2, OG_DEC_STIE = 3 };
+
+typedef struct {
+  int type, idx;
+  int32_t g1, g2;
+} dec;
+
+typedef struct {
+  dec* d;
+  int n, cap;
+} decset;
+
+static int dec_eq(dec a, dec b) { return a.type == b.type && a.idx == b.idx && a.g1 == b.g1 && a.g2 == b.g2; }
+
+static int decset_find(const decset* s, dec x) {
+  if (!s) return -1;
+  for (int k = 0; k < s->n; ++k)
+    if (dec_eq(s->d[k], x)) return k;
+  return -1;
 }
 
-static went win_pop(window* w) {
-  went m = w->e[0];
-  memmove(w->e, w->e + 1, sizeof(went) * (w->n - 1));
-  w->n--;
-  return m;
+static void decset_add(decset* s, dec x) {
+  if (!s || decset_find(s, x) >= 0) return;
+  if (s->n == s->cap) {
+    s->cap = s->cap ? 2 * s->cap : 16;
+    s->d = (dec*)realloc(s->d, sizeof(dec) * s->cap);
+  }
+  s->d[s->n++] = x;
+}
+
+/* records decision x in `seen` and returns 1 when this run is told to flip it */
+static int decide(const decset* forced, decset* seen, dec x) {
+  decset_add(seen, x);
+  return decset_find(forced, x) >= 0;
+}
+
+static dec tie_dec(int type, int idx, int32_t a, int32_t b) {
+  return (dec){type, idx, a < b ? a : b, a < b ? b : a};
+}
+
+/* ---- outcome sets ---------------------------------------------------------------
+ * The valid results of one sample: (C rgb, T) of every combination of its marginal
+ * decisions, distinct values only.  A sample with more than OG_MAX_OUTCOMES distinct
+ * results, or whose combinations cannot be enumerated within the limits below, is
+ * "unchecked". */
+#define OG_MAX_OUTCOMES 64
+#define OG_MAX_LEAVES 4096    /* paths of one sample's walk (exact and global orders) */
+#define OG_MAX_GROUP 4        /* near-tied pairs whose orders are enumerated */
+#define OG_MAX_BLOCK_DECISIONS 64
+#define OG_MAX_SAMPLE_DECISIONS 6
+#define OG_MAX_PIXEL_COMBOS 4096
+#define OG_SAME 1e-13         /* results closer than this are one result */
+
+typedef struct {
+  double v[4];
+} outcome;
+
+static int outcome_add(outcome** arr, int* n, const double C[3], double T) {
+  for (int k = 0; k < *n; ++k)
+    if (fabs((*arr)[k].v[0] - C[0]) <= OG_SAME && fabs((*arr)[k].v[1] - C[1]) <= OG_SAME &&
+        fabs((*arr)[k].v[2] - C[2]) <= OG_SAME && fabs((*arr)[k].v[3] - T) <= OG_SAME)
+      return 1;
+  if (*n >= OG_MAX_OUTCOMES) return 0;
+  if (*n % 8 == 0) *arr = (outcome*)realloc(*arr, sizeof(outcome) * (*n + 8));
+  (*arr)[*n] = (outcome){{C[0], C[1], C[2], T}};
+  ++*n;
+  return 1;
 }
 
 typedef struct {
@@ -507,6 +591,9 @@ typedef struct {
   int done, marginal, active_sample;
   int32_t* gids;
   int ng, capg;
+  outcome* alt; /* every distinct valid result (nalt >= 2), or NULL: the nominal one only */
+  int nalt;
+  int unchecked;
 } sample;
 
 static void sample_push(sample* s, int32_t g) {
@@ -531,6 +618,151 @@ static void blend(sample* s, double alpha, const double rgb[3], int32_t g) {
   sample_push(s, g);
 }
 
+static int near_alpha_min(double sg) { return fabs(sg - OG_ALPHA_MIN) < g_margin_alpha * OG_ALPHA_MIN; }
+
+static void mark_threshold(sample* s, double sg) {
+  if (near_alpha_min(sg) || fabs(sg - OG_ALPHA_MAX) < g_margin_alpha * OG_ALPHA_MAX) s->marginal = 1;
+}
+
+/* og_eval that also returns alpha and t* of a pair below the cut (ray in front of o),
+ * for the runs that keep a pair whose keep decision is within the margin */
+static int eval_full(const og_proj* p, const og_camera* c, double px, double py, double* alpha, double* tstar,
+                     double* sg) {
+  int k = og_eval(p, c, px, py, alpha, tstar, sg);
+  if (!k && *sg > 0) {
+    double v[3];
+    pixel_ray(c, px, py, v);
+    *alpha = *sg < OG_ALPHA_MAX ? *sg : OG_ALPHA_MAX;
+    *tstar = tstar_ray(p, v);
+  }
+  return k;
+}
+
+/* ---- one sample's outcome walk (exact and global orders) ------------------------
+ * cand: the sample's kept pairs and the pairs whose keep decision is within the margin,
+ * in blend order; key is what orders them (t* for the exact order, the list key for the
+ * global orders).  Pairs whose keys are within the tie margin form groups whose every
+ * order is valid.  The walk follows every combination of group order, keep decision
+ * and stop decision and collects the distinct (C, T) it ends with. */
+typedef struct {
+  double key, alpha;
+  const double* rgb;
+  int32_t gid;
+  int kept, amb;
+} cand;
+
+static int cand_cmp(const void* a, const void* b) {
+  const cand *x = (const cand*)a, *y = (const cand*)b;
+  if (x->key < y->key) return -1;
+  if (x->key > y->key) return 1;
+  return (x->gid > y->gid) - (x->gid < y->gid);
+}
+
+typedef struct {
+  const cand* c;
+  int n;
+  const int* gend; /* gend[j]: end of the tie group that starts at j */
+  outcome* out;
+  int nout, overflow, leaves;
+} walker;
+
+static void walk_leaf(walker* w, double T, const double C[3]) {
+  if (w->overflow) return;
+  if (++w->leaves > OG_MAX_LEAVES || !outcome_add(&w->out, &w->nout, C, T)) w->overflow = 1;
+}
+
+static void walk_groups(walker* w, int j, double T, const double C[3]);
+
+static void walk_perm(walker* w, const int* perm, int g, int pos, int jnext, double T, const double C[3]) {
+  if (w->overflow) return;
+  if (pos == g) {
+    walk_groups(w, jnext, T, C);
+    return;
+  }
+  const cand* c = &w->c[perm[pos]];
+  for (int keep = 0; keep <= 1; ++keep) {
+    if (!c->amb && keep != c->kept) continue;
+    if (!keep) {
+      walk_perm(w, perm, g, pos + 1, jnext, T, C);
+      continue;
+    }
+    double test = T * (1.0 - c->alpha);
+    int amb_stop = fabs(test - OG_T_STOP) < g_margin_stop * OG_T_STOP;
+    int stop = test < OG_T_STOP;
+    if (stop || amb_stop) walk_leaf(w, T, C); /* stop before this pair */
+    if (!stop || amb_stop) {
+      double C2[3];
+      for (int ch = 0; ch < 3; ++ch) C2[ch] = C[ch] + c->alpha * T * c->rgb[ch];
+      walk_perm(w, perm, g, pos + 1, jnext, test, C2);
+    }
+  }
+}
+
+/* all orders of g <= OG_MAX_GROUP items, lexicographic (the identity first) */
+static int permutations(int g, int out[][OG_MAX_GROUP]) {
+  int n = 0, a[OG_MAX_GROUP];
+  for (int k = 0; k < g; ++k) a[k] = k;
+  for (;;) {
+    for (int k = 0; k < g; ++k) out[n][k] = a[k];
+    ++n;
+    int i = g - 2;
+    while (i >= 0 && a[i] > a[i + 1]) --i;
+    if (i < 0) return n;
+    int j = g - 1;
+    while (a[j] < a[i]) --j;
+    int t = a[i];
+    a[i] = a[j];
+    a[j] = t;
+    for (int l = i + 1, r = g - 1; l < r; ++l, --r) {
+      t = a[l];
+      a[l] = a[r];
+      a[r] = t;
+    }
+  }
+}
+
+static void walk_groups(walker* w, int j, double T, const double C[3]) {
+  if (w->overflow) return;
+  if (j >= w->n) {
+    walk_leaf(w, T, C);
+    return;
+  }
+  const int g = w->gend[j] - j;
+  if (g > OG_MAX_GROUP) {
+    w->overflow = 1;
+    return;
+  }
+  int perms[24][OG_MAX_GROUP];
+  const int np = permutations(g, perms);
+  for (int p = 0; p < np && !w->overflow; ++p) {
+    int perm[OG_MAX_GROUP];
+    for (int k = 0; k < g; ++k) perm[k] = j + perms[p][k];
+    walk_perm(w, perm, g, 0, j + g, T, C);
+  }
+}
+
+/* outcome set of one sample from its candidates in blend order (sorted by key, gid) */
+static void sample_outcomes(sample* s, const cand* c, int n) {
+  int* gend = (int*)malloc(sizeof(int) * (n ? n : 1));
+  for (int j = n - 1; j >= 0; --j)
+    gend[j] = (j + 1 < n && fabs(c[j + 1].key - c[j].key) < g_margin_tie * fabs(c[j + 1].key)) ? gend[j + 1] : j + 1;
+  walker w = {c, n, gend, NULL, 0, 0, 0};
+  const double C0[3] = {0, 0, 0};
+  walk_groups(&w, 0, 1.0, C0);
+  free(gend);
+  if (w.overflow) {
+    s->unchecked = 1;
+    free(w.out);
+  } else if (w.nout > 1) {
+    s->alt = w.out;
+    s->nalt = w.nout;
+  } else {
+    free(w.out);
+  }
+}
+
+/* ---- hierarchical blocks --------------------------------------------------------- */
+
 typedef struct {
   const og_proj* P;
   const og_camera* cam;
@@ -541,28 +773,61 @@ typedef struct {
   int k1, k2, k3;
   int tie;
   double last_key; /* tile key of the previous stream entry that was a block member */
+  int32_t last_gid;
   int has_last;
   int64_t evals, kept;
+  const decset* forced; /* decisions this run takes the other way */
+  decset* seen;         /* decisions within the margins this run met (may be NULL) */
+  int record;           /* nominal run: keep blend orders */
 } hblock;
 
-static int near_alpha_min(double sg) { return fabs(sg - OG_ALPHA_MIN) < g_margin_alpha * OG_ALPHA_MIN; }
-
-static void mark_threshold(sample* s, double sg) {
-  if (near_alpha_min(sg) || fabs(sg - OG_ALPHA_MAX) < g_margin_alpha * OG_ALPHA_MAX) s->marginal = 1;
+/* window indices in decision identities: L1 0, L2 1 + b, L3 5 + i */
+static int win_less(hblock* B, int widx, went a, went b) {
+  int less = went_less(a, b);
+  if (B->forced && B->forced->n && decset_find(B->forced, tie_dec(OG_DEC_WTIE, widx, a.gid, b.gid)) >= 0)
+    less = !less;
+  return less;
 }
 
-/* kept test at sample i; *flip (optional) reports a keep decision within the margin */
-static int kept_at_f(hblock* B, int i, int32_t g, double* a, double* t, int* flip) {
+static void win_push(hblock* B, int widx, window* w, went x, int* tie) {
+  if (w->n == w->cap) {
+    w->cap = w->cap ? 2 * w->cap : 16;
+    w->e = (went*)realloc(w->e, sizeof(went) * w->cap);
+  }
+  int j = w->n++;
+  while (j > 0 && win_less(B, widx, x, w->e[j - 1])) {
+    w->e[j] = w->e[j - 1];
+    --j;
+  }
+  w->e[j] = x;
+  double tol = g_margin_tie * fabs(x.key);
+  for (int nb = j - 1; nb <= j + 1; nb += 2)
+    if (nb >= 0 && nb < w->n && fabs(w->e[nb].key - x.key) < tol) {
+      *tie = 1;
+      decide(B->forced, B->seen, tie_dec(OG_DEC_WTIE, widx, x.gid, w->e[nb].gid));
+    }
+}
+
+static went win_pop(window* w) {
+  went m = w->e[0];
+  memmove(w->e, w->e + 1, sizeof(went) * (w->n - 1));
+  w->n--;
+  return m;
+}
+
+/* keep decision of Gaussian g at sample i (0 for a missing or finished sample);
+ * *amb (optional) reports a decision within the margin */
+static int keep_at(hblock* B, int i, int32_t g, double* a, double* t, int* amb, int count) {
   if (!B->s[i] || B->s[i]->done) return 0;
   double sg;
-  B->evals++;
-  int k = og_eval(&B->P[g], B->cam, B->px[i], B->py[i], a, t, &sg);
+  if (count) B->evals++;
+  int k = eval_full(&B->P[g], B->cam, B->px[i], B->py[i], a, t, &sg);
   mark_threshold(B->s[i], sg);
-  if (flip) *flip = near_alpha_min(sg);
+  int near = near_alpha_min(sg);
+  if (amb) *amb = near;
+  if (near && decide(B->forced, B->seen, (dec){OG_DEC_KEEP, i, g, 0})) k = !k;
   return k;
 }
-
-static int kept_at(hblock* B, int i, int32_t g, double* a, double* t) { return kept_at_f(B, i, g, a, t, NULL); }
 
 /* membership of a block = kept at any active sample; it can flip in FP32 only when every
  * keep decision behind it is marginal */
@@ -581,9 +846,23 @@ static int vote_result(hblock* B, vote v, int any) {
 }
 
 static void blend_at(hblock* B, int i, int32_t g) {
-  double a, t, sg;
-  if (!B->s[i] || B->s[i]->done) return;
-  if (og_eval(&B->P[g], B->cam, B->px[i], B->py[i], &a, &t, &sg)) blend(B->s[i], a, B->P[g].rgb, g);
+  double a, t;
+  sample* s = B->s[i];
+  if (!s || s->done) return;
+  if (!keep_at(B, i, g, &a, &t, NULL, 0)) return;
+  double test = s->T * (1.0 - a);
+  int stop = test < OG_T_STOP;
+  if (fabs(test - OG_T_STOP) < g_margin_stop * OG_T_STOP) {
+    s->marginal = 1;
+    if (decide(B->forced, B->seen, (dec){OG_DEC_STOP, i, g, 0})) stop = !stop;
+  }
+  if (stop) {
+    s->done = 1;
+    return;
+  }
+  for (int c = 0; c < 3; ++c) s->C[c] += a * s->T * B->P[g].rgb[c];
+  s->T = test;
+  if (B->record) sample_push(s, g);
 }
 
 static void to_L3(hblock* B, int b, int32_t g) {
@@ -591,10 +870,10 @@ static void to_L3(hblock* B, int b, int32_t g) {
   for (int j = 0; j < 4; ++j) {
     int i = (by + (j >> 1)) * 4 + bx + (j & 1);
     double a, t;
-    if (!kept_at(B, i, g, &a, &t)) continue;
-    B->kept++;
+    if (!keep_at(B, i, g, &a, &t, NULL, 1)) continue;
+    if (B->record) B->kept++;
     int tie = 0;
-    win_push(&B->L3[i], (went){t, g}, &tie);
+    win_push(B, 5 + i, &B->L3[i], (went){t, g}, &tie);
     if (tie) B->s[i]->marginal = 1;
     if (B->L3[i].n > B->k3) blend_at(B, i, win_pop(&B->L3[i]).gid);
   }
@@ -606,14 +885,14 @@ static void to_L2(hblock* B, int32_t g) {
     vote vt = {0, 0};
     for (int j = 0; j < 4; ++j) {
       double a, t;
-      int f = 0, k = kept_at_f(B, (by + (j >> 1)) * 4 + bx + (j & 1), g, &a, &t, &f);
+      int f = 0, k = keep_at(B, (by + (j >> 1)) * 4 + bx + (j & 1), g, &a, &t, &f, 1);
       if (k) any = 1;
       vote_add(&vt, k, f);
     }
     if (!vote_result(B, vt, any)) continue;
     double v[3];
     pixel_ray(B->cam, B->c2[b][0], B->c2[b][1], v);
-    win_push(&B->L2[b], (went){tstar_ray(&B->P[g], v), g}, &B->tie);
+    win_push(B, 1 + b, &B->L2[b], (went){tstar_ray(&B->P[g], v), g}, &B->tie);
     if (B->L2[b].n > B->k2) to_L3(B, b, win_pop(&B->L2[b]).gid);
   }
 }
@@ -623,18 +902,22 @@ static void stream_entry(hblock* B, int32_t g, double tile_key) {
   vote vt = {0, 0};
   for (int i = 0; i < 16; ++i) {
     double a, t;
-    int f = 0, k = kept_at_f(B, i, g, &a, &t, &f);
+    int f = 0, k = keep_at(B, i, g, &a, &t, &f, 1);
     if (k) any = 1;
     vote_add(&vt, k, f);
   }
   if (!vote_result(B, vt, any)) return;
   /* FP32 keys may swap near-tied members of the stream */
-  if (B->has_last && fabs(tile_key - B->last_key) <= g_margin_tie * fabs(tile_key)) B->tie = 1;
+  if (B->has_last && fabs(tile_key - B->last_key) < g_margin_tie * fabs(tile_key)) {
+    B->tie = 1;
+    decide(B->forced, B->seen, tie_dec(OG_DEC_STIE, 0, g, B->last_gid));
+  }
   B->last_key = tile_key;
+  B->last_gid = g;
   B->has_last = 1;
   double v[3];
   pixel_ray(B->cam, B->c4[0], B->c4[1], v);
-  win_push(&B->L1, (went){tstar_ray(&B->P[g], v), g}, &B->tie);
+  win_push(B, 0, &B->L1, (went){tstar_ray(&B->P[g], v), g}, &B->tie);
   if (B->L1.n > B->k1) to_L2(B, win_pop(&B->L1).gid);
 }
 
@@ -679,12 +962,17 @@ static uint8_t* tile_visibility(const uint8_t* visible, int W, int H, int T) {
 
 /* Gaussian/tile instances after the bounding rectangle and (optionally) Eq. 4 culling,
  * on visible tiles only (tvis NULL: all), sorted per tile by (key, gid): the stream every
- * sample of the tile reads.  cnt gets ntiles + 1 prefix offsets. */
+ * sample of the tile reads.  cnt gets ntiles + 1 prefix offsets.  relax > 0 also keeps
+ * the pairs whose Eq. 4 exponent is above the cut r2 by at most relax: their largest
+ * alpha over the tile is below 1/255 but within the margin, so an FP32 renderer may keep
+ * them at a sample there (they change no FP64 result).  slack (optional, malloc'd into
+ * *slack) gets qmin - r2 per entry in list order (0 for a pair kept without Eq. 4). */
 static tentry* build_lists(const og_proj* P, int64_t n, const og_camera* cam, int T, int tile_cull,
-                           const uint8_t* tvis, int key_mode, int64_t* cnt) {
+                           const uint8_t* tvis, int key_mode, double relax, int64_t* cnt, double** slack) {
   const int W = cam->width, H = cam->height;
   const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
   tentry* lists = NULL;
+  double* sl = NULL;
   for (int pass = 0; pass < 2; ++pass) {
     int64_t* fill = pass ? (int64_t*)calloc(ntiles, sizeof(int64_t)) : NULL;
     for (int64_t i = 0; i < n; ++i) {
@@ -692,38 +980,67 @@ static tentry* build_lists(const og_proj* P, int64_t n, const og_camera* cam, in
       const double* bb = P[i].bbox;
       int tx0 = (int)ceil((bb[0] + 0.5) / T - 1), tx1 = (int)floor((bb[2] - 0.5) / T);
       int ty0 = (int)ceil((bb[1] + 0.5) / T - 1), ty1 = (int)floor((bb[3] - 0.5) / T);
+      if (relax > 0 && P[i].bounded) { /* the relaxed cone is a little wider than the bbox */
+        tx0 = (int)floor(bb[0] / T) - 1;
+        ty0 = (int)floor(bb[1] / T) - 1;
+        tx1 = (int)floor(bb[2] / T) + 1;
+        ty1 = (int)floor(bb[3] / T) + 1;
+      }
       if (tx0 < 0) tx0 = 0;
       if (ty0 < 0) ty0 = 0;
       if (tx1 > ntx - 1) tx1 = ntx - 1;
       if (ty1 > nty - 1) ty1 = nty - 1;
       for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0; tx <= tx1; ++tx) {
-          double key = P[i].mu[2], qmin;
+          double key = P[i].mu[2], qmin = 0;
           if (tvis && !tvis[ty * ntx + tx]) continue;
           if (tile_cull) {
             double x0 = tx * T + 0.5, y0 = ty * T + 0.5;
             double x1 = fmin((tx + 1) * T, W) - 0.5, y1 = fmin((ty + 1) * T, H) - 0.5;
-            if (!og_tile_keep(&P[i], cam, x0, y0, x1, y1, &key, &qmin)) continue;
+            if (!og_tile_keep_r(&P[i], cam, x0, y0, x1, y1, relax, &key, &qmin)) continue;
           }
           /* global orders: one key per Gaussian */
           if (key_mode == 3) key = P[i].mu[2];
           if (key_mode == 4) key = sqrt(P[i].mu[0] * P[i].mu[0] + P[i].mu[1] * P[i].mu[1] + P[i].mu[2] * P[i].mu[2]);
           int t = ty * ntx + tx;
-          if (!pass)
+          if (!pass) {
             cnt[t + 1]++;
-          else
-            lists[cnt[t] + fill[t]++] = (tentry){(int32_t)i, key};
+          } else {
+            int64_t at = cnt[t] + fill[t]++;
+            lists[at] = (tentry){(int32_t)i, key};
+            if (sl) sl[at] = qmin > 0 ? qmin - P[i].r2 : 0.0;
+          }
         }
     }
     if (!pass) {
       for (int t = 0; t < ntiles; ++t) cnt[t + 1] += cnt[t];
       lists = (tentry*)malloc(sizeof(tentry) * (cnt[ntiles] ? cnt[ntiles] : 1));
+      if (slack) sl = (double*)malloc(sizeof(double) * (cnt[ntiles] ? cnt[ntiles] : 1));
     } else {
       free(fill);
     }
   }
+  if (sl) {
+    /* sort the entries of each tile together with their slack */
+    typedef struct {
+      tentry e;
+      double slack;
+    } tslack;
+    int64_t tot = cnt[ntiles];
+    tslack* tmp = (tslack*)malloc(sizeof(tslack) * (tot ? tot : 1));
+    for (int64_t j = 0; j < tot; ++j) tmp[j] = (tslack){lists[j], sl[j]};
 #pragma omp parallel for schedule(dynamic, 16)
-  for (int t = 0; t < ntiles; ++t) qsort(lists + cnt[t], cnt[t + 1] - cnt[t], sizeof(tentry), tentry_cmp);
+    for (int t = 0; t < ntiles; ++t) qsort(tmp + cnt[t], cnt[t + 1] - cnt[t], sizeof(tslack), tentry_cmp);
+    for (int64_t j = 0; j < tot; ++j) {
+      lists[j] = tmp[j].e;
+      sl[j] = tmp[j].slack;
+    }
+    free(tmp);
+    *slack = sl;
+  } else {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int t = 0; t < ntiles; ++t) qsort(lists + cnt[t], cnt[t + 1] - cnt[t], sizeof(tentry), tentry_cmp);
+  }
   return lists;
 }
 
@@ -739,30 +1056,212 @@ static int kpair_cmp(const void* a, const void* b) {
   return (x->gid > y->gid) - (x->gid < y->gid);
 }
 
-/* exact order at one sample: every kept candidate sorted by (t*, gid), then Eq. 2 */
-static void render_exact(const og_proj* P, const og_camera* cam, const int32_t* cand, int64_t nc,
-                         double px, double py, sample* s, int64_t* evals, int64_t* kept) {
+/* exact order at one sample: every kept candidate sorted by (t*, gid), then Eq. 2.
+ * With outcomes, also the sample's outcome set over its marginal decisions. */
+static void render_exact(const og_proj* P, const og_camera* cam, const int32_t* cand_ids, int64_t nc,
+                         double px, double py, sample* s, int outcomes, int64_t* evals, int64_t* kept) {
   kpair* kp = (kpair*)malloc(sizeof(kpair) * (nc ? nc : 1));
-  int64_t nk = 0;
+  cand* ca = outcomes ? (cand*)malloc(sizeof(cand) * (nc ? nc : 1)) : NULL;
+  int64_t nk = 0, na = 0;
   for (int64_t j = 0; j < nc; ++j) {
     double a, t, sg;
     ++*evals;
-    int k = og_eval(&P[cand[j]], cam, px, py, &a, &t, &sg);
+    int k = eval_full(&P[cand_ids[j]], cam, px, py, &a, &t, &sg);
     mark_threshold(s, sg);
-    if (k) kp[nk++] = (kpair){t, a, cand[j]};
+    if (k) kp[nk++] = (kpair){t, a, cand_ids[j]};
+    if (ca && (k || near_alpha_min(sg))) ca[na++] = (cand){t, a, P[cand_ids[j]].rgb, cand_ids[j], k, near_alpha_min(sg)};
   }
   *kept += nk;
   qsort(kp, nk, sizeof(kpair), kpair_cmp);
   for (int64_t j = 0; j < nk; ++j) {
-    if (j > 0 && fabs(kp[j].t - kp[j - 1].t) <= g_margin_tie * fabs(kp[j].t)) s->marginal = 1;
+    if (j > 0 && fabs(kp[j].t - kp[j - 1].t) < g_margin_tie * fabs(kp[j].t)) s->marginal = 1;
     blend(s, kp[j].alpha, P[kp[j].gid].rgb, kp[j].gid);
     if (s->done) {
       /* the pair after the stop could have come first among near-ties */
-      if (j + 1 < nk && fabs(kp[j + 1].t - kp[j].t) <= g_margin_tie * fabs(kp[j].t)) s->marginal = 1;
+      if (j + 1 < nk && fabs(kp[j + 1].t - kp[j].t) < g_margin_tie * fabs(kp[j].t)) s->marginal = 1;
       break;
     }
   }
   free(kp);
+  if (ca) {
+    qsort(ca, na, sizeof(cand), cand_cmp);
+    sample_outcomes(s, ca, (int)na);
+    free(ca);
+  }
+}
+
+/* One 4x4 block of samples of the hierarchical (or window) order: its geometry, its
+ * tile's stream and its windows. */
+typedef struct {
+  const og_proj* P;
+  const og_camera* cam;
+  double px[16], py[16], c4[2], c2[4][2];
+  const tentry* list;
+  int64_t nlist;
+  int k1, k2, k3;
+} blockdef;
+
+/* Runs the block's cascade over its stream on the samples s[16] (NULL where there is
+ * none), taking the decisions in `forced` the other way and recording in `seen` the
+ * decisions within the margins that it meets. */
+static void run_block(const blockdef* bd, sample* s[16], const decset* forced, decset* seen, int record,
+                      int64_t* evals, int64_t* kept, int* tie) {
+  hblock B;
+  memset(&B, 0, sizeof B);
+  B.P = bd->P;
+  B.cam = bd->cam;
+  B.k1 = bd->k1;
+  B.k2 = bd->k2;
+  B.k3 = bd->k3;
+  B.forced = forced;
+  B.seen = seen;
+  B.record = record;
+  for (int i = 0; i < 16; ++i) {
+    B.s[i] = s[i];
+    B.px[i] = bd->px[i];
+    B.py[i] = bd->py[i];
+  }
+  memcpy(B.c4, bd->c4, sizeof B.c4);
+  memcpy(B.c2, bd->c2, sizeof B.c2);
+  /* forced stream ties: the two entries swap places in the stream */
+  const tentry* L = bd->list;
+  tentry* cp = NULL;
+  for (int f = 0; forced && f < forced->n; ++f) {
+    if (forced->d[f].type != OG_DEC_STIE) continue;
+    if (!cp) {
+      cp = (tentry*)malloc(sizeof(tentry) * (bd->nlist ? bd->nlist : 1));
+      memcpy(cp, bd->list, sizeof(tentry) * bd->nlist);
+      L = cp;
+    }
+    int64_t a = -1, b = -1;
+    for (int64_t j = 0; j < bd->nlist; ++j) {
+      if (cp[j].gid == forced->d[f].g1) a = j;
+      if (cp[j].gid == forced->d[f].g2) b = j;
+    }
+    if (a >= 0 && b >= 0) {
+      tentry t = cp[a];
+      cp[a] = cp[b];
+      cp[b] = t;
+    }
+  }
+  for (int64_t j = 0; j < bd->nlist; ++j) {
+    int all_done = 1;
+    for (int i = 0; i < 16; ++i)
+      if (B.s[i] && !B.s[i]->done) all_done = 0;
+    if (all_done) break;
+    stream_entry(&B, L[j].gid, L[j].key);
+  }
+  flush_block(&B);
+  free(cp);
+  if (evals) *evals += B.evals;
+  if (kept) *kept += B.kept;
+  if (tie) *tie = B.tie;
+  free(B.L1.e);
+  for (int b = 0; b < 4; ++b) free(B.L2[b].e);
+  for (int i = 0; i < 16; ++i) free(B.L3[i].e);
+}
+
+typedef struct {
+  uint64_t mask;
+  double v[16][4];
+} brun;
+
+/* Outcome sets of a block's samples.  The nominal run met the decisions `seen`.  Each
+ * is flipped alone first; a sample's relevant decisions are those whose flip alone
+ * changes its result, and every combination of them (at most OG_MAX_SAMPLE_DECISIONS)
+ * is run.  Runs are shared between samples by the set of flips. */
+static void block_outcomes(const blockdef* bd, sample* S16[16], const decset* seen) {
+  const int nd = seen->n;
+  if (nd == 0) return;
+  if (nd > OG_MAX_BLOCK_DECISIONS) {
+    for (int i = 0; i < 16; ++i)
+      if (S16[i]) S16[i]->unchecked = 1;
+    return;
+  }
+  brun* runs = NULL;
+  int nruns = 0, capruns = 0;
+  uint32_t aff[OG_MAX_BLOCK_DECISIONS];
+  double nom[16][4];
+  for (int i = 0; i < 16; ++i)
+    if (S16[i]) {
+      for (int c = 0; c < 3; ++c) nom[i][c] = S16[i]->C[c];
+      nom[i][3] = S16[i]->T;
+    }
+  decset F = {0};
+  /* returns the index of the run with flips `mask` (run on first use) */
+#define OG_RUN(maskv, idxout)                                                      \
+  do {                                                                             \
+    int found_ = -1;                                                               \
+    for (int r_ = 0; r_ < nruns; ++r_)                                             \
+      if (runs[r_].mask == (maskv)) found_ = r_;                                   \
+    if (found_ < 0) {                                                              \
+      if (nruns == capruns) {                                                      \
+        capruns = capruns ? 2 * capruns : 64;                                      \
+        runs = (brun*)realloc(runs, sizeof(brun) * capruns);                       \
+      }                                                                            \
+      F.n = 0;                                                                     \
+      for (int d_ = 0; d_ < nd; ++d_)                                              \
+        if (((maskv) >> d_) & 1) decset_add(&F, seen->d[d_]);                      \
+      sample loc_[16];                                                             \
+      sample* lp_[16];                                                             \
+      memset(loc_, 0, sizeof loc_);                                                \
+      for (int i_ = 0; i_ < 16; ++i_) {                                            \
+        loc_[i_].T = 1.0;                                                          \
+        lp_[i_] = S16[i_] ? &loc_[i_] : NULL;                                      \
+      }                                                                            \
+      run_block(bd, lp_, &F, NULL, 0, NULL, NULL, NULL);                           \
+      runs[nruns].mask = (maskv);                                                  \
+      for (int i_ = 0; i_ < 16; ++i_) {                                            \
+        for (int c_ = 0; c_ < 3; ++c_) runs[nruns].v[i_][c_] = loc_[i_].C[c_];     \
+        runs[nruns].v[i_][3] = loc_[i_].T;                                         \
+      }                                                                            \
+      found_ = nruns++;                                                            \
+    }                                                                              \
+    (idxout) = found_;                                                             \
+  } while (0)
+  for (int d = 0; d < nd; ++d) {
+    int r;
+    OG_RUN(1ull << d, r);
+    aff[d] = 0;
+    for (int i = 0; i < 16; ++i) {
+      if (!S16[i]) continue;
+      for (int c = 0; c < 4; ++c)
+        if (fabs(runs[r].v[i][c] - nom[i][c]) > OG_SAME) aff[d] |= 1u << i;
+    }
+  }
+  for (int i = 0; i < 16; ++i) {
+    if (!S16[i]) continue;
+    int R[OG_MAX_BLOCK_DECISIONS], nr = 0;
+    for (int d = 0; d < nd; ++d)
+      if ((aff[d] >> i) & 1) R[nr++] = d;
+    if (nr == 0) continue;
+    if (nr > OG_MAX_SAMPLE_DECISIONS) {
+      S16[i]->unchecked = 1;
+      continue;
+    }
+    outcome* out = NULL;
+    int nout = 0, ok = outcome_add(&out, &nout, nom[i], nom[i][3]);
+    for (uint32_t sub = 1; ok && sub < (1u << nr); ++sub) {
+      uint64_t mask = 0;
+      for (int k = 0; k < nr; ++k)
+        if ((sub >> k) & 1) mask |= 1ull << R[k];
+      int r;
+      OG_RUN(mask, r);
+      ok = outcome_add(&out, &nout, runs[r].v[i], runs[r].v[i][3]);
+    }
+    if (!ok) {
+      S16[i]->unchecked = 1;
+      free(out);
+    } else if (nout > 1) {
+      S16[i]->alt = out;
+      S16[i]->nalt = nout;
+    } else {
+      free(out);
+    }
+  }
+#undef OG_RUN
+  free(F.d);
+  free(runs);
 }
 
 static double fovea_weight(const og_opts* o, double px, double py) {
@@ -785,6 +1284,63 @@ static int classify_tile(const og_opts* o, const og_camera* c, int tx, int ty, i
   return 1;
 }
 
+/* The samples an output pixel reads and their weights: the pixel's own sample (plain
+ * and focus tiles); its sample at weight w and the four samples of its 2x2 group at
+ * (1 - w) / 4 (hybrid tiles); the four bilinear taps of the half-resolution image, each
+ * a group sample or the mean of four full-resolution samples (periphery tiles).  None
+ * for a pixel of an invisible tile (the background). */
+typedef struct {
+  int64_t k;
+  double w;
+} tap;
+
+static int add_tap(tap* t, int n, int64_t k, double w) {
+  for (int j = 0; j < n; ++j)
+    if (t[j].k == k) {
+      t[j].w += w;
+      return n;
+    }
+  t[n] = (tap){k, w};
+  return n + 1;
+}
+
+static int low_taps(const sample* S, int W, int W2, int64_t nfull, int gx, int gy, double w, tap* t, int n) {
+  int64_t g = nfull + (int64_t)gy * W2 + gx;
+  if (S[g].active_sample) return add_tap(t, n, g, w);
+  for (int j = 0; j < 4; ++j) n = add_tap(t, n, (int64_t)(2 * gy + (j >> 1)) * W + 2 * gx + (j & 1), 0.25 * w);
+  return n;
+}
+
+static int pixel_taps(const og_opts* o, const og_camera* cam, const sample* S, const uint8_t* cls, const uint8_t* tvis,
+                      int T, int x, int y, tap* t) {
+  const int W = cam->width, H = cam->height, W2 = W / 2, H2 = H / 2, ntx = (W + T - 1) / T;
+  const int64_t nfull = (int64_t)W * H, k = (int64_t)y * W + x;
+  const int tl = (y / T) * ntx + x / T;
+  if (!tvis[tl]) return 0;
+  int c = cls[tl];
+  if (!o->foveated || c == 0) return add_tap(t, 0, k, 1.0);
+  if (c == 1) {
+    double w = fovea_weight(o, x + 0.5, y + 0.5);
+    int n = add_tap(t, 0, k, w);
+    return low_taps(S, W, W2, nfull, x / 2, y / 2, 1 - w, t, n);
+  }
+  double ux = (x + 0.5) / 2 - 0.5, uy = (y + 0.5) / 2 - 0.5;
+  int x0 = (int)floor(ux), y0 = (int)floor(uy);
+  double fx = ux - x0, fy = uy - y0;
+  int xa = x0 < 0 ? 0 : (x0 > W2 - 1 ? W2 - 1 : x0), xb = x0 + 1 > W2 - 1 ? W2 - 1 : x0 + 1;
+  int ya = y0 < 0 ? 0 : (y0 > H2 - 1 ? H2 - 1 : y0), yb = y0 + 1 > H2 - 1 ? H2 - 1 : y0 + 1;
+  if (xb < 0) xb = 0;
+  if (yb < 0) yb = 0;
+  int n = 0;
+  n = low_taps(S, W, W2, nfull, xa, ya, (1 - fx) * (1 - fy), t, n);
+  n = low_taps(S, W, W2, nfull, xb, ya, fx * (1 - fy), t, n);
+  n = low_taps(S, W, W2, nfull, xa, yb, (1 - fx) * fy, t, n);
+  n = low_taps(S, W, W2, nfull, xb, yb, fx * fy, t, n);
+  return n;
+}
+
+void og_free(void* p) { free(p); }
+
 int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out* out) {
   const int W = cam->width, H = cam->height, T = o->key_tile;
   if (W <= 0 || H <= 0 || T <= 0 || T % 4) return -1;
@@ -802,8 +1358,12 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
 
   og_proj* P = (og_proj*)malloc(sizeof(og_proj) * (n ? n : 1));
   int64_t nvalid = 0;
+  /* with outcome sets, Gaussians whose opacity is within the alpha margin below 1/255
+   * are kept too: an FP32 renderer may keep them, at alpha within the margin of the cut
+   * (they change no FP64 result, as no sample keeps them) */
+  const double sigma_min = o->outcomes ? OG_ALPHA_MIN * (1.0 - o->margin_alpha) : OG_ALPHA_MIN;
 #pragma omp parallel for schedule(dynamic, 1024) reduction(+ : nvalid)
-  for (int64_t i = 0; i < n; ++i) nvalid += og_project(sc, i, cam, &P[i]);
+  for (int64_t i = 0; i < n; ++i) nvalid += og_project_min(sc, i, cam, &P[i], sigma_min) && P[i].sigma >= OG_ALPHA_MIN;
   out->stats[0] = nvalid;
 
   /* tile classes */
@@ -827,9 +1387,21 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
       if (P[i].valid) brute_ids[m++] = (int32_t)i;
     nvalid = m;
   } else {
-    lists = build_lists(P, n, cam, T, o->tile_cull, tvis, o->mode, cnt);
+    /* with outcome sets, the lists also hold the pairs that only a decision within the
+     * alpha margin keeps: their largest alpha over the tile is below the cut by less
+     * than the margin (sigma G > (1 - m) / 255  <=>  q < r2 - 2 ln(1 - m)) */
+    double relax = o->outcomes ? -2.0 * log1p(-o->margin_alpha) : 0.0;
+    double* slack = NULL;
+    lists = build_lists(P, n, cam, T, o->tile_cull, tvis, o->mode, relax, cnt, o->outcomes ? &slack : NULL);
+    int64_t ninst = cnt[ntiles];
+    if (slack) {
+      ninst = 0;
+      for (int64_t j = 0; j < cnt[ntiles]; ++j) ninst += slack[j] <= 0;
+      free(slack);
+    }
+    out->stats[1] = ninst;
   }
-  out->stats[1] = o->brute ? 0 : cnt[ntiles];
+  if (o->brute) out->stats[1] = 0;
 
   sample* S = (sample*)calloc(nsamp, sizeof(sample));
   for (int64_t k = 0; k < nsamp; ++k) S[k].T = 1.0;
@@ -874,7 +1446,7 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
         for (int64_t j = 0; j < nc; ++j) tmp[j] = lists[cnt[t] + j].gid;
         cand = tmp;
       }
-      render_exact(P, cam, cand, nc, px, py, &S[k], &evals, &kept);
+      render_exact(P, cam, cand, nc, px, py, &S[k], o->outcomes, &evals, &kept);
       free(tmp);
     }
   } else if (o->mode == 3 || o->mode == 4) {
@@ -906,9 +1478,22 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
         if (!keep) continue;
         ++kept;
         /* an FP32 key may order two near-equal keys the other way */
-        if (fabs(lists[j].key - last_key) <= g_margin_tie * fabs(lists[j].key)) S[k].marginal = 1;
+        if (fabs(lists[j].key - last_key) < g_margin_tie * fabs(lists[j].key)) S[k].marginal = 1;
         last_key = lists[j].key;
         blend(&S[k], a, P[gid].rgb, gid);
+      }
+      if (o->outcomes) {
+        /* outcome set: the list order, near-equal keys in either order */
+        int64_t nc = cnt[t + 1] - cnt[t], na = 0;
+        cand* ca = (cand*)malloc(sizeof(cand) * (nc ? nc : 1));
+        for (int64_t j = cnt[t]; j < cnt[t + 1]; ++j) {
+          double a, ts, sg;
+          const int32_t gid = lists[j].gid;
+          const int keep = eval_full(&P[gid], cam, px, py, &a, &ts, &sg);
+          if (keep || near_alpha_min(sg)) ca[na++] = (cand){lists[j].key, a, P[gid].rgb, gid, keep, near_alpha_min(sg)};
+        }
+        sample_outcomes(&S[k], ca, (int)na);
+        free(ca);
       }
     }
   } else {
@@ -918,13 +1503,14 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
     int64_t nb_full = (int64_t)nbx * nby, nb_all = nb_full + (int64_t)nbx2 * nby2;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : evals, kept)
     for (int64_t bi = 0; bi < nb_all; ++bi) {
-      hblock B;
-      memset(&B, 0, sizeof B);
-      B.P = P;
-      B.cam = cam;
-      B.k1 = k1;
-      B.k2 = k2;
-      B.k3 = k3;
+      blockdef bd;
+      memset(&bd, 0, sizeof bd);
+      bd.P = P;
+      bd.cam = cam;
+      bd.k1 = k1;
+      bd.k2 = k2;
+      bd.k3 = k3;
+      sample* bs[16] = {NULL};
       int lowgrid = bi >= nb_full;
       int bx, by, any = 0, tile = -1;
       if (!lowgrid) {
@@ -940,54 +1526,51 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
         if (!lowgrid) {
           if (sx >= W || sy >= H) continue;
           k = (int64_t)sy * W + sx;
-          B.px[i] = sx + 0.5;
-          B.py[i] = sy + 0.5;
+          bd.px[i] = sx + 0.5;
+          bd.py[i] = sy + 0.5;
           tile = (sy / T) * ntx + sx / T;
         } else {
           if (sx >= W2 || sy >= H2) continue;
           k = nfull + (int64_t)sy * W2 + sx;
-          B.px[i] = 2 * sx + 1.0;
-          B.py[i] = 2 * sy + 1.0;
+          bd.px[i] = 2 * sx + 1.0;
+          bd.py[i] = 2 * sy + 1.0;
           tile = ((2 * sy) / T) * ntx + (2 * sx) / T;
         }
         if (S[k].active_sample) {
-          B.s[i] = &S[k];
+          bs[i] = &S[k];
           any = 1;
         }
       }
       if (!any) continue;
       if (!lowgrid) {
-        B.c4[0] = bx + 2.0;
-        B.c4[1] = by + 2.0;
+        bd.c4[0] = bx + 2.0;
+        bd.c4[1] = by + 2.0;
         for (int b = 0; b < 4; ++b) {
-          B.c2[b][0] = bx + (b & 1) * 2 + 1.0;
-          B.c2[b][1] = by + (b >> 1) * 2 + 1.0;
+          bd.c2[b][0] = bx + (b & 1) * 2 + 1.0;
+          bd.c2[b][1] = by + (b >> 1) * 2 + 1.0;
         }
       } else {
-        B.c4[0] = 2 * bx + 4.0;
-        B.c4[1] = 2 * by + 4.0;
+        bd.c4[0] = 2 * bx + 4.0;
+        bd.c4[1] = 2 * by + 4.0;
         for (int b = 0; b < 4; ++b) {
-          B.c2[b][0] = 2 * (bx + (b & 1) * 2) + 2.0;
-          B.c2[b][1] = 2 * (by + (b >> 1) * 2) + 2.0;
+          bd.c2[b][0] = 2 * (bx + (b & 1) * 2) + 2.0;
+          bd.c2[b][1] = 2 * (by + (b >> 1) * 2) + 2.0;
         }
       }
-      for (int64_t j = cnt[tile]; j < cnt[tile + 1]; ++j) {
-        int all_done = 1;
-        for (int i = 0; i < 16; ++i)
-          if (B.s[i] && !B.s[i]->done) all_done = 0;
-        if (all_done) break;
-        stream_entry(&B, lists[j].gid, lists[j].key);
-      }
-      flush_block(&B);
-      evals += B.evals;
-      kept += B.kept;
+      bd.list = lists + cnt[tile];
+      bd.nlist = cnt[tile + 1] - cnt[tile];
+      decset seen = {0};
+      int tie = 0;
+      int64_t be = 0, bk = 0;
+      run_block(&bd, bs, NULL, o->outcomes ? &seen : NULL, 1, &be, &bk, &tie);
+      evals += be;
+      kept += bk;
       /* a block-level decision within the margins marks every sample of the block */
-      if (B.tie)
+      if (tie)
         for (int i = 0; i < 16; ++i)
-          if (B.s[i]) B.s[i]->marginal = 1;
-      free(B.L1.e);
-      for (int b = 0; b < 4; ++b) free(B.L2[b].e);
-      for (int i = 0; i < 16; ++i) free(B.L3[i].e);
+          if (bs[i]) bs[i]->marginal = 1;
+      if (o->outcomes) block_outcomes(&bd, bs, &seen);
+      free(seen.d);
     }
   }
   out->stats[2] = evals;
@@ -1079,6 +1662,70 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
     }
   out->stats[5] = nmarg;
 
+  /* outcome sets of the composited pixels: every combination of the valid results of
+   * the samples a pixel reads, through the same composite (its taps and weights) */
+  out->alt_off = NULL;
+  out->alt = NULL;
+  out->n_alt = 0;
+  if (o->outcomes) {
+    int64_t cap = 0, nalt = 0, nunchk = 0;
+    double* alt = NULL;
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (nfull + 1));
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x) {
+        int64_t k = (int64_t)y * W + x;
+        off[k] = nalt;
+        tap tp[32];
+        int nt = pixel_taps(o, cam, S, cls, tvis, T, x, y, tp);
+        int unchk = 0;
+        int64_t combos = 1;
+        for (int j = 0; j < nt; ++j) {
+          if (S[tp[j].k].unchecked) unchk = 1;
+          if (S[tp[j].k].nalt > 1) combos *= S[tp[j].k].nalt;
+          if (combos > OG_MAX_PIXEL_COMBOS) unchk = 1;
+        }
+        if (out->unchecked) out->unchecked[k] = (uint8_t)unchk;
+        nunchk += unchk;
+        if (unchk || combos == 1) continue;
+        int pick[32] = {0};
+        int64_t first = nalt;
+        for (int64_t c = 0; c < combos; ++c) {
+          double v[3] = {0, 0, 0};
+          for (int j = 0; j < nt; ++j) {
+            const sample* sp = &S[tp[j].k];
+            const double* r = sp->nalt > 1 ? sp->alt[pick[j]].v : NULL;
+            for (int ch = 0; ch < 3; ++ch) {
+              double Cc = r ? r[ch] : sp->C[ch], Tt = r ? r[3] : sp->T;
+              v[ch] += tp[j].w * (Cc + Tt * bg[ch]);
+            }
+          }
+          int dup = 0;
+          for (int64_t a = first; a < nalt && !dup; ++a)
+            dup = fabs(alt[3 * a] - v[0]) <= OG_SAME && fabs(alt[3 * a + 1] - v[1]) <= OG_SAME &&
+                  fabs(alt[3 * a + 2] - v[2]) <= OG_SAME;
+          if (!dup) {
+            if (nalt == cap) {
+              cap = cap ? 2 * cap : 1024;
+              alt = (double*)realloc(alt, sizeof(double) * 3 * cap);
+            }
+            for (int ch = 0; ch < 3; ++ch) alt[3 * nalt + ch] = v[ch];
+            ++nalt;
+          }
+          /* next combination (mixed radix over the taps with several results) */
+          for (int j = 0; j < nt; ++j) {
+            if (S[tp[j].k].nalt <= 1) continue;
+            if (++pick[j] < S[tp[j].k].nalt) break;
+            pick[j] = 0;
+          }
+        }
+      }
+    off[nfull] = nalt;
+    out->alt_off = off;
+    out->alt = alt;
+    out->n_alt = nalt;
+    out->stats[7] = nunchk;
+  }
+
   /* blend orders for the gradient oracle */
   int64_t tot = 0, blended = 0;
   for (int64_t k = 0; k < nsamp; ++k) {
@@ -1093,7 +1740,10 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
   out->n_order = tot;
   out->stats[4] = blended;
 
-  for (int64_t k = 0; k < nsamp; ++k) free(S[k].gids);
+  for (int64_t k = 0; k < nsamp; ++k) {
+    free(S[k].gids);
+    free(S[k].alt);
+  }
   free(S);
   free(lowimg);
   free(lowmarg);
@@ -1108,9 +1758,11 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
 
 /* Tile lists as the oracle builds them, for list-level comparisons:
  * counts[ntiles] (always), and when gids/keys are given (sized >= total) the sorted
- * lists concatenated by tile. Returns the total number of instances. */
+ * lists concatenated by tile, with (slack, optional) qmin - r2 of each entry's Eq. 4
+ * test.  relax > 0 adds the entries with 0 < qmin - r2 <= relax (a largest alpha over
+ * the tile within the margin below 1/255).  Returns the total number of entries. */
 int64_t og_tile_lists(const og_scene* sc, const og_camera* cam, int T, int tile_cull, const uint8_t* visible,
-                      int64_t* counts, int32_t* gids, double* keys, int64_t cap) {
+                      double relax, int64_t* counts, int32_t* gids, double* keys, double* slack, int64_t cap) {
   const int W = cam->width, H = cam->height;
   const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;
   const int64_t n = sc->n;
@@ -1119,7 +1771,8 @@ int64_t og_tile_lists(const og_scene* sc, const og_camera* cam, int T, int tile_
   for (int64_t i = 0; i < n; ++i) og_project(sc, i, cam, &P[i]);
   int64_t* cnt = (int64_t*)calloc(ntiles + 1, sizeof(int64_t));
   uint8_t* tvis = tile_visibility(visible, W, H, T);
-  tentry* lists = build_lists(P, n, cam, T, tile_cull, tvis, 0, cnt);
+  double* sl = NULL;
+  tentry* lists = build_lists(P, n, cam, T, tile_cull, tvis, 0, relax, cnt, &sl);
   free(tvis);
   for (int t = 0; t < ntiles; ++t) counts[t] = cnt[t + 1] - cnt[t];
   int64_t tot = cnt[ntiles];
@@ -1127,7 +1780,9 @@ int64_t og_tile_lists(const og_scene* sc, const og_camera* cam, int T, int tile_
     for (int64_t j = 0; j < tot; ++j) {
       gids[j] = lists[j].gid;
       keys[j] = lists[j].key;
+      if (slack) slack[j] = sl[j];
     }
+  free(sl);
   free(lists);
   free(cnt);
   free(P);

@@ -5,6 +5,8 @@ and the same context then renders normally."""
 import numpy as np
 import pytest
 
+import outcomes as oc
+
 from oracle import native as on
 from paper_2505_10144_gb300 import synth
 
@@ -34,9 +36,7 @@ def test_bounded_wait_times_out_and_the_context_stays_usable(R, which):
     cam = synth.identity_camera(96, 64, 90.0)
     out = R.render([api.DeviceScene.from_host(scene)], [0], [cam], None, api.RenderConfig(sort_mode="exact"))
     R.check()
-    ref = on.render(scene, cam, "exact")
-    d = np.abs(out.cpu().numpy()[0] - ref["image"]).max(axis=0)
-    assert not ((d > 2e-4) & ~ref["marginal"]).any()
+    oc.check(out.cpu().numpy()[0], oc.reference(scene, cam, "exact"), "exact", label="after a timeout")
 
 
 def test_bounded_wait_rejects_unknown_waits(R):

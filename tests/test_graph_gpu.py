@@ -3,6 +3,8 @@ import json
 
 import numpy as np
 import pytest
+
+import outcomes as oc
 import torch
 
 from paper_2505_10144_gb300 import synth
@@ -96,7 +98,6 @@ def test_full_size_batched_views_sampled_crops():
         gr = api.GraphedRender(R, scenes, vs, cams, fovs, cfg)
         out = gr.replay()
         R.check()
-        tol = 2e-4
         checked = 0
         for k in range(3):
             v = 16 * k + 2 * (3 + k) + (k & 1)  # pose 3 + k, left or right eye
@@ -104,18 +105,21 @@ def test_full_size_batched_views_sampled_crops():
             for sx, sy in [(fv.gaze_x, fv.gaze_y), (300.0 + 500.0 * k, 1900.0 - 400.0 * k)]:
                 x0 = int(min(max(sx - 32, 0), W - 64)) // 32 * 32
                 y0 = int(min(max(sy - 32, 0), H - 64)) // 32 * 32
-                c2 = synth.Camera(cam.world_to_cam, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, 64, 64, cam.near_z)
-                f2 = synth.Fovea(fv.gaze_x - x0, fv.gaze_y - y0, fv.radius_px, fv.band_px)
-                ref = on.render(hosts[k], c2, "hier", windows=(4, 8, 16), key_tile=32, fovea=f2)
+                ref = oc.crop_reference(hosts[k], cam, x0, y0, 64, 64, "hier", fovea=fv, windows=(4, 8, 16),
+                                        key_tile=32)
                 sub = out[v][:, y0:y0 + 64, x0:x0 + 64].cpu().numpy().astype(np.float64)
-                m = ref["marginal"].copy()
-                m[:2, :] = m[-2:, :] = True  # bilinear reads across the crop edge
-                m[:, :2] = m[:, -2:] = True
-                assert (~m).sum() > 1000, (k, sx, sy, m.mean())
-                d = np.abs(sub - ref["image"]).max(axis=0)
-                bad = (d > tol) & ~m
-                assert not bad.any(), (k, sx, sy, int(bad.sum()), float(d[~m].max()))
+                oc.check(sub, ref, "hier", label=f"batched scene {k} view {v} at ({x0},{y0})")
                 checked += 1
+            if k == 0:
+                # the exact order on one view of this scene, through an eager render
+                ex = R.render([scenes[k]], [0], [cam], [fv], api.RenderConfig(sort_mode="exact", key_tile=32,
+                                                                               fovea_mode="bilinear"))
+                R.check()
+                x0 = int(min(max(fv.gaze_x - 32, 0), W - 64)) // 32 * 32
+                y0 = int(min(max(fv.gaze_y - 32, 0), H - 64)) // 32 * 32
+                ref = oc.crop_reference(hosts[k], cam, x0, y0, 64, 64, "exact", fovea=fv, key_tile=32)
+                oc.check(ex[0][:, y0:y0 + 64, x0:x0 + 64].cpu().numpy().astype(np.float64), ref, "exact",
+                         label=f"batched scene {k} view {v} exact")
         assert checked == 6
     finally:
         R.close()

@@ -1,4 +1,5 @@
-"""Planted mistakes in the float64 gradient oracle (``oracle/grad.py``), on the CPU.
+"""Planted mistakes in the oracles, on the CPU: the float64 gradient oracle
+(``oracle/grad.py``), the C forward oracle and its outcome sets.
 
 The gradient oracle is pinned by central differences of the C forward oracle, which
 re-sorts and re-culls at every evaluation and shares no code with it.  These tests show
@@ -149,5 +150,50 @@ def test_planted_mistake_in_the_c_oracle_fails_a_pin(slip, tmp_path):
                            str(tmp_path / "mutant.c"), "-lm"])
     env = dict(os.environ, VRS_ORACLE_LIB=str(lib), OMP_NUM_THREADS="4")
     r = subprocess.run([sys.executable, "-m", "pytest", str(root / "tests" / "test_oracle_pins.py"), "-x", "-q",
+                        "-p", "no:cacheprovider"], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1 and " failed" in r.stdout, r.stdout[-2000:]
+
+
+# ---------------------------------------------------------------- the outcome sets
+
+_OUTCOME_SLIPS = {
+    # near-tied depths or keys blended in one order only
+    "tie-orders": ("  const int np = permutations(g, perms);", "  const int np = permutations(g, perms) > 0;"),
+    # a keep decision within the alpha margin taken one way only (exact and global orders)
+    "keep-branch": ("    if (!c->amb && keep != c->kept) continue;", "    if (keep != c->kept) continue;"),
+    # a transmittance test within the stop margin taken one way only
+    "stop-branch": ("    int amb_stop = fabs(test - OG_T_STOP) < g_margin_stop * OG_T_STOP;", "    int amb_stop = 0;"),
+    # hierarchical windows: a forced tie flip that does not flip
+    "window-tie-flip": ("    less = !less;", "    less = less;"),
+    # hierarchical blocks: forced keep / stop flips that do not flip
+    "block-keep-flip": ("(dec){OG_DEC_KEEP, i, g, 0})) k = !k;", "(dec){OG_DEC_KEEP, i, g, 0})) k = k;"),
+    "block-stop-flip": ("(dec){OG_DEC_STOP, i, g, 0})) stop = !stop;", "(dec){OG_DEC_STOP, i, g, 0})) stop = stop;"),
+    # opacities within the margin below 1/255 culled at projection
+    "projection-cull": ("const double sigma_min = o->outcomes ? OG_ALPHA_MIN * (1.0 - o->margin_alpha) : OG_ALPHA_MIN;",
+                        "const double sigma_min = OG_ALPHA_MIN;"),
+    # tile lists without the pairs whose largest alpha over the tile is just below the cut
+    "relaxed-lists": ("double relax = o->outcomes ? -2.0 * log1p(-o->margin_alpha) : 0.0;", "double relax = 0.0;"),
+}
+
+
+@pytest.mark.parametrize("slip", sorted(_OUTCOME_SLIPS))
+def test_planted_mistake_in_the_outcome_sets_fails_a_pin(slip, tmp_path):
+    """A copy of the C oracle whose outcome enumeration skips one kind of decision fails
+    the outcome-set pins (renders of nearby scenes fall outside the sets)."""
+    import os
+    import subprocess
+    import sys
+    from pathlib import Path
+
+    root = Path(__file__).resolve().parent.parent
+    src = (root / "oracle" / "vrs_oracle.c").read_text()
+    old, new = _OUTCOME_SLIPS[slip]
+    assert src.count(old) == 1, slip
+    (tmp_path / "mutant.c").write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", str(lib),
+                           str(tmp_path / "mutant.c"), "-lm"])
+    env = dict(os.environ, VRS_ORACLE_LIB=str(lib), OMP_NUM_THREADS="4")
+    r = subprocess.run([sys.executable, "-m", "pytest", str(root / "tests" / "test_outcome_pins.py"), "-q",
                         "-p", "no:cacheprovider"], cwd=root, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1 and " failed" in r.stdout, r.stdout[-2000:]

@@ -1,10 +1,12 @@
 """GPU vs FP64 oracle, element by element, through the C ABI.
 
-Tolerance (from the workload statement): 2e-4 per FP32 channel on every pixel that the
-oracle does not flag as marginal; a pixel is marginal when one of its decisions (alpha
-against 1/255 or 0.99, transmittance against 1e-4, depth order between near-tied
-pairs, block membership of the hierarchical windows) lies within FP32 reach of its
-threshold, where a correct FP32 renderer may legitimately decide the other way.
+Tolerance (from the workload statement): 2e-4 per FP32 channel.  A pixel passes when it
+is within the bound of the oracle's value or of one of the values its samples' decisions
+within the comparison margins allow (alpha against 1/255, transmittance against 1e-4,
+near-equal depths, hierarchical window and stream ties): a correct FP32 renderer may take
+those decisions either way.  The oracle enumerates these outcome sets; every test bounds,
+asserts and prints the fraction of pixels whose set is too large to enumerate
+("unchecked", see tests/outcomes.py).
 """
 import math
 
@@ -12,13 +14,14 @@ import numpy as np
 import pytest
 import torch
 
+import outcomes as oc
 from oracle import native as on
 from paper_2505_10144_gb300 import synth
 from scenes import random_scene
 
 pytestmark = pytest.mark.gpu
 
-TOL = 2e-4
+TOL = oc.TOL
 
 
 @pytest.fixture(scope="module")
@@ -45,14 +48,10 @@ def render_gpu(R, scene, cams, foveas=None, **cfg):
     return out.cpu().numpy().astype(np.float64)
 
 
-def parity(gpu, ref, marginal, tol=TOL, allowed_frac=0.0):
-    d = np.abs(gpu - ref).max(axis=0)
-    bad = (d > tol) & ~marginal
-    frac = bad.mean()
-    worst = d[~marginal].max() if (~marginal).any() else 0.0
-    assert frac <= allowed_frac, f"{bad.sum()} non-marginal pixels off by > {tol} (worst {worst:.3g}, " \
-                                 f"marginal {marginal.mean():.4%})"
-    return worst, marginal.mean()
+def parity(gpu, scene, cam, mode, label="", **kw):
+    """The GPU image of one view against the oracle's outcome sets of the same view."""
+    ref = oc.reference(scene, cam, mode, **kw)
+    return oc.check(gpu, ref, mode, label=label or mode), ref
 
 
 # ---------------------------------------------------------------- sort (integer work)
@@ -77,12 +76,63 @@ def test_sort_pairs_is_stable_and_bit_exact(R, n, bits):
 
 # ---------------------------------------------------------------- preprocess
 
-def _oracle_projection(scene, cam, idx):
-    return [on.project_one(scene, int(i), cam) for i in idx]
+U32 = 2.0 ** -24  # FP32 unit roundoff
+
+
+def expected_record(p, cam):
+    """The record fields of one Gaussian from the oracle's FP64 projection p (same
+    tangent basis e1 = (u_z, 0, -u_x)/|.|, e2 = u x e1 as the product): the projected
+    mean; the plane map [E; u] K^-1 in pixel offsets from it; the conic scaled by
+    1/2 log2(e); log2 sigma; the depth form t* = (n0 dx + n1 dy + n2) / (m00 dx^2 +
+    m01x2 dx dy + m11 dy^2 + m02x2 dx + m12x2 dy + 1), normalised so that t*(mean) = z of
+    the mean (Sec. 4.1, 4.2)."""
+    fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    mu, E, u, A, Sci = p["mu"], p["E"], p["u"], p["A"], p["Sci"]
+    k = 0.5 / math.log(2.0)
+    sv = Sci @ mu
+    den0 = mu @ sv / mu[2] ** 2
+    n0, n1 = sv[0] / (fx * den0), sv[1] / (fy * den0)
+    return dict(
+        pm=np.array([fx * mu[0] / mu[2] + cx, fy * mu[1] / mu[2] + cy]),
+        plane=np.array([E[0, 0] / fx, E[0, 1] / fy, E[1, 0] / fx, E[1, 1] / fy, u[0] / fx, u[1] / fy,
+                        p["d"] / mu[2]]),
+        conic=k * np.array([A[0, 0], 2 * A[0, 1], A[1, 1]]),
+        lg2s=math.log2(p["sigma"]),
+        depth_num=np.array([n0, n1, mu[2]]),
+        depth_den=np.array([Sci[0, 0] / (fx * fx * den0), 2 * Sci[0, 1] / (fx * fy * den0),
+                            Sci[1, 1] / (fy * fy * den0), 2 * n0 / mu[2], 2 * n1 / mu[2]]),
+        rgb=p["rgb"])
+
+
+def record_fields(r):
+    """The same fields from a product record (six float4, see csrc/common.cuh)."""
+    r = r.astype(np.float64)
+    return dict(pm=r[0:2], plane=np.array([r[2], r[3], r[4], r[5], r[6], r[7], r[8]]), conic=r[9:12], lg2s=r[12],
+                depth_num=r[13:16], depth_den=np.array([r[16], r[17], r[18], r[19], r[20]]), rgb=r[21:24])
+
+
+def condition_factors(p):
+    """FP32 error bounds of the record's fields scale with these condition numbers: the
+    conic inverts the tangent-plane covariance (kappa(Sigma_p)), itself a projection of
+    the 3D covariance that can lose relative accuracy when the Gaussian is elongated along
+    the ray (|Sigma| / (d^2 |Sigma_p|)); the depth form is a quadratic form of Sigma^-1
+    (kappa(Sigma))."""
+    Sp, Sc = p["Sp"], p["Sc"]
+    k2 = np.linalg.cond(Sp)
+    proj = np.linalg.norm(Sc, 2) / (p["d"] ** 2 * np.linalg.norm(Sp, 2))
+    return dict(plane=1.0, conic=k2 * max(1.0, proj), depth_num=np.linalg.cond(Sc), depth_den=np.linalg.cond(Sc))
+
+
+# per-group bound on the normwise relative error, in units of U32 times the group's factor
+# (measured on a GB300: plane 2.2, conic 11.4, depth numerator 1.0, denominator 36.2)
+RECORD_ULPS = dict(plane=16.0, conic=64.0, depth_num=16.0, depth_den=128.0)
 
 
 @pytest.mark.parametrize("which", ["tiny", "shell"])
-def test_projection_records_match_oracle(R, which):
+def test_projection_records_match_oracle_field_by_field(R, which):
+    """Every record field of 2000 Gaussians against the oracle's FP64 projection: the
+    plane map, the conic and the depth form normwise within RECORD_ULPS x U32 x their
+    condition factor; the projected mean, log2 sigma and colour elementwise."""
     a = api()
     if which == "tiny":
         scene = synth.tiny_scene(4000, synth.rng_for(0))
@@ -93,56 +143,132 @@ def test_projection_records_match_oracle(R, which):
     ds = a.DeviceScene.from_host(scene)
     rec, bbox, cnt = R.project(ds, cam, 16)
     rec, bbox, cnt = rec.cpu().numpy(), bbox.cpu().numpy(), cnt.cpu().numpy()
-    counts, gids, _ = on.tile_lists(scene, cam, 16)
-    ocnt = np.bincount(gids, minlength=scene.n)
     rng = np.random.default_rng(0)
-    idx = rng.choice(scene.n, size=400, replace=False)
-    for i, p in zip(idx, _oracle_projection(scene, cam, idx)):
+    worst = {g: 0.0 for g in RECORD_ULPS}
+    compared = 0
+    idx = rng.choice(scene.n, size=2000, replace=False)
+    sub = scene.subset(idx)  # the projection is per Gaussian: the oracle needs only these
+    for j, i in enumerate(idx):
+        p = on.project_one(sub, j, cam)
         if not p["valid"]:
             assert cnt[i] == 0 and not rec[i].any()
             continue
         if cnt[i] == 0:
-            continue
-        fx, cx, cy = np.float32(cam.fx), np.float32(cam.cx), np.float32(cam.cy)
-        pm = np.array([fx * p["mu"][0] / p["mu"][2] + cx, fx * p["mu"][1] / p["mu"][2] + cy])
-        assert np.allclose(rec[i, :2], pm, rtol=1e-5, atol=1e-3)
-        assert abs(rec[i, 12] - math.log2(p["sigma"])) < 1e-5
-        assert abs(rec[i, 15] - p["mu"][2]) <= 1e-6 * abs(p["mu"][2])
-        assert np.allclose(rec[i, 21:24], p["rgb"], rtol=1e-5, atol=2e-6)
+            continue  # no tile kept: no record is written
+        e, g, f = expected_record(p, cam), record_fields(rec[i]), condition_factors(p)
+        assert np.allclose(g["pm"], e["pm"], rtol=1e-5, atol=1e-3), i
+        assert abs(g["lg2s"] - e["lg2s"]) < 1e-5, i
+        assert np.allclose(g["rgb"], e["rgb"], rtol=1e-5, atol=2e-6), i
+        for grp in RECORD_ULPS:
+            err = np.linalg.norm(g[grp] - e[grp]) / np.linalg.norm(e[grp])
+            ulps = err / (U32 * f[grp])
+            worst[grp] = max(worst[grp], ulps)
+            assert ulps <= RECORD_ULPS[grp], (i, grp, err, f[grp], g[grp], e[grp])
         if p["bounded"]:
             ob = p["bbox"]
             assert bbox[i, 0] <= ob[0] and bbox[i, 1] <= ob[1] and bbox[i, 2] >= ob[2] and bbox[i, 3] >= ob[3]
-    # a Gaussian the GPU drops entirely (view-frustum cull of its alpha >= 1/255 cone) must
-    # render nothing in the oracle, which keeps such pairs only conservatively
-    W, H = int(cam.width), int(cam.height)
-    for i in np.nonzero((cnt == 0) & (ocnt > 0))[0][:20]:
-        one = scene.subset([i])
-        assert not on.render(one, cam, "exact", brute=True)["image"].any(), i
+        compared += 1
+    print(f"[records {which}] {compared} compared; worst error / (U32 x factor): "
+          + ", ".join(f"{k} {v:.1f}" for k, v in worst.items()))
+    assert compared > 400
 
 
-def test_tile_lists_match_oracle(R):
-    scene = synth.tiny_scene(10_000, synth.rng_for(0))
-    cam = synth.identity_camera(256, 256, 90.0)
-    render_gpu(R, scene, [cam], sort_mode="exact", key_tile=16)
-    tpv = 16 * 16
-    keys, vals, ranges = R.instances(1, tpv)
+def _key_float(keys):
+    """The depth of a 64-bit sort key (low 32 bits: order-preserving float bits)."""
+    b = (keys & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    neg = (b & np.uint32(0x80000000)) == 0
+    b = np.where(neg, ~b, b ^ np.uint32(0x80000000)).astype(np.uint32)
+    return b.view(np.float32).astype(np.float64)
+
+
+# The product's Eq. 4 test keeps a pair while qmin' <= cut (1 + 1e-4) + 1e-5, in its log2
+# units (q' = q / (2 ln 2), cut = log2(255 sigma)): a hair wider than FP64, so that it never
+# drops a pair FP64 keeps.  In the oracle's units that band is qmin - r2 <= 1e-4 r2 + 2 ln2 1e-5.
+def conservative_band(r2):
+    return 1e-4 * r2 + 2.0 * math.log(2.0) * 1e-5
+
+
+@pytest.mark.parametrize("which", ["tiny", "shell"])
+def test_tile_lists_match_oracle(R, which):
+    """Index work: the GPU's per-tile lists against the oracle's, entry by entry.  Equal,
+    except these kinds of entries, counted and printed:
+      - margin-dropped: in the oracle's list, its Eq. 4 exponent within the alpha margin
+        below the cut (0 >= qmin - r2 >= -relax);
+      - margin-added: in the GPU's list only, within the alpha margin above the cut
+        (0 < qmin - r2 <= relax);
+      - conservative-added: in the GPU's list only, above that but within the product's
+        documented conservative band (conservative_band); their alpha is below the cut by
+        more than the margin at every sample of the tile, so no sample blends them;
+      - frustum-culled: the GPU drops the whole Gaussian (no entry in any tile) because its
+        alpha >= 1/255 cone misses the view; such a Gaussian must render nothing in the
+        oracle (brute force over every pixel).
+    Every other Gaussian the oracle keeps in some tile, the GPU keeps too.  Within a tile
+    both lists are in (key, index) order; two entries may swap only where their oracle
+    keys tie to within 1e-5 (the FP32 key of the Eq. 4 maximum point)."""
+    a = api()
+    if which == "tiny":
+        scene = synth.tiny_scene(10_000, synth.rng_for(0))
+        cam = synth.identity_camera(256, 256, 90.0)
+    else:
+        scene = synth.shell_scene(20_000, synth.rng_for(1), sh_degree=3)
+        cam = synth.stereo_cameras((0.03, 0, 0.02), 0.4, 512, 544, 110.0)[0]
+    T = 16
+    render_gpu(R, scene, [cam], sort_mode="exact", key_tile=T)
+    ntx, nty = (cam.width + T - 1) // T, (cam.height + T - 1) // T
+    keys, vals, ranges = R.instances(1, ntx * nty)
     keys, vals, ranges = keys.cpu().numpy().view(np.uint64), vals.cpu().numpy(), ranges.cpu().numpy()
-    counts, ogids, okeys = on.tile_lists(scene, cam, 16)
+    _, _, gcnt = R.project(a.DeviceScene.from_host(scene), cam, T)
+    gcnt = gcnt.cpu().numpy()
+    relax = on.alpha_relax()
+    sigma = 1.0 / (1.0 + np.exp(-scene.opacity_logit.astype(np.float64)))
+    r2 = 2.0 * np.log(np.maximum(255.0 * sigma, 1e-300))
+    counts, ogids, okeys, slack = on.tile_lists(scene, cam, T, relax=float(conservative_band(r2.max())) + relax,
+                                                want_slack=True)
     off = np.concatenate([[0], np.cumsum(counts.ravel())])
-    assert np.all(np.diff(keys.astype(np.float64)) >= 0) or np.all(keys[1:] >= keys[:-1])
-    for t in range(tpv):
+    assert np.all(keys[1:] >= keys[:-1])
+    n = dict(equal=0, margin_dropped=0, margin_added=0, conservative_added=0, frustum=0)
+    frustum = set()
+    for t in range(ntx * nty):
         s, e = ranges[t]
-        g = vals[s:e]
+        g = vals[s:e].astype(np.int64)
         assert np.all((keys[s:e] >> np.uint64(32)) == t)
-        og = ogids[off[t]:off[t + 1]]
-        ok = okeys[off[t]:off[t + 1]]
-        assert set(og.tolist()) <= set(g.tolist())
-        # common entries appear in the same order unless their oracle keys nearly tie
+        og, ok, sl = ogids[off[t]:off[t + 1]], okeys[off[t]:off[t + 1]], slack[off[t]:off[t + 1]]
+        slack_of = {int(x): y for x, y in zip(og, sl)}
+        definite = {x for x, y in slack_of.items() if y <= 0}
+        gs = set(g.tolist())
+        for x in definite - gs:
+            if gcnt[x] == 0:  # no entry anywhere: the whole Gaussian culled (checked below)
+                frustum.add(x)
+                n["frustum"] += 1
+            else:
+                assert -relax <= slack_of[x] < 0, (t, x, slack_of[x])
+                n["margin_dropped"] += 1
+        for x in gs - definite:
+            assert x in slack_of, (t, x)  # beyond even the conservative band
+            if slack_of[x] <= relax:
+                n["margin_added"] += 1
+            else:
+                assert slack_of[x] <= conservative_band(r2[x]) * 1.01 + relax, (t, x, slack_of[x], r2[x])
+                n["conservative_added"] += 1
+        n["equal"] += len(gs & definite)
+        # order: common entries in the same order unless their oracle keys nearly tie
         pos = {int(x): k for k, x in enumerate(g.tolist())}
-        p = np.array([pos[int(x)] for x in og])
-        inv = np.nonzero(np.diff(p) < 0)[0]
-        for k in inv:
-            assert abs(ok[k + 1] - ok[k]) <= 1e-5 * abs(ok[k]), (t, k)
+        common = [(k, int(x)) for k, x in enumerate(og) if int(x) in pos]
+        p = np.array([pos[x] for _, x in common])
+        for j in np.nonzero(np.diff(p) < 0)[0] if len(p) > 1 else []:
+            k0, k1 = ok[common[j][0]], ok[common[j + 1][0]]
+            assert abs(k1 - k0) <= 1e-5 * abs(k0), (t, common[j], common[j + 1])
+    # a Gaussian the GPU culls whole renders nothing in the oracle
+    for x in sorted(frustum):
+        assert not on.render(scene.subset([x]), cam, "exact", brute=True)["image"].any(), x
+    # conservativeness over every Gaussian: kept by the oracle => kept by the GPU, unless culled whole
+    okept = np.zeros(scene.n, bool)
+    okept[ogids[(slack < -relax) | (slack == 0)]] = True
+    lost = np.nonzero(okept & (gcnt == 0))[0]
+    assert set(lost.tolist()) <= frustum, sorted(set(lost.tolist()) - frustum)[:10]
+    print(f"[lists {which}] " + ", ".join(f"{k} {v}" for k, v in n.items()) + f" ({len(frustum)} Gaussians culled whole)")
+    assert n["margin_dropped"] + n["margin_added"] <= 1e-3 * n["equal"]
+    assert n["conservative_added"] <= 1e-2 * n["equal"]
 
 
 # ---------------------------------------------------------------- whole renders
@@ -154,19 +280,17 @@ def config0():
 
 def test_render_exact_config0(R, config0):
     scene, cam = config0
-    ref = on.render(scene, cam, "exact", key_tile=16)
     gpu = render_gpu(R, scene, [cam], sort_mode="exact", key_tile=16)[0]
-    worst, mf = parity(gpu, ref["image"], ref["marginal"])
-    assert mf < 0.005
+    st, _ = parity(gpu, scene, cam, "exact", key_tile=16, label="config0 exact")
+    assert st["unchecked"] == 0.0
 
 
 @pytest.mark.parametrize("mode,win", [("window", (0, 0, 16)), ("window", (0, 0, 4)), ("hier", (4, 8, 16)),
                                       ("hier", (8, 16, 32)), ("hier", (1, 1, 1))])
 def test_render_windows_config0(R, config0, mode, win):
     scene, cam = config0
-    ref = on.render(scene, cam, mode, windows=win, key_tile=16)
     gpu = render_gpu(R, scene, [cam], sort_mode=mode, windows=win, key_tile=16)[0]
-    parity(gpu, ref["image"], ref["marginal"])
+    parity(gpu, scene, cam, mode, windows=win, key_tile=16, label=f"config0 {mode} {win}")
 
 
 @pytest.fixture(scope="module")
@@ -183,9 +307,9 @@ def test_render_foveated_stereo(R, vr_small, mode, win):
     scene, cams, fov = vr_small
     gpu = render_gpu(R, scene, cams, fov, sort_mode=mode, windows=win, key_tile=32, fovea_mode="bilinear")
     for v in range(2):
-        ref = on.render(scene, cams[v], mode, windows=win, key_tile=32, fovea=fov[v])
+        _, ref = parity(gpu[v], scene, cams[v], mode, windows=win, key_tile=32, fovea=fov[v],
+                        label=f"foveated stereo {mode} eye {v}")
         assert (ref["tile_class"] == 0).any() and (ref["tile_class"] == 2).any()
-        parity(gpu[v], ref["image"], ref["marginal"])
 
 
 @pytest.mark.parametrize("mode", ["exact", "hier"])
@@ -193,8 +317,7 @@ def test_render_plain_stereo_shell(R, vr_small, mode):
     scene, cams, _ = vr_small
     gpu = render_gpu(R, scene, cams, sort_mode=mode, key_tile=16)
     for v in range(2):
-        ref = on.render(scene, cams[v], mode, key_tile=16)
-        parity(gpu[v], ref["image"], ref["marginal"])
+        parity(gpu[v], scene, cams[v], mode, key_tile=16, label=f"plain stereo {mode} eye {v}")
 
 
 @pytest.mark.parametrize("mode", ["global_z", "global_dist"])
@@ -204,10 +327,8 @@ def test_render_global_orders(R, vr_small, mode):
     gpu = render_gpu(R, scene, cams, sort_mode=mode, key_tile=16)
     gpf = render_gpu(R, scene, cams, fov, sort_mode=mode, key_tile=32, fovea_mode="bilinear")
     for v in range(2):
-        ref = on.render(scene, cams[v], mode, key_tile=16)
-        parity(gpu[v], ref["image"], ref["marginal"])
-        ref = on.render(scene, cams[v], mode, key_tile=32, fovea=fov[v])
-        parity(gpf[v], ref["image"], ref["marginal"])
+        parity(gpu[v], scene, cams[v], mode, key_tile=16, label=f"{mode} plain eye {v}")
+        parity(gpf[v], scene, cams[v], mode, key_tile=32, fovea=fov[v], label=f"{mode} foveated eye {v}")
 
 
 # ---------------------------------------------------------------- edge cases
@@ -228,10 +349,9 @@ def test_ragged_image_and_culled_inputs(R):
     scene.opacity_logit[60:80] = -np.inf
     cam = synth.identity_camera(250, 130, 100.0)
     for mode in ("exact", "hier"):
-        ref = on.render(scene, cam, mode, key_tile=16)
         gpu = render_gpu(R, scene, [cam], sort_mode=mode, key_tile=16)[0]
         assert np.isfinite(gpu).all()
-        parity(gpu, ref["image"], ref["marginal"])
+        parity(gpu, scene, cam, mode, key_tile=16, label=f"ragged {mode}")
 
 
 def test_single_pixel_and_single_tile_images(R):
@@ -239,9 +359,8 @@ def test_single_pixel_and_single_tile_images(R):
     scene = random_scene(500, rng)
     for W, H in [(1, 1), (16, 16), (17, 3)]:
         cam = synth.identity_camera(W, H, 60.0)
-        ref = on.render(scene, cam, "exact", key_tile=16)
         gpu = render_gpu(R, scene, [cam], sort_mode="exact", key_tile=16)[0]
-        parity(gpu, ref["image"], ref["marginal"])
+        parity(gpu, scene, cam, "exact", key_tile=16, label=f"{W}x{H}")
 
 
 def test_large_and_near_gaussians_span_many_tiles(R):
@@ -257,13 +376,11 @@ def test_large_and_near_gaussians_span_many_tiles(R):
     assert (per > 8).sum() > 0.8 * (per > 0).sum() and per.max() > 0.8 * counts.size
     fov = synth.fovea_for(192, (90.0, 70.0), radius_frac=0.2)
     for mode, win in (("exact", (0, 0, 0)), ("hier", (4, 8, 16))):
-        ref = on.render(scene, cam, mode, windows=win, key_tile=16)
         gpu = render_gpu(R, scene, [cam], sort_mode=mode, windows=win, key_tile=16)[0]
-        parity(gpu, ref["image"], ref["marginal"])
-        ref = on.render(scene, cam, mode, windows=win, key_tile=32, fovea=fov)
-        assert (ref["tile_class"] == 2).any()
+        parity(gpu, scene, cam, mode, windows=win, key_tile=16, label=f"large {mode} plain")
         gpu = render_gpu(R, scene, [cam], [fov], sort_mode=mode, windows=win, key_tile=32, fovea_mode="bilinear")[0]
-        parity(gpu, ref["image"], ref["marginal"])
+        _, ref = parity(gpu, scene, cam, mode, windows=win, key_tile=32, fovea=fov, label=f"large {mode} foveated")
+        assert (ref["tile_class"] == 2).any()
 
 
 def test_invalid_arguments_are_rejected(R):
@@ -288,31 +405,39 @@ def crop_camera(cam, x0, y0, w, h):
     return synth.Camera(cam.world_to_cam, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, w, h, cam.near_z)
 
 
-def test_full_size_vr_frame_sampled_crops(R):
-    """500k Gaussians, stereo 2064x2208, foveated, hierarchical 4/8/16 windows: the GPU
-    frame against oracle renders of 32-aligned crops (same rays, tiles, blocks and
-    streams as the full frame), interior pixels."""
+def crop_spots(fv, W=2064, H=2208):
+    """32-aligned 64x64 windows: at the gaze (focus), on the blend band (hybrid), in the
+    periphery, and at the ragged bottom-right corner (16-pixel tile column)."""
+    out = []
+    for sx, sy in [(fv.gaze_x, fv.gaze_y), (fv.gaze_x + fv.radius_px + 0.5 * fv.band_px, fv.gaze_y), (200.0, 300.0),
+                   (W - 24.0, H - 28.0)]:
+        x0 = int(min(max(sx - 32, 0), W - 48)) // 32 * 32
+        y0 = int(min(max(sy - 32, 0), H - 64)) // 32 * 32
+        out.append((x0, y0, min(64, W - x0), min(64, H - y0)))
+    return out
+
+
+@pytest.fixture(scope="module")
+def vr_full():
     scene = synth.shell_scene(500_000, synth.rng_for(1), sh_degree=3)
     wl = synth.vr_trajectory(3, synth.rng_for(1, salt=7))
-    fr = wl.frames[2]
-    gpu = render_gpu(R, scene, fr.cameras, fr.foveas, sort_mode="hier", windows=(4, 8, 16), key_tile=32,
+    return scene, wl.frames[2]
+
+
+@pytest.mark.parametrize("mode,win", [("hier", (4, 8, 16)), ("exact", (0, 0, 0))])
+def test_full_size_vr_frame_sampled_crops(R, vr_full, mode, win):
+    """500k Gaussians, stereo 2064x2208, foveated, as the benchmark renders it: the
+    hierarchical 4/8/16 windows, and the exact per-ray order the workload's 2e-4 rule is
+    stated for.  The GPU frame against oracle renders of the same rays in 64x64 windows
+    (focus, blend band, periphery, ragged corner; every pixel of each window)."""
+    scene, fr = vr_full
+    gpu = render_gpu(R, scene, fr.cameras, fr.foveas, sort_mode=mode, windows=win, key_tile=32,
                      fovea_mode="bilinear")
     checked = 0
     for v in range(2):
         cam, fv = fr.cameras[v], fr.foveas[v]
-        gx, gy = fv.gaze_x, fv.gaze_y
-        spots = [(gx, gy), (gx + fv.radius_px + 0.5 * fv.band_px, gy), (200.0, 300.0), (2040.0, 2180.0)]
-        for sx, sy in spots:
-            x0 = int(min(max(sx - 32, 0), 2064 - 64)) // 32 * 32
-            y0 = int(min(max(sy - 32, 0), 2208 - 64)) // 32 * 32
-            w, h = min(64, 2064 - x0), min(64, 2208 - y0)
-            c2 = crop_camera(cam, x0, y0, w, h)
-            f2 = synth.Fovea(gx - x0, gy - y0, fv.radius_px, fv.band_px)
-            ref = on.render(scene, c2, "hier", windows=(4, 8, 16), key_tile=32, fovea=f2)
-            sub = gpu[v][:, y0:y0 + h, x0:x0 + w]
-            m = ref["marginal"].copy()
-            m[:2, :] = m[-2:, :] = True  # bilinear reads across the crop edge
-            m[:, :2] = m[:, -2:] = True
-            parity(sub, ref["image"], m)
+        for x0, y0, w, h in crop_spots(fv):
+            ref = oc.crop_reference(scene, cam, x0, y0, w, h, mode, fovea=fv, windows=win, key_tile=32)
+            oc.check(gpu[v][:, y0:y0 + h, x0:x0 + w], ref, mode, label=f"full-size {mode} eye {v} at ({x0},{y0})")
             checked += 1
     assert checked == 8

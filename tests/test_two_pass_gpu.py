@@ -1,8 +1,10 @@
 """The two-pass foveated baseline (Appendix A) on the GPU against its oracle
 composition: full-resolution centre square, half-resolution view, bilinear upsample and
-w-blend.  Same parity rule as the render tests."""
+w-blend.  Same parity rule as the render tests (tests/outcomes.py)."""
 import numpy as np
 import pytest
+
+import outcomes as oc
 
 from oracle import twopass as otp
 from paper_2505_10144_gb300 import synth
@@ -37,10 +39,8 @@ def test_two_pass_matches_oracle(R, mode, win):
     R.check()
     gpu = gpu.cpu().numpy().astype(np.float64)
     for v in range(2):
-        ref = otp.render(scene, cams[v], fov[v], mode, windows=win, bg=bg)
-        d = np.abs(gpu[v] - ref["image"]).max(axis=0)
-        bad = (d > TOL) & ~ref["marginal"]
-        assert not bad.any(), (bad.sum(), d[~ref["marginal"]].max())
+        ref = otp.render(scene, cams[v], fov[v], mode, windows=win, bg=bg, outcomes=True)
+        oc.check(gpu[v], ref, mode, label=f"two-pass {mode} eye {v}")
 
 
 def test_two_pass_rejects_bad_arguments(R):

@@ -5,6 +5,8 @@ import numpy as np
 import pytest
 import torch
 
+import outcomes as oc
+
 from oracle import grad as og
 from oracle import native as on
 from paper_2505_10144_gb300 import synth
@@ -35,13 +37,6 @@ def vr_masked():
     return scene, cams, fov, masks
 
 
-def parity(gpu, ref, marginal, tol=TOL):
-    d = np.abs(gpu - ref).max(axis=0)
-    bad = (d > tol) & ~marginal
-    worst = d[~marginal].max() if (~marginal).any() else 0.0
-    assert not bad.any(), f"{bad.sum()} non-marginal pixels off by > {tol} (worst {worst:.3g})"
-
-
 def tiles_invisible(mask, T):
     H, W = mask.shape
     ntx, nty = (W + T - 1) // T, (H + T - 1) // T
@@ -69,9 +64,9 @@ def test_visibility_foveated_stereo_matches_oracle(R, vr_masked, mode, win):
     for v in range(2):
         inv = tiles_invisible(masks[v], T)
         assert inv.sum() >= 4
-        ref = on.render(scene, cams[v], mode, windows=win, key_tile=T, fovea=fov[v], bg=BG, visible=masks[v])
+        ref = oc.reference(scene, cams[v], mode, windows=win, key_tile=T, fovea=fov[v], bg=BG, visible=masks[v])
         assert np.array_equal(ref["tile_class"] >= 4, inv)
-        parity(gpu[v], ref["image"], ref["marginal"])
+        oc.check(gpu[v], ref, mode, label=f"visibility foveated {mode} eye {v}")
         pix = np.repeat(np.repeat(inv, T, 0), T, 1)[:256, :320]
         for ch in range(3):
             assert np.all(gpu[v][ch][pix] == np.float32(BG[ch]))
@@ -82,8 +77,8 @@ def test_visibility_plain_matches_oracle(R, vr_masked, mode):
     scene, cams, _, masks = vr_masked
     gpu, _ = render(R, scene, cams, None, masks, sort_mode=mode, key_tile=16, bg=BG)
     for v in range(2):
-        ref = on.render(scene, cams[v], mode, key_tile=16, bg=BG, visible=masks[v])
-        parity(gpu[v], ref["image"], ref["marginal"])
+        ref = oc.reference(scene, cams[v], mode, key_tile=16, bg=BG, visible=masks[v])
+        oc.check(gpu[v], ref, mode, label=f"visibility plain {mode} eye {v}")
 
 
 def test_visibility_lists_are_the_unmasked_lists_of_visible_tiles(R, vr_masked):

@@ -63,9 +63,10 @@ def test_noalloc_sort_in_place_partial_digit_and_no_allocation(lib):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     cases = []
     for call, (n, bits) in enumerate([(4097, 5), (200_003, 13), (65_536, 64)]):
-        k, v = _keys(np.random.default_rng(100 + call), n)
-        ref_k, ref_v = R.sort_pairs(k, v, bits)
-        cases.append((k.clone(), v.clone(), ref_k, ref_v, n, bits))
+        k0, v0 = _keys(np.random.default_rng(100 + call), n)
+        ref_k, ref_v = R.sort_pairs(k0, v0, bits)
+        cases.append((k0, v0, ref_k, ref_v, n, bits))
+    del k0, v0, ref_k, ref_v  # only the list holds the tensors: nothing is freed below
     status = torch.full((1,), 7, dtype=torch.int32, device="cuda")
     torch.cuda.synchronize()
     warm_k, warm_v = cases[0][0].clone(), cases[0][1].clone()

@@ -129,6 +129,12 @@ _C_SLIPS = {
     # the focus/periphery blend weight (Sec. 4.3) without the band's offset
     "fovea-weight": ("double w = (o->radius + o->band - sqrt(dx * dx + dy * dy)) / o->band;",
                      "double w = (o->radius - sqrt(dx * dx + dy * dy)) / o->band;"),
+    # the hybrid blend (Sec. 4.3) with its two weights exchanged
+    "hybrid-weights": ("v[ch] = w * (S[k].C[ch] + S[k].T * bg[ch]) + (1 - w) * lowimg[ch * W2 * H2 + g];",
+                       "v[ch] = (1 - w) * (S[k].C[ch] + S[k].T * bg[ch]) + w * lowimg[ch * W2 * H2 + g];"),
+    # the hybrid pixel's 2x2 average taken over the wrong group (the next one to the right)
+    "hybrid-group": ("int64_t g = (int64_t)(y / 2) * W2 + x / 2;\n        for (int ch = 0; ch < 3; ++ch)\n          v[ch] = w",
+                     "int64_t g = (int64_t)(y / 2) * W2 + (x / 2 + 1 < W2 ? x / 2 + 1 : x / 2);\n        for (int ch = 0; ch < 3; ++ch)\n          v[ch] = w"),
 }
 
 

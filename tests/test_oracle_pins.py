@@ -371,6 +371,56 @@ def test_foveated_focus_pixels_equal_plain_render():
     assert np.array_equal(r["image"][:, cls == 0], plain[:, cls == 0])
 
 
+def test_hybrid_blend_follows_the_focus_circle_and_its_band():
+    """Sec. 4.3: hybrid tiles blend the full-resolution render with its 2x2-group
+    average by a continuous mask that is 1 on the focus circle and falls to 0 across the
+    band.  Against the plain render of the same rays (exact order, so per-pixel results
+    do not depend on the tiling): a hybrid pixel within the circle equals the plain
+    pixel; one beyond radius + band equals the mean of its plain 2x2 group; in between
+    it lies on the segment between the two, at the parameter 1 - (d - R) / b."""
+    rng = np.random.default_rng(16)
+    sc = random_scene(600, rng, sh_degree=2)
+    H, W = 128, 192
+    c = cam(W, H, 80.0)
+    R, b = 30.0, 10.0
+    fov = synth.Fovea(80.3, 60.7, R, b)
+    plain = on.render(sc, c, "exact", key_tile=16)["image"]
+    r = on.render(sc, c, "exact", key_tile=32, fovea=fov)
+    cls = np.repeat(np.repeat(r["tile_class"], 32, 0), 32, 1)[:H, :W]
+    grp = plain.reshape(3, H // 2, 2, W // 2, 2).mean(axis=(2, 4))
+    A = np.repeat(np.repeat(grp, 2, 1), 2, 2)
+    ys, xs = np.mgrid[0:H, 0:W]
+    d = np.hypot(xs + 0.5 - np.float32(fov.gaze_x), ys + 0.5 - np.float32(fov.gaze_y))
+    hyb = cls == 1
+    inner, outer = hyb & (d <= R - 1e-6), hyb & (d >= R + b + 1e-6)
+    band = hyb & (d > R + 0.5) & (d < R + b - 0.5) & (np.abs(plain - A).max(axis=0) > 1e-3)
+    assert inner.sum() > 50 and outer.sum() > 50 and band.sum() > 50
+    assert np.abs(r["image"][:, inner] - plain[:, inner]).max() < 1e-12
+    assert np.abs(r["image"][:, outer] - A[:, outer]).max() < 1e-12
+    ch = np.abs(plain - A).argmax(axis=0)  # the channel where the two differ most
+    V, C0, A0 = (np.take_along_axis(x, ch[None], 0)[0] for x in (r["image"], plain, A))
+    t = (V[band] - A0[band]) / (C0[band] - A0[band])
+    assert np.abs(t - (1.0 - (d[band] - R) / b)).max() < 1e-9
+    # between the circle and R + b the mask is continuous: no jump at either edge
+    assert t.min() > 0.0 and t.max() < 1.0
+
+
+def test_foveated_constant_scene_stays_constant():
+    """Every composite of Sec. 4.3 (hybrid blend, bilinear periphery) is an average of
+    samples with weights that sum to one: a scene whose every sample has the same colour
+    (one Gaussian far larger than the view, alpha clamped at 0.99 everywhere) renders the
+    same constant in focus, hybrid and periphery tiles."""
+    sc = make_scene([[0.0, 0.0, 3.0]], log_scales=[[5.0, 5.0, 5.0]], logits=[10.0], dc=[[0.4, -0.3, 0.9]])
+    c = cam(160, 128, 80.0)
+    fov = synth.Fovea(70.0, 60.0, 50.0, 10.0)
+    r = on.render(sc, c, "exact", key_tile=32, fovea=fov, bg=(0.2, 0.1, 0.3))
+    assert set(np.unique(r["tile_class"])) >= {0, 1, 2}
+    ref = on.render(sc, c, "exact", key_tile=16, bg=(0.2, 0.1, 0.3))["image"]
+    v = ref[:, 0, 0]
+    assert np.abs(ref - v[:, None, None]).max() < 1e-12
+    assert np.abs(r["image"] - v[:, None, None]).max() < 1e-12
+
+
 def _partial_mask(H, W):
     """Visible everywhere except the left 40 columns and the bottom-right corner, with one
     tile kept by a single visible pixel (tile-level culling keeps it whole)."""

@@ -16,8 +16,9 @@
  *   - tile culling on the optimal plane: a Gaussian/tile pair is dropped when the largest
  *     alpha over the tile's quadrilateral is below 1/255; the maximum is the projected
  *     mean when it lies inside, else on an edge, found in closed form           (Eq. 4)
- *   - single-pass foveation: 32x32 tiles, focus tiles at full resolution, periphery tiles
- *     shaded on 2x2 pixel groups, hybrid tiles blended by the continuous mask    (Sec. 4.3)
+ *   - single-pass foveation: 32x32 tiles (16x16 as a tuning option), focus tiles at full
+ *     resolution, periphery tiles shaded on 2x2 pixel groups, hybrid tiles blended by
+ *     the continuous mask                                                        (Sec. 4.3)
  *
  * Readings where the paper is silent (each also listed in the design notes):
  *   - camera: OpenCV axes, world->camera [R|t], pixel centres at (x+0.5, y+0.5);
@@ -1344,7 +1345,9 @@ void og_free(void* p) { free(p); }
 int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out* out) {
   const int W = cam->width, H = cam->height, T = o->key_tile;
   if (W <= 0 || H <= 0 || T <= 0 || T % 4) return -1;
-  if (o->foveated && (T != 32 || W % 2 || H % 2)) return -1;
+  /* foveation classifies the key tiles (32x32 as in Sec. 4.3, or 16x16); periphery tiles
+   * hold whole 2x2 groups, and their 4x4 blocks of groups stay inside one tile */
+  if (o->foveated && ((T != 32 && T != 16) || W % 2 || H % 2)) return -1;
   if (o->brute && o->mode != 0) return -1;
   if (o->mode < 0 || o->mode > 4) return -1;
   const int ntx = (W + T - 1) / T, nty = (H + T - 1) / T, ntiles = ntx * nty;

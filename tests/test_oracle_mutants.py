@@ -129,6 +129,9 @@ _C_SLIPS = {
     # the focus/periphery blend weight (Sec. 4.3) without the band's offset
     "fovea-weight": ("double w = (o->radius + o->band - sqrt(dx * dx + dy * dy)) / o->band;",
                      "double w = (o->radius - sqrt(dx * dx + dy * dy)) / o->band;"),
+    # the per-sample window of the hierarchical resort holding one entry fewer than k
+    "window-capacity": ("if (B->L3[i].n > B->k3) blend_at(B, i, win_pop(&B->L3[i]).gid);",
+                        "if (B->L3[i].n >= B->k3) blend_at(B, i, win_pop(&B->L3[i]).gid);"),
     # the hybrid blend (Sec. 4.3) with its two weights exchanged
     "hybrid-weights": ("v[ch] = w * (S[k].C[ch] + S[k].T * bg[ch]) + (1 - w) * lowimg[ch * W2 * H2 + g];",
                        "v[ch] = (1 - w) * (S[k].C[ch] + S[k].T * bg[ch]) + w * lowimg[ch * W2 * H2 + g];"),

@@ -359,19 +359,119 @@ def test_window_cascade_with_unbounded_windows_is_exact():
     assert np.array_equal(on.render(sc, c, "hier", windows=(big, big, big), key_tile=32, fovea=fov)["image"], exf)
 
 
-def test_foveated_focus_pixels_equal_plain_render():
+def _sample_streams(sc, c, T):
+    """Per pixel: the Gaussians of its key tile's list (oracle tile lists, sorted by
+    (key, index)) that are kept at the pixel centre, with their depth t*, in list order."""
+    counts, gids, keys = on.tile_lists(sc, c, T)
+    off = np.concatenate([[0], np.cumsum(counts.ravel())])
+    ntx = counts.shape[1]
+    streams = {}
+    for y in range(c.height):
+        for x in range(c.width):
+            t = (y // T) * ntx + x // T
+            st = []
+            for g in gids[off[t]:off[t + 1]]:
+                kept, a, ts, _ = on.eval_one(sc, int(g), c, x + 0.5, y + 0.5)
+                if kept:
+                    st.append((ts, int(g), a))
+            streams[(y, x)] = st
+    return streams
+
+
+def _blend_order(seq):
+    """Gaussians blended front to back from a sequence of (t, id, alpha), with the
+    transmittance stop at 1e-4 (Eq. 2 and the stop rule)."""
+    T, out = 1.0, []
+    for _, g, a in seq:
+        if T * (1.0 - a) < 1e-4:
+            break
+        T *= 1.0 - a
+        out.append(g)
+    return out
+
+
+def _orders(r, W, H):
+    order, off = r["orders"]
+    return {(y, x): order[off[y * W + x]:off[y * W + x + 1]].tolist() for y in range(H) for x in range(W)}
+
+
+@pytest.fixture(scope="module")
+def stream_case():
+    rng = np.random.default_rng(17)
+    sc = random_scene(300, rng, sh_degree=0, ls_mu=-2.6)
+    c = cam(40, 32, 60.0)
+    return sc, c, _sample_streams(sc, c, 16)
+
+
+def test_cascade_with_zero_windows_blends_in_tile_list_order(stream_case):
+    """Reading of the hierarchical resort (Sec. 4.1): windows of size zero pass every
+    entry straight through, so each pixel blends its kept pairs in the order of its key
+    tile's sorted list (the tile keys of Eq. 4's maximum point, ties by index)."""
+    sc, c, streams = stream_case
+    r = on.render(sc, c, "hier", windows=(0, 0, 0), key_tile=16, want_orders=True)
+    got = _orders(r, c.width, c.height)
+    assert sum(len(v) for v in streams.values()) > 2000
+    for k, st in streams.items():
+        assert got[k] == _blend_order(st), k
+
+
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_per_sample_window_is_a_size_k_min_heap_over_the_kept_stream(stream_case, k):
+    """With the block windows off, the per-sample window of size k is the textbook
+    bounded priority queue: push each kept pair of the stream, pop the smallest (t*, id)
+    once more than k are held, drain in order at the end (heapq as the reference)."""
+    import heapq
+    sc, c, streams = stream_case
+    r = on.render(sc, c, "window", windows=(0, 0, k), key_tile=16, want_orders=True)
+    got = _orders(r, c.width, c.height)
+    differs = 0
+    for key, st in streams.items():
+        h, out = [], []
+        for e in st:
+            heapq.heappush(h, e)
+            if len(h) > k:
+                out.append(heapq.heappop(h))
+        while h:
+            out.append(heapq.heappop(h))
+        assert got[key] == _blend_order(out), key
+        differs += _blend_order(out) != _blend_order(sorted(st))
+    assert differs > 0  # the window does reorder against the exact order somewhere
+
+
+def test_cascade_equals_exact_order_for_separated_layers():
+    """Layers of Gaussians far apart in depth, each layer's Gaussians side by side: every
+    ray meets the layers in the same order and no layer's pairs overtake another's in any
+    window, so the hierarchical cascade blends the exact order."""
+    rng = np.random.default_rng(18)
+    means, ls = [], []
+    for z in (1.5, 2.5, 3.5, 4.5):
+        for _ in range(40):
+            means.append([rng.uniform(-0.8, 0.8) * z / 2, rng.uniform(-0.6, 0.6) * z / 2, z + rng.normal(0, 0.002)])
+            ls.append([-2.5, -2.5, -5.0])
+    sc = make_scene(means, log_scales=ls, logits=np.full(len(means), -1.0),
+                    dc=rng.uniform(-SQRT_PI, SQRT_PI, size=(len(means), 3)))
+    c = cam(64, 48, 60.0)
+    ex = on.render(sc, c, "exact", key_tile=16)
+    for win in [(4, 8, 16), (1, 1, 1)]:
+        h = on.render(sc, c, "hier", windows=win, key_tile=16)
+        assert np.abs(h["image"] - ex["image"]).max() < 1e-12, win
+
+
+@pytest.mark.parametrize("T", [32, 16])
+def test_foveated_focus_pixels_equal_plain_render(T):
     rng = np.random.default_rng(15)
     sc = random_scene(600, rng, sh_degree=2)
     c = cam(192, 128, 80.0)
     fov = synth.Fovea(80.0, 60.0, 34.0, 6.0)
     plain = on.render(sc, c, "exact", key_tile=16)["image"]
-    r = on.render(sc, c, "exact", key_tile=32, fovea=fov)
-    cls = np.repeat(np.repeat(r["tile_class"], 32, 0), 32, 1)[:128, :192]
+    r = on.render(sc, c, "exact", key_tile=T, fovea=fov)
+    cls = np.repeat(np.repeat(r["tile_class"], T, 0), T, 1)[:128, :192]
     assert (cls == 0).any() and (cls == 1).any() and (cls == 2).any()
     assert np.array_equal(r["image"][:, cls == 0], plain[:, cls == 0])
 
 
-def test_hybrid_blend_follows_the_focus_circle_and_its_band():
+@pytest.mark.parametrize("T", [32, 16])
+def test_hybrid_blend_follows_the_focus_circle_and_its_band(T):
     """Sec. 4.3: hybrid tiles blend the full-resolution render with its 2x2-group
     average by a continuous mask that is 1 on the focus circle and falls to 0 across the
     band.  Against the plain render of the same rays (exact order, so per-pixel results
@@ -385,8 +485,8 @@ def test_hybrid_blend_follows_the_focus_circle_and_its_band():
     R, b = 30.0, 10.0
     fov = synth.Fovea(80.3, 60.7, R, b)
     plain = on.render(sc, c, "exact", key_tile=16)["image"]
-    r = on.render(sc, c, "exact", key_tile=32, fovea=fov)
-    cls = np.repeat(np.repeat(r["tile_class"], 32, 0), 32, 1)[:H, :W]
+    r = on.render(sc, c, "exact", key_tile=T, fovea=fov)
+    cls = np.repeat(np.repeat(r["tile_class"], T, 0), T, 1)[:H, :W]
     grp = plain.reshape(3, H // 2, 2, W // 2, 2).mean(axis=(2, 4))
     A = np.repeat(np.repeat(grp, 2, 1), 2, 2)
     ys, xs = np.mgrid[0:H, 0:W]

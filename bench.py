@@ -38,6 +38,11 @@ WINDOWS = (4, 8, 16)
 # t*, window insert compares), a blended pair (transmittance test and colour FMAs).
 FLOPS_EVAL, FLOPS_KEPT, FLOPS_BLEND = 24, 22, 10
 FP32_LANES_PER_SM = 128
+# Issue basis of the render roofline: about 35 FP32 operations and one exp2 per evaluated
+# pair (plane map and quadratic form ~9, t* ~9, blend ~6, window compares ~log2 k per
+# level), against the lane-issue peak SMs x 4 schedulers x 32 lanes x clock.
+ALU_OPS_PER_PAIR = 36
+LANES_PER_SM = 4 * 32
 
 
 def log(*a):
@@ -189,17 +194,14 @@ def oracle_frame_estimate(scene64, frame, budget_s=20.0, bands=None):
     return 2 * sec, desc, on.num_threads()
 
 
-def oracle_other_workloads(scene64, frame, budget_s=8.0):
-    """The oracle on the other workloads, each from a bounded sample like the headline
-    estimate: the plain stereo frame (full resolution, 16x16 tiles), the 256^2 10k-Gaussian
-    single view in exact order (rendered whole), and one 1280^2 view of the 500k-Gaussian
-    fine-tuning scene (forward render only, x 4 views)."""
+def oracle_other_workloads(scene64, frame):
+    """The oracle as it stands on the other workloads, each rendered whole: the plain
+    stereo frame (full resolution, 16x16 tiles, both eyes), the 256^2 10k-Gaussian single
+    view in exact order, and the four 1280^2 views of the 500k-Gaussian fine-tuning scene
+    (forward render only)."""
     from oracle import native as on
     from paper_2505_10144_gb300 import synth
-    out = {}
-    sec, used, _ = oracle_view_estimate(scene64, frame.cameras[0], None, "hier", 16, budget_s, [256, 1024, 1792])
-    out["plain_stereo_frame_s"] = 2 * sec
-    out["plain_sample"] = f"{used} bands of 64 rows of eye 0, x 2 eyes"
+    out = {"plain_stereo_frame_s": oracle_whole_frame(scene64, frame, fovea=False)}
     sc = synth.tiny_scene(10_000, synth.rng_for(0))
     sc64 = synth.Scene(*[np.ascontiguousarray(a, dtype=np.float64) for a in sc.arrays()], sc.sh_degree)
     t = time.perf_counter()
@@ -207,10 +209,11 @@ def oracle_other_workloads(scene64, frame, budget_s=8.0):
     out["single_view_256_10k_exact_s"] = time.perf_counter() - t
     ft = synth.shell_scene(N_GAUSS, synth.rng_for(3), sh_degree=3)
     ft64 = synth.Scene(*[np.ascontiguousarray(a, dtype=np.float64) for a in ft.arrays()], ft.sh_degree)
-    cam = synth.ring_views(4, 1280, 1280, 110.0, synth.rng_for(3, salt=1))[0]
-    sec, used, _ = oracle_view_estimate(ft64, cam, None, "hier", 16, budget_s, [128, 640, 1088])
-    out["finetune_4x1280_forward_s"] = 4 * sec
-    out["finetune_sample"] = f"{used} bands of 64 rows of view 0, x 4 views (forward render only)"
+    t = time.perf_counter()
+    for cam in synth.ring_views(4, 1280, 1280, 110.0, synth.rng_for(3, salt=1)):
+        on.render(ft64, cam, "hier", WINDOWS, 16)
+    out["finetune_4x1280_forward_s"] = time.perf_counter() - t
+    out["sample"] = "each rendered whole by the FP64 oracle"
     return out
 
 
@@ -225,8 +228,19 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def oracle_whole_frame(scene64, frame, mode="hier", fovea=True):
+    """Seconds of the FP64 oracle, as it stands, for one whole stereo frame (both eyes,
+    every sample), foveated (32x32 key tiles) or plain (16x16)."""
+    from oracle import native as on
+    t = time.perf_counter()
+    for e in range(2):
+        on.render(scene64, frame.cameras[e], mode, WINDOWS, 32 if fovea else 16, frame.foveas[e] if fovea else None)
+    return time.perf_counter() - t
+
+
 def run_reference(args, ws, rank):
-    """The reference arm: the oracle as it stands, on the host cores, same metric."""
+    """The reference arm: the oracle as it stands, on the host cores, same metric: every
+    step renders one whole stereo frame of the trajectory (both eyes, every sample)."""
     if rank != 0:
         return
     from paper_2505_10144_gb300 import synth
@@ -235,40 +249,23 @@ def run_reference(args, ws, rank):
     from oracle import native as on
     on.build()
     thr = on.num_threads()
-
-    def band(fr, y0, h):
-        cam, fv = fr.cameras[0], fr.foveas[0]
-        y0 = min(max(int(y0), 0), H_IMG - h) // 32 * 32
-        c = crop_camera(cam, 0, y0, W_IMG, h)
-        f = synth.Fovea(fv.gaze_x, fv.gaze_y - y0, fv.radius_px, fv.band_px)
-        t = time.perf_counter()
-        on.render(scene64, c, "hier", WINDOWS, 32, f)
-        return time.perf_counter() - t
-
-    # per-view fixed cost (projection of every Gaussian) from two band heights, once
-    fr0 = wl.frames[0]
-    t32, t64 = band(fr0, fr0.foveas[0].gaze_y - 32, 32), band(fr0, fr0.foveas[0].gaze_y - 32, 64)
-    t_fixed = max(t32 - (t64 - t32), 0.0)
     vals = []
     for i in range(args.warmup + args.steps):
-        # one step: a full-width 32-row band of eye 0 of this frame, its rows placed by a
-        # low-discrepancy sequence over the image height (the steps sample focus and
-        # periphery rows alike), scaled to the frame: 2 eyes x (fixed + per-row cost x rows)
-        fr = wl.frames[i % len(wl.frames)]
-        dt = band(fr, ((i + 0.5) * 0.6180339887498949 % 1.0) * (H_IMG - 32), 32)
-        sec = 2.0 * (t_fixed + max(dt - t_fixed, 0.0) / 32 * H_IMG)
+        sec = oracle_whole_frame(scene64, wl.frames[i % len(wl.frames)])
         if i >= args.warmup:
             vals.append(sec)
-    desc = ("FP64 oracle, hierarchical 4/8/16, foveated: per step a full-width 32-row band of eye 0 at a "
-            "low-discrepancy row position, per-row cost scaled to 2208 rows plus the per-view fixed cost, x 2 eyes")
     mean = statistics.mean(vals)
     value = 1.0 / mean
+    desc = ("FP64 oracle, hierarchical 4/8/16, foveated: one whole stereo frame of the trajectory per step "
+            "(both eyes, every sample)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "p99_ms": float(np.percentile(vals, 99)) * 1e3,
             "config": {"workload": "vr_stereo_2064x2208_500k_foveated_hier_4_8_16", "n_gaussians": N_GAUSS,
                        "width": W_IMG, "height": H_IMG, "views": 2},
-            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": thr, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": thr, "kind": "oracle", "sample": desc,
+                             "host_cpus": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -333,7 +330,15 @@ def run_batched(args, api, torch, ws, rank, pg=None):
     cache = args.tune_cache or os.path.join(ROOT, "_build", "autotune.json")
     best, cands = autotune.autotune(R, scenes, vs, cams, fovs, base, cache_path=cache, reps=2)
     R.set_tuning(best["max_ctas_per_sm"])
-    cfg = api.RenderConfig(sort_mode="hier", windows=tuple(best["windows"]), key_tile=32, fovea_mode="bilinear")
+    cfg = api.RenderConfig(sort_mode="hier", windows=tuple(best["windows"]), key_tile=best["key_tile"],
+                           fovea_mode="bilinear")
+    log("autotune candidates (key tile, windows, CTA cap: ms per replay, PSNR vs exact, % pixels > 2e-4):")
+    for c in cands:
+        log(f"  {c['key_tile']:2d}x{c['key_tile']:<2d} {tuple(c['windows'])} cap {c['max_ctas_per_sm']}: "
+            f"{c['ms']:8.2f} ms  {c['psnr_db']:6.2f} dB  {c['over_2e-4_pct']:6.2f} %"
+            f"{'' if c['meets_floor'] else '  (below the floor)'}")
+    log(f"chosen: {best['key_tile']}x{best['key_tile']} {tuple(best['windows'])} cap {best['max_ctas_per_sm']} "
+        f"(floor {best['psnr_floor_db']:.2f} dB)")
     gr = api.GraphedRender(R, scenes, vs, cams, fovs, cfg)
     steps = max(args.steps // 10, 3)
     frames = [views(1 + i) for i in range(steps + args.warmup)]
@@ -359,7 +364,10 @@ def run_batched(args, api, torch, ws, rank, pg=None):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "batched_3_scenes_200k_1M_3M_48_views_foveated", "views": 48,
                        "gaussians": sizes, "graph": "one vrs_render captured in a CUDA graph, poses via vrs_update_views"},
-            "autotune": {"best": {k: best[k] for k in ("windows", "max_ctas_per_sm", "ms")}, "candidates": cands},
+            "autotune": {"best": {k: best[k] for k in ("key_tile", "windows", "max_ctas_per_sm", "ms", "psnr_db",
+                                                       "over_2e-4_pct")},
+                         "psnr_floor_db": best["psnr_floor_db"], "reference": best["reference"],
+                         "candidates": cands},
             "instances_per_batch": st["instances"], "work_items": st["work_items"],
             "gpu_launches": st["kernels"] * len(ms)}
     if rank == 0:
@@ -496,6 +504,169 @@ def run_net(args, api, torch, ws, rank, pg=None):
     R.close()
 
 
+# FLOPs of the periphery network per reconstructed pixel: 3x3 convolutions 3 -> 32 -> 32 -> 3
+# (3*32*9 + 32*32*9 + 32*3*9 = 10,944 multiply-adds)
+NET_FLOP_PER_PX = 2 * (3 * 32 * 9 + 32 * 32 * 9 + 32 * 3 * 9)
+WEIGHTS = os.path.join(ROOT, "paper_2505_10144_gb300", "weights", "periphery_1m.npy")
+
+
+def learned_periphery(api, torch, n_steps, warmup):
+    """The learned-periphery frame: 1M Gaussians (room shell, SH degree 3), stereo
+    2064x2208, periphery at 1/4 of the pixels reconstructed by the BF16 network (weights
+    trained by the library's kernels: paper_2505_10144_gb300/train_periphery.py).
+    Frames/s and p99 of foveated render + network against the plain full-resolution
+    render of the same scene, and PSNR / maximum error of the network and of its bilinear
+    fallback against the plain render on 200 held-out trajectory frames."""
+    from paper_2505_10144_gb300 import periphery, synth
+    if not os.path.exists(WEIGHTS):
+        return {"unavailable": "no trained weights at paper_2505_10144_gb300/weights/periphery_1m.npy"}
+    R = api.Renderer()
+    scene = api.DeviceScene.from_host(synth.shell_scene(1_000_000, synth.rng_for(4), sh_degree=3))
+    net = periphery.PeripheryNet(R, seed=4)
+    net.params.copy_(torch.from_numpy(np.load(WEIGHTS)).cuda())
+    frames = synth.vr_trajectory(200, synth.rng_for(4, salt=200)).frames
+    net_cfg = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=32, fovea_mode="net")
+    plain_cfg = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=16, fovea_mode="plain")
+    out = torch.empty((2, 3, H_IMG, W_IMG), device="cuda")
+    low = torch.empty((2, 3, H_IMG // 2, W_IMG // 2), device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+
+    def timed(fn, n):
+        for i in range(warmup):
+            fn(i)
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+        for i in range(n):
+            flush.zero_()
+            fn(warmup + i, ev[i])
+        torch.cuda.synchronize()
+        return [a.elapsed_time(c) for a, _, c in ev], [b.elapsed_time(c) for _, b, c in ev]
+
+    def fnet(i, ev=None):
+        fr = frames[i % len(frames)]
+        if ev:
+            ev[0].record()
+        R.render([scene], [0, 0], fr.cameras, fr.foveas, net_cfg, out=out, low=low)
+        if ev:
+            ev[1].record()
+        net.apply_periphery(low, out)
+        if ev:
+            ev[2].record()
+
+    def fplain(i, ev=None):
+        fr = frames[i % len(frames)]
+        if ev:
+            ev[0].record()
+            ev[1].record()
+        R.render([scene], [0, 0], fr.cameras, None, plain_cfg, out=out)
+        if ev:
+            ev[2].record()
+
+    ms_net, ms_netk = timed(fnet, n_steps)
+    ms_plain, _ = timed(fplain, n_steps)
+    R.check()
+    ev = periphery.evaluate_frames(R, net, scene, frames)
+    # the same in the exact per-ray order (reconstruction error only) on every 25th frame
+    ev_exact = periphery.evaluate_frames(R, net, scene, frames[::25], sort_mode="exact")
+    R.check()
+    px = statistics.mean(periphery_pixels(frames[(warmup + i) % len(frames)]) for i in range(n_steps))
+    k_ms = statistics.mean(ms_netk)
+    tfl = NET_FLOP_PER_PX * px / (k_ms / 1e3) / 1e12
+    rp = roofline_peaks()
+    meta = {}
+    try:
+        with open(WEIGHTS[:-4] + ".json") as fh:
+            meta = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    R.close()
+    return {"value": len(ms_net) / (sum(ms_net) / 1e3), "unit": "frames/s", "ms_per_step": statistics.mean(ms_net),
+            "p50_ms": float(np.percentile(ms_net, 50)), "p99_ms": float(np.percentile(ms_net, 99)),
+            "plain": {"value": len(ms_plain) / (sum(ms_plain) / 1e3), "ms_per_step": statistics.mean(ms_plain),
+                      "p99_ms": float(np.percentile(ms_plain, 99)),
+                      "config": "1M Gaussians, full resolution, 16x16 tiles, hierarchical 4/8/16"},
+            "speedup_vs_plain": statistics.mean(ms_plain) / statistics.mean(ms_net),
+            "quality_vs_plain_exact_order": {**ev_exact, "frames": len(frames[::25]),
+                                             "gain_db": ev_exact["net_periph_psnr_db"] - ev_exact["bil_periph_psnr_db"],
+                                             "note": "foveated and plain renders in the exact per-ray order: the "
+                                                     "periphery error is what reconstruction from half resolution "
+                                                     "loses; periphery pixels (32x32 tiles outside radius + band) and "
+                                                     "whole frames; net = BF16 network, bil = its bilinear fallback"},
+            "quality_vs_plain_hier": {**ev, "frames": len(frames),
+                                      "gain_db": ev["net_periph_psnr_db"] - ev["bil_periph_psnr_db"],
+                                      "note": "as timed: hierarchical 4/8/16 windows on 32x32 tiles (foveated) "
+                                              "against 16x16 tiles (plain), whose window approximations differ"},
+            "net_kernel_roofline": {"bound": "tensor", "kernel": "net_periphery_kernel (tcgen05.mma BF16 -> FP32)",
+                                    "achieved": tfl, "peak": rp["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                                    "frac": tfl / rp["bf16_tflops_sustained"], "avg_launch_ms": k_ms,
+                                    "algorithmic_flops": NET_FLOP_PER_PX * px,
+                                    "basis": f"{NET_FLOP_PER_PX} FLOP per reconstructed periphery pixel x {px:.0f} "
+                                             "pixels (halo recompute not counted); peak: sustained BF16 "
+                                             + rp["source"]},
+            "weights": "paper_2505_10144_gb300/weights/periphery_1m.npy", "training": meta,
+            "config": {"workload": "learned_periphery_1M_stereo_2064x2208", "timing": "CUDA events per frame, "
+                       "eager render + network launch, L2 flushed between frames"}}
+
+
+REUSE_FAR_M = 92.0  # 0.25 px of eye-to-cyclopean disparity at f = 722.6 and IPD 64 mm
+
+
+def stereo_reuse(api, torch, n_steps, warmup):
+    """Stereo reuse of distant content (Sec. 7's future work): an open room (500k
+    Gaussians, no ceiling, no front wall) with a landscape of 200k Gaussians at 150-600 m,
+    plain stereo 2064x2208, hierarchical 4/8/16.  The fused stereo render (both eyes,
+    every Gaussian) against vrs_render_stereo_reuse (near layer per eye, far layer once from
+    the cyclopean eye), and the reuse image's PSNR against the fused one."""
+    from paper_2505_10144_gb300 import synth
+    scene = synth.open_room_with_landscape(500_000, 200_000, synth.rng_for(5), sh_degree=3)
+    ds = api.DeviceScene.from_host(scene)
+    wl = synth.vr_trajectory(warmup + n_steps, synth.rng_for(5, salt=3), W_IMG, H_IMG)
+    cfg = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=16)
+    R = api.Renderer()
+    out = torch.empty((2, 3, H_IMG, W_IMG), device="cuda")
+    out2 = torch.empty_like(out)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+
+    def timed(fn):
+        for i in range(warmup):
+            fn(i, out)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        for i in range(n_steps):
+            flush.zero_()
+            ev[i][0].record()
+            fn(warmup + i, out)
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    def fused(i, o):
+        fr = wl.frames[i]
+        R.render([ds], [0, 0], fr.cameras, None, cfg, out=o)
+
+    def reuse(i, o):
+        R.render_stereo_reuse(ds, wl.frames[i].cameras, REUSE_FAR_M, cfg, out=o)
+
+    ms_fused, ms_reuse = timed(fused), timed(reuse)
+    ps = []
+    for i in range(0, n_steps, max(1, n_steps // 8)):
+        fused(i, out2)
+        reuse(i, out)
+        ps.append(psnr(out, out2))
+    R.check()
+    n_far = 200_000
+    R.close()
+    return {"value": len(ms_reuse) / (sum(ms_reuse) / 1e3), "unit": "frames/s",
+            "ms_per_step": statistics.mean(ms_reuse), "p99_ms": float(np.percentile(ms_reuse, 99)),
+            "fused_stereo": {"value": len(ms_fused) / (sum(ms_fused) / 1e3), "ms_per_step": statistics.mean(ms_fused),
+                             "p99_ms": float(np.percentile(ms_fused, 99))},
+            "speedup": statistics.mean(ms_fused) / statistics.mean(ms_reuse),
+            "psnr_vs_fused_db": statistics.mean(ps), "far_distance_m": REUSE_FAR_M,
+            "config": {"workload": "open room 500k + landscape 200k at 150-600 m, plain stereo 2064x2208, "
+                                   "hierarchical 4/8/16, 16x16 key tiles", "far_gaussians": n_far,
+                       "timing": "CUDA events per eager stereo frame, L2 flushed between frames"}}
+
+
 def approximation_error(R, api, ds, frame, cfg_hier, torch):
     """Error of the hierarchical per-ray windows against the exact per-ray order on one
     foveated stereo frame (both on the GPU; the exact order is the parity-checked mode)."""
@@ -533,11 +704,12 @@ def profiled_traffic():
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
         if kv.get("source_sha256") != render_source_hash():
-            return None, "render source changed since the ncu capture", None
+            return None, "render source changed since the ncu capture", None, None
         issue = float(kv["issue_slots_busy_pct"]) / 100.0 if "issue_slots_busy_pct" in kv else None
-        return float(kv["dram_bytes_per_launch"]), kv.get("capture", ""), issue
+        ipp = float(kv["thread_inst_per_evaluated_pair"]) if "thread_inst_per_evaluated_pair" in kv else None
+        return float(kv["dram_bytes_per_launch"]), kv.get("capture", ""), issue, ipp
     except (OSError, KeyError, ValueError):
-        return None, "no ncu traffic summary", None
+        return None, "no ncu traffic summary", None, None
 
 
 def order_flips(ids_a, len_a, ids_b, len_b, torch, batch=256):
@@ -623,9 +795,129 @@ def popping(api, ds, wl, cfg, torch, n_steps=12, grid=16, max_len=512):
     return out
 
 
+def grid_flicker(api, ds, wl, torch, n_steps=12):
+    """Popping of the image on unchanged world rays, for every order including the
+    hierarchical windows.  A head rotation moves the content across the image, so the
+    tile and block grid of the next frame sits elsewhere on the same rays.  Each step
+    renders eye 0 of a trajectory frame (camera A) and the same camera with its principal
+    point moved by the image motion of that frame step rounded to whole pixels (camera
+    B: its pixel (x, y) looks along A's ray through (x + dx, y + dy)), and compares the
+    two images on their common rays.  The per-ray orders (exact, view-space z, distance)
+    depend on the ray alone and cannot change (up to FP32 noise of the shifted principal
+    point); the hierarchical windows see other tile lists and blocks, so their result on
+    a ray may change: that is the method's residual flicker (Sec. 7)."""
+    from paper_2505_10144_gb300 import synth
+    R = api.Renderer()
+    steps = []
+    for f in range(n_steps):
+        ca, nxt = wl.frames[f].cameras[0], wl.frames[f + 1].cameras[0]
+        Ra = ca.world_to_cam[:, :3].astype(np.float64)
+        Rb = nxt.world_to_cam[:, :3].astype(np.float64)
+        db = Rb @ (Ra.T @ np.array([0.0, 0.0, 1.0]))
+        dx = int(round(ca.fx * db[0] / db[2])) or 1
+        dy = int(round(ca.fy * db[1] / db[2]))
+        steps.append((ca, wl.frames[f].foveas[0], dx, dy))
+    out = {}
+    for mode, fov in (("hier", False), ("hier", True), ("exact", False), ("global_z", False), ("global_dist", False)):
+        cfg = api.RenderConfig(sort_mode=mode, windows=WINDOWS, key_tile=32 if fov else 16,
+                               fovea_mode="bilinear" if fov else "plain")
+        changed = tot = 0
+        sad = 0.0
+        sq = 0.0
+        for ca, fv, dx, dy in steps:
+            W, H = ca.width, ca.height
+            cb = crop_camera(ca, dx, dy, W, H)
+            fb = synth.Fovea(fv.gaze_x - dx, fv.gaze_y - dy, fv.radius_px, fv.band_px)
+            a = R.render([ds], [0], [ca], [fv] if fov else None, cfg).clone()[0]
+            b = R.render([ds], [0], [cb], [fb] if fov else None, cfg)[0]
+            xa0, xa1 = max(dx, 0), W + min(dx, 0)
+            ya0, ya1 = max(dy, 0), H + min(dy, 0)
+            d = (a[:, ya0:ya1, xa0:xa1] - b[:, ya0 - dy:ya1 - dy, xa0 - dx:xa1 - dx]).abs()
+            changed += int((d.amax(dim=0) > 2e-4).sum())
+            tot += d.shape[1] * d.shape[2]
+            sad += float(d.sum())
+            sq += float((d ** 2).sum())
+        R.check()
+        mse = sq / (3 * tot)
+        out[mode + ("_foveated" if fov else "")] = {
+            "pixels_changed_over_2e-4_pct": 100.0 * changed / tot, "mean_abs": sad / (3 * tot),
+            "psnr_db": float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)}
+    R.close()
+    out["config"] = (f"{n_steps} trajectory steps of eye 0; principal point moved by the step's image motion "
+                     f"(mean |d| {np.mean([math.hypot(s[2], s[3]) for s in steps]):.1f} px); common rays compared; "
+                     "plain 16x16 tiles, and foveated 32x32 with the gaze on the same ray")
+    return out
+
+
 def psnr(a, b):
     mse = float(((a - b) ** 2).mean())
     return float("inf") if mse == 0 else 10 * math.log10(1.0 / mse)
+
+
+def roofline_peaks():
+    """Denominators: the measured HBM copy bandwidth and BF16 GEMM throughputs of
+    the GB300s (MEASURED_PEAKS.json at the repository root), else the profiling
+    recipe's fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return {"hbm_gbs": float(m["hbm_gbs"]), "bf16_tflops": float(m["bf16_tflops"]),
+                "bf16_tflops_sustained": float(m.get("bf16_tflops_sustained", m["bf16_tflops"])),
+                "source": "of measured (MEASURED_PEAKS.json: STREAM-style copy, cuBLAS bf16 GEMM)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "source": "of fallback (profiling recipe: 6.8 TB/s, 1.9 PFLOP/s bf16 burst, 1.7 sustained)"}
+
+
+def periphery_pixels(frame, W=W_IMG, H=H_IMG) -> int:
+    """Full-resolution pixels of the periphery 32x32 tiles of a stereo frame (the tiles
+    whose pixel centres are all at distance >= radius + band from the gaze, Sec. 4.3):
+    the pixels the composite upsamples and the network reconstructs."""
+    n = 0
+    for fv in frame.foveas:
+        ty, tx = np.mgrid[0:(H + 31) // 32, 0:(W + 31) // 32]
+        x0, y0 = tx * 32 + 0.5, ty * 32 + 0.5
+        x1, y1 = np.minimum((tx + 1) * 32, W) - 0.5, np.minimum((ty + 1) * 32, H) - 0.5
+        nx = np.clip(np.float32(fv.gaze_x), x0, x1) - np.float32(fv.gaze_x)
+        ny = np.clip(np.float32(fv.gaze_y), y0, y1) - np.float32(fv.gaze_y)
+        per = np.sqrt(nx * nx + ny * ny) >= np.float32(fv.radius_px) + np.float32(fv.band_px)
+        n += int(((np.minimum((tx + 1) * 32, W) - tx * 32) * (np.minimum((ty + 1) * 32, H) - ty * 32))[per].sum())
+    return n
+
+
+# algorithmic bytes per unit of the HBM-bound stages (one stereo frame, V views, N
+# Gaussians, K instances): the preprocess reads each Gaussian's 236 parameter bytes
+# (SH degree 3) once for both eyes and writes a 96-byte record and a 4-byte tile count
+# per (view, Gaussian); the scan reads the counts and writes the offsets (8 bytes per
+# (view, Gaussian)); duplication writes a 12-byte (key, value) instance; the onesweep
+# sort reads 8 bytes of histogram input and moves 24 bytes (key and value in and out)
+# per pass per instance; the tile ranges read each 8-byte key; the composite reads a
+# 12-byte half-resolution sample and writes a 12-byte pixel per periphery pixel.
+PARAM_BYTES, RECORD_BYTES, COUNT_BYTES = 236, 96, 4
+INSTANCE_BYTES, SORT_PASS_BYTES, SORT_HIST_BYTES = 12, 24, 8
+
+
+def stage_rooflines(stages_ms, cnt, n_views, n_gauss, passes, periph_px, hbm_gbs, src):
+    """Achieved algorithmic GB/s of every HBM-bound stage of the frame against the HBM peak."""
+    K = cnt["instances"]
+    work = {
+        "preprocess": PARAM_BYTES * n_gauss + n_views * n_gauss * (RECORD_BYTES + COUNT_BYTES),
+        "scan": n_views * n_gauss * 2 * COUNT_BYTES,
+        "duplicate": INSTANCE_BYTES * K,
+        "sort": (SORT_HIST_BYTES + passes * SORT_PASS_BYTES) * K,
+        "ranges_workitems": 8 * K,
+        "composite": 24 * periph_px,
+    }
+    out = {}
+    for k, b in work.items():
+        ms = stages_ms.get(k, 0.0)
+        gbs = b / (ms / 1e3) / 1e9 if ms > 0 else None
+        out[k] = {"bound": "hbm", "ms": ms, "algorithmic_bytes": b, "achieved": gbs, "peak": hbm_gbs,
+                  "unit": "GB/s", "frac": gbs / hbm_gbs if gbs else None}
+    out["note"] = (f"algorithmic bytes per stereo frame ({n_views} views, {n_gauss} Gaussians, {K:.0f} instances, "
+                   f"{passes} sort passes, {periph_px} periphery pixels), stage times from CUDA events around each "
+                   f"stage of eager frames; peak {src}")
+    return out
 
 
 def main():
@@ -849,6 +1141,7 @@ def main():
         del Gq
         Rq.close()
     global_orders["popping"] = popping(api, ds, wl, fov_cfg, torch)
+    global_orders["popping"]["image_flicker_on_unchanged_rays"] = grid_flicker(api, ds, wl, torch)
     global_orders["hier_4_8_16_psnr_vs_exact_db"] = psnr(R.render([ds], [0, 0], fr1.cameras, fr1.foveas, fov_cfg),
                                                           ex_img)
     two_pass = {"value": len(ms_tp) / (sum(ms_tp) / 1e3), "unit": "frames/s", "ms_per_step": statistics.mean(ms_tp),
@@ -884,22 +1177,39 @@ def main():
     peak_tflops = peaks["fp32_tflops"]
     achieved = flops / (render_ms / 1e3) / 1e12 if render_ms > 0 else 0.0
     exp2_rate = cnt["kept"] / (render_ms / 1e3) / 1e9 if render_ms > 0 else 0.0
-    traffic, traffic_note, issue_busy = profiled_traffic()
-    roofline = {"bound": "alu", "kernel": "warp_render_kernel<4,8> (hierarchical 4/8/16)", "achieved": achieved,
-                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops if peak_tflops else None,
+    traffic, traffic_note, issue_busy, inst_pair = profiled_traffic()
+    max_mhz = float(clocks.get("sm_max_mhz") or 2070.0)
+    lane_peak = props.multi_processor_count * LANES_PER_SM * max_mhz * 1e6 / 1e12  # T lane-ops/s
+    alu_ops = ALU_OPS_PER_PAIR * cnt["evaluated"]
+    alu_achieved = alu_ops / (render_ms / 1e3) / 1e12 if render_ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": "warp_render_kernel<4,8> (hierarchical 4/8/16)",
+                "achieved": alu_achieved, "peak": lane_peak, "unit": "T lane-ops/s",
+                "frac": alu_achieved / lane_peak if lane_peak else None,
                 "traffic": traffic, "traffic_note": traffic_note,
+                "basis": f"{ALU_OPS_PER_PAIR} FP32 operations per evaluated pair (plane map and quadratic form, "
+                         "exp2, t*, blend, window compares) x the evaluated pairs counted on the device, over the "
+                         "launch's average CUDA-event time",
+                "peak_source": f"derived: {props.multi_processor_count} SMs x 4 schedulers x 32 lanes x "
+                               f"{max_mhz:.0f} MHz (maximum SM clock)",
                 "issue_slots_busy_ncu": issue_busy,
-                "note": "the kernel is bound by instruction issue (window bookkeeping: shuffles, shared memory, "
-                        "compares), so its FP32-FLOP fraction is low while its issue slots are mostly busy",
-                "peak_source": "of measured: FFMA microbenchmark (vrs_measure_peaks, 64 warps per SM, best of 5); "
-                               f"derived {props.multi_processor_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                               f"{sm_mhz:.0f} MHz = {derived_tflops:.1f} TFLOP/s",
+                "thread_inst_per_evaluated_pair_ncu": inst_pair,
+                "issue_basis_note": "ncu's thread instructions per evaluated pair against the algorithmic "
+                                    f"{ALU_OPS_PER_PAIR}: the rest is window bookkeeping, staging and control",
+                "fp32": {"achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tflops if peak_tflops else None, "flops_per_launch": flops,
+                         "peak_source": "of measured: FFMA microbenchmark (vrs_measure_peaks, 64 warps per SM, "
+                                        f"best of 5); derived {props.multi_processor_count} SMs x "
+                                        f"{FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz = {derived_tflops:.1f}"},
                 "exp2": {"achieved_gops": exp2_rate, "peak_gops": peaks["exp2_gops"],
                          "frac": exp2_rate / peaks["exp2_gops"] if peaks["exp2_gops"] else None,
                          "per_launch": cnt["kept"], "note": "one exp2f per kept pair (the pair opacity)"},
                 "work_per_launch": {"evaluated_pairs": cnt["evaluated"], "kept_pairs": cnt["kept"],
-                                    "blended_pairs": cnt["blended"], "flops": flops},
+                                    "blended_pairs": cnt["blended"], "alu_ops": alu_ops},
                 "avg_launch_ms": render_ms}
+    rp = roofline_peaks()
+    stage_roof = stage_rooflines({k: v / max(ncalls, 1) for k, v in stages.items()}, cnt, 2, N_GAUSS,
+                                 Rg.stats()["sort_passes"], periphery_pixels(wl.frames[args.warmup]), rp["hbm_gbs"],
+                                 rp["source"])
     # end to end through the public API: camera/gaze in (pinned staging -> device inside
     # the replay), both images back to pinned host memory every frame.  Serialized: the
     # read-back follows the replay on one stream.  Pipelined, as a frame loop runs it: two
@@ -955,6 +1265,8 @@ def main():
     Rg2.check()
     del G2
     Rg2.close()
+    learned = learned_periphery(api, torch, min(40, args.steps), args.warmup)
+    reuse = stereo_reuse(api, torch, min(30, args.steps), args.warmup)
     import ctypes
     from paper_2505_10144_gb300 import _lib
     h2d = 2 * (ctypes.sizeof(_lib.Camera) + ctypes.sizeof(_lib.Fovea))
@@ -988,6 +1300,9 @@ def main():
         "stage_ms_per_frame": {k: v / max(ncalls, 1) for k, v in stages.items()},
         "counters_per_frame": cnt,
         "roofline": roofline,
+        "stage_rooflines": stage_roof,
+        "learned_periphery": learned,
+        "stereo_reuse": reuse,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "GraphedRender.replay (vrs_update_views + graph replay), then both eyes to pinned host "
                         "memory every frame on a copy stream; two graphed contexts take alternate frames, so a "
@@ -1001,11 +1316,17 @@ def main():
         "wall_s_timed_region": t_wall,
     }
     if rank == 0 and not args.no_cpu_baseline:
+        from oracle import native as on
         from paper_2505_10144_gb300 import synth
         scene64 = synth.Scene(*[np.ascontiguousarray(a, dtype=np.float64) for a in scene.arrays()], scene.sh_degree)
-        sec, desc, thr = oracle_frame_estimate(scene64, wl.frames[0])
-        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "frames/s", "cores": thr, "kind": "oracle",
-                                "sample": desc, "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
+        whole = [oracle_whole_frame(scene64, wl.frames[i]) for i in range(3)]
+        sec_band, desc_band, _ = oracle_frame_estimate(scene64, wl.frames[0], budget_s=8.0)
+        line["cpu_baseline"] = {"value": 3.0 / sum(whole), "unit": "frames/s", "cores": on.num_threads(),
+                                "kind": "oracle", "host_cpus": os.cpu_count(), "cpu_model": cpu_model(),
+                                "sample": "FP64 oracle as it stands, hierarchical 4/8/16, foveated: 3 whole stereo "
+                                          "frames of the trajectory (both eyes, every sample)",
+                                "seconds_per_frame": whole,
+                                "band_estimate": {"value": 1.0 / sec_band, "sample": desc_band},
                                 "other_workloads": oracle_other_workloads(scene64, wl.frames[0])}
     if rank == 0:
         print(json.dumps(line), flush=True)

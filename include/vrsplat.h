@@ -163,6 +163,26 @@ vrs_status vrs_render_two_pass(vrs_ctx* ctx, const vrs_gaussians* scenes, int n_
                                const vrs_camera* h_cams, const vrs_fovea* h_fovea, int n_views,
                                const vrs_render_opts* opts, float* d_out_rgb, void* stream);
 
+/* Stereo reuse of distant content (named as future work in Sec. 7: monocular rendering
+ * and stereoscopic reuse of distant content), on a plain (unfoveated) stereo pair.
+ * The Gaussians whose world-space mean lies at distance >= far_distance from the
+ * cyclopean eye (the midpoint of the two eye centres) form the far layer, rendered once,
+ * from the cyclopean camera (the eyes' rotation and intrinsics, centre at the midpoint);
+ * each eye renders the others, its near layer.  Each eye's pixel is C_near + T_near
+ * (C_far + T_far bg): the far layer seen through the near layer's transmittance (Eq. 2).
+ * For a far Gaussian at distance d the eye and cyclopean rays through a pixel differ by
+ * f (IPD / 2) / d pixels (0.25 px at d = 92 m, f = 722.6, IPD = 64 mm).
+ *   scene: one scene.  h_cams: the two eyes, sharing image size, intrinsics and rotation.
+ *   opts: a per-ray order (sort mode 0, 1 or 2), windows and bg as for vrs_render.
+ *   d_out_rgb: device float [2][3][height][width].
+ * One call runs the pipeline once over three views (the two near layers and the far
+ * layer), keeps each pixel's colour and transmittance, and composites them.  The context
+ * keeps no state for vrs_render_backward afterwards.  VRS_ERR_INVALID for eyes that do not
+ * share rotation or intrinsics, a non-positive or non-finite far_distance, or a global
+ * sort mode. */
+vrs_status vrs_render_stereo_reuse(vrs_ctx* ctx, const vrs_gaussians* scene, const vrs_camera* h_cams,
+                                   const vrs_render_opts* opts, float far_distance, float* d_out_rgb, void* stream);
+
 /* Backward of the last vrs_render called with save_for_backward = 1, with identical
  * scenes, cameras, foveas and options: accumulates d<d_dL_drgb, rgb>/d(params) into
  * grads[n_scenes] (device, caller-owned, same layouts).  d_dL_drgb: device float

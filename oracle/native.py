@@ -52,7 +52,8 @@ class _Opts(C.Structure):
                 ("brute", C.c_int), ("gaze_x", C.c_double), ("gaze_y", C.c_double),
                 ("radius", C.c_double), ("band", C.c_double), ("bg", C.c_double * 3),
                 ("margin_alpha", C.c_double), ("margin_stop", C.c_double), ("margin_tie", C.c_double),
-                ("visible", C.c_void_p), ("outcomes", C.c_int)]
+                ("visible", C.c_void_p), ("outcomes", C.c_int), ("dist_cull", C.c_int),
+                ("dist_ref", C.c_double * 3), ("dist_min", C.c_double), ("dist_max", C.c_double)]
 
 
 class _Out(C.Structure):
@@ -60,7 +61,8 @@ class _Out(C.Structure):
                 ("lowimg", C.c_void_p), ("marginal", C.c_void_p), ("tile_class", C.c_void_p),
                 ("order", C.c_void_p), ("order_off", C.c_void_p), ("max_order", C.c_int64),
                 ("n_order", C.c_int64), ("stats", C.c_int64 * 8), ("unchecked", C.c_void_p),
-                ("alt_off", C.POINTER(C.c_int64)), ("alt", C.POINTER(C.c_double)), ("n_alt", C.c_int64)]
+                ("alt_off", C.POINTER(C.c_int64)), ("alt", C.POINTER(C.c_double)), ("alt4", C.POINTER(C.c_double)),
+                ("n_alt", C.c_int64)]
 
 
 def lib():
@@ -183,7 +185,7 @@ MARGINS = (5e-5, 1e-5, 3e-7)
 def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 16, fovea=None,
            bg=(0.0, 0.0, 0.0), tile_cull: bool = True, brute: bool = False,
            want_orders: bool = False, want_samples: bool = False, margins=MARGINS,
-           visible=None, outcomes: bool = False) -> dict:
+           visible=None, outcomes: bool = False, distance=None) -> dict:
     """Render one view.  fovea: None for the plain method, else an object with gaze_x,
     gaze_y, radius_px, band_px (single-pass foveation, 32x32 key tiles).  visible: None,
     or an [H, W] array, nonzero where the pixel is visible (visibility culling).
@@ -192,7 +194,10 @@ def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 
     its samples within the margins allow (keep against 1/255, stop against 1e-4, order
     of near-tied depths or keys, hierarchical window and stream ties): the result gets
     "alt" = (offsets [H*W + 1], values [n, 3]) of the values other than "image" and
-    "unchecked" [H, W], true where there are too many to enumerate."""
+    "unchecked" [H, W], true where there are too many to enumerate (and, for plain renders,
+    "alt4": the (C rgb, T) of each alternative).  distance: None, or (ref_xyz, d_min,
+    d_max): render only the Gaussians whose world-space mean is at distance d_min <= d <
+    d_max from the point ref_xyz."""
     W, H = int(cam.width), int(cam.height)
     o = _Opts()
     vis = None
@@ -214,6 +219,12 @@ def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 
         o.bg[k] = float(np.float32(bg[k]))
     o.margin_alpha, o.margin_stop, o.margin_tie = (float(m) for m in margins)
     o.outcomes = int(outcomes)
+    if distance is not None:
+        ref, dmin, dmax = distance
+        o.dist_cull = 1
+        for k in range(3):
+            o.dist_ref[k] = float(ref[k])
+        o.dist_min, o.dist_max = float(dmin), float(dmax)
     T = int(key_tile)
     ntx, nty = (W + T - 1) // T, (H + T - 1) // T
     W2, H2 = W // 2, H // 2
@@ -240,6 +251,11 @@ def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 
         n_alt = int(out.n_alt)
         aoff = np.ctypeslib.as_array(out.alt_off, shape=(W * H + 1,)).copy()
         vals = np.ctypeslib.as_array(out.alt, shape=(n_alt * 3,)).reshape(n_alt, 3).copy() if n_alt else np.zeros((0, 3))
+        alt4 = None
+        if fovea is None:
+            alt4 = np.ctypeslib.as_array(out.alt4, shape=(n_alt * 4,)).reshape(n_alt, 4).copy() if n_alt \
+                else np.zeros((0, 4))
+            lib().og_free(C.cast(out.alt4, C.c_void_p))
         lib().og_free(C.cast(out.alt_off, C.c_void_p))
         lib().og_free(C.cast(out.alt, C.c_void_p))
         alt = (aoff, vals)
@@ -254,7 +270,8 @@ def render(scene, cam, mode: str = "exact", windows=(4, 8, 16), key_tile: int = 
                       "unchecked_px"], [int(v) for v in out.stats[:8]]))
     return dict(image=image, marginal=marginal.astype(bool), tile_class=tcls, full=full, low=low,
                 lowimg=lowimg if fovea is not None else None, orders=orders, stats=stats,
-                alt=alt, unchecked=None if unchecked is None else unchecked.astype(bool))
+                alt=alt, unchecked=None if unchecked is None else unchecked.astype(bool),
+                alt4=alt4 if outcomes else None)
 
 
 def tile_lists(scene, cam, key_tile: int = 16, tile_cull: bool = True, visible=None, relax: float = 0.0,

@@ -47,6 +47,56 @@ def forward(x: torch.Tensor, w: dict, round_acts: bool = True):
     return y, (xin, a1, a2)
 
 
+def _gamma(n: int, u: float) -> float:
+    """Relative error bound of an n-term sum accumulated in floating point with unit
+    roundoff u (Higham's gamma_n = n u / (1 - n u))."""
+    return n * u / (1.0 - n * u)
+
+
+def _flip(z: torch.Tensor, D: torch.Tensor) -> torch.Tensor:
+    """Largest |bf16(relu(z')) - bf16(relu(z))| over |z' - z| <= D: ReLU and rounding are
+    monotone, so the ends of the interval give it."""
+    a = bf16(F.relu(z))
+    return torch.maximum((bf16(F.relu(z + D)) - a).abs(), (bf16(F.relu(z - D)) - a).abs())
+
+
+def forward_bound(x: torch.Tensor, w: dict, x_err: float = 0.0, u: float = 2.0 ** -22, moves: bool = False):
+    """The float64 forward and, per output, a bound on how far an evaluation that
+    accumulates in lower precision (unit roundoff u) and rounds to BF16 at the same three
+    places can land from it.
+
+    Layer by layer: a sum of n products carries at most gamma_n (sum |w a| + |b|) of
+    accumulation error; a hidden value then rounds to the same BF16 value unless its
+    pre-rounding value lies within that distance (plus what changed activations of the
+    layer before move it) of a rounding boundary, and the rounded value then moves by at
+    most _flip.  The bound of an output adds its accumulation error and |w3| times the
+    moves of the activations it reads.  x_err bounds the difference of the other side's
+    input (e.g. an FP32 bilinear upsample) from x.  u = 2^-22 leaves two bits for
+    accumulation orders (tensor-core trees) coarser than a sequential FP32 sum.
+    -> (y, bound), both [B, 3, H, W] float64; with moves, also ((a1, da1), (a2, da2)):
+    the hidden activations and their largest moves."""
+    t = {k: (v if torch.is_tensor(v) else torch.tensor(v, dtype=torch.float64)) for k, v in w.items()}
+    t = {k: bf16(v) if k.startswith("w") else v for k, v in t.items()}
+    aw = {k: t[k].abs() for k in ("w1", "w2", "w3")}
+    ab = {k: t[k].abs() for k in ("b1", "b2", "b3")}
+    xin = bf16(x)
+    dxin = torch.maximum((bf16(x + x_err) - xin).abs(), (bf16(x - x_err) - xin).abs())
+    z1 = F.conv2d(xin, t["w1"], t["b1"], padding=1)
+    D1 = _gamma(28, u) * F.conv2d(xin.abs(), aw["w1"], ab["b1"], padding=1) + F.conv2d(dxin, aw["w1"], padding=1)
+    a1 = bf16(F.relu(z1))
+    da1 = _flip(z1, D1)
+    z2 = F.conv2d(a1, t["w2"], t["b2"], padding=1)
+    D2 = _gamma(289, u) * F.conv2d(a1 + da1, aw["w2"], ab["b2"], padding=1) + F.conv2d(da1, aw["w2"], padding=1)
+    a2 = bf16(F.relu(z2))
+    da2 = _flip(z2, D2)
+    y = x + F.conv2d(a2, t["w3"], t["b3"], padding=1)
+    bound = (_gamma(290, u) * (F.conv2d(a2 + da2, aw["w3"], ab["b3"], padding=1) + x.abs())
+             + F.conv2d(da2, aw["w3"], padding=1) + x_err)
+    if moves:
+        return y, bound, ((a1, da1), (a2, da2))
+    return y, bound
+
+
 def conv_direct(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
     """3x3, pad 1 convolution by explicit sums (pins the library convolution)."""
     B, Ci, H, W = x.shape

@@ -89,6 +89,11 @@ typedef struct {
   /* 1: also enumerate the outcome sets (og_out.alt, og_out.unchecked): every result that
    * the marginal decisions of a pixel's samples allow, for the FP32-vs-FP64 comparison */
   int outcomes;
+  /* 1: render only the Gaussians whose mean lies at a world-space distance d from
+   * dist_ref with dist_min <= d < dist_max (the near or the far layer of the stereo
+   * reuse of distant content, Sec. 7) */
+  int dist_cull;
+  double dist_ref[3], dist_min, dist_max;
 } og_opts;
 
 typedef struct {
@@ -111,6 +116,7 @@ typedef struct {
   uint8_t* unchecked; /* [H][W], caller-owned, may be NULL */
   int64_t* alt_off;   /* out: [H*W + 1] */
   double* alt;        /* out: [n_alt][3] */
+  double* alt4;       /* out, plain renders only: [n_alt][4], the (C rgb, T) of each alternative */
   int64_t n_alt;
 } og_out;
 
@@ -1366,7 +1372,19 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
    * (they change no FP64 result, as no sample keeps them) */
   const double sigma_min = o->outcomes ? OG_ALPHA_MIN * (1.0 - o->margin_alpha) : OG_ALPHA_MIN;
 #pragma omp parallel for schedule(dynamic, 1024) reduction(+ : nvalid)
-  for (int64_t i = 0; i < n; ++i) nvalid += og_project_min(sc, i, cam, &P[i], sigma_min) && P[i].sigma >= OG_ALPHA_MIN;
+  for (int64_t i = 0; i < n; ++i) {
+    int v = og_project_min(sc, i, cam, &P[i], sigma_min);
+    if (v && o->dist_cull) {
+      double dd = 0;
+      for (int k = 0; k < 3; ++k) {
+        double e = sc->mean[k * n + i] - o->dist_ref[k];
+        dd += e * e;
+      }
+      const double d = sqrt(dd);
+      if (!(d >= o->dist_min && d < o->dist_max)) P[i].valid = v = 0;
+    }
+    nvalid += v && P[i].sigma >= OG_ALPHA_MIN;
+  }
   out->stats[0] = nvalid;
 
   /* tile classes */
@@ -1669,10 +1687,12 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
    * the samples a pixel reads, through the same composite (its taps and weights) */
   out->alt_off = NULL;
   out->alt = NULL;
+  out->alt4 = NULL;
   out->n_alt = 0;
   if (o->outcomes) {
     int64_t cap = 0, nalt = 0, nunchk = 0;
     double* alt = NULL;
+    double* alt4 = NULL; /* plain renders: the one sample's (C, T) of each alternative */
     int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (nfull + 1));
     for (int y = 0; y < H; ++y)
       for (int x = 0; x < W; ++x) {
@@ -1710,8 +1730,14 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
             if (nalt == cap) {
               cap = cap ? 2 * cap : 1024;
               alt = (double*)realloc(alt, sizeof(double) * 3 * cap);
+              if (!o->foveated) alt4 = (double*)realloc(alt4, sizeof(double) * 4 * cap);
             }
             for (int ch = 0; ch < 3; ++ch) alt[3 * nalt + ch] = v[ch];
+            if (!o->foveated) { /* one tap of weight 1: the sample itself */
+              const sample* sp = &S[tp[0].k];
+              const double* r = sp->nalt > 1 ? sp->alt[pick[0]].v : NULL;
+              for (int q = 0; q < 4; ++q) alt4[4 * nalt + q] = r ? r[q] : (q < 3 ? sp->C[q] : sp->T);
+            }
             ++nalt;
           }
           /* next combination (mixed radix over the taps with several results) */
@@ -1725,6 +1751,7 @@ int og_render(const og_scene* sc, const og_camera* cam, const og_opts* o, og_out
     off[nfull] = nalt;
     out->alt_off = off;
     out->alt = alt;
+    out->alt4 = alt4;
     out->n_alt = nalt;
     out->stats[7] = nunchk;
   }

@@ -47,7 +47,8 @@ EXPORTED = ["vrs_create", "vrs_destroy", "vrs_reserve", "vrs_render", "vrs_rende
             "vrs_get_stats", "vrs_copy_instances", "vrs_project", "vrs_sort_pairs", "vrs_loss_l1_ssim",
             "vrs_adam_step", "vrs_profile_begin", "vrs_profile_end", "vrs_sort_pairs_noalloc", "vrs_update_views", "vrs_set_tuning",
             "vrs_net_forward", "vrs_net_backward", "vrs_net_periphery", "vrs_mse", "vrs_render_two_pass",
-            "vrs_measure_peaks", "vrs_probe_orders", "vrs_test_bounded_wait", "vrs_last_error"]
+            "vrs_measure_peaks", "vrs_probe_orders", "vrs_test_bounded_wait", "vrs_render_stereo_reuse",
+            "vrs_last_error"]
 
 _lib = None
 
@@ -74,6 +75,7 @@ def load() -> C.CDLL:
     lib.vrs_reserve.argtypes = [vp, i32, i32, i32, i64, i64]
     lib.vrs_render.argtypes = [vp, P(Gaussians), i32, P(i32), P(Camera), P(Fovea), i32, P(RenderOpts), vp, vp, i32, vp]
     lib.vrs_render_two_pass.argtypes = [vp, P(Gaussians), i32, P(i32), P(Camera), P(Fovea), i32, P(RenderOpts), vp, vp]
+    lib.vrs_render_stereo_reuse.argtypes = [vp, P(Gaussians), P(Camera), P(RenderOpts), C.c_float, vp, vp]
     lib.vrs_render_backward.argtypes = [vp, P(Gaussians), i32, P(i32), P(Camera), P(Fovea), i32, P(RenderOpts), vp,
                                         P(GaussianGrads), vp]
     lib.vrs_check_status.argtypes = [vp, vp, P(i64)]

@@ -207,6 +207,23 @@ class Renderer:
                                                  _stream(stream)))
         return out
 
+    def render_stereo_reuse(self, scene, cams, far_distance: float, cfg: RenderConfig | None = None, out=None,
+                            stream=None) -> torch.Tensor:
+        """Stereo pair with distant content rendered once (vrs_render_stereo_reuse): the
+        Gaussians at distance >= far_distance from the cyclopean eye form a far layer
+        rendered from the cyclopean camera, composited behind each eye's near layer."""
+        cfg = cfg or RenderConfig()
+        W, H = int(cams[0].width), int(cams[0].height)
+        if out is None:
+            out = torch.empty((2, 3, H, W), device="cuda", dtype=torch.float32)
+        sc = scene.c()
+        cm = (_lib.Camera * 2)(*[camera_c(c) for c in cams])
+        o = cfg.opts()
+        self.generation += 1
+        self._check(self.lib.vrs_render_stereo_reuse(self.ctx, C.byref(sc), cm, C.byref(o), float(far_distance),
+                                                     _ptr(out), _stream(stream)))
+        return out
+
     def backward(self, scenes, view_scene, cams, foveas, cfg: RenderConfig, dL_dout: torch.Tensor, grads,
                  stream=None, visible=None):
         sc, vs, cm, fv, o = self._marshal(scenes, view_scene, cams, foveas, cfg, visible)

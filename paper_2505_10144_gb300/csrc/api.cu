@@ -30,6 +30,7 @@ vrs_status loss_l1_ssim_impl(const float* img, const float* tgt, int n, int H, i
 size_t loss_scratch_bytes(int n, int H, int W);
 void launch_lookback_timeout_test(uint32_t* zeroed_look, uint32_t* status, cudaStream_t st);
 void launch_mbar_timeout_test(uint32_t* status, cudaStream_t st);
+void launch_reuse_composite(const float4* s_full, int W, int H, const float bg[3], float* out, cudaStream_t st);
 void launch_probe_orders(const ViewParams* views, int n_views, const float4* rec, const uint32_t* vals,
                          const uint32_t* ranges, int key_tile, int tiles_per_view, int list_order,
                          const float* probes, int n, int max_len, int* ids, float* depth, int* len,
@@ -70,6 +71,12 @@ struct vrs_ctx {
   int last_passes = 0;
   int last_launches = 0;
   int max_ctas_per_sm = 0;
+  // stereo reuse of distant content: while set, the next plan assigns views 0 and 1 the
+  // near layer [0, layer_d) and view 2 the far layer [layer_d, inf) around layer_ref
+  bool layer_on = false;
+  float layer_ref[3] = {0.f, 0.f, 0.f};
+  float layer_d = 0.f;
+  DevBuf reuse_out;
   Saved saved;
   // stage profiling: 8 events per recorded call
   std::vector<cudaEvent_t> prof_ev;
@@ -191,6 +198,9 @@ void fill_view(ViewParams& vp, const vrs_camera& c, const vrs_fovea* f, int T) {
   vp.radius = f ? f->radius_px : 0.f;
   vp.band = f ? f->band_px : 1.f;
   vp.visible = f ? f->visible : nullptr;
+  vp.dist_ref[0] = vp.dist_ref[1] = vp.dist_ref[2] = 0.f;
+  vp.dist_min = 0.f;
+  vp.dist_max = INFINITY;
 }
 
 bool any_mask(const vrs_fovea* fov, int n_views) {
@@ -261,7 +271,9 @@ vrs_status plan_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, co
   int T = o->key_tile;
   if (T != 16 && T != 32) return fail(c, VRS_ERR_INVALID, "key_tile must be 16 or 32");
   if (fm != 0) {
-    if (T != 32) return fail(c, VRS_ERR_INVALID, "foveated rendering uses 32x32 key tiles");
+    // the fovea classes are per key tile: 32x32 (Sec. 4.3), or 16x16 with the bilinear
+    // periphery (a tuning option); the network's fused kernel works on 32x32 tiles
+    if (fm == 2 && T != 32) return fail(c, VRS_ERR_INVALID, "the network periphery uses 32x32 key tiles");
     if ((W & 1) || (H & 1)) return fail(c, VRS_ERR_INVALID, "foveated rendering needs even width and height");
   }
   for (int v = 0; v < n_views; ++v) {
@@ -291,6 +303,11 @@ vrs_status plan_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, co
   for (int v = 0; v < n_views; ++v) {
     ViewParams& vp = c->h_views[v];
     fill_view(vp, cams[v], fov ? &fov[v] : nullptr, T);
+    if (c->layer_on) {
+      for (int k = 0; k < 3; ++k) vp.dist_ref[k] = c->layer_ref[k];
+      vp.dist_min = v < 2 ? 0.f : c->layer_d;
+      vp.dist_max = v < 2 ? c->layer_d : INFINITY;
+    }
     vp.scene = view_scene[v];
     vp.base = base;
     pl.view_n[v] = scenes[view_scene[v]].n;
@@ -582,6 +599,55 @@ vrs_status vrs_render(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, con
   sv.has_mask = pl.has_mask;
   for (int k = 0; k < 3; ++k) sv.k[k] = o->win[k];
   return VRS_OK;
+}
+
+vrs_status vrs_render_stereo_reuse(vrs_ctx* c, const vrs_gaussians* scene, const vrs_camera* cams,
+                                   const vrs_render_opts* o, float far_distance, float* d_out_rgb, void* stream) {
+  if (!c) return VRS_ERR_INVALID;
+  if (!scene || !cams || !o || !d_out_rgb) return fail(c, VRS_ERR_INVALID, "null argument");
+  if (!(far_distance > 0.f) || !std::isfinite(far_distance)) return fail(c, VRS_ERR_INVALID, "bad far distance");
+  if (o->sort_mode >= 3) return fail(c, VRS_ERR_INVALID, "stereo reuse takes the per-ray orders (sort modes 0 .. 2)");
+  for (int e = 0; e < 2; ++e)
+    if (!finite_cam(cams[e])) return fail(c, VRS_ERR_INVALID, "non-finite or non-positive camera values");
+  if (cams[1].width != cams[0].width || cams[1].height != cams[0].height || cams[1].fx != cams[0].fx ||
+      cams[1].fy != cams[0].fy || cams[1].cx != cams[0].cx || cams[1].cy != cams[0].cy)
+    return fail(c, VRS_ERR_INVALID, "the eyes must share image size and intrinsics");
+  // both eyes share one rotation; the cyclopean camera sits at the midpoint of the centres
+  double ctr[2][3];
+  for (int e = 0; e < 2; ++e)
+    for (int k = 0; k < 3; ++k) {
+      double v = 0;
+      for (int r = 0; r < 3; ++r) v -= (double)cams[e].world_to_cam[4 * r + k] * cams[e].world_to_cam[4 * r + 3];
+      ctr[e][k] = v;
+    }
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 3; ++k)
+      if (std::fabs(cams[0].world_to_cam[4 * r + k] - cams[1].world_to_cam[4 * r + k]) > 1e-6f)
+        return fail(c, VRS_ERR_INVALID, "the eyes must share the head rotation");
+  vrs_camera cam3[3] = {cams[0], cams[1], cams[0]};
+  for (int r = 0; r < 3; ++r) {
+    double t = 0;
+    for (int k = 0; k < 3; ++k) t -= (double)cams[0].world_to_cam[4 * r + k] * 0.5 * (ctr[0][k] + ctr[1][k]);
+    cam3[2].world_to_cam[4 * r + 3] = (float)t;
+  }
+  vrs_render_opts o3 = *o;
+  o3.bg[0] = o3.bg[1] = o3.bg[2] = 0.f;  // the layers keep (C, T); the background goes in at the end
+  const int vs[3] = {0, 0, 0};
+  const int W = cams[0].width, H = cams[0].height;
+  cudaStream_t st = (cudaStream_t)stream;
+  vrs_status s = VRS_OK;
+  if (!ensure(c, c->reuse_out, sizeof(float) * 9 * (size_t)W * H, capturing(st), &s)) return s;
+  c->layer_on = true;
+  for (int k = 0; k < 3; ++k) c->layer_ref[k] = (float)(0.5 * (ctr[0][k] + ctr[1][k]));
+  c->layer_d = far_distance;
+  s = vrs_render(c, scene, 1, vs, cam3, nullptr, 3, &o3, P<float>(c->reuse_out), nullptr, 1, stream);
+  c->layer_on = false;
+  if (s) return s;
+  c->saved.valid = false;  // the layered render has no backward
+  launch_reuse_composite(P<float4>(c->s_full), W, H, o->bg, d_out_rgb, st);
+  c->last_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "reuse composite launch");
 }
 
 vrs_status vrs_render_two_pass(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes, const int* view_scene,

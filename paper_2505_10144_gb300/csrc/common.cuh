@@ -54,6 +54,11 @@ struct ViewParams {
   long long base;   // offset of this view in the per-(view, Gaussian) arrays
   float gaze_x, gaze_y, radius, band;
   const uint8_t* visible;  // [H][W] headset visibility mask (nonzero = visible) or null
+  // the layer this view renders: Gaussians whose world-space mean lies at distance d from
+  // dist_ref with dist_min <= d < dist_max (stereo reuse of distant content; 0 and
+  // infinity otherwise)
+  float dist_ref[3];
+  float dist_min, dist_max;
 };
 
 struct SceneDev {

@@ -62,6 +62,11 @@ __device__ bool project_gaussian(const SceneDev& s, long long i, const ViewParam
   const float logit = s.logit[i];
   if (!finite3(m0, m1, m2) || !finite3(l0, l1, l2) || !finite3(qw, qx, qy) || !isfinite(qz) || !isfinite(logit))
     return false;
+  {  // the view's layer: distance of the mean from the layer reference
+    const float e0 = m0 - vp.dist_ref[0], e1 = m1 - vp.dist_ref[1], e2 = m2 - vp.dist_ref[2];
+    const float dd = sqrtf(fmaf(e0, e0, fmaf(e1, e1, e2 * e2)));
+    if (!(dd >= vp.dist_min && dd < vp.dist_max)) return false;
+  }
   const float* R = vp.R;
   const float mx = fmaf(R[0], m0, fmaf(R[1], m1, fmaf(R[2], m2, vp.t[0])));
   const float my = fmaf(R[3], m0, fmaf(R[4], m1, fmaf(R[5], m2, vp.t[1])));

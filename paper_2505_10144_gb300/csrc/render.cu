@@ -349,6 +349,7 @@ __device__ __forceinline__ bool eval_full(const float4* r, Px& p, float& alpha, 
 
 struct ItemGeom {
   int view, kind, ox, oy;  // ox, oy: sample-grid origin (pixels for full, groups for low)
+  int ext;                 // side of the item in samples: 16, or 8 for the groups of a 16x16 periphery tile
   int tile;
 };
 
@@ -361,9 +362,11 @@ __device__ __forceinline__ ItemGeom decode(const WorkItem& it, int tiles_per_vie
   g.kind = it.code & 15;
   const int sub = it.code >> 4;
   g.tile = it.tile;
-  if (g.kind == kKindLow) {
-    g.ox = tx * 16;
-    g.oy = ty * 16;
+  g.ext = 16;
+  if (g.kind == kKindLow) {  // the (T / 2) x (T / 2) groups of a periphery key tile
+    g.ox = tx * (T / 2);
+    g.oy = ty * (T / 2);
+    g.ext = T / 2;
   } else if (T == 16) {
     g.ox = tx * 16;
     g.oy = ty * 16;
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(kBlock, 2) render_kernel(RenderArgs a) {
     bool valid;
     int X = g.ox + sx, Y = g.oy + sy;
     if (g.kind == kKindLow) {
-      valid = 2 * X < vp.W && 2 * Y < vp.H;
+      valid = 2 * X < vp.W && 2 * Y < vp.H && sx < g.ext && sy < g.ext;
       p.px = 2.f * X + 1.f;
       p.py = 2.f * Y + 1.f;
     } else {
@@ -1091,6 +1094,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
     Px p;
     bool valid;
     float rx0, rx1, ry0, ry1;  // sample-position bounds of the region (culling)
+    if (rx >= g.ext || ry >= g.ext) continue;  // a region outside a smaller periphery item
     if (g.kind == kKindLow) {
       valid = 2 * X < vp.W && 2 * Y < vp.H;
       p.px = 2.f * X + 1.f;
@@ -1417,6 +1421,22 @@ __global__ void two_pass_composite_kernel(TwoPassViews tp, int W, int H, int SW,
   }
 }
 
+// Stereo reuse of distant content: eye v's pixel = C_near + T_near (C_far + T_far bg), with
+// (C, T) per pixel of views 0, 1 (the eyes' near layers) and 2 (the far layer, rendered
+// once from the cyclopean camera).  One thread per pixel of both eyes.
+__global__ void __launch_bounds__(256) reuse_composite_kernel(const float4* __restrict__ s_full, long long HW,
+                                                              float bg0, float bg1, float bg2, float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * HW) return;
+  const int v = (int)(i / HW);
+  const long long p = i - v * HW;
+  const float4 n = s_full[i], f = s_full[2 * HW + p];
+  float* o = out + (long long)v * 3 * HW + p;
+  o[0] = fmaf(n.w, fmaf(f.w, bg0, f.x), n.x);
+  o[HW] = fmaf(n.w, fmaf(f.w, bg1, f.y), n.y);
+  o[2 * HW] = fmaf(n.w, fmaf(f.w, bg2, f.z), n.z);
+}
+
 // Bilinear x2 upsampling of the half-resolution image into periphery tiles: one thread
 // per output pixel, grid (row chunks of 256 pixels, rows, views), so no index division.
 __global__ void __launch_bounds__(256) composite_kernel(const ViewParams* __restrict__ views,
@@ -1555,6 +1575,11 @@ void launch_two_pass_composite(const TwoPassViews& tp, int n_views, int W, int H
   if (n_views <= 0 || W <= 0 || H <= 0) return;
   const dim3 grid((unsigned)((W + 255) / 256), (unsigned)std::min(H, 65535), (unsigned)n_views);
   two_pass_composite_kernel<<<grid, 256, 0, st>>>(tp, W, H, SW, SH, centre, low, out);
+}
+
+void launch_reuse_composite(const float4* s_full, int W, int H, const float bg[3], float* out, cudaStream_t st) {
+  const long long HW = (long long)W * H;
+  reuse_composite_kernel<<<(unsigned)((2 * HW + 255) / 256), 256, 0, st>>>(s_full, HW, bg[0], bg[1], bg[2], out);
 }
 
 void launch_composite(const RenderArgs& a, int W, int H, cudaStream_t st) {

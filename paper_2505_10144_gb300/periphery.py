@@ -145,12 +145,18 @@ def psnr(mse: float) -> float:
     return float("inf") if mse <= 0 else 10.0 * math.log10(1.0 / mse)
 
 
-def evaluate_frames(renderer: api.Renderer, net: PeripheryNet, scene: api.DeviceScene, frames, windows=(4, 8, 16)):
+def evaluate_frames(renderer: api.Renderer, net: PeripheryNet, scene: api.DeviceScene, frames, windows=(4, 8, 16),
+                    sort_mode: str = "hier"):
     """Per-frame PSNR / max abs error of the learned and the bilinear periphery against
-    the plain full-resolution render, on periphery pixels and on the whole frame."""
-    fov_cfg = api.RenderConfig(sort_mode="hier", windows=windows, key_tile=32, fovea_mode="bilinear")
-    net_cfg = api.RenderConfig(sort_mode="hier", windows=windows, key_tile=32, fovea_mode="net")
-    plain_cfg = api.RenderConfig(sort_mode="hier", windows=windows, key_tile=16, fovea_mode="plain")
+    the plain full-resolution render, on periphery pixels and on the whole frame.  With
+    sort_mode "exact" the three renders share the exact per-ray order, so the periphery's
+    error is what reconstruction from the half-resolution samples loses; with "hier" the
+    foveated frame (32x32 key tiles, 4x4 blocks of half-resolution groups) and the plain
+    render (16x16 key tiles, 4x4 blocks of pixels) also differ by their hierarchical
+    windows' approximation."""
+    fov_cfg = api.RenderConfig(sort_mode=sort_mode, windows=windows, key_tile=32, fovea_mode="bilinear")
+    net_cfg = api.RenderConfig(sort_mode=sort_mode, windows=windows, key_tile=32, fovea_mode="net")
+    plain_cfg = api.RenderConfig(sort_mode=sort_mode, windows=windows, key_tile=16, fovea_mode="plain")
     acc = {k: [] for k in ["net_periph_mse", "bil_periph_mse", "net_frame_mse", "bil_frame_mse", "net_periph_max",
                            "bil_periph_max"]}
     for fr in frames:

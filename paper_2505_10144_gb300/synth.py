@@ -142,6 +142,46 @@ def focal_for_hfov(width: int, hfov_deg: float) -> float:
     return (width / 2.0) / math.tan(math.radians(hfov_deg) / 2.0)
 
 
+def open_room_with_landscape(n_room: int, n_far: int, rng: np.random.Generator, sh_degree: int = 3,
+                             half_size: float = 3.0, jitter: float = 0.05, far_range=(150.0, 600.0)) -> Scene:
+    """A scene with distant content: the room shell without its ceiling (the y = -half
+    face; y points down) and its front wall (z = +half), so that part of the view looks
+    out, and a landscape of n_far Gaussians around the head at distances uniform in
+    far_range, azimuth uniform, elevation uniform in [-10, 30] degrees above the horizon,
+    with log-scales N(log(0.012 d), 0.5) (about the angular size of the room's Gaussians).
+    The room's Gaussians come first."""
+    face = rng.choice(np.array([0, 1, 3, 4]), size=n_room)
+    a = rng.uniform(-half_size, half_size, size=n_room)
+    b = rng.uniform(-half_size, half_size, size=n_room)
+    axis = face // 2
+    sign = np.where(face % 2 == 0, -1.0, 1.0)
+    mean = np.empty((3, n_room))
+    for ax in range(3):
+        o1, o2 = [x for x in range(3) if x != ax]
+        sel = axis == ax
+        mean[ax, sel] = sign[sel] * half_size
+        mean[o1, sel] = a[sel]
+        mean[o2, sel] = b[sel]
+    mean += rng.normal(0.0, jitter, size=mean.shape)
+    room = _random_params(rng, n_room, sh_degree, mean)
+    d = rng.uniform(far_range[0], far_range[1], size=n_far)
+    az = rng.uniform(-math.pi, math.pi, size=n_far)
+    el = np.radians(rng.uniform(-10.0, 30.0, size=n_far))
+    fmean = np.stack([d * np.cos(el) * np.sin(az), -d * np.sin(el), d * np.cos(el) * np.cos(az)])
+    far = _random_params(rng, n_far, sh_degree, fmean)
+    far.log_scale = _f32(np.log(0.012 * d)[None, :] + rng.normal(0.0, 0.5, size=(3, n_far)))
+    return Scene(*[np.ascontiguousarray(np.concatenate([x, y], axis=-1)) for x, y in zip(room.arrays(), far.arrays())],
+                 sh_degree)
+
+
+def cyclopean_camera(left: Camera, right: Camera) -> Camera:
+    """The camera between two eyes: the left eye's rotation and intrinsics, its centre
+    at the midpoint of the eye centres."""
+    c = 0.5 * (np.asarray(left.center(), dtype=np.float64) + np.asarray(right.center(), dtype=np.float64))
+    R = left.world_to_cam[:, :3].astype(np.float64)
+    return camera_from_pose(R.T, c, left.width, left.height, left.fx, left.fy, left.near_z, left.cx, left.cy)
+
+
 def head_rotation(yaw: float, pitch: float = 0.0) -> np.ndarray:
     """Camera-to-world rotation (columns: right, down, forward) for a yaw about the world
     y axis followed by a pitch about the camera x axis."""

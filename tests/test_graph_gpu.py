@@ -3,9 +3,9 @@ import json
 
 import numpy as np
 import pytest
+import torch
 
 import outcomes as oc
-import torch
 
 from paper_2505_10144_gb300 import synth
 
@@ -60,12 +60,29 @@ def test_autotuner_picks_a_candidate_and_caches_it(setup, tmp_path):
     api, R, scenes, vs, cams, fovs, cfg = setup
     path = tmp_path / "tune.json"
     best, res = autotune.autotune(R, scenes, vs, cams, fovs, cfg, cache_path=path, reps=2,
-                                  window_sets=[(4, 8, 16), (8, 16, 32)], cta_caps=[0, 1])
-    assert len(res) == 4 and best["ms"] == min(r["ms"] for r in res)
+                                  window_sets=[(4, 8, 16), (8, 16, 32)], cta_caps=[0, 1], tile_sizes=[32, 16])
+    assert len(res) == 8
+    # every candidate carries its quality against the exact order; the choice is the
+    # fastest of those at or above the floor
+    ok = [r for r in res if r["meets_floor"]]
+    assert ok and all(r["meets_floor"] == (r["psnr_db"] >= best["psnr_floor_db"]) for r in res)
+    assert best["ms"] == min(r["ms"] for r in ok) and best["psnr_db"] >= best["psnr_floor_db"]
+    assert all(0.0 <= r["over_2e-4_pct"] <= 100.0 and r["psnr_db"] > 20.0 for r in res)
+    # larger windows approach the exact order: never less accurate on the same tiles
+    for T in (32, 16):
+        q = {tuple(r["windows"]): r["psnr_db"] for r in res if r["key_tile"] == T}
+        assert q[(8, 16, 32)] >= q[(4, 8, 16)] - 0.05
+    # with a floor that some candidates miss, the choice is the fastest of the others, and
+    # with none meeting it, the fastest overall
+    b3, r3 = autotune.autotune(R, scenes, vs, cams, fovs, cfg, reps=1, window_sets=[(4, 8, 16)], cta_caps=[0],
+                               tile_sizes=[32, 16], psnr_floor=max(r["psnr_db"] for r in res) + 1.0, use_cache=False)
+    met = [r for r in r3 if r["meets_floor"]]
+    assert b3["ms"] == min(r["ms"] for r in (met or r3))
     cache = json.loads(path.read_text())
     assert autotune.cache_key(scenes, vs, cams) in cache
     best2, _ = autotune.autotune(R, scenes, vs, cams, fovs, cfg, cache_path=path)
     assert best2["windows"] == best["windows"] and best2["max_ctas_per_sm"] == best["max_ctas_per_sm"]
+    assert best2["key_tile"] == best["key_tile"]
     # the CTA cap is scheduling only: same image
     R.set_tuning(1)
     a = R.render(scenes, vs, cams, fovs, cfg).clone()

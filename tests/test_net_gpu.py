@@ -1,20 +1,30 @@
-"""Periphery network kernels against the float64 oracle (oracle/net.py), the fused
-tensor-core inference against the training forward, and what training buys over the
-bilinear fallback on held-out crops.
+"""Periphery network kernels against the float64 oracle (oracle/net.py), and what
+training buys over the bilinear fallback on held-out crops.
 
-Tolerance: activations are BF16 on both sides, rounded at the same three points; a
-hidden value whose FP32 (GPU) and FP64 (oracle) pre-activation fall on opposite sides
-of a BF16 rounding boundary moves by one BF16 ulp (2^-8 relative).  Such flips are rare
-(the FP32 accumulation error is ~1e-6 of a value, a BF16 ulp ~4e-3), so the bound is a
-small absolute error on almost every output plus a larger one on a few outputs."""
+Tolerance, derived per output (oracle.net.forward_bound): the GPU accumulates in FP32
+(its tensor-core kernel in the MMA's accumulation order) and rounds to BF16 at the same
+three points as the oracle.  A sum of n products carries at most gamma_n sum |w a| of
+accumulation error (unit roundoff 2^-23 here: one bit of slack for the order); a hidden
+activation then rounds to the same BF16 value unless its pre-rounding value lies within
+that reach of a rounding boundary, and it moves by at most the rounding of the reach's
+ends otherwise; an output moves by its own accumulation error plus |w3| times the moves
+of the activations it reads.  Every test asserts |GPU - oracle| <= that bound on every
+output and prints the largest error and the bound's quantiles.
+
+Inputs are seeded: random images, and for the fused kernel seeded half-resolution images
+handed to vrs_net_periphery (its d_low argument), so neither side reads the other's
+values."""
 import numpy as np
 import pytest
 import torch
 
+from oracle import grad as ograd
 from oracle import net as onet
 from paper_2505_10144_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+
+U_ACC = 2.0 ** -23
 
 
 @pytest.fixture(scope="module")
@@ -26,9 +36,16 @@ def R():
     r.close()
 
 
-def oracle_forward(net, x):
-    y, _ = onet.forward(torch.tensor(x, dtype=torch.float64), net.numpy_weights())
-    return y.numpy()
+def within_bound(gpu, x, net, label, x_err=0.0):
+    """gpu: [B, 3, H, W] GPU outputs for the float64 network input x."""
+    y, b = onet.forward_bound(torch.as_tensor(x, dtype=torch.float64), net.numpy_weights(), x_err=x_err, u=U_ACC)
+    d = (torch.as_tensor(np.asarray(gpu, dtype=np.float64)) - y).abs()
+    print(f"[net {label}] {d.numel()} outputs: max |d| {float(d.max()):.3g}, q99 {float(torch.quantile(d.flatten()[:2**24], 0.99)):.3g}; "
+          f"bound q50 {float(torch.quantile(b.flatten()[:2**24], 0.5)):.3g}, max {float(b.max()):.3g}; "
+          f"max |d| / bound {float((d / b).max()):.3f}")
+    bad = d > b + 1e-7
+    assert not bool(bad.any()), f"{label}: {int(bad.sum())} outputs beyond the derived bound (worst {float((d - b).max()):.3g})"
+    return y
 
 
 def test_net_forward_matches_oracle(R):
@@ -37,12 +54,17 @@ def test_net_forward_matches_oracle(R):
     rng = np.random.default_rng(0)
     x = rng.uniform(0, 1, size=(2, 3, 37, 45)).astype(np.float32)
     y, acts = net.forward(torch.tensor(x).cuda())
-    yr = oracle_forward(net, x)
-    d = np.abs(y.cpu().numpy() - yr)
-    assert np.quantile(d, 0.99) < 1e-3 and d.max() < 3e-2, (np.quantile(d, 0.99), d.max())
+    within_bound(y.cpu().numpy(), x.astype(np.float64), net, "training forward")
 
 
 def test_net_backward_matches_oracle(R):
+    """Parameter gradients (BF16 rounding passed straight through) against the float64
+    gradient.  Derived tolerance: each gradient is a sum over pixels of products with the
+    hidden activations, which the GPU forms from its own rounded activations; those differ
+    from the oracle's by at most the moves of forward_bound, so the relative error of a
+    gradient is bounded by a few times the relative size of those moves, plus the FP32
+    accumulation error of a sum of n = B H W 9 terms (gamma_n, a bound on cancellation-
+    free sums; 4 times it for the cancellation of signed dy)."""
     from paper_2505_10144_gb300 import periphery
     net = periphery.PeripheryNet(R, seed=2, last_scale=1.0)
     rng = np.random.default_rng(1)
@@ -53,10 +75,19 @@ def test_net_backward_matches_oracle(R):
     net.backward(xt, acts, torch.tensor(dy).cuda())
     g = net.grad.cpu().numpy().astype(np.float64)
     gr = onet.grads(x.astype(np.float64), net.numpy_weights(), dy.astype(np.float64))
+    _, _, ((a1, da1), (a2, da2)) = onet.forward_bound(torch.tensor(x, dtype=torch.float64), net.numpy_weights(),
+                                                      u=U_ACC, moves=True)
+    move = max(float(da1.norm() / a1.norm()), float(da2.norm() / a2.norm()))
+    n = x.shape[0] * x.shape[2] * x.shape[3] * 9
+    tol = 4.0 * move + 4.0 * onet._gamma(n, 2.0 ** -24)
+    worst = 0.0
     for k, (o, shape) in periphery.OFF.items():
         a, b = g[o:o + int(np.prod(shape))], gr[k].ravel()
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        assert rel < 2e-2, (k, rel)
+        worst = max(worst, rel)
+        assert rel < tol, (k, rel, tol)
+    print(f"[net backward] worst relative L2 {worst:.3g} against the derived {tol:.3g} "
+          f"(activation moves {move:.3g} of their norm)")
 
 
 def test_mse_kernel(R):
@@ -79,25 +110,40 @@ def vr_frame(R):
     return scene, cams, fov, W, H
 
 
-def test_fused_periphery_kernel_matches_training_forward(R, vr_frame):
-    """Every tile in the periphery: the render's output is then bilinear(low) everywhere,
-    the exact input of the network, so the fused tensor-core kernel must agree with the
-    training forward (and the oracle) on the whole frame."""
-    from paper_2505_10144_gb300 import api, periphery
+def seeded_low(rng, shape):
+    """A seeded half-resolution image with structure at every scale: a smooth gradient,
+    blobs and pixel noise in [0, 1]."""
+    V, C, H2, W2 = shape
+    yy, xx = np.mgrid[0:H2, 0:W2] / max(H2, W2)
+    img = 0.3 + 0.3 * np.sin(6 * xx + 3 * yy)[None, None] + 0.25 * rng.uniform(0, 1, size=shape)
+    return np.clip(img, 0, 1).astype(np.float32)
+
+
+def fused_periphery(R, scene, cams, fov, net, low_img):
+    """A foveated render sets the tile classes; the fused kernel then reconstructs every
+    periphery tile from low_img (handed to it in place of the render's own)."""
+    from paper_2505_10144_gb300 import api
+    W, H = cams[0].width, cams[0].height
+    low = torch.empty((len(cams), 3, H // 2, W // 2), device="cuda")
+    out = R.render([scene], [0] * len(cams), cams, fov, api.RenderConfig(key_tile=32, fovea_mode="net"), low=low)
+    low.copy_(torch.from_numpy(low_img))
+    net.apply_periphery(low, out)
+    R.check()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def test_fused_periphery_kernel_matches_oracle(R, vr_frame):
+    """Every tile in the periphery: the fused tensor-core kernel's output on the whole
+    frame against the float64 network on the float64 bilinear upsample of the same
+    half-resolution image (the kernel upsamples in FP32: input error <= 4 ulp)."""
+    from paper_2505_10144_gb300 import periphery
     scene, cams, _, W, H = vr_frame
     allp = [periphery.ALL_PERIPHERY] * 2
     net = periphery.PeripheryNet(R, seed=4, last_scale=1.0)
-    x = R.render([scene], [0, 0], cams, allp, api.RenderConfig(key_tile=32, fovea_mode="bilinear")).clone()
-    low = torch.empty((2, 3, H // 2, W // 2), device="cuda")
-    out = R.render([scene], [0, 0], cams, allp, api.RenderConfig(key_tile=32, fovea_mode="net"), low=low)
-    net.apply_periphery(low, out)
-    R.check()
-    y, _ = net.forward(x, save=False)
-    d = (out - y).abs()
-    assert float(torch.quantile(d.flatten(), 0.99)) < 1e-3 and float(d.max()) < 3e-2
-    yr = oracle_forward(net, x.cpu().numpy().astype(np.float64))
-    dr = np.abs(out.cpu().numpy() - yr)
-    assert np.quantile(dr, 0.99) < 1e-3 and dr.max() < 3e-2
+    low = seeded_low(np.random.default_rng(21), (2, 3, H // 2, W // 2))
+    out = fused_periphery(R, scene, cams, allp, net, low)
+    x = np.stack([ograd.bilinear_up2(torch.tensor(low[v].astype(np.float64))).numpy() for v in range(2)])
+    within_bound(out, x, net, "fused kernel, whole frame", x_err=4 * 2.0 ** -24)
 
 
 def test_network_leaves_focus_and_hybrid_pixels_alone(R, vr_frame):
@@ -143,38 +189,35 @@ def test_training_beats_bilinear_on_held_out_crops(R):
 
 
 def test_full_size_vr_frame_network_sampled_crops(R):
-    """1M Gaussians, stereo 2064x2208, foveated with the network (the learned-periphery
-    workload's frame): the fused tensor-core kernel runs once over every periphery tile of
-    both eyes.  Crops of its output against the float64 network applied to the float64
-    bilinear upsample of the GPU's half-resolution image (the network's input): the top-left
-    and bottom-right corners (zero padding, the ragged last tile column) and an interior
-    crop, each compared where the crop's 3-pixel halo is complete."""
-    from oracle import grad as ograd
+    """Stereo 2064x2208, foveated with the network (the learned-periphery frame's shape):
+    the fused tensor-core kernel runs once over every periphery tile of both eyes, here
+    from a seeded half-resolution image.  Crops of its output against the float64 network
+    on the float64 bilinear upsample of that image: the top-left and bottom-right corners
+    (zero padding, the ragged last tile column) and an interior crop, each where the
+    crop's 3-pixel halo is complete, within the derived bound."""
     from paper_2505_10144_gb300 import api, periphery
     W, H = 2064, 2208
-    scene = api.DeviceScene.from_host(synth.shell_scene(1_000_000, synth.rng_for(4), sh_degree=3))
+    scene = api.DeviceScene.from_host(synth.shell_scene(200_000, synth.rng_for(4), sh_degree=3))
     fr = synth.vr_trajectory(3, synth.rng_for(4, salt=200), W, H).frames[2]
     net = periphery.PeripheryNet(R, seed=4, last_scale=1.0)
-    low = torch.empty((2, 3, H // 2, W // 2), device="cuda")
-    cfg = api.RenderConfig(sort_mode="hier", windows=(4, 8, 16), key_tile=32, fovea_mode="net")
-    out = R.render([scene], [0, 0], fr.cameras, fr.foveas, cfg, low=low)
-    net.apply_periphery(low, out)
-    R.check()
+    low = seeded_low(np.random.default_rng(22), (2, 3, H // 2, W // 2))
+    outs = fused_periphery(R, scene, fr.cameras, fr.foveas, net, low)
     mask = periphery.periphery_mask(fr, W, H).numpy()
-    outs = out.cpu().numpy().astype(np.float64)
-    lows = low.cpu().numpy().astype(np.float64)
     checked = 0
     for v in range(2):
-        x = ograd.bilinear_up2(torch.tensor(lows[v]))  # [3, H, W]
-        # (crop origin, input window origin): outputs [y0, y0 + 64) x [x0, x0 + 64)
+        x = ograd.bilinear_up2(torch.tensor(low[v].astype(np.float64)))  # [3, H, W]
         for y0, x0 in [(0, 0), (64, W - 128), (H - 64, W - 64)]:
             wy0, wx0 = max(y0 - 3, 0), max(x0 - 3, 0)
             wy1, wx1 = min(y0 + 67, H), min(x0 + 67, W)
             assert mask[v, y0:y0 + 64, x0:x0 + 64].all()
-            y, _ = onet.forward(x[None, :, wy0:wy1, wx0:wx1], net.numpy_weights())
-            ref = y[0, :, y0 - wy0:y0 - wy0 + 64, x0 - wx0:x0 - wx0 + 64].numpy()
-            d = np.abs(outs[v][:, y0:y0 + 64, x0:x0 + 64] - ref)
-            assert np.quantile(d, 0.99) < 1e-3 and d.max() < 3e-2, (v, y0, x0, np.quantile(d, 0.99), d.max())
-            assert np.abs(ref - x[:, y0:y0 + 64, x0:x0 + 64].numpy()).max() > 1e-3  # the network acts here
+            xin = x[None, :, wy0:wy1, wx0:wx1]
+            y, b = onet.forward_bound(xin, net.numpy_weights(), x_err=4 * 2.0 ** -24, u=U_ACC)
+            sl = (slice(None), slice(None), slice(y0 - wy0, y0 - wy0 + 64), slice(x0 - wx0, x0 - wx0 + 64))
+            d = np.abs(outs[v][None, :, y0:y0 + 64, x0:x0 + 64] - y[sl].numpy())
+            bb = b[sl].numpy()
+            print(f"[net full-size eye {v} at ({x0},{y0})] max |d| {d.max():.3g}, bound q50 {np.median(bb):.3g}, "
+                  f"max |d| / bound {(d / bb).max():.3f}")
+            assert (d <= bb + 1e-7).all(), (v, y0, x0, float((d - bb).max()))
+            assert np.abs(y[sl].numpy() - xin[sl].numpy()).max() > 1e-3  # the network acts here
             checked += 1
     assert checked == 6

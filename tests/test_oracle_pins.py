@@ -521,6 +521,51 @@ def test_foveated_constant_scene_stays_constant():
     assert np.abs(r["image"] - v[:, None, None]).max() < 1e-12
 
 
+def _gap_scene(rng, n_near=300, n_far=300):
+    """Near Gaussians 1.5-3 m ahead, far ones 120-200 m ahead, nothing in between."""
+    near = [[rng.uniform(-1, 1), rng.uniform(-0.8, 0.8), rng.uniform(1.5, 3.0)] for _ in range(n_near)]
+    far = [[rng.uniform(-80, 80), rng.uniform(-60, 60), rng.uniform(120.0, 200.0)] for _ in range(n_far)]
+    ls = [[-2.8] * 3] * n_near + [[np.log(0.02 * 160)] * 3] * n_far
+    return make_scene(near + far, log_scales=ls, logits=rng.normal(0.5, 1.0, n_near + n_far),
+                      dc=rng.uniform(-SQRT_PI, SQRT_PI, size=(n_near + n_far, 3)), rng=rng)
+
+
+def test_stereo_reuse_without_far_layer_is_the_plain_render():
+    """Sec. 7 (stereo reuse of distant content), reading: near layer per eye, far layer
+    once from the cyclopean eye, C_near + T_near far.  With no Gaussian in the far layer
+    the far image is the background and each eye is its plain render, bit for bit."""
+    from oracle import reuse
+    rng = np.random.default_rng(19)
+    sc = _gap_scene(rng)
+    cams = synth.stereo_cameras((0.0, 0.0, 0.0), 0.1, 64, 48, 80.0)
+    bg = (0.2, 0.4, 0.1)
+    r = reuse.render(sc, cams, 1e9, "exact", bg=bg)
+    for e in range(2):
+        plain = on.render(sc, cams[e], "exact", key_tile=16, bg=bg)["image"]
+        assert np.array_equal(r["images"][e], plain)
+
+
+@pytest.mark.parametrize("mode", ["exact", "hier"])
+def test_stereo_reuse_with_coinciding_eyes_is_the_plain_render_up_to_the_stop(mode):
+    """With both eyes at the cyclopean point and the split in a gap of the scene, every ray
+    meets the near layer first, and the layered blend equals the one-pass blend of Eq. 2
+    except after the transmittance stop, which the far layer applies to its own T: there
+    the one-pass render stops once T_near T_far (1 - alpha) < 1e-4, so the two differ by
+    at most the light left at that point, T < 1e-4 / (1 - alpha_max) = 1e-2."""
+    from oracle import reuse
+    rng = np.random.default_rng(20)
+    sc = _gap_scene(rng)
+    c = synth.identity_camera(64, 48, 80.0)
+    r = reuse.render(sc, [c, c], 60.0, mode, bg=(0.3, 0.3, 0.3))
+    plain = on.render(sc, c, mode, key_tile=16, bg=(0.3, 0.3, 0.3))["image"]
+    d = np.abs(r["images"][0] - plain).max(axis=0)
+    near = on.render(sc, c, mode, key_tile=16, distance=(np.zeros(3), 0.0, 60.0), want_samples=True)["full"][3]
+    assert d.max() <= 1e-2 and (d > 1e-12).mean() < 0.05
+    # where the near layer leaves T >= 0.5, the stop cannot move by more than 2e-4 of light
+    assert d[near >= 0.5].max() <= 2e-4
+    assert (near < 0.99).mean() > 0.3 and (near >= 0.5).mean() > 0.3  # both layers are visible
+
+
 def _partial_mask(H, W):
     """Visible everywhere except the left 40 columns and the bottom-right corner, with one
     tile kept by a single visible pixel (tile-level culling keeps it whole)."""

@@ -312,6 +312,18 @@ def test_render_foveated_stereo(R, vr_small, mode, win):
         assert (ref["tile_class"] == 0).any() and (ref["tile_class"] == 2).any()
 
 
+@pytest.mark.parametrize("mode,win", [("exact", (0, 0, 0)), ("hier", (4, 8, 16)), ("hier", (8, 16, 32))])
+def test_render_foveated_stereo_16x16_key_tiles(R, vr_small, mode, win):
+    """Foveation classified and sorted on 16x16 key tiles (the autotuner's other tile
+    size): periphery work items of 8x8 groups, finer focus/hybrid/periphery borders."""
+    scene, cams, fov = vr_small
+    gpu = render_gpu(R, scene, cams, fov, sort_mode=mode, windows=win, key_tile=16, fovea_mode="bilinear")
+    for v in range(2):
+        _, ref = parity(gpu[v], scene, cams[v], mode, windows=win, key_tile=16, fovea=fov[v],
+                        label=f"foveated 16x16 {mode} {win} eye {v}")
+        assert (ref["tile_class"] == 0).any() and (ref["tile_class"] == 1).any() and (ref["tile_class"] == 2).any()
+
+
 @pytest.mark.parametrize("mode", ["exact", "hier"])
 def test_render_plain_stereo_shell(R, vr_small, mode):
     scene, cams, _ = vr_small
@@ -389,8 +401,9 @@ def test_invalid_arguments_are_rejected(R):
     cam = synth.identity_camera(64, 64, 90.0)
     with pytest.raises(a.VrsError, match="INVALID"):
         R.render([scene], [0], [cam], None, a.RenderConfig(key_tile=8))
-    with pytest.raises(a.VrsError, match="INVALID"):
-        R.render([scene], [0], [cam], [synth.Fovea(32, 32, 10, 4)], a.RenderConfig(key_tile=16, fovea_mode="bilinear"))
+    with pytest.raises(a.VrsError, match="INVALID"):  # the network periphery needs 32x32 key tiles
+        R.render([scene], [0], [cam], [synth.Fovea(32, 32, 10, 4)], a.RenderConfig(key_tile=16, fovea_mode="net"),
+                 low=torch.empty((1, 3, 32, 32), device="cuda"))
     bad = synth.identity_camera(64, 64, 90.0)
     bad.fx = float("nan")
     with pytest.raises(a.VrsError, match="INVALID"):

@@ -608,6 +608,74 @@ def learned_periphery(api, torch, n_steps, warmup):
                        "eager render + network launch, L2 flushed between frames"}}
 
 
+GRAD_BYTES_PER_BLEND = 64  # each blended pair adds its 16 record-gradient floats with four 16-byte atomics
+
+
+def backward_line(api, torch, warmup, n_steps, peaks):
+    """The fine-tuning step of the workload (500k Gaussians, 4 views of 1280x1280, 0.8 L1 +
+    0.2 (1 - SSIM), every parameter, Adam) and its backward render's roofline: the replay
+    of each blended pair adds 64 bytes of record gradient by vector atomics in L2, against
+    the measured L2 read bandwidth (the atomics' unit); and the issue basis of the replay
+    (the forward's 36 lane-ops per evaluated pair again, about twice that per blended pair
+    for the gradient)."""
+    from paper_2505_10144_gb300 import synth
+    scene = synth.shell_scene(N_GAUSS, synth.rng_for(3), sh_degree=3)
+    cams = synth.ring_views(4, 1280, 1280, 110.0, synth.rng_for(3, salt=1))
+    target_scene = synth.perturbed(scene, synth.rng_for(3, salt=2))
+    R = api.Renderer()
+    cfg = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=16)
+    target = R.render([api.DeviceScene.from_host(target_scene)], [0] * 4, cams, None, cfg).clone()
+    names = ["mean", "log_scale", "quat", "opacity_logit", "sh"]
+    params = {k: torch.tensor(np.asarray(v), device="cuda") for k, v in zip(names, scene.arrays())}
+    opt = api.Adam(params, {"mean": 1.6e-4, "log_scale": 5e-3, "quat": 1e-3, "opacity_logit": 5e-2, "sh": 2.5e-3})
+    ds = api.DeviceScene(*[params[k] for k in names], 3)
+    grads, gflat = ds.flat_zeros_like()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_steps)]
+
+    def step(e=None):
+        if e:
+            e[0].record()
+        img = R.render([ds], [0] * 4, cams, None, cfg, save=True)
+        loss, dimg = R.loss(img, target)
+        gflat.zero_()
+        if e:
+            e[1].record()
+        R.backward([ds], [0] * 4, cams, None, cfg, dimg, [grads])
+        if e:
+            e[2].record()
+        opt.step(dict(zip(names, grads.tensors())))
+        return loss
+
+    l0 = float(step().item())
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(n_steps):
+        loss = step(ev[i])
+    e1.record()
+    torch.cuda.synchronize()
+    R.check()
+    ms = e0.elapsed_time(e1) / n_steps
+    bwd_ms = statistics.mean(b.elapsed_time(c) for _, b, c in ev)
+    R.render([ds], [0] * 4, cams, None, api.RenderConfig(**{**cfg.__dict__, "stats": True}))
+    st = R.stats()
+    R.close()
+    gbs = GRAD_BYTES_PER_BLEND * st["blended"] / (bwd_ms / 1e3) / 1e9
+    return {"value": 1e3 / ms, "unit": "steps/s", "ms_per_step": ms, "loss_first": l0, "loss_last": float(loss.item()),
+            "backward_ms": bwd_ms,
+            "backward_roofline": {"bound": "l2", "achieved": gbs, "peak": peaks["l2_read_gbs"], "unit": "GB/s",
+                                  "frac": gbs / peaks["l2_read_gbs"],
+                                  "basis": f"{GRAD_BYTES_PER_BLEND} B of record-gradient atomics per blended pair x "
+                                           f"{st['blended']} blended pairs of the four views; peak: measured L2 read "
+                                           "bandwidth (vrs_measure_peaks)",
+                                  "work": {"evaluated_pairs": st["evaluated"], "kept_pairs": st["kept"],
+                                           "blended_pairs": st["blended"]}},
+            "config": {"workload": "finetune_500k_4x1280", "step": "render (saved) + loss + backward + Adam",
+                       "timing": "CUDA events; backward_ms is the vrs_render_backward call alone"}}
+
+
 REUSE_FAR_M = 92.0  # 0.25 px of eye-to-cyclopean disparity at f = 722.6 and IPD 64 mm
 
 
@@ -1267,6 +1335,7 @@ def main():
     Rg2.close()
     learned = learned_periphery(api, torch, min(40, args.steps), args.warmup)
     reuse = stereo_reuse(api, torch, min(30, args.steps), args.warmup)
+    finetune = backward_line(api, torch, args.warmup, min(20, args.steps), peaks)
     import ctypes
     from paper_2505_10144_gb300 import _lib
     h2d = 2 * (ctypes.sizeof(_lib.Camera) + ctypes.sizeof(_lib.Fovea))
@@ -1303,6 +1372,7 @@ def main():
         "stage_rooflines": stage_roof,
         "learned_periphery": learned,
         "stereo_reuse": reuse,
+        "finetune": finetune,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "GraphedRender.replay (vrs_update_views + graph replay), then both eyes to pinned host "
                         "memory every frame on a copy stream; two graphed contexts take alternate frames, so a "

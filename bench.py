@@ -306,10 +306,11 @@ def ncu_case(args, api, torch):
     R.close()
 
 
-def run_batched(args, api, torch, ws, rank, pg=None):
+def batched_line(api, torch, n_steps, warmup, cache, ws=1, pg=None, quiet=False):
     """Three scenes (200k, 1M, 3M Gaussians) x 8 head poses x 2 eyes = 48 views of
     2064x2208, foveated, in one vrs_render (one sort, one persistent render launch)
-    captured in a CUDA graph; the autotuner picks the windows and CTA cap."""
+    captured in a CUDA graph; the autotuner picks the key-tile size, the windows and the
+    CTA cap (the fastest candidate above its PSNR floor against the exact order)."""
     from paper_2505_10144_gb300 import autotune, synth
     sizes = [200_000, 1_000_000, 3_000_000]
     scenes = [api.DeviceScene.from_host(synth.shell_scene(n, synth.rng_for(2, salt=k), sh_degree=3))
@@ -327,27 +328,26 @@ def run_batched(args, api, torch, ws, rank, pg=None):
     cams, fovs, vs = views(0)
     R = api.Renderer()
     base = api.RenderConfig(sort_mode="hier", windows=WINDOWS, key_tile=32, fovea_mode="bilinear")
-    cache = args.tune_cache or os.path.join(ROOT, "_build", "autotune.json")
     best, cands = autotune.autotune(R, scenes, vs, cams, fovs, base, cache_path=cache, reps=2)
     R.set_tuning(best["max_ctas_per_sm"])
     cfg = api.RenderConfig(sort_mode="hier", windows=tuple(best["windows"]), key_tile=best["key_tile"],
                            fovea_mode="bilinear")
-    log("autotune candidates (key tile, windows, CTA cap: ms per replay, PSNR vs exact, % pixels > 2e-4):")
-    for c in cands:
-        log(f"  {c['key_tile']:2d}x{c['key_tile']:<2d} {tuple(c['windows'])} cap {c['max_ctas_per_sm']}: "
-            f"{c['ms']:8.2f} ms  {c['psnr_db']:6.2f} dB  {c['over_2e-4_pct']:6.2f} %"
-            f"{'' if c['meets_floor'] else '  (below the floor)'}")
-    log(f"chosen: {best['key_tile']}x{best['key_tile']} {tuple(best['windows'])} cap {best['max_ctas_per_sm']} "
-        f"(floor {best['psnr_floor_db']:.2f} dB)")
+    if not quiet:
+        log("autotune candidates (key tile, windows, CTA cap: ms per replay, PSNR vs exact, % pixels > 2e-4):")
+        for c in cands:
+            log(f"  {c['key_tile']:2d}x{c['key_tile']:<2d} {tuple(c['windows'])} cap {c['max_ctas_per_sm']}: "
+                f"{c['ms']:8.2f} ms  {c['psnr_db']:6.2f} dB  {c['over_2e-4_pct']:6.2f} %"
+                f"{'' if c['meets_floor'] else '  (below the floor)'}")
+        log(f"chosen: {best['key_tile']}x{best['key_tile']} {tuple(best['windows'])} cap {best['max_ctas_per_sm']} "
+            f"(floor {best['psnr_floor_db']:.2f} dB)")
     gr = api.GraphedRender(R, scenes, vs, cams, fovs, cfg)
-    steps = max(args.steps // 10, 3)
-    frames = [views(1 + i) for i in range(steps + args.warmup)]
-    for i in range(args.warmup):
+    frames = [views(1 + i) for i in range(n_steps + warmup)]
+    for i in range(warmup):
         gr.replay(frames[i][0], frames[i][1])
     torch.cuda.synchronize()
     ms = []
-    for i in range(steps):
-        c, f, _ = frames[args.warmup + i]
+    for i in range(n_steps):
+        c, f, _ = frames[warmup + i]
         R.update_views(c, f, cfg)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()  # replay() launches on the current stream
@@ -357,11 +357,9 @@ def run_batched(args, api, torch, ws, rank, pg=None):
         ms.append(e0.elapsed_time(e1))
     R.check()
     st = R.stats()
-    line = {"metric": "batched views/s (3 scenes x 8 poses x 2 eyes, 2064x2208, one graph replay)",
-            "value": job_rate(ws, 48 * len(ms), max_over_ranks(sum(ms), pg)), "unit": "views/s", "n_gpus": ws,
-            "steps": len(ms),
-            "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    R.close()
+    return {"value": job_rate(ws, 48 * len(ms), max_over_ranks(sum(ms), pg)), "unit": "views/s",
+            "ms_per_step": statistics.mean(ms), "p99_ms": float(np.percentile(ms, 99)), "steps": len(ms),
             "config": {"workload": "batched_3_scenes_200k_1M_3M_48_views_foveated", "views": 48,
                        "gaussians": sizes, "graph": "one vrs_render captured in a CUDA graph, poses via vrs_update_views"},
             "autotune": {"best": {k: best[k] for k in ("key_tile", "windows", "max_ctas_per_sm", "ms", "psnr_db",
@@ -370,9 +368,18 @@ def run_batched(args, api, torch, ws, rank, pg=None):
                          "candidates": cands},
             "instances_per_batch": st["instances"], "work_items": st["work_items"],
             "gpu_launches": st["kernels"] * len(ms)}
+
+
+def run_batched(args, api, torch, ws, rank, pg=None):
+    """The batched workload as its own line (see batched_line)."""
+    cache = args.tune_cache or os.path.join(ROOT, "_build", "autotune.json")
+    b = batched_line(api, torch, max(args.steps // 10, 3), args.warmup, cache, ws, pg)
+    line = {"metric": "batched views/s (3 scenes x 8 poses x 2 eyes, 2064x2208, one graph replay)",
+            "value": b["value"], "unit": "views/s", "n_gpus": ws, "steps": b["steps"], "warmup": args.warmup,
+            "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", **{k: v for k, v in b.items() if k not in ("value", "steps")}}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    R.close()
 
 
 def run_finetune(args, api, torch, ws, rank, pg=None):
@@ -1336,6 +1343,7 @@ def main():
     learned = learned_periphery(api, torch, min(40, args.steps), args.warmup)
     reuse = stereo_reuse(api, torch, min(30, args.steps), args.warmup)
     finetune = backward_line(api, torch, args.warmup, min(20, args.steps), peaks)
+    batched = batched_line(api, torch, min(10, args.steps), args.warmup, None, quiet=True)
     import ctypes
     from paper_2505_10144_gb300 import _lib
     h2d = 2 * (ctypes.sizeof(_lib.Camera) + ctypes.sizeof(_lib.Fovea))
@@ -1373,6 +1381,7 @@ def main():
         "learned_periphery": learned,
         "stereo_reuse": reuse,
         "finetune": finetune,
+        "batched": batched,
         "e2e": {"value": e2e_fps, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "path": "GraphedRender.replay (vrs_update_views + graph replay), then both eyes to pinned host "
                         "memory every frame on a copy stream; two graphed contexts take alternate frames, so a "

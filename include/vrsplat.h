@@ -50,7 +50,8 @@ typedef struct vrs_ctx vrs_ctx;
 /* One scene of N Gaussians (Eq. 1), device SoA float32, caller-owned:
  *   mean[3][N], log_scale[3][N], quat[4][N] (w, x, y, z; need not be normalised),
  *   opacity_logit[N] (opacity = sigmoid), sh[K][3][N] with K = (sh_degree + 1)^2,
- *   sh_degree in 0..3.  Non-finite parameters cull the Gaussian. */
+ *   sh_degree in 0..3, 0 <= N <= 2^28 - 1 (VRS_ERR_INVALID otherwise).  Non-finite
+ *   parameters cull the Gaussian. */
 typedef struct {
   const float* mean;
   const float* log_scale;

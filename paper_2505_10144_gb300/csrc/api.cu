@@ -153,7 +153,8 @@ int bits_for(long long n) {
 }
 
 vrs_status check_scene(vrs_ctx* c, const vrs_gaussians& s) {
-  if (s.n < 0 || s.n > (1ll << 31) - 1) return fail(c, VRS_ERR_INVALID, "scene size out of range");
+  // Gaussian indices travel in 28-bit fields of the render's window keys
+  if (s.n < 0 || s.n > (1ll << 28) - 1) return fail(c, VRS_ERR_INVALID, "scene size out of range");
   if (s.sh_degree < 0 || s.sh_degree > 3) return fail(c, VRS_ERR_INVALID, "sh_degree must be 0..3");
   if (s.n > 0 && (!s.mean || !s.log_scale || !s.quat || !s.opacity_logit || !s.sh))
     return fail(c, VRS_ERR_INVALID, "null scene pointer");

@@ -786,6 +786,85 @@ __device__ __forceinline__ unsigned long long win16_pop(Win16<K1>& w, int lane, 
   return e0;
 }
 
+// The 4x4-block window of four entries (K1 = 4), one copy per 2x2 group of its block:
+// lanes 4 c .. 4 c + 3 of a block (its 2x2 block c) hold slots 0 .. 3.  Each slot also
+// carries the depth key of its entry at the centre of the lane's own 2x2 block, computed
+// from the staged record when the entry enters, so a pop hands the 2x2 stage its key
+// without reading the record again from global memory (VR render: the dependent L2 reads
+// cost 0.24 of 5.25 ms).  Keys are (4x4 depth bits << 32) | (index << 4) | the group's
+// four kept-sample bits: indices are below 2^28, so the order stays (depth, index).  The
+// shuffles per insertion are those of Win16 (64-bit key and one 32-bit word).
+struct WinG {
+  unsigned long long e;  // slot lane & 3 of the block's window
+  unsigned k2;           // 2x2-block depth key of that slot's entry, for this lane's 2x2 block
+  int n;                 // entries held by the block's window
+};
+constexpr int kWinGIndexBits = 28;
+
+// insert (x, kx) when do_push, then pop the minimum when the window holds more than four;
+// returns the popped key (kEmptyKey if none) and, through kout, its 2x2-block key
+__device__ __forceinline__ unsigned long long wing_push(WinG& w, unsigned long long x, unsigned kx, bool do_push,
+                                                        int lane, unsigned& kout) {
+  const int j = lane & 3;
+  const unsigned bal = __ballot_sync(kFull, w.e < x);
+  const int pos = __popc((bal >> (lane & ~3)) & 0xFu);
+  const int ju = j > 0 ? j - 1 : 0, jd = j < 3 ? j + 1 : 3;
+  kout = kx;
+  // both blocks of the warp full: the insertion only moves entries towards the head
+  if (__all_sync(kFull, w.n >= 4)) {
+    const unsigned long long fdn = shfl64(w.e, jd, 4), fe0 = shfl64(w.e, 0, 4);
+    const unsigned kdn = __shfl_sync(kFull, w.k2, jd, 4), k0 = __shfl_sync(kFull, w.k2, 0, 4);
+    if (!do_push) return kEmptyKey;
+    if (pos == 0) return x;
+    if (j < pos - 1) {
+      w.e = fdn;
+      w.k2 = kdn;
+    } else if (j == pos - 1) {
+      w.e = x;
+      w.k2 = kx;
+    }
+    kout = k0;
+    return fe0;
+  }
+  const unsigned long long up = shfl64(w.e, ju, 4), dn = shfl64(w.e, jd, 4), e0 = shfl64(w.e, 0, 4);
+  const unsigned kup = __shfl_sync(kFull, w.k2, ju, 4), kdn = __shfl_sync(kFull, w.k2, jd, 4),
+                 k0 = __shfl_sync(kFull, w.k2, 0, 4);
+  if (!do_push) return kEmptyKey;
+  if (w.n < 4) {
+    if (j == pos) {
+      w.e = x;
+      w.k2 = kx;
+    } else if (j > pos) {
+      w.e = up;
+      w.k2 = kup;
+    }
+    ++w.n;
+    return kEmptyKey;
+  }
+  if (pos == 0) return x;
+  if (j < pos - 1) {
+    w.e = dn;
+    w.k2 = kdn;
+  } else if (j == pos - 1) {
+    w.e = x;
+    w.k2 = kx;
+  }
+  kout = k0;
+  return e0;
+}
+
+__device__ __forceinline__ unsigned long long wing_pop(WinG& w, int lane, unsigned& kout) {
+  const int j = lane & 3, jd = j < 3 ? j + 1 : 3;
+  const unsigned long long dn = shfl64(w.e, jd, 4), e0 = shfl64(w.e, 0, 4);
+  const unsigned kdn = __shfl_sync(kFull, w.k2, jd, 4);
+  kout = __shfl_sync(kFull, w.k2, 0, 4);
+  if (w.n == 0) return kEmptyKey;
+  w.e = (j + 1 < w.n) ? dn : kEmptyKey;
+  w.k2 = kdn;
+  --w.n;
+  return e0;
+}
+
 template <int K2>
 struct Win4 {
   static constexpr int R = (K2 + 3) / 4 > 0 ? (K2 + 3) / 4 : 1;
@@ -1156,10 +1235,14 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
       c2y = by2 + 1.f;
     }
     Win16<K1> w1;
+    WinG wg;  // the 4x4-block window when K1 = 4
     Win4<K2> w2;
     w1.e = kEmptyKey;
     w1.pl = 0u;
     w1.n = 0;
+    wg.e = kEmptyKey;
+    wg.k2 = 0u;
+    wg.n = 0;
     float3 hc = make_float3(0.f, 0.f, 0.f);
     // per-sample window: tournament tree when K3 <= 16 (every slot starts empty), else ring
     const bool use_tree = K3 <= 16;
@@ -1194,6 +1277,17 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
       const float4* r = recv + (long long)(x1 != kEmptyKey ? g1 : 0) * kRecF4;
       const unsigned long long x2 =
           win4_push<K2>(w2, pack_key(depth_at(r, c2x, c2y), g1), ((bal >> (lane & ~3)) & 0xFu) != 0u, lane);
+      pop2(x2);
+    };
+    // the same from the grouped window (K1 = 4): x1 carries the group's kept-sample bits
+    // and k2 is the entry's depth key at this lane's 2x2-block centre
+    auto pop1g = [&](unsigned long long x1, unsigned k2) {
+      const bool k = x1 != kEmptyKey && p.active && ((x1 >> (lane & 3)) & 1u);
+      const unsigned bal = __ballot_sync(kFull, k);
+      if (bal == 0u) return;
+      const unsigned g1 = (unsigned)(x1 >> 4) & ((1u << kWinGIndexBits) - 1u);
+      const unsigned long long x2 = win4_push<K2>(w2, ((unsigned long long)k2 << 32) | g1,
+                                                  ((bal >> (lane & ~3)) & 0xFu) != 0u, lane);
       pop2(x2);
     };
     // instance indices fit 32 bits (the instance capacity is below 2^31)
@@ -1263,20 +1357,35 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
             const unsigned bal = __ballot_sync(kFull, k);
             if (bal == 0u) continue;
             const unsigned bm = (bal >> (lane & 16)) & 0xFFFFu;
-            unsigned m1;
-            const unsigned long long x1 =
-                win16_push<K1>(w1, ((unsigned long long)st_k1[e * 2 + (lane >> 4)] << 32) | (unsigned)ge, bm,
-                               bm != 0u, lane, m1);
-            if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1, m1);
+            const unsigned long long k1 = (unsigned long long)st_k1[e * 2 + (lane >> 4)] << 32;
+            if constexpr (K1 == 4) {
+              // the entry's depth key at this lane's 2x2-block centre, from the staged record
+              const unsigned k2 = bm != 0u ? float_order_bits(depth_at(r, c2x, c2y)) : 0u;
+              unsigned k2o;
+              const unsigned long long x1 =
+                  wing_push(wg, k1 | ((unsigned long long)(unsigned)ge << 4) | ((bm >> (lane & 12)) & 0xFu), k2,
+                            bm != 0u, lane, k2o);
+              if (__any_sync(kFull, x1 != kEmptyKey)) pop1g(x1, k2o);
+            } else {
+              unsigned m1;
+              const unsigned long long x1 = win16_push<K1>(w1, k1 | (unsigned)ge, bm, bm != 0u, lane, m1);
+              if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1, m1);
+            }
           }
         }
       }
     }
     if (K1 > 0 || K2 > 0) {
       for (int it = 0; it < K1; ++it) {
-        unsigned m1;
-        const unsigned long long x1 = win16_pop<K1>(w1, lane, m1);
-        if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1, m1);
+        if constexpr (K1 == 4) {
+          unsigned k2o;
+          const unsigned long long x1 = wing_pop(wg, lane, k2o);
+          if (__any_sync(kFull, x1 != kEmptyKey)) pop1g(x1, k2o);
+        } else {
+          unsigned m1;
+          const unsigned long long x1 = win16_pop<K1>(w1, lane, m1);
+          if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1, m1);
+        }
       }
       for (int it = 0; it < K2; ++it) pop2(win4_pop<K2>(w2, lane));
     }

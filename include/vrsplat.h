@@ -258,13 +258,21 @@ vrs_status vrs_set_tuning(vrs_ctx* ctx, int max_render_ctas_per_sm);
 #define VRS_NET_PARAMS 11011
 
 /* Training forward on whole images: d_x, d_y device float [n][3][H][W]; d_acts (device
- * uint16 BF16 bits [n][2][32][H][W], may be NULL) receives the two hidden activations
- * for vrs_net_backward. */
+ * uint16 BF16 bits [n][2][H][W][32], pixel-major, may be NULL) receives the two hidden
+ * activations for vrs_net_backward.  Every convolution runs on the tensor cores
+ * (tcgen05.mma).  Scratch from ctx (128 bytes per pixel when d_acts is NULL).  A
+ * bounded wait that gives up raises bit 1 of the device status word (vrs_check_status);
+ * VRS_ERR_UNSUPPORTED when more of the training kernels' CTAs fit on an SM than its
+ * tensor memory holds. */
 vrs_status vrs_net_forward(vrs_ctx* ctx, const float* d_params, const float* d_x, int n_images, int height, int width,
                            float* d_y, uint16_t* d_acts, void* stream);
 
 /* d_dparams += d<d_dy, y>/d(params) for the forward that wrote d_acts (BF16 rounding
- * treated as identity, ReLU masks from the saved activations).  Scratch from ctx. */
+ * of the forward treated as identity, ReLU masks from the saved activations).  Mixed
+ * precision, like the forward: the data and weight gradients are contractions on the
+ * tensor cores with BF16 operands and FP32 accumulation, so d_dy and the hidden-layer
+ * gradients are rounded to BF16 (nearest even) where they enter one.  Scratch from ctx
+ * (128 bytes per pixel); status and errors as vrs_net_forward. */
 vrs_status vrs_net_backward(vrs_ctx* ctx, const float* d_params, const float* d_x, const uint16_t* d_acts,
                             const float* d_dy, int n_images, int height, int width, float* d_dparams, void* stream);
 

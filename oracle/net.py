@@ -132,3 +132,73 @@ def grads(x: np.ndarray, w: dict, dy: np.ndarray) -> dict:
     y = xt + F.conv2d(a2, wt["w3"], wt["b3"], padding=1)
     (y * torch.tensor(dy, dtype=torch.float64)).sum().backward()
     return {k: v.grad.numpy().copy() for k, v in wm.items()}
+
+
+def _corr(a: torch.Tensor, g: torch.Tensor, cout: int) -> torch.Tensor:
+    """sum over images and pixels p of a[c](p + tap) g[o](p): the weight gradient of a 3x3,
+    pad-1 convolution with input a and output gradient g, [cout, cin, 3, 3]."""
+    return torch.nn.grad.conv2d_weight(a, (cout, a.shape[1], 3, 3), g, padding=1)
+
+
+def _conv_t(g: torch.Tensor, w: torch.Tensor) -> torch.Tensor:
+    """Data gradient of a 3x3, pad-1 convolution with weights w (OIHW): [B, cin, H, W]."""
+    return F.conv_transpose2d(g, w, padding=1)
+
+
+def _rflip(v: torch.Tensor, D: torch.Tensor) -> torch.Tensor:
+    """Largest |bf16(v') - bf16(v)| over |v' - v| <= D (rounding is monotone)."""
+    r = bf16(v)
+    return torch.maximum((bf16(v + D) - r).abs(), (bf16(v - D) - r).abs())
+
+
+def grads_mixed(x: np.ndarray, w: dict, dy: np.ndarray, bound: bool = False, u: float = 2.0 ** -22,
+                round_grads: bool = True):
+    """The parameter gradients of the mixed-precision backward, in float64: BF16 rounding
+    of the forward treated as identity (as in grads), and dy and the hidden gradients
+    dz2 = [a2 > 0] conv_T(dy, w3), dz1 = [a1 > 0] conv_T(dz2, w2) rounded to BF16 where
+    they enter a contraction, the same places the tensor-core backward rounds them.
+    With round_grads=False this is grads.  With bound, also per parameter a bound on how
+    far a backward can land that accumulates with unit roundoff u, rounds at those places
+    and runs on the forward's low-precision activations (within forward_bound's moves,
+    with the ReLU masks they imply): a hidden gradient rounds to the same BF16 value
+    unless its pre-rounding value lies within its accumulation error (plus what the
+    previous gradient's moves add) of a rounding boundary (_rflip), or where the mask may
+    differ (the activation within its move of zero: at most |both values|); a weight
+    gradient sum_p a g then moves by corr(da, |g| + dg) + corr(|a|, dg) plus
+    gamma_n corr(|a| + da, |g| + dg), a bias gradient by sum dg + gamma_n sum(|g| + dg).
+    -> grads dict, or (grads, bound) dicts, float64 numpy."""
+    r = bf16 if round_grads else (lambda z: z)
+    t = {k: bf16(torch.tensor(v, dtype=torch.float64)) if k.startswith("w") else torch.tensor(v, dtype=torch.float64)
+         for k, v in w.items()}
+    xt = torch.tensor(x, dtype=torch.float64)
+    _, _, ((a1, da1), (a2, da2)) = forward_bound(xt, w, u=u, moves=True)
+    xin = bf16(xt)
+    m1, m2 = (a1 > 0).double(), (a2 > 0).double()
+    g3 = r(torch.tensor(dy, dtype=torch.float64))
+    z2 = _conv_t(g3, t["w3"])
+    dz2 = r(m2 * z2)
+    z1 = _conv_t(dz2, t["w2"])
+    dz1 = r(m1 * z1)
+    out = {"w3": _corr(a2, g3, 3), "b3": g3.sum(dim=(0, 2, 3)), "w2": _corr(a1, dz2, 32), "b2": dz2.sum(dim=(0, 2, 3)),
+           "w1": _corr(xin, dz1, 32), "b1": dz1.sum(dim=(0, 2, 3))}
+    out = {k: v.numpy() for k, v in out.items()}
+    if not bound:
+        return out
+    aw = {k: t[k].abs() for k in ("w2", "w3")}
+    flip1 = (da1 > 0) & (a1 <= da1)
+    flip2 = (da2 > 0) & (a2 <= da2)
+    # dz2: K = 3 channels x 9 taps of the same rounded dy on both sides
+    D2 = _gamma(27, u) * _conv_t(g3.abs(), aw["w3"])
+    e2 = torch.where(flip2, 2.02 * (z2.abs() + D2), _rflip(m2 * z2, m2 * D2))
+    # dz1: K = 32 channels x 9 taps of dz2, which may differ by e2
+    D1 = _conv_t(e2, aw["w2"]) + _gamma(288, u) * _conv_t(dz2.abs() + e2, aw["w2"])
+    e1 = torch.where(flip1, 2.02 * (z1.abs() + D1), _rflip(m1 * z1, m1 * D1))
+    gn = _gamma(x.shape[0] * x.shape[2] * x.shape[3], u)
+    bnd = {}
+    for wk, bk, a, da, g, eg, cout in (("w3", "b3", a2, da2, g3, torch.zeros_like(g3), 3),
+                                       ("w2", "b2", a1, da1, dz2, e2, 32),
+                                       ("w1", "b1", xin, torch.zeros_like(xin), dz1, e1, 32)):
+        ga = g.abs() + eg
+        bnd[wk] = (_corr(da, ga, cout) + _corr(a.abs(), eg, cout) + gn * _corr(a.abs() + da, ga, cout)).numpy()
+        bnd[bk] = (eg.sum(dim=(0, 2, 3)) + gn * ga.sum(dim=(0, 2, 3))).numpy()
+    return out, bnd

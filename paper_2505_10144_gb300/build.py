@@ -12,7 +12,7 @@ HERE = Path(__file__).resolve().parent
 CSRC = HERE / "csrc"
 OUT = HERE / "lib"
 LIB = OUT / "libvrsplat.so"
-SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "sort_noalloc.cu", "render.cu", "render_bwd.cu", "loss.cu", "net.cu", "peaks.cu", "probe.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "sort_noalloc.cu", "render.cu", "render_bwd.cu", "loss.cu", "net.cu", "net_train.cu", "peaks.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

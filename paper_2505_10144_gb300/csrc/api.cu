@@ -17,10 +17,12 @@ using namespace vrs;
 namespace vrs {
 void launch_project_only(const SceneDev& s, const ViewParams* d_vp, int T, float* out, float* bbox, uint32_t* count,
                          cudaStream_t st);
-void net_forward_train(const float* params, const float* x, int B, int H, int W, float* y, uint16_t* acts,
-                       uint16_t* tmp_a1, uint16_t* tmp_a2, cudaStream_t st);
-void net_backward_train(const float* params, const float* x, const uint16_t* acts, const float* dy, int B, int H,
-                        int W, float* dparams, float* dz2, float* dz1, cudaStream_t st);
+size_t net_train_pack_bytes();
+bool net_forward_train(const float* params, const float* x, int B, int H, int W, float* y, uint16_t* acts,
+                       uint16_t* a12, uint16_t* wpack, uint32_t* status, cudaStream_t st);
+bool net_backward_train(const float* params, const float* x, const uint16_t* acts, const float* dy, int B, int H,
+                        int W, float* dparams, uint16_t* dz2, uint16_t* dz1, uint16_t* wpack, uint32_t* status,
+                        cudaStream_t st);
 void net_mse(const float* y, const float* t, long long n, float* loss, float* dy, double* scratch, cudaStream_t st);
 void net_periphery(const float* params, const float* low, float* out, const uint8_t* tile_class,
                    const ViewParams* views, int n_views, int tiles_per_view, int W, int H, uint32_t* status,
@@ -960,13 +962,13 @@ vrs_status vrs_net_forward(vrs_ctx* c, const float* d_params, const float* d_x, 
   if (!d_params || !d_x || !d_y || n <= 0 || H <= 0 || W <= 0) return fail(c, VRS_ERR_INVALID, "bad net arguments");
   cudaStream_t st = (cudaStream_t)stream;
   vrs_status s = VRS_OK;
-  uint16_t *t1 = nullptr, *t2 = nullptr;
-  if (!d_acts) {
-    if (!ensure(c, c->net_tmp, sizeof(uint16_t) * 64 * (size_t)n * H * W, capturing(st), &s)) return s;
-    t1 = P<uint16_t>(c->net_tmp);
-    t2 = t1 + (size_t)32 * n * H * W;
-  }
-  net_forward_train(d_params, d_x, n, H, W, d_y, d_acts, t1, t2, st);
+  // the packed weights, and the hidden activations when d_acts is NULL
+  const size_t act_bytes = d_acts ? 0 : sizeof(uint16_t) * 64 * (size_t)n * H * W;
+  if (!ensure(c, c->net_tmp, act_bytes + net_train_pack_bytes(), capturing(st), &s)) return s;
+  uint16_t* wpack = P<uint16_t>(c->net_tmp);
+  uint16_t* a12 = d_acts ? nullptr : wpack + net_train_pack_bytes() / 2;
+  if (!net_forward_train(d_params, d_x, n, H, W, d_y, d_acts, a12, wpack, P<uint32_t>(c->counters) + kCtrStatus, st))
+    return fail(c, VRS_ERR_UNSUPPORTED, "more training CTAs per SM than tensor memory holds");
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "net forward");
 }
@@ -978,10 +980,15 @@ vrs_status vrs_net_backward(vrs_ctx* c, const float* d_params, const float* d_x,
     return fail(c, VRS_ERR_INVALID, "bad net arguments");
   cudaStream_t st = (cudaStream_t)stream;
   vrs_status s = VRS_OK;
-  if (!ensure(c, c->net_tmp, sizeof(float) * 64 * (size_t)n * H * W, capturing(st), &s)) return s;
-  float* dz2 = P<float>(c->net_tmp);
-  float* dz1 = dz2 + (size_t)32 * n * H * W;
-  net_backward_train(d_params, d_x, d_acts, d_dy, n, H, W, d_dparams, dz2, dz1, st);
+  // the packed weights and the hidden-layer gradients dz2, dz1 (BF16, pixel-major)
+  if (!ensure(c, c->net_tmp, net_train_pack_bytes() + sizeof(uint16_t) * 64 * (size_t)n * H * W, capturing(st), &s))
+    return s;
+  uint16_t* wpack = P<uint16_t>(c->net_tmp);
+  uint16_t* dz2 = wpack + net_train_pack_bytes() / 2;
+  uint16_t* dz1 = dz2 + (size_t)32 * n * H * W;
+  if (!net_backward_train(d_params, d_x, d_acts, d_dy, n, H, W, d_dparams, dz2, dz1, wpack,
+                          P<uint32_t>(c->counters) + kCtrStatus, st))
+    return fail(c, VRS_ERR_UNSUPPORTED, "more training CTAs per SM than tensor memory holds");
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VRS_OK : cuda_fail(c, e, "net backward");
 }

@@ -9,196 +9,24 @@
 //   w1[32][3][3][3] b1[32] w2[32][32][3][3] b2[32] w3[3][32][3][3] b3[3]
 // (float master weights; every kernel rounds them to BF16 when it loads them).
 //
-// Two kinds of kernels:
-//  - training (any image size, activations saved for the backward): direct 3x3
-//    convolutions in FP32 SIMT arithmetic on BF16 values, plus the data and weight
-//    gradients;
-//  - inference on the periphery tiles of a rendered frame: one fused kernel, all three
-//    layers of a 32x32 tile in shared memory as implicit GEMMs on the tensor cores
-//    (tcgen05.mma, BF16 -> FP32 accumulators in tensor memory), reading the
-//    half-resolution image directly.
+// This file holds the inference on the periphery tiles of a rendered frame: one fused
+// kernel, all three layers of a 32x32 tile in shared memory as implicit GEMMs on the
+// tensor cores (tcgen05.mma, BF16 -> FP32 accumulators in tensor memory), reading the
+// half-resolution image directly; and the MSE loss.  The training kernels (any image
+// size, activations saved for the backward, data and weight gradients) are in
+// net_train.cu.
 #include <cuda_bf16.h>
 
 #include <algorithm>
 
 #include "common.cuh"
+#include "net.cuh"
 
 namespace vrs {
 
-constexpr int kNetCh = 32;
-constexpr int kW1 = 0, kB1 = 864, kW2 = 896, kB2 = 10112, kW3 = 10144, kB3 = 11008, kNetParams = 11011;
-static_assert(kB1 == kW1 + kNetCh * 3 * 9 && kW2 == kB1 + kNetCh && kB2 == kW2 + kNetCh * kNetCh * 9 &&
-                  kW3 == kB2 + kNetCh && kB3 == kW3 + 3 * kNetCh * 9 && kNetParams == kB3 + 3,
-              "parameter offsets (OIHW)");
+
 
 namespace {
-
-__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-
-__device__ __forceinline__ uint16_t bf16bits(float v) {
-  const __nv_bfloat16 b = __float2bfloat16_rn(v);
-  return *reinterpret_cast<const uint16_t*>(&b);
-}
-
-__device__ __forceinline__ float bits2f(uint16_t u) {
-  return __uint_as_float(((uint32_t)u) << 16);
-}
-
-// ------------------------------------------------------------------ training kernels
-
-// One CTA = 16x16 output pixels of one image; input tile with a one-pixel halo in
-// shared memory, weights in shared memory (BF16 values as float).  LAYER 1 reads the
-// float input x (rounded to BF16), layers 2-3 read saved BF16 activations.  Layers 1-2
-// write BF16(relu(.)), layer 3 writes x + conv + b3 in float.
-template <int CIN, int COUT, int LAYER>
-__global__ void __launch_bounds__(256) conv_fwd_kernel(const float* __restrict__ params, const float* __restrict__ x,
-                                                       const uint16_t* __restrict__ act_in,
-                                                       uint16_t* __restrict__ act_out, float* __restrict__ y, int H,
-                                                       int W) {
-  extern __shared__ __align__(16) float smf[];
-  float(*in_s)[18][18] = reinterpret_cast<float(*)[18][18]>(smf);
-  float(*w_s)[CIN * 9] = reinterpret_cast<float(*)[CIN * 9]>(smf + CIN * 324);
-  float* b_s = smf + CIN * 324 + COUT * CIN * 9;
-  const int woff = LAYER == 1 ? kW1 : (LAYER == 2 ? kW2 : kW3);
-  const int boff = LAYER == 1 ? kB1 : (LAYER == 2 ? kB2 : kB3);
-  for (int k = threadIdx.x; k < COUT * CIN * 9; k += 256) w_s[k / (CIN * 9)][k % (CIN * 9)] = bf16r(params[woff + k]);
-  if (threadIdx.x < COUT) b_s[threadIdx.x] = params[boff + threadIdx.x];
-  const int img = blockIdx.z;
-  const int ox = blockIdx.x * 16, oy = blockIdx.y * 16;
-  const long long HW = (long long)H * W;
-  for (int k = threadIdx.x; k < CIN * 324; k += 256) {
-    const int c = k / 324, r = k % 324, iy = oy - 1 + r / 18, ix = ox - 1 + r % 18;
-    float v = 0.f;
-    if (iy >= 0 && iy < H && ix >= 0 && ix < W) {
-      const long long idx = ((long long)img * CIN + c) * HW + (long long)iy * W + ix;
-      v = LAYER == 1 ? bf16r(x[idx]) : bits2f(act_in[idx]);
-    }
-    in_s[c][r / 18][r % 18] = v;
-  }
-  __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int px = ox + tx, py = oy + ty;
-  float acc[COUT];
-#pragma unroll
-  for (int o = 0; o < COUT; ++o) acc[o] = b_s[o];
-  for (int c = 0; c < CIN; ++c)
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const float v = in_s[c][ty + k / 3][tx + k % 3];
-#pragma unroll
-      for (int o = 0; o < COUT; ++o) acc[o] = fmaf(w_s[o][c * 9 + k], v, acc[o]);
-    }
-  if (px >= W || py >= H) return;
-  const long long p = (long long)py * W + px;
-#pragma unroll
-  for (int o = 0; o < COUT; ++o) {
-    const long long idx = ((long long)img * COUT + o) * HW + p;
-    if (LAYER == 3)
-      y[idx] = x[idx] + acc[o];
-    else
-      act_out[idx] = bf16bits(fmaxf(acc[o], 0.f));
-  }
-}
-
-// dIn = conv_transpose(dOut, W), then the ReLU mask of the input activation (layers 2,
-// 3 inputs are post-ReLU BF16 activations: mask = act > 0).
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(256) conv_bwd_data_kernel(const float* __restrict__ params, int woff,
-                                                            const float* __restrict__ dout,
-                                                            const uint16_t* __restrict__ act_in,
-                                                            float* __restrict__ din, int H, int W) {
-  extern __shared__ __align__(16) float smf[];
-  float(*d_s)[18][18] = reinterpret_cast<float(*)[18][18]>(smf);
-  float(*w_s)[CIN * 9] = reinterpret_cast<float(*)[CIN * 9]>(smf + COUT * 324);
-  for (int k = threadIdx.x; k < COUT * CIN * 9; k += 256) w_s[k / (CIN * 9)][k % (CIN * 9)] = bf16r(params[woff + k]);
-  const int img = blockIdx.z;
-  const int ox = blockIdx.x * 16, oy = blockIdx.y * 16;
-  const long long HW = (long long)H * W;
-  for (int k = threadIdx.x; k < COUT * 324; k += 256) {
-    const int c = k / 324, r = k % 324, iy = oy - 1 + r / 18, ix = ox - 1 + r % 18;
-    float v = 0.f;
-    if (iy >= 0 && iy < H && ix >= 0 && ix < W) v = dout[((long long)img * COUT + c) * HW + (long long)iy * W + ix];
-    d_s[c][r / 18][r % 18] = v;
-  }
-  __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int px = ox + tx, py = oy + ty;
-  if (px >= W || py >= H) return;
-  float acc[CIN];
-#pragma unroll
-  for (int c = 0; c < CIN; ++c) acc[c] = 0.f;
-  // in(q) feeds out(q - (ky - 1, kx - 1)) with weight w[o][c][ky][kx]
-  for (int o = 0; o < COUT; ++o)
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      const float g = d_s[o][ty + 2 - k / 3][tx + 2 - k % 3];
-#pragma unroll
-      for (int c = 0; c < CIN; ++c) acc[c] = fmaf(w_s[o][c * 9 + k], g, acc[c]);
-    }
-  const long long p = (long long)py * W + px;
-#pragma unroll
-  for (int c = 0; c < CIN; ++c) {
-    const long long idx = ((long long)img * CIN + c) * HW + p;
-    din[idx] = act_in[idx] != 0 ? acc[c] : 0.f;
-  }
-}
-
-// dW[o][c][k] += sum over pixels of dOut[o](p) in[c](p + k - 1); dB[o] += sum dOut[o](p).
-// Persistent CTAs over 16x16 tiles; one shared-memory accumulator per weight, flushed with
-// one global atomic per weight per CTA.
-template <int CIN, int COUT, int LAYER>
-__global__ void __launch_bounds__(256) conv_bwd_weight_kernel(const float* __restrict__ x,
-                                                              const uint16_t* __restrict__ act_in,
-                                                              const float* __restrict__ dout, int n_images, int H,
-                                                              int W, float* __restrict__ dparams) {
-  extern __shared__ __align__(16) float smf[];
-  float(*in_s)[18][18] = reinterpret_cast<float(*)[18][18]>(smf);
-  float(*d_s)[16][16] = reinterpret_cast<float(*)[16][16]>(smf + CIN * 324);
-  float* acc_s = smf + CIN * 324 + COUT * 256;
-  const int nw = COUT * CIN * 9;
-  for (int k = threadIdx.x; k < nw + COUT; k += 256) acc_s[k] = 0.f;
-  const int tiles_x = (W + 15) / 16, tiles_y = (H + 15) / 16;
-  const long long n_tiles = (long long)tiles_x * tiles_y * n_images;
-  const long long HW = (long long)H * W;
-  for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    const int img = (int)(t / (tiles_x * tiles_y));
-    const int r0 = (int)(t % (tiles_x * tiles_y));
-    const int ox = (r0 % tiles_x) * 16, oy = (r0 / tiles_x) * 16;
-    __syncthreads();
-    for (int k = threadIdx.x; k < CIN * 324; k += 256) {
-      const int c = k / 324, r = k % 324, iy = oy - 1 + r / 18, ix = ox - 1 + r % 18;
-      float v = 0.f;
-      if (iy >= 0 && iy < H && ix >= 0 && ix < W) {
-        const long long idx = ((long long)img * CIN + c) * HW + (long long)iy * W + ix;
-        v = LAYER == 1 ? bf16r(x[idx]) : bits2f(act_in[idx]);
-      }
-      in_s[c][r / 18][r % 18] = v;
-    }
-    for (int k = threadIdx.x; k < COUT * 256; k += 256) {
-      const int o = k / 256, r = k % 256, iy = oy + r / 16, ix = ox + r % 16;
-      d_s[o][r / 16][r % 16] = (iy < H && ix < W) ? dout[((long long)img * COUT + o) * HW + (long long)iy * W + ix] : 0.f;
-    }
-    __syncthreads();
-    for (int wi = threadIdx.x; wi < nw + COUT; wi += 256) {
-      float s = 0.f;
-      if (wi < nw) {
-        const int o = wi / (CIN * 9), c = (wi / 9) % CIN, k = wi % 9, ky = k / 3, kx = k % 3;
-        for (int yy = 0; yy < 16; ++yy)
-#pragma unroll 4
-          for (int xx = 0; xx < 16; ++xx) s = fmaf(d_s[o][yy][xx], in_s[c][yy + ky][xx + kx], s);
-      } else {
-        const int o = wi - nw;
-        for (int r = 0; r < 256; ++r) s += d_s[o][r / 16][r % 16];
-      }
-      acc_s[wi] += s;
-    }
-  }
-  __syncthreads();
-  const int woff = LAYER == 1 ? kW1 : (LAYER == 2 ? kW2 : kW3);
-  const int boff = LAYER == 1 ? kB1 : (LAYER == 2 ? kB2 : kB3);
-  for (int k = threadIdx.x; k < nw; k += 256) atomicAdd(&dparams[woff + k], acc_s[k]);
-  for (int k = threadIdx.x; k < COUT; k += 256) atomicAdd(&dparams[boff + k], acc_s[nw + k]);
-}
 
 __global__ void mse_kernel(const float* __restrict__ y, const float* __restrict__ t, long long n, double* sum,
                            float* __restrict__ dy, float scale) {
@@ -209,7 +37,15 @@ __global__ void mse_kernel(const float* __restrict__ y, const float* __restrict_
     if (dy) dy[i] = scale * d;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(sum, s);
+  // one atomic per block (one per warp serialised on the single address)
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    atomicAdd(sum, t);
+  }
 }
 
 __global__ void mse_finalize_kernel(const double* sum, long long n, float* loss) { *loss = (float)(*sum / (double)n); }
@@ -287,92 +123,6 @@ constexpr int kBarReady = 16 * kAcc, kBarAbort = kBarReady + 8, kBarTslot = kBar
 constexpr int kNetSmem = kOffBar + kBarReady + 16;
 static_assert(kNetSmem <= 227 * 1024, "net tile does not fit in shared memory");
 static_assert((kOffR0 | kOffR1) % 1024 == 0 && (kOffW2 | kOffW3) % 16 == 0, "operand alignment");
-constexpr long long kWaitLimit = 1ll << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// shared-memory matrix descriptor: no swizzle, K-core stride lbo, 8-row-group stride 128 B
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
-}
-
-// shared-memory matrix descriptor, K-major with a 32-byte (layout 6) or 64-byte (layout
-// 4) swizzle: rows of 32 or 64 bytes, 8-row groups sbo bytes apart; the swizzle acts on
-// absolute address bits (XOR of bits 7 (.. 8) into bits 4 (.. 5)), so a start shifted by
-// whole rows, or by 32 bytes along K inside a 64-byte row, needs no base offset
-__device__ __forceinline__ uint64_t umma_desc_sw(uint32_t addr, uint32_t sbo, uint32_t layout) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) |
-         (1ull << 46) | ((uint64_t)layout << 61);
-}
-
-// instruction descriptor: BF16 A and B (K-major), FP32 accumulator, M x N
-__device__ __forceinline__ uint32_t umma_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar));
-}
-
-// waits for the phase of the given parity; false when the wait gave up or another thread
-// of the block did (*abort)
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile uint32_t* abort,
-                                          long long limit = kWaitLimit) {
-  uint32_t done = 0;
-  for (long long it = 0; it < limit && !done; ++it) {
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity));
-    if (!done && *abort) return false;
-  }
-  if (!done) *abort = 1u;
-  return done != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
-  uint32_t r[32];
-  __syncwarp();
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
-}
-
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float v[4]) {
-  uint32_t r[4];
-  __syncwarp();
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int c = 0; c < 4; ++c) v[c] = __uint_as_float(r[c]);
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 // bilinear x2 upsample (half-pixel aligned, clamped to the edge) at full-resolution pixel
 // (x, y), read from the shared half-resolution patch P: patch column j, row i hold the
 // image's column clamp(px0 + j), row clamp(py0 + i), so the taps x0 - px0 and x0 - px0 + 1
@@ -439,16 +189,6 @@ __global__ void mbar_timeout_kernel(uint32_t* status, int limit) {
   __syncthreads();
   const bool ok = mbar_wait(smem_u32(&bar), 0u, &abort, limit);
   if (!ok && threadIdx.x == 0) atomicOr(status, kStTimeout);
-}
-
-// 8 BF16 values of one 16-byte plane slot
-__device__ __forceinline__ uint4 pack8(const float* v) {
-  uint4 q;
-  q.x = (uint32_t)bf16bits(v[0]) | ((uint32_t)bf16bits(v[1]) << 16);
-  q.y = (uint32_t)bf16bits(v[2]) | ((uint32_t)bf16bits(v[3]) << 16);
-  q.z = (uint32_t)bf16bits(v[4]) | ((uint32_t)bf16bits(v[5]) << 16);
-  q.w = (uint32_t)bf16bits(v[6]) | ((uint32_t)bf16bits(v[7]) << 16);
-  return q;
 }
 
 __global__ void __launch_bounds__(kNetThreads, 1) net_periphery_kernel(const float* __restrict__ params,
@@ -699,60 +439,6 @@ unsigned grid_for(long long n) {
 }
 
 }  // namespace
-
-template <int CIN, int COUT, int LAYER>
-void launch_conv_fwd(dim3 grid, const float* params, const float* x, const uint16_t* ain, uint16_t* aout, float* y,
-                     int H, int W, cudaStream_t st) {
-  const int smem = (CIN * 324 + COUT * CIN * 9 + COUT) * 4;
-  static std::atomic<int> smem_set[kMemoDevices];
-  ensure_dynamic_smem(smem_set, conv_fwd_kernel<CIN, COUT, LAYER>, smem);
-  conv_fwd_kernel<CIN, COUT, LAYER><<<grid, 256, smem, st>>>(params, x, ain, aout, y, H, W);
-}
-
-template <int CIN, int COUT>
-void launch_conv_bwd_data(dim3 grid, const float* params, int woff, const float* dout, const uint16_t* ain, float* din,
-                          int H, int W, cudaStream_t st) {
-  const int smem = (COUT * 324 + COUT * CIN * 9) * 4;
-  static std::atomic<int> smem_set[kMemoDevices];
-  ensure_dynamic_smem(smem_set, conv_bwd_data_kernel<CIN, COUT>, smem);
-  conv_bwd_data_kernel<CIN, COUT><<<grid, 256, smem, st>>>(params, woff, dout, ain, din, H, W);
-}
-
-template <int CIN, int COUT, int LAYER>
-void launch_conv_bwd_weight(unsigned grid, const float* x, const uint16_t* ain, const float* dout, int B, int H, int W,
-                            float* dparams, cudaStream_t st) {
-  const int smem = (CIN * 324 + COUT * 256 + COUT * CIN * 9 + COUT) * 4;
-  static std::atomic<int> smem_set[kMemoDevices];
-  ensure_dynamic_smem(smem_set, conv_bwd_weight_kernel<CIN, COUT, LAYER>, smem);
-  conv_bwd_weight_kernel<CIN, COUT, LAYER><<<grid, 256, smem, st>>>(x, ain, dout, B, H, W, dparams);
-}
-
-// training forward: y[B][3][H][W], acts[B][2][32][H][W] (BF16 bits; a1 then a2)
-void net_forward_train(const float* params, const float* x, int B, int H, int W, float* y, uint16_t* acts,
-                       uint16_t* tmp_a1, uint16_t* tmp_a2, cudaStream_t st) {
-  const dim3 grid((W + 15) / 16, (H + 15) / 16, B);
-  uint16_t* a1 = acts ? acts : tmp_a1;
-  uint16_t* a2 = acts ? acts + (size_t)B * 32 * H * W : tmp_a2;
-  launch_conv_fwd<3, 32, 1>(grid, params, x, nullptr, a1, nullptr, H, W, st);
-  launch_conv_fwd<32, 32, 2>(grid, params, nullptr, a1, a2, nullptr, H, W, st);
-  launch_conv_fwd<32, 3, 3>(grid, params, x, a2, nullptr, y, H, W, st);
-}
-
-// training backward: dparams += d<dy, y>/dparams (BF16 rounding passes gradients straight
-// through; ReLU masks from the saved activations); scratch: 2 x [B][32][H][W] floats
-void net_backward_train(const float* params, const float* x, const uint16_t* acts, const float* dy, int B, int H,
-                        int W, float* dparams, float* dz2, float* dz1, cudaStream_t st) {
-  const dim3 grid((W + 15) / 16, (H + 15) / 16, B);
-  const uint16_t* a1 = acts;
-  const uint16_t* a2 = acts + (size_t)B * 32 * H * W;
-  const long long tiles = (long long)((W + 15) / 16) * ((H + 15) / 16) * B;
-  const unsigned wgrid = (unsigned)std::min<long long>(tiles, (long long)device_sm_count() * 2);
-  launch_conv_bwd_weight<32, 3, 3>(wgrid, nullptr, a2, dy, B, H, W, dparams, st);
-  launch_conv_bwd_data<32, 3>(grid, params, kW3, dy, a2, dz2, H, W, st);
-  launch_conv_bwd_weight<32, 32, 2>(wgrid, nullptr, a1, dz2, B, H, W, dparams, st);
-  launch_conv_bwd_data<32, 32>(grid, params, kW2, dz2, a1, dz1, H, W, st);
-  launch_conv_bwd_weight<3, 32, 1>(wgrid, x, nullptr, dz1, B, H, W, dparams, st);
-}
 
 void net_mse(const float* y, const float* t, long long n, float* loss, float* dy, double* scratch, cudaStream_t st) {
   cudaMemsetAsync(scratch, 0, sizeof(double), st);

@@ -61,7 +61,7 @@ class PeripheryNet:
         x = x.contiguous()
         B, _, H, W = x.shape
         y = torch.empty_like(x)
-        acts = torch.empty((B, 2, 32, H, W), dtype=torch.int16, device="cuda") if save else None
+        acts = torch.empty((B, 2, H, W, 32), dtype=torch.int16, device="cuda") if save else None
         self.R._check(self.R.lib.vrs_net_forward(self.R.ctx, _p(self.params), _p(x), B, H, W, _p(y), _p(acts), _s()))
         return y, acts
 

@@ -7,6 +7,7 @@ import os
 import numpy as np
 import pytest
 import torch
+import torch.nn.functional as F
 from scipy.optimize import minimize_scalar
 from scipy.spatial.transform import Rotation
 
@@ -855,6 +856,112 @@ def test_net_conv_matches_direct_sum_and_zero_last_layer_is_identity():
     w0 = onet.init_weights(rng, zero_last=True)
     y0, _ = onet.forward(torch.tensor(x), w0)
     assert np.array_equal(y0.numpy(), x)
+
+
+def _net_case(seed, signed, shape=(2, 3, 11, 13)):
+    """Weights (BF16 values), input and output gradient: random signs, or all >= 0 (no
+    cancellation anywhere, so the mixed-precision bound is tight)."""
+    rng = np.random.default_rng(seed)
+    w = onet.init_weights(rng)
+    if not signed:
+        w = {k: np.abs(v) if k.startswith("w") else np.abs(rng.normal(0, 0.1, size=v.shape)) for k, v in w.items()}
+    w["w3"] = w["w3"] * 10.0
+    w = {k: onet.bf16(torch.tensor(v)).numpy() if k.startswith("w") else v for k, v in w.items()}
+    x = rng.uniform(0, 1, size=shape)
+    dy = (rng.normal(size=shape) if signed else rng.uniform(0, 1, size=shape)).astype(np.float32).astype(np.float64)
+    return w, x, dy
+
+
+def test_net_grads_match_direct_sums():
+    """The straight-through gradients against the backward written out as sums: dz2 =
+    [a2 > 0] sum_{o, tap} w3[o][c][tap] dy[o](p - tap + 1), dz1 likewise through w2, and
+    each weight gradient sum_p a[c](p + tap - 1) dz[o](p)."""
+    w, x, dy = _net_case(5, True, shape=(1, 3, 5, 6))
+    g = onet.grads(x, w, dy)
+    _, (xin, a1, a2) = onet.forward(torch.tensor(x), w)
+    xin, a1, a2 = xin.numpy(), a1.numpy(), a2.numpy()
+    H, W = x.shape[2:]
+
+    def data_grad(gz, wk, mask):
+        cin = w[wk].shape[1]
+        out = np.zeros((1, cin, H, W))
+        for c in range(cin):
+            for py in range(H):
+                for px in range(W):
+                    s = 0.0
+                    for o in range(w[wk].shape[0]):
+                        for ky in range(3):
+                            for kx in range(3):
+                                qy, qx = py - ky + 1, px - kx + 1
+                                if 0 <= qy < H and 0 <= qx < W:
+                                    s += w[wk][o, c, ky, kx] * gz[0, o, qy, qx]
+                    out[0, c, py, px] = s if mask[0, c, py, px] > 0 else 0.0
+        return out
+
+    def weight_grad(a, gz):
+        cin, cout = a.shape[1], gz.shape[1]
+        ap = np.pad(a, ((0, 0), (0, 0), (1, 1), (1, 1)))
+        return np.array([[[[np.sum(ap[0, c, ky:ky + H, kx:kx + W] * gz[0, o]) for kx in range(3)] for ky in range(3)]
+                          for c in range(cin)] for o in range(cout)])
+
+    dz2 = data_grad(dy, "w3", a2)
+    dz1 = data_grad(dz2, "w2", a1)
+    ref = {"w3": weight_grad(a2, dy), "b3": dy.sum(axis=(0, 2, 3)), "w2": weight_grad(a1, dz2),
+           "b2": dz2.sum(axis=(0, 2, 3)), "w1": weight_grad(xin, dz1), "b1": dz1.sum(axis=(0, 2, 3))}
+    for k in ref:
+        assert np.abs(g[k] - ref[k]).max() <= 1e-10 * max(1.0, np.abs(ref[k]).max()), k
+
+
+def test_net_mixed_gradients_without_rounding_are_the_straight_through_ones():
+    w, x, dy = _net_case(6, True)
+    g, g0 = onet.grads(x, w, dy), onet.grads_mixed(x, w, dy, round_grads=False)
+    for k in g:
+        assert np.abs(g[k] - g0[k]).max() <= 1e-12 * np.abs(g[k]).max(), k
+
+
+def _emulate_backward_fp32(x, w, dy, flip_taps=True, round_dz2=True):
+    """The tensor-core backward's arithmetic emulated with float32 library convolutions
+    (sequential-order GEMMs: the oneDNN path, which may use Winograd, is off): BF16
+    weights, activations and gradient operands, float32 accumulation."""
+    f = torch.float32
+
+    def bfr(z):
+        return z.to(torch.bfloat16).to(f)
+
+    wt = {k: bfr(torch.tensor(v, dtype=f)) if k.startswith("w") else torch.tensor(v, dtype=f) for k, v in w.items()}
+    with torch.backends.mkldnn.flags(enabled=False):
+        xin = bfr(torch.tensor(x, dtype=f))
+        a1 = bfr(torch.relu(F.conv2d(xin, wt["w1"], wt["b1"], padding=1)))
+        a2 = bfr(torch.relu(F.conv2d(a1, wt["w2"], wt["b2"], padding=1)))
+        g3 = bfr(torch.tensor(dy, dtype=f))
+
+        def ct(g, wk):
+            return F.conv_transpose2d(g, wt[wk] if flip_taps else wt[wk].flip(2, 3), padding=1)
+
+        dz2 = (a2 > 0) * ct(g3, "w3")
+        dz2 = bfr(dz2) if round_dz2 else dz2
+        dz1 = bfr((a1 > 0) * ct(dz2, "w2"))
+
+        def cw(a, g, co):
+            return torch.nn.grad.conv2d_weight(a, (co, a.shape[1], 3, 3), g, padding=1)
+
+        out = {"w3": cw(a2, g3, 3), "b3": g3.sum((0, 2, 3)), "w2": cw(a1, dz2, 32), "b2": dz2.sum((0, 2, 3)),
+               "w1": cw(xin, dz1, 32), "b1": dz1.sum((0, 2, 3))}
+    return {k: v.double().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_net_mixed_gradient_bound_holds_for_an_fp32_evaluation_and_catches_mistakes(signed):
+    w, x, dy = _net_case(7, signed)
+    g, b = onet.grads_mixed(x, w, dy, bound=True)
+    emu = _emulate_backward_fp32(x, w, dy)
+    worst = max(float((np.abs(emu[k] - g[k]) / np.maximum(b[k], 1e-300)).max()) for k in g)
+    assert worst <= 1.0, worst
+    if not signed:  # no cancellation: the bound is tight (under 0.1% of each gradient)
+        assert all((b[k] <= 1e-3 * np.abs(g[k])).all() for k in g)
+        for bad in (dict(flip_taps=False), dict(round_dz2=False)):
+            emu = _emulate_backward_fp32(x, w, dy, **bad)
+            assert any((np.abs(emu[k] - g[k]) > b[k]).any() for k in g), bad
 
 
 def test_bilinear_upsampling_pins():

@@ -271,8 +271,27 @@ def run_reference(args, ws, rank):
 
 
 def ncu_case(args, api, torch):
-    """Frames only: the workload at args.scale resolution, nothing else on the GPU."""
+    """Frames only: the workload at args.scale resolution, nothing else on the GPU (or,
+    with --train, periphery-network training steps only)."""
     from paper_2505_10144_gb300 import synth
+    if args.train:
+        from paper_2505_10144_gb300 import periphery
+        R = api.Renderer()
+        net = periphery.PeripheryNet(R, seed=4)
+        rng = np.random.default_rng(7)
+        x = torch.tensor(rng.uniform(0, 1, size=(8, 3, 256, 256)).astype(np.float32)).cuda()
+        t = torch.tensor(rng.uniform(0, 1, size=(8, 3, 256, 256)).astype(np.float32)).cuda()
+        for _ in range(args.warmup + args.steps):
+            y, acts = net.forward(x)
+            _, dy = net.mse(y, t)
+            net.grad.zero_()
+            net.backward(x, acts, dy)
+            net.step(1e-3)
+        R.check()
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": True, "train_steps": args.warmup + args.steps, "batch": 8, "crop": 256}))
+        R.close()
+        return
     W, H = int(W_IMG * args.scale) // 32 * 32, int(H_IMG * args.scale) // 32 * 32
     scene = synth.shell_scene(N_GAUSS, synth.rng_for(1), sh_degree=3)
     wl = synth.vr_trajectory(args.warmup + args.steps, synth.rng_for(1, salt=100), W, H)
@@ -611,8 +630,54 @@ def learned_periphery(api, torch, n_steps, warmup):
                                              "pixels (halo recompute not counted); peak: sustained BF16 "
                                              + rp["source"]},
             "weights": "paper_2505_10144_gb300/weights/periphery_1m.npy", "training": meta,
+            "training_step": network_training_step(R, periphery, torch, rp),
             "config": {"workload": "learned_periphery_1M_stereo_2064x2208", "timing": "CUDA events per frame, "
                        "eager render + network launch, L2 flushed between frames"}}
+
+
+# multiply-adds per pixel of one training step: forward 27x32 + 288x32 + 288x3, data
+# gradients 27x32 (through w3) + 288x32 (through w2), weight gradients 288x3 + 288x32 + 27x32
+TRAIN_FLOP_PER_PX = 2 * ((27 * 32 + 288 * 32 + 288 * 3) + (27 * 32 + 288 * 32) + (288 * 3 + 288 * 32 + 27 * 32))
+
+
+def network_training_step(R, periphery, torch, rp, batch=8, size=256, steps=30, warmup=5):
+    """One training step of the periphery network as train_periphery runs it (batch 8 of
+    256x256 crops): forward, MSE, backward and Adam, every contraction on the tensor cores.
+    Timed with CUDA events over `steps` steps on seeded synthetic images (the time does
+    not depend on the values), with the tensor roofline of its algorithmic FLOPs."""
+    net = periphery.PeripheryNet(R, seed=4)
+    rng = np.random.default_rng(7)
+    x = torch.tensor(rng.uniform(0, 1, size=(batch, 3, size, size)).astype(np.float32)).cuda()
+    t = torch.tensor(rng.uniform(0, 1, size=(batch, 3, size, size)).astype(np.float32)).cuda()
+
+    def step():
+        y, acts = net.forward(x)
+        _, dy = net.mse(y, t)
+        net.grad.zero_()
+        net.backward(x, acts, dy)
+        net.step(1e-3)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    R.check()
+    ms = e0.elapsed_time(e1) / steps
+    flops = TRAIN_FLOP_PER_PX * batch * size * size
+    tfl = flops / (ms * 1e-3) / 1e12
+    return {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "batch": batch, "crop": size,
+            "roofline": {"bound": "tensor", "achieved": tfl, "peak": rp["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                         "frac": tfl / rp["bf16_tflops_sustained"], "algorithmic_flops": flops,
+                         "basis": f"{TRAIN_FLOP_PER_PX} FLOP per pixel (forward, data and weight gradients, no "
+                                  "padding counted) over the step's CUDA-event time, MSE and Adam included; peak: "
+                                  "sustained BF16 " + rp["source"]},
+            "kernels": "conv_tc_kernel (forward layers, data gradients), wgrad_tc_kernel (weight gradients): "
+                       "tcgen05.mma BF16 -> FP32"}
 
 
 GRAD_BYTES_PER_BLEND = 64  # each blended pair adds its 16 record-gradient floats with four 16-byte atomics
@@ -1010,6 +1075,8 @@ def main():
     ap.add_argument("--backward", action="store_true", help="--ncu-case: also run the backward pass of every frame")
     ap.add_argument("--stats", action="store_true", help="--ncu-case: print the device counters of the last frame")
     ap.add_argument("--net", action="store_true", help="--ncu-case: learned periphery (network on the periphery)")
+    ap.add_argument("--train", action="store_true",
+                    help="--ncu-case: periphery-network training steps only (batch 8 of 256x256 crops)")
     ap.add_argument("--workload", default="vr", choices=["vr", "batched", "finetune", "net"],
                     help="vr: the headline stereo frame; batched: 3 scenes x 8 poses x 2 eyes in one graph "
                          "replay; finetune: 4 views at 1280^2, render + loss + backward + Adam")

@@ -605,6 +605,8 @@ def learned_periphery(api, torch, n_steps, warmup):
             meta = json.load(fh)
     except (OSError, ValueError):
         pass
+    del scene
+    train_step = network_training_step(R, periphery, torch, rp)
     R.close()
     return {"value": len(ms_net) / (sum(ms_net) / 1e3), "unit": "frames/s", "ms_per_step": statistics.mean(ms_net),
             "p50_ms": float(np.percentile(ms_net, 50)), "p99_ms": float(np.percentile(ms_net, 99)),
@@ -630,7 +632,7 @@ def learned_periphery(api, torch, n_steps, warmup):
                                              "pixels (halo recompute not counted); peak: sustained BF16 "
                                              + rp["source"]},
             "weights": "paper_2505_10144_gb300/weights/periphery_1m.npy", "training": meta,
-            "training_step": network_training_step(R, periphery, torch, rp),
+            "training_step": train_step,
             "config": {"workload": "learned_periphery_1M_stereo_2064x2208", "timing": "CUDA events per frame, "
                        "eager render + network launch, L2 flushed between frames"}}
 

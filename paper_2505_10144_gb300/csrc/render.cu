@@ -792,11 +792,17 @@ __device__ __forceinline__ unsigned long long win16_pop(Win16<K1>& w, int lane, 
 // from the staged record when the entry enters, so a pop hands the 2x2 stage its key
 // without reading the record again from global memory (VR render: the dependent L2 reads
 // cost 0.24 of 5.25 ms).  Keys are (4x4 depth bits << 32) | (index << 4) | the group's
-// four kept-sample bits: indices are below 2^28, so the order stays (depth, index).  The
-// shuffles per insertion are those of Win16 (64-bit key and one 32-bit word).
+// four kept-sample bits: indices are below 2^28, so the order stays (depth, index).
+// Slots do not move: each holds its rank in the window (0 = smallest), so an insertion
+// counts the smaller keys with one ballot, finds the minimum's lane with another and
+// fetches it with one shuffle (three 32-bit shuffles where a sorted, shifting window
+// needs six), and the new key takes the popped minimum's slot.  Keys are unique, so the
+// entries leave in the same order as from a sorted window.
+constexpr int kRankEmpty = 64;  // rank of an empty slot
 struct WinG {
-  unsigned long long e;  // slot lane & 3 of the block's window
+  unsigned long long e;  // slot lane & 3 of the block's window (kEmptyKey when empty)
   unsigned k2;           // 2x2-block depth key of that slot's entry, for this lane's 2x2 block
+  int rk;                // the slot's rank in the window, kRankEmpty when empty
   int n;                 // entries held by the block's window
 };
 constexpr int kWinGIndexBits = 28;
@@ -805,64 +811,137 @@ constexpr int kWinGIndexBits = 28;
 // returns the popped key (kEmptyKey if none) and, through kout, its 2x2-block key
 __device__ __forceinline__ unsigned long long wing_push(WinG& w, unsigned long long x, unsigned kx, bool do_push,
                                                         int lane, unsigned& kout) {
-  const int j = lane & 3;
-  const unsigned bal = __ballot_sync(kFull, w.e < x);
-  const int pos = __popc((bal >> (lane & ~3)) & 0xFu);
-  const int ju = j > 0 ? j - 1 : 0, jd = j < 3 ? j + 1 : 3;
+  const unsigned gm = 0xFu << (lane & 28);  // the lanes of this 2x2 group
+  const bool lt = w.e < x;
+  const int cnt = __popc(__ballot_sync(kFull, lt) & gm);
+  const unsigned b0 = __ballot_sync(kFull, w.rk == 0) & gm;
+  const int src = b0 ? __ffs(b0) - 1 : lane;
+  const unsigned long long m = shfl64(w.e, src, 32);
+  const unsigned km = __shfl_sync(kFull, w.k2, src);
   kout = kx;
-  // both blocks of the warp full: the insertion only moves entries towards the head
-  if (__all_sync(kFull, w.n >= 4)) {
-    const unsigned long long fdn = shfl64(w.e, jd, 4), fe0 = shfl64(w.e, 0, 4);
-    const unsigned kdn = __shfl_sync(kFull, w.k2, jd, 4), k0 = __shfl_sync(kFull, w.k2, 0, 4);
-    if (!do_push) return kEmptyKey;
-    if (pos == 0) return x;
-    if (j < pos - 1) {
-      w.e = fdn;
-      w.k2 = kdn;
-    } else if (j == pos - 1) {
-      w.e = x;
-      w.k2 = kx;
-    }
-    kout = k0;
-    return fe0;
-  }
-  const unsigned long long up = shfl64(w.e, ju, 4), dn = shfl64(w.e, jd, 4), e0 = shfl64(w.e, 0, 4);
-  const unsigned kup = __shfl_sync(kFull, w.k2, ju, 4), kdn = __shfl_sync(kFull, w.k2, jd, 4),
-                 k0 = __shfl_sync(kFull, w.k2, 0, 4);
   if (!do_push) return kEmptyKey;
-  if (w.n < 4) {
-    if (j == pos) {
+  if (w.n < 4) {  // filling: slots 0 .. 3 in order
+    if ((lane & 3) == w.n) {
       w.e = x;
       w.k2 = kx;
-    } else if (j > pos) {
-      w.e = up;
-      w.k2 = kup;
+      w.rk = cnt;
+    } else if (w.e != kEmptyKey && !lt) {
+      ++w.rk;
     }
     ++w.n;
     return kEmptyKey;
   }
-  if (pos == 0) return x;
-  if (j < pos - 1) {
-    w.e = dn;
-    w.k2 = kdn;
-  } else if (j == pos - 1) {
+  if (cnt == 0) return x;  // x is the smallest: out at once
+  if (w.rk == 0) {         // the minimum leaves; x takes its slot
     w.e = x;
     w.k2 = kx;
+    w.rk = cnt - 1;
+  } else if (lt) {
+    --w.rk;
   }
-  kout = k0;
-  return e0;
+  kout = km;
+  return m;
 }
 
 __device__ __forceinline__ unsigned long long wing_pop(WinG& w, int lane, unsigned& kout) {
-  const int j = lane & 3, jd = j < 3 ? j + 1 : 3;
-  const unsigned long long dn = shfl64(w.e, jd, 4), e0 = shfl64(w.e, 0, 4);
-  const unsigned kdn = __shfl_sync(kFull, w.k2, jd, 4);
-  kout = __shfl_sync(kFull, w.k2, 0, 4);
+  const unsigned gm = 0xFu << (lane & 28);
+  const unsigned b0 = __ballot_sync(kFull, w.rk == 0) & gm;
+  const int src = b0 ? __ffs(b0) - 1 : lane;
+  const unsigned long long m = shfl64(w.e, src, 32);
+  kout = __shfl_sync(kFull, w.k2, src);
   if (w.n == 0) return kEmptyKey;
-  w.e = (j + 1 < w.n) ? dn : kEmptyKey;
-  w.k2 = kdn;
+  if (w.rk == 0) {
+    w.e = kEmptyKey;
+    w.rk = kRankEmpty;
+  } else if (w.e != kEmptyKey) {
+    --w.rk;
+  }
   --w.n;
-  return e0;
+  return m;
+}
+
+// The 2x2-block window of eight entries (K2 = 8) on the four lanes of its block, slots j
+// and 4 + j on lane 4 c + j, ranked like WinG: two 32-bit shuffles per insertion where
+// the sorted, shifting window (Win4) needs ten.  Measured on the VR stereo frame, with
+// identical images: both windows ranked 5.19 -> 5.14 ms, and with the two ranks of this
+// window in one register (fewer spills at the 72-register budget) 5.11 ms.  Packing
+// every rank and count of both windows into two registers spilled less again but ran
+// slower (5.16 ms): the bit-field work outweighed the spills.
+struct Win8R {
+  unsigned long long f0, f1;  // slots j and 4 + j
+  unsigned rk;                // their ranks, slot j in bits 0 .. 7 and 4 + j in bits 8 .. 15
+                              // (kRankEmpty when empty): one register for both
+  int n;
+};
+
+__device__ __forceinline__ unsigned long long win8r_push(Win8R& w, unsigned long long x, bool do_push, int lane) {
+  const unsigned gm = 0xFu << (lane & 28);
+  const bool lt0 = w.f0 < x, lt1 = w.f1 < x;
+  const unsigned r0 = w.rk & 0xFFu, r1 = w.rk >> 8;
+  const int cnt = __popc(__ballot_sync(kFull, lt0) & gm) + __popc(__ballot_sync(kFull, lt1) & gm);
+  const unsigned b0 = __ballot_sync(kFull, r0 == 0u || r1 == 0u) & gm;
+  const int src = b0 ? __ffs(b0) - 1 : lane;
+  const unsigned long long m = shfl64(r0 == 0u ? w.f0 : w.f1, src, 32);
+  if (!do_push) return kEmptyKey;
+  unsigned n0 = r0, n1 = r1;
+  if (w.n < 8) {  // filling: slot n (lane n & 3, register n >> 2)
+    const bool mine = (lane & 3) == (w.n & 3);
+    if (mine && w.n < 4) {
+      w.f0 = x;
+      n0 = (unsigned)cnt;
+    } else if (w.f0 != kEmptyKey && !lt0) {
+      ++n0;
+    }
+    if (mine && w.n >= 4) {
+      w.f1 = x;
+      n1 = (unsigned)cnt;
+    } else if (w.f1 != kEmptyKey && !lt1) {
+      ++n1;
+    }
+    w.rk = n0 | (n1 << 8);
+    ++w.n;
+    return kEmptyKey;
+  }
+  if (cnt == 0) return x;
+  if (r0 == 0u) {
+    w.f0 = x;
+    n0 = (unsigned)(cnt - 1);
+  } else if (lt0) {
+    --n0;
+  }
+  if (r1 == 0u) {
+    w.f1 = x;
+    n1 = (unsigned)(cnt - 1);
+  } else if (lt1) {
+    --n1;
+  }
+  w.rk = n0 | (n1 << 8);
+  return m;
+}
+
+__device__ __forceinline__ unsigned long long win8r_pop(Win8R& w, int lane) {
+  const unsigned gm = 0xFu << (lane & 28);
+  const unsigned r0 = w.rk & 0xFFu, r1 = w.rk >> 8;
+  const unsigned b0 = __ballot_sync(kFull, r0 == 0u || r1 == 0u) & gm;
+  const int src = b0 ? __ffs(b0) - 1 : lane;
+  const unsigned long long m = shfl64(r0 == 0u ? w.f0 : w.f1, src, 32);
+  if (w.n == 0) return kEmptyKey;
+  unsigned n0 = r0, n1 = r1;
+  if (r0 == 0u) {
+    w.f0 = kEmptyKey;
+    n0 = kRankEmpty;
+  } else if (w.f0 != kEmptyKey) {
+    --n0;
+  }
+  if (r1 == 0u) {
+    w.f1 = kEmptyKey;
+    n1 = kRankEmpty;
+  } else if (w.f1 != kEmptyKey) {
+    --n1;
+  }
+  w.rk = n0 | (n1 << 8);
+  --w.n;
+  return m;
 }
 
 template <int K2>
@@ -1242,7 +1321,12 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
     w1.n = 0;
     wg.e = kEmptyKey;
     wg.k2 = 0u;
+    wg.rk = kRankEmpty;
     wg.n = 0;
+    Win8R w8;  // the 2x2-block window when K2 = 8 (with K1 = 4)
+    w8.f0 = w8.f1 = kEmptyKey;
+    w8.rk = kRankEmpty | (kRankEmpty << 8);
+    w8.n = 0;
     float3 hc = make_float3(0.f, 0.f, 0.f);
     // per-sample window: tournament tree when K3 <= 16 (every slot starts empty), else ring
     const bool use_tree = K3 <= 16;
@@ -1286,8 +1370,13 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
       const unsigned bal = __ballot_sync(kFull, k);
       if (bal == 0u) return;
       const unsigned g1 = (unsigned)(x1 >> 4) & ((1u << kWinGIndexBits) - 1u);
-      const unsigned long long x2 = win4_push<K2>(w2, ((unsigned long long)k2 << 32) | g1,
-                                                  ((bal >> (lane & ~3)) & 0xFu) != 0u, lane);
+      const unsigned long long key2 = ((unsigned long long)k2 << 32) | g1;
+      const bool push2 = ((bal >> (lane & ~3)) & 0xFu) != 0u;
+      unsigned long long x2;
+      if constexpr (K2 == 8)
+        x2 = win8r_push(w8, key2, push2, lane);
+      else
+        x2 = win4_push<K2>(w2, key2, push2, lane);
       pop2(x2);
     };
     // instance indices fit 32 bits (the instance capacity is below 2^31)
@@ -1387,7 +1476,12 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
           if (__any_sync(kFull, x1 != kEmptyKey)) pop1(x1, m1);
         }
       }
-      for (int it = 0; it < K2; ++it) pop2(win4_pop<K2>(w2, lane));
+      for (int it = 0; it < K2; ++it) {
+        if constexpr (K1 == 4 && K2 == 8)
+          pop2(win8r_pop(w8, lane));
+        else
+          pop2(win4_pop<K2>(w2, lane));
+      }
     }
     if (use_tree)
       while (p.n3 > 0 && p.active) tree3_pop<STATS, BWD>(p, tree, hc, k3s, a3s, lane, recv);

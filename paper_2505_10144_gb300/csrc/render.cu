@@ -1313,6 +1313,19 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
       c2x = bx2 + 1.f;
       c2y = by2 + 1.f;
     }
+    // K1 = 4: lane L evaluates, every fourth entry, the 2x2-block depth key of entry
+    // e + (L >> 3) for 2x2 group L & 7 of the warp (group g's block starts at sample
+    // x 2 (g & 1) + 4 (g >> 2 & 1), y 2 (g >> 1 & 1) of the region), and each entry's key
+    // then reaches its group by one shuffle: one evaluation per lane and four entries
+    // instead of one per lane and entry
+    float gcx, gcy;
+    {
+      const int gl = lane & 7;
+      const int bxg = g.ox + rx + 2 * (gl & 1) + 4 * ((gl >> 2) & 1), byg = g.oy + ry + 2 * ((gl >> 1) & 1);
+      gcx = g.kind == kKindLow ? 2.f * bxg + 2.f : bxg + 1.f;
+      gcy = g.kind == kKindLow ? 2.f * byg + 2.f : byg + 1.f;
+    }
+    unsigned kb = 0u;
     Win16<K1> w1;
     WinG wg;  // the 4x4-block window when K1 = 4
     Win4<K2> w2;
@@ -1437,6 +1450,12 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
                   ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
             }
           } else {
+            if constexpr (K1 == 4) {
+              if ((e & 3) == 0) {
+                const int ee = e + (lane >> 3);
+                kb = ee < nrel ? float_order_bits(depth_at(st_rec + ee * kRecF4, gcx, gcy)) : 0u;
+              }
+            }
             bool k = false;
             if (p.active) {
               float dx, dy, qw;
@@ -1448,8 +1467,9 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
             const unsigned bm = (bal >> (lane & 16)) & 0xFFFFu;
             const unsigned long long k1 = (unsigned long long)st_k1[e * 2 + (lane >> 4)] << 32;
             if constexpr (K1 == 4) {
-              // the entry's depth key at this lane's 2x2-block centre, from the staged record
-              const unsigned k2 = bm != 0u ? float_order_bits(depth_at(r, c2x, c2y)) : 0u;
+              // the entry's depth key at this lane's 2x2-block centre (evaluated by lane
+              // (e & 3) * 8 + this lane's group)
+              const unsigned k2 = __shfl_sync(kFull, kb, ((e & 3) << 3) | (lane >> 2));
               unsigned k2o;
               const unsigned long long x1 =
                   wing_push(wg, k1 | ((unsigned long long)(unsigned)ge << 4) | ((bm >> (lane & 12)) & 0xFu), k2,

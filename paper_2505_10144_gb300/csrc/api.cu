@@ -396,7 +396,11 @@ vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes
   }
   if (c->key_cap <= 0) return fail(c, VRS_ERR_CAPACITY, "no instance capacity reserved");
   prof_mark(c, 2, st);
-  for (int v = 0; v < pl.n_views; ++v) launches += pl.view_n[v] > 0 ? 1 : 0;
+  for (int v = 0; v < pl.n_views; ++v)
+    if (pl.view_n[v] > 0) {
+      ++launches;  // one duplicate_kernel launch for every view
+      break;
+    }
   launch_duplicate(P<ViewParams>(c->views), pl.n_views, P<float4>(c->rec), P<float4>(c->bbox), P<uint32_t>(c->count),
                    P<uint32_t>(c->offsets), pl.view_n.data(), pl.T, pl.tiles_per_view, vis,
                    P<unsigned long long>(c->kcache), pl.key_mode, P<uint64_t>(c->keys[0]),

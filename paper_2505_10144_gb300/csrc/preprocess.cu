@@ -4,6 +4,8 @@
 // view of its scene, so the parameter traffic of a batch of views is paid once.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace vrs {
@@ -460,18 +462,23 @@ __global__ void __launch_bounds__(256, 2) preprocess_kernel(SceneDev s, const Vi
 // as the count, with a ballot prefix giving each kept tile its slot (row-major order of
 // the rectangle, so the output is deterministic).  64 registers (4 blocks per SM): 0.139
 // against 0.151 ms per VR stereo frame at 80 registers (3 blocks).
-__global__ void __launch_bounds__(256, 4) duplicate_kernel(const ViewParams* __restrict__ views, int view,
-                                                        const float4* __restrict__ rec,
+__global__ void __launch_bounds__(256, 4) duplicate_kernel(const ViewParams* __restrict__ views, int n_views,
+                                                        long long total_nv, const float4* __restrict__ rec,
                                                         const float4* __restrict__ bbox,
                                                         const uint32_t* __restrict__ count,
-                                                        const uint32_t* __restrict__ offsets, long long nview, int T,
+                                                        const uint32_t* __restrict__ offsets, int T,
                                                         int tiles_per_view, const uint8_t* __restrict__ tvis,
                                                         const unsigned long long* __restrict__ kcache, int key_mode,
                                                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                         long long cap, uint32_t* status) {
+  // every view in one launch: blockIdx.y is the view, and its Gaussians run from its base
+  // to the next view's (the last view's to the total)
+  const int view = blockIdx.y;
+  const ViewParams& vp = views[view];
+  const long long nview = (view + 1 < n_views ? views[view + 1].base : total_nv) - vp.base;
+  if ((long long)blockIdx.x * blockDim.x >= nview) return;  // the whole block is past this view
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const ViewParams& vp = views[view];
   const long long vg = vp.base + i;
   const uint32_t cnt = i < nview ? count[vg] : 0u;
   const uint64_t vbase = (uint64_t)view * (uint64_t)tiles_per_view;
@@ -595,12 +602,15 @@ void launch_duplicate(const ViewParams* d_views, int n_views, const float4* rec,
                       int tiles_per_view, const Visibility& vis, const unsigned long long* kcache, int key_mode,
                       uint64_t* keys, uint32_t* vals, const uint32_t* /*d_total*/, long long cap, uint32_t* status,
                       cudaStream_t st) {
+  long long max_n = 0, total = 0;
   for (int v = 0; v < n_views; ++v) {
-    if (h_view_n[v] <= 0) continue;
-    const unsigned grid = (unsigned)((h_view_n[v] + 255) / 256);
-    duplicate_kernel<<<grid, 256, 0, st>>>(d_views, v, rec, bbox, count, offsets, h_view_n[v], T, tiles_per_view,
-                                           vis.tvis, kcache, key_mode, keys, vals, cap, status);
+    max_n = std::max(max_n, h_view_n[v]);
+    total += h_view_n[v];
   }
+  if (max_n <= 0) return;
+  const dim3 grid((unsigned)((max_n + 255) / 256), (unsigned)n_views);
+  duplicate_kernel<<<grid, 256, 0, st>>>(d_views, n_views, total, rec, bbox, count, offsets, T, tiles_per_view,
+                                         vis.tvis, kcache, key_mode, keys, vals, cap, status);
 }
 
 // ---- visibility culling (Sec. 4.3) ----------------------------------------------------

@@ -24,12 +24,19 @@
 //    activation).
 //  - wgrad_tc_kernel: the weight and bias gradients of one layer, D[(tap, in channel) or
 //    the bias row][out channel], K running over pixels.  Each chunk of 64 pixels of an
-//    image row builds the im2col matrix of the layer's input (one row per tap and input
-//    channel, plus a row of ones whose product is the bias gradient) and the output
-//    gradient, both K-major without swizzle; the CTA's accumulators in tensor memory
-//    collect all its chunks, and one atomic add per gradient value and CTA ends it.
+//    image row stages the layer input's three rows and the output gradient with 16-byte
+//    asynchronous copies (double-buffered: the next chunk's copies are in flight while
+//    this one is built), then builds the im2col matrix of the input (one row per tap and
+//    input channel, plus a row of ones whose product is the bias gradient) and the
+//    gradient matrix, both K-major without swizzle, by transposing the pixel-major staged
+//    rows in shared memory.  The CTA's accumulators in tensor memory collect all its
+//    chunks, and one atomic add per gradient value and CTA ends it.
+// Activations and hidden-layer gradients are pixel-major BF16 ([B][H][W][32]); the
+// weights are packed once per call into the B-operand planes (pack_weights_kernel).
 // Both hold 128 tensor-memory columns and ask for at least kTcSmemFloor bytes of shared
-// memory, so that at most four CTAs share an SM and their 4 x 128 columns fit its 512.
+// memory, so that at most four CTAs share an SM and their 4 x 128 columns fit its 512;
+// the launchers check the residency from the device's shared memory and refuse a launch
+// that could oversubscribe tensor memory.
 // Every mbarrier wait is bounded: a thread that gives up raises kStTimeout in the status
 // word, and the block waits for its committed MMAs before it frees tensor memory.
 #include <algorithm>

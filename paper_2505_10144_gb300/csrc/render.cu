@@ -2,17 +2,23 @@
 //
 // Work items are 16x16-sample squares: full-resolution 16x16 pixel subtiles (focus and
 // hybrid 32x32 tiles split into four, or plain 16x16 tiles) and half-resolution 32x32
-// periphery tiles whose 256 samples are 2x2 pixel groups.  Every work item is one CTA
-// pass of 256 threads, one sample per thread, so focus and periphery run in the same
-// persistent launch.  Threads map to samples so that 16 consecutive lanes form a 4x4
-// sample block and 4 consecutive lanes a 2x2 block: the hierarchical windows of a block
-// live in shared memory, owned by the block's first lane, and membership is a ballot.
+// periphery tiles whose 256 samples are 2x2 pixel groups, so focus and periphery run in
+// the same persistent launch.  Per entry of the tile's depth-sorted list, a sample
+// evaluates the pair (Eq. 1 on the optimal plane); kept pairs enter the per-ray windows;
+// popped entries are blended front to back (Eq. 2) with the 3DGS stopping rule.
 //
-// Per entry of the tile's depth-sorted list, a thread evaluates its sample (Eq. 1 on
-// the optimal plane); kept pairs enter the per-ray windows; popped entries are blended
-// front to back (Eq. 2) with the 3DGS stopping rule.  Lists are staged through shared
-// memory 256 records at a time; each warp skips entries whose bounding box misses its
-// 8x4-sample region.
+// Two kernels:
+//  - warp_render_kernel (hierarchical windows, the global orders, the window-only
+//    order): every warp is an independent worker on 8x4-sample region tasks taken from
+//    an atomic queue.  It stages the entries whose bounding box meets its region 16 at a
+//    time in warp-private shared memory; the 4x4- and 2x2-block windows live in the
+//    registers of their blocks' lanes (ballots and shuffles, ranked slots for the default
+//    4/8 windows) and the per-sample window is a per-lane tournament tree in shared
+//    memory.  The same kernel replays the blends for the backward pass.
+//  - render_kernel (the exact per-ray order, used for parity, and window shapes the warp
+//    kernel is not compiled for): one CTA pass of 256 threads per work item, one sample
+//    per thread; in the exact order every kept pair is sorted per sample by selection
+//    over the tile list.
 #include <algorithm>
 
 #include "common.cuh"

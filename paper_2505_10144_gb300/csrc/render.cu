@@ -1248,11 +1248,14 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
   const unsigned lt = (1u << lane) - 1u;
   unsigned n_eval = 0, n_kept = 0, n_blend = 0;
   const unsigned n_tasks = 8u * *a.n_items;
+  // the next task is taken from the queue while the current one runs, so the atomic's
+  // round trip is off the warp's path (each warp overshoots the queue by one claim)
+  unsigned next_task = 0;
+  if (lane == 0) next_task = atomicAdd(a.queue, 1u);
   for (;;) {
-    unsigned task = 0;
-    if (lane == 0) task = atomicAdd(a.queue, 1u);
-    task = __shfl_sync(kFull, task, 0);
+    const unsigned task = __shfl_sync(kFull, next_task, 0);
     if (task >= n_tasks) break;
+    if (lane == 0) next_task = atomicAdd(a.queue, 1u);
     const ItemGeom g = decode(a.items[task >> 3], a.tiles_per_view, a.key_tile, a.views);
     const int region = task & 7, rx = 8 * (region & 1), ry = 4 * (region >> 1);
     const ViewParams& vp = a.views[g.view];

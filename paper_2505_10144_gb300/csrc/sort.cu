@@ -28,29 +28,57 @@ constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1u;
 constexpr int kSpinLimit = 1 << 22;
 
+// tiles a look-back step reads at once
+constexpr int kLookWindow = 16;
+
+__device__ __forceinline__ uint32_t load_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Decoupled look-back: the sum of digit d's counts over the tiles before `tile`, read from
 // their published (flag | count) words, walking back until a tile that holds its full
-// prefix.  A word not yet published is polled again; after spin_limit such polls the wait
-// gives up, raises kStTimeout and returns false (excl then holds a partial sum).
+// prefix.  Each step reads the words of kLookWindow preceding tiles at once (for a warp,
+// one 128-byte line per tile) and consumes them nearest first.  The tiles of a CTA wave
+// publish their aggregates at about the same time, and tile k of the wave would otherwise
+// read one word per L2 round trip until it meets a prefix, about k / 2 steps in; with a
+// window it is about k / (kLookWindow + 1) steps.  A word not yet published is polled
+// again; after spin_limit such polls the wait gives up, raises kStTimeout and returns
+// false (excl then holds a partial sum).  The words carry the counts themselves, so
+// relaxed loads suffice.
 __device__ __forceinline__ bool lookback_prefix(uint32_t* look, long long tile, int d, int spin_limit,
                                                 uint32_t* status, uint32_t& excl) {
   excl = 0;
-  long long j = tile - 1;
+  long long j = tile - 1;  // the nearest tile not yet consumed
   int spins = 0;
   while (j >= 0) {
-    const uint32_t lv = atomicAdd(look + j * 256 + d, 0u);
-    const uint32_t flag = lv & ~kCountMask;
-    if (flag == 0u) {
+    uint32_t lv[kLookWindow];
+#pragma unroll
+    for (int q = 0; q < kLookWindow; ++q) lv[q] = j - q >= 0 ? load_relaxed(look + (j - q) * 256 + d) : kFlagPrefix;
+    bool blocked = false, done = false;
+    int used = 0;
+#pragma unroll
+    for (int q = 0; q < kLookWindow; ++q) {
+      if (blocked || done) continue;
+      const uint32_t flag = lv[q] & ~kCountMask;
+      if (flag == 0u) {
+        blocked = true;
+      } else {
+        excl += lv[q] & kCountMask;
+        ++used;
+        done = flag == kFlagPrefix;
+      }
+    }
+    if (done) return true;
+    j -= used;
+    if (blocked) {
       if (++spins > spin_limit) {
         atomicOr(status, kStTimeout);
         return false;
       }
       __nanosleep(20);
-      continue;
     }
-    excl += lv & kCountMask;
-    if (flag == kFlagPrefix) break;
-    --j;
   }
   return true;
 }
@@ -161,20 +189,12 @@ __global__ void __launch_bounds__(kBlock) histogram_kernel(const uint64_t* __res
   }
 }
 
-__global__ void __launch_bounds__(kBlock) histogram_scan_kernel(uint32_t* hist, int passes) {
-  __shared__ uint32_t ws[32];
-  for (int p = 0; p < passes; ++p) {
-    const uint32_t v = hist[p * 256 + threadIdx.x];
-    const uint32_t e = block_exclusive_scan(v, ws, nullptr);
-    hist[p * 256 + threadIdx.x] = e;
-  }
-}
-
 struct SortSmem {
   uint64_t keys[kSortTile];
   uint32_t vals[kSortTile];
   uint32_t warp_hist[kSortWarps][256];
   uint32_t digit_start[256];
+  uint32_t digit_offset[256];  // first output position of each digit (scan of the pass's histogram)
   uint32_t global_base[256];
   uint32_t ws[32];
   uint32_t tile;
@@ -184,7 +204,7 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const uint64_t* __rest
                                                           const uint32_t* __restrict__ vin,
                                                           uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                           const uint32_t* d_n, int shift, uint32_t dmask,
-                                                          const uint32_t* __restrict__ digit_offsets,
+                                                          const uint32_t* __restrict__ digit_counts,
                                                           uint32_t* __restrict__ look, uint32_t* tile_counter,
                                                           uint32_t* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -192,6 +212,9 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const uint64_t* __rest
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long n = *d_n;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  // the pass's digit offsets, scanned by every CTA from the histogram (256 values) instead
+  // of by a separate one-block launch
+  S.digit_offset[threadIdx.x] = block_exclusive_scan(digit_counts[threadIdx.x], S.ws, nullptr);
   for (;;) {
     if (threadIdx.x == 0) S.tile = atomicAdd(tile_counter, 1u);
     for (int i = threadIdx.x; i < kSortWarps * 256; i += kBlock) (&S.warp_hist[0][0])[i] = 0u;
@@ -245,7 +268,7 @@ __global__ void __launch_bounds__(kBlock) onesweep_kernel(const uint64_t* __rest
       lookback_prefix(look, tile, d, kSpinLimit, status, excl);
       atomicExch(my_look, kFlagPrefix | (excl + cnt));
     }
-    S.global_base[d] = digit_offsets[d] + excl;
+    S.global_base[d] = S.digit_offset[d] + excl;
     const uint32_t start = block_exclusive_scan(cnt, S.ws, nullptr);
     S.digit_start[d] = start;
     __syncthreads();
@@ -334,7 +357,6 @@ int launch_radix_sort(uint64_t* keys[2], uint32_t* vals[2], const uint32_t* d_n,
   const int sms = device_sm_count();
   const unsigned hgrid = (unsigned)std::min<long long>((cap + kBlock * 8 - 1) / (kBlock * 8), (long long)sms * 8);
   histogram_kernel<<<hgrid, kBlock, 0, st>>>(keys[0], d_n, passes, bits, s.hist);
-  histogram_scan_kernel<<<1, kBlock, 0, st>>>(s.hist, passes);
   const int smem = (int)sizeof(SortSmem);
   static std::atomic<int> smem_set[kMemoDevices], occupancy[kMemoDevices];
   ensure_dynamic_smem(smem_set, onesweep_kernel, smem);

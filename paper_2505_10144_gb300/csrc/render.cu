@@ -1053,45 +1053,52 @@ __device__ __forceinline__ float3 rec_colour(const float4* __restrict__ recv, in
   return make_float3(f5.y, f5.z, f5.w);
 }
 
-// Per-sample window as a tournament tree over 16 slots (K3 <= 16).  The keys and alphas
-// sit in shared memory, [slot][lane]; the winners (smallest key) of the 15 internal nodes
-// (node n = 1 .. 15, children 2n and 2n + 1, slot s at node 16 + s) are 4-bit slot
-// numbers in two 32-bit registers: nodes 8 .. 15 in lo (nibble n - 8), nodes 1 .. 7 in hi
-// (nibble n - 1), so each level of a replay touches one word with 32-bit shifts.
-// Putting a key into a slot replays the four matches on the slot's path to the root, so
-// every insertion costs the same: no data-dependent shifting and no divergence.  Unused
-// slots hold kEmptyKey.  hc is the colour of the root winner, loaded when it changes.
+// Per-sample window as a tournament tree over 16 slots (K3 <= 16).  The depth keys
+// (order-preserving bits of t*), indices and alphas sit in shared memory, [slot][lane];
+// the winners (smallest key) of the 15 internal nodes (node n = 1 .. 15, children 2n and
+// 2n + 1, slot s at node 16 + s) are 4-bit slot numbers in two 32-bit registers: nodes
+// 8 .. 15 in lo (nibble n - 8), nodes 1 .. 7 in hi (nibble n - 1), so each level of a
+// replay touches one word with 32-bit shifts.  Putting a key into a slot replays the four
+// matches on the slot's path to the root, so every insertion costs the same: no
+// data-dependent shifting and no divergence.  Unused slots hold kEmptyT.  hc is the colour
+// of the root winner, loaded when it changes.
+// The matches compare the 32-bit depth keys alone (one compare and one select each, where
+// (depth, index) keys take two of each): an opponent wins only when strictly nearer, so
+// of two entries with bit-equal t* at a sample the one that reached the match later goes
+// on.  That differs from the (t*, index) order only for bit-equal FP32 depths, a tie whose
+// two orders both lie within the float64 reading's near-tie margin.
 struct Tree16 {
   unsigned lo, hi;
 };
 // every internal node starts with the leftmost slot of its subtree (all slots empty)
 constexpr unsigned kTreeInitLo = 0xeca86420u, kTreeInitHi = 0x0c840800u;
+constexpr unsigned kEmptyT = 0xFFFFFFFFu;  // above every finite depth's key
 __device__ __forceinline__ int tree_root(const Tree16& t) { return (int)(t.hi & 0xFu); }
 
 // The opponents of a replay of slot s: the winners of the siblings of the path's nodes,
 // which the replay does not change, with their keys (loaded together)
 struct TreeOpp {
   int s0, s1, s2, s3;
-  unsigned long long k0, k1, k2, k3;
+  unsigned k0, k1, k2, k3;
 };
-__device__ __forceinline__ TreeOpp tree_opponents(const Tree16& t, const unsigned long long* kk, int lane, int s) {
+__device__ __forceinline__ TreeOpp tree_opponents(const Tree16& t, const unsigned* kt, int lane, int s) {
   TreeOpp o;
   o.s0 = s ^ 1;
   o.s1 = (int)((t.lo >> (4 * ((s >> 1) ^ 1))) & 0xFu);
   o.s2 = (int)((t.hi >> (4 * (3 + ((s >> 2) ^ 1)))) & 0xFu);
   o.s3 = (int)((t.hi >> (4 * (1 + ((s >> 3) ^ 1)))) & 0xFu);
-  o.k0 = kk[o.s0 * 32 + lane];
-  o.k1 = kk[o.s1 * 32 + lane];
-  o.k2 = kk[o.s2 * 32 + lane];
-  o.k3 = kk[o.s3 * 32 + lane];
+  o.k0 = kt[o.s0 * 32 + lane];
+  o.k1 = kt[o.s1 * 32 + lane];
+  o.k2 = kt[o.s2 * 32 + lane];
+  o.k3 = kt[o.s3 * 32 + lane];
   return o;
 }
 
 // key x now sits in slot s: the four matches of s's path against the opponents, as a
-// chain of compares; returns the root winner's key
-__device__ __forceinline__ unsigned long long tree_play(Tree16& t, int s, unsigned long long x, const TreeOpp& o) {
+// chain of compares
+__device__ __forceinline__ void tree_play(Tree16& t, int s, unsigned x, const TreeOpp& o) {
   int cs = s;
-  unsigned long long ck = x;
+  unsigned ck = x;
   if (o.k0 < ck) {
     ck = o.k0;
     cs = o.s0;
@@ -1117,60 +1124,59 @@ __device__ __forceinline__ unsigned long long tree_play(Tree16& t, int s, unsign
     const int sh = 4 * (1 + (s >> 3));
     hi = (hi & ~(0xFu << sh)) | ((unsigned)cs << sh);
   }
-  if (o.k3 < ck) {
-    ck = o.k3;
-    cs = o.s3;
-  }
+  if (o.k3 < ck) cs = o.s3;
   t.hi = (hi & ~0xFu) | (unsigned)cs;
-  return ck;
 }
 
 template <bool STATS, bool BWD>
-__device__ __forceinline__ void tree3_push(Px& p, Tree16& t, float3& hc, unsigned long long* kk, float* aa,
-                                           int K3, int lane, unsigned long long x, float alpha, float3 c,
+__device__ __forceinline__ void tree3_push(Px& p, Tree16& t, float3& hc, unsigned* kt, int* kg, float* aa, int K3,
+                                           int lane, unsigned x, int g, float alpha, float3 c,
                                            const float4* __restrict__ recv) {
   if (p.n3 < K3) {  // filling: the next free slot
     const int s = p.n3++;
-    const TreeOpp o = tree_opponents(t, kk, lane, s);
-    kk[s * 32 + lane] = x;
+    const TreeOpp o = tree_opponents(t, kt, lane, s);
+    kt[s * 32 + lane] = x;
+    kg[s * 32 + lane] = g;
     aa[s * 32 + lane] = alpha;
     const int w0 = tree_root(t);
     tree_play(t, s, x, o);
     if (tree_root(t) != w0 || s == 0) hc = c;
     return;
   }
-  // the root's key and alpha and the opponents of its slot, loaded together
+  // the root's key, index and alpha and the opponents of its slot, loaded together
   const int w = tree_root(t);
-  const TreeOpp o = tree_opponents(t, kk, lane, w);
-  const unsigned long long m = kk[w * 32 + lane];
+  const TreeOpp o = tree_opponents(t, kt, lane, w);
+  const unsigned m = kt[w * 32 + lane];
+  const int gm = kg[w * 32 + lane];
   const float am = aa[w * 32 + lane];
-  if (x < m) {  // x is the smallest: out at once
-    blend_c<STATS, BWD>(p, alpha, (int)(x & 0xffffffffu), c, recv);
+  if (x < m) {  // x is the nearest: out at once
+    blend_c<STATS, BWD>(p, alpha, g, c, recv);
     return;
   }
   const float3 mc = hc;
-  kk[w * 32 + lane] = x;
+  kt[w * 32 + lane] = x;
+  kg[w * 32 + lane] = g;
   aa[w * 32 + lane] = alpha;
-  const unsigned long long nk = tree_play(t, w, x, o);
+  tree_play(t, w, x, o);
   const int nw = tree_root(t);
-  hc = nw == w ? c : rec_colour(recv, (int)(nk & 0xffffffffu));
-  blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);
+  hc = nw == w ? c : rec_colour(recv, kg[nw * 32 + lane]);
+  blend_c<STATS, BWD>(p, am, gm, mc, recv);
 }
 
 // pops the root winner and blends it
 template <bool STATS, bool BWD>
-__device__ __forceinline__ void tree3_pop(Px& p, Tree16& t, float3& hc, unsigned long long* kk,
+__device__ __forceinline__ void tree3_pop(Px& p, Tree16& t, float3& hc, unsigned* kt, const int* kg,
                                           const float* aa, int lane, const float4* __restrict__ recv) {
   const int w = tree_root(t);
-  const TreeOpp o = tree_opponents(t, kk, lane, w);
-  const unsigned long long m = kk[w * 32 + lane];
+  const TreeOpp o = tree_opponents(t, kt, lane, w);
+  const int gm = kg[w * 32 + lane];
   const float am = aa[w * 32 + lane];
   const float3 mc = hc;
-  kk[w * 32 + lane] = kEmptyKey;
-  const unsigned long long nk = tree_play(t, w, kEmptyKey, o);
+  kt[w * 32 + lane] = kEmptyT;
+  tree_play(t, w, kEmptyT, o);
   p.n3--;
-  if (p.n3 > 0) hc = rec_colour(recv, (int)(nk & 0xffffffffu));
-  blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);
+  if (p.n3 > 0) hc = rec_colour(recv, kg[tree_root(t) * 32 + lane]);
+  blend_c<STATS, BWD>(p, am, gm, mc, recv);
 }
 
 // Per-lane ring of the per-sample window: packed keys and alphas, [slot][lane], ascending
@@ -1239,6 +1245,9 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
   float4* st_rec = reinterpret_cast<float4*>(ws);
   int* st_gid = reinterpret_cast<int*>(ws + kStage * 96);
   unsigned long long* k3s = reinterpret_cast<unsigned long long*>(ws + kStage * 100);
+  // the tree's depth keys and indices (k3 <= 16) share the key slots' bytes
+  unsigned* k3t = reinterpret_cast<unsigned*>(k3s);
+  int* k3g = reinterpret_cast<int*>(k3t + 16 * 32);
   float* a3s = reinterpret_cast<float*>(ws + kStage * 100 + (size_t)window_key_slots(K3) * 256);
   // 4x4-block keys of the staged batch (order-preserving depth bits), [entry][block of the warp]
   uint32_t* st_k1 = reinterpret_cast<uint32_t*>(ws + kStage * 100 + (size_t)window_key_slots(K3) * 256 +
@@ -1354,7 +1363,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
     const bool use_tree = K3 <= 16;
     Tree16 tree{kTreeInitLo, kTreeInitHi};
     if (use_tree)
-      for (int s3 = 0; s3 < 16; ++s3) k3s[s3 * 32 + lane] = kEmptyKey;
+      for (int s3 = 0; s3 < 16; ++s3) k3t[s3 * 32 + lane] = kEmptyT;
 #pragma unroll
     for (int r = 0; r < Win4<K2>::R; ++r) w2.f[r] = kEmptyKey;
     w2.n = 0;
@@ -1367,7 +1376,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
         float3 c;
         if (eval_full<STATS, false>(r, p, al, t, c)) {
           if (use_tree)
-            tree3_push<STATS, BWD>(p, tree, hc, k3s, a3s, K3, lane, pack_key(t, g2), al, c, recv);
+            tree3_push<STATS, BWD>(p, tree, hc, k3t, k3g, a3s, K3, lane, float_order_bits(t), g2, al, c, recv);
           else
             ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, g2), al, c, recv);
         }
@@ -1454,7 +1463,8 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
                 blend_c<STATS, BWD>(p, al, ge, c, recv);
               else
                 if (use_tree)
-                  tree3_push<STATS, BWD>(p, tree, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
+                  tree3_push<STATS, BWD>(p, tree, hc, k3t, k3g, a3s, K3, lane, float_order_bits(t), ge, al, c,
+                                         recv);
                 else
                   ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, ge), al, c, recv);
             }
@@ -1513,7 +1523,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
       }
     }
     if (use_tree)
-      while (p.n3 > 0 && p.active) tree3_pop<STATS, BWD>(p, tree, hc, k3s, a3s, lane, recv);
+      while (p.n3 > 0 && p.active) tree3_pop<STATS, BWD>(p, tree, hc, k3t, k3g, a3s, lane, recv);
     else
       while (p.n3 > 0 && p.active) ring3_pop<STATS, BWD>(p, hc, k3s, a3s, K3, lane, recv);
     if (STATS) {

@@ -145,7 +145,7 @@ void launch_visibility(const ViewParams* d_views, int n_views, int key_tile, int
 void launch_preprocess(const SceneDev& s, const ViewParams* d_views, const int* d_view_list, int n_views_scene,
                        int key_tile, int key_mode, const Visibility& vis, float4* rec, float4* bbox, uint32_t* count,
                        unsigned long long* kcache, cudaStream_t st);
-constexpr int kKeyCacheSlots = 8;  // kept-tile keys the count pass stores per (view, Gaussian)
+constexpr int kKeyCacheSlots = 32;  // kept-tile keys the count pass stores per (view, Gaussian)
 void launch_scan_u32(const uint32_t* in, uint32_t* out, long long n, uint32_t* d_total, uint32_t* partials,
                      cudaStream_t st);
 size_t scan_partials_bytes(long long n);

@@ -1698,31 +1698,64 @@ __global__ void __launch_bounds__(256) reuse_composite_kernel(const float4* __re
 
 // Bilinear x2 upsampling of the half-resolution image into periphery tiles: one thread
 // per output pixel, grid (row chunks of 256 pixels, rows, views), so no index division.
+// Bilinear periphery upsampling (clamp to edge, half-pixel aligned): one thread per 2x2
+// quad of output pixels (2i .. 2i + 1, 2j .. 2j + 1), whose taps all lie in the 3x3
+// half-resolution neighbourhood of (i, j), loaded once for the four pixels.  Key tiles
+// have an even side, so a quad lies in one tile and takes one class lookup.  Each pixel
+// keeps the plain per-pixel formula.
 __global__ void __launch_bounds__(256) composite_kernel(const ViewParams* __restrict__ views,
                                                         const uint8_t* __restrict__ tile_class, int tiles_per_view,
                                                         int T, const float* __restrict__ low, float* __restrict__ out,
                                                         int W, int H) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, view = blockIdx.z;
-  if (x >= W) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int view = blockIdx.z;
+  const int x = 2 * i, y = 2 * j;
+  if (x >= W || y >= H) return;
   const ViewParams& vp = views[view];
-  for (int y = blockIdx.y; y < H; y += gridDim.y) {
-    if (tile_class[(long long)view * tiles_per_view + (y / T) * vp.ntx + x / T] != kClassPeriphery) continue;
-    const long long HW = (long long)W * H;
-    const int W2 = W / 2, H2 = H / 2;
-    const long long HW2 = (long long)W2 * H2;
-    const float ux = (x + 0.5f) * 0.5f - 0.5f, uy = (y + 0.5f) * 0.5f - 0.5f;
-    const int x0 = (int)floorf(ux), y0 = (int)floorf(uy);
-    const float fx = ux - x0, fy = uy - y0;
-    const int xa = min(max(x0, 0), W2 - 1), xb = min(max(x0 + 1, 0), W2 - 1);
-    const int ya = min(max(y0, 0), H2 - 1), yb = min(max(y0 + 1, 0), H2 - 1);
-    const float* L = low + (long long)view * 3 * HW2;
-    float* o = out + (long long)view * 3 * HW + (long long)y * W + x;
+  if (tile_class[(long long)view * tiles_per_view + (y / T) * vp.ntx + x / T] != kClassPeriphery) return;
+  const long long HW = (long long)W * H;
+  const int W2 = W / 2, H2 = H / 2;
+  const long long HW2 = (long long)W2 * H2;
+  // the tap columns and rows of the quad: i - 1, i, i + 1 (clamped)
+  const int cx[3] = {min(max(i - 1, 0), W2 - 1), min(max(i, 0), W2 - 1), min(max(i + 1, 0), W2 - 1)};
+  const int cy[3] = {min(max(j - 1, 0), H2 - 1), min(max(j, 0), H2 - 1), min(max(j + 1, 0), H2 - 1)};
+  const float* L = low + (long long)view * 3 * HW2;
+  float* o = out + (long long)view * 3 * HW + (long long)y * W + x;
+  // float2 stores where both pixels exist and every plane's pair is 8-byte aligned (even
+  // width, an 8-byte aligned pair in the first plane)
+  const bool x1ok = x + 1 < W, y1ok = y + 1 < H;
+  const bool pair = x1ok && (W & 1) == 0 && (reinterpret_cast<uintptr_t>(o) & 7u) == 0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float* Lc = L + c * HW2;
-      const float top = (1.f - fx) * Lc[ya * W2 + xa] + fx * Lc[ya * W2 + xb];
-      const float bot = (1.f - fx) * Lc[yb * W2 + xa] + fx * Lc[yb * W2 + xb];
-      o[c * HW] = (1.f - fy) * top + fy * bot;
+  for (int c = 0; c < 3; ++c) {
+    const float* Lc = L + c * HW2;
+    float v[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) v[r][q] = Lc[(long long)cy[r] * W2 + cx[q]];
+    float res[2][2];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        // pixel (x + dx, y + dy): u = (p + 0.5) / 2 - 0.5 has floor i - 1 + dx and fraction 0.75 or 0.25
+        const float ux = (x + dx + 0.5f) * 0.5f - 0.5f, uy = (y + dy + 0.5f) * 0.5f - 0.5f;
+        const float fx = ux - floorf(ux), fy = uy - floorf(uy);
+        const float top = (1.f - fx) * v[dy][dx] + fx * v[dy][dx + 1];
+        const float bot = (1.f - fx) * v[dy + 1][dx] + fx * v[dy + 1][dx + 1];
+        res[dy][dx] = (1.f - fy) * top + fy * bot;
+      }
+    float* oc = o + c * HW;
+    if (pair) {
+      *reinterpret_cast<float2*>(oc) = make_float2(res[0][0], res[0][1]);
+      if (y1ok) *reinterpret_cast<float2*>(oc + W) = make_float2(res[1][0], res[1][1]);
+    } else {
+      oc[0] = res[0][0];
+      if (x1ok) oc[1] = res[0][1];
+      if (y1ok) {
+        oc[W] = res[1][0];
+        if (x1ok) oc[W + 1] = res[1][1];
+      }
     }
   }
 }
@@ -1843,8 +1876,9 @@ void launch_reuse_composite(const float4* s_full, int W, int H, const float bg[3
 
 void launch_composite(const RenderArgs& a, int W, int H, cudaStream_t st) {
   if (W <= 0 || H <= 0 || a.n_views <= 0) return;
-  const dim3 grid((unsigned)((W + 255) / 256), (unsigned)std::min(H, 65535), (unsigned)a.n_views);
-  composite_kernel<<<grid, 256, 0, st>>>(a.views, a.tile_class, a.tiles_per_view, a.key_tile, a.low, a.out, W, H);
+  const dim3 block(32, 8);  // 2x2 quads: 64 x 16 pixels per block
+  const dim3 grid((unsigned)((W + 63) / 64), (unsigned)((H + 15) / 16), (unsigned)a.n_views);
+  composite_kernel<<<grid, block, 0, st>>>(a.views, a.tile_class, a.tiles_per_view, a.key_tile, a.low, a.out, W, H);
 }
 
 }  // namespace vrs

@@ -274,6 +274,31 @@ def ncu_case(args, api, torch):
     """Frames only: the workload at args.scale resolution, nothing else on the GPU (or,
     with --train, periphery-network training steps only)."""
     from paper_2505_10144_gb300 import synth
+    if args.sort:
+        # keys like the frame's: 14 tile bits over the order-preserving bits of a depth in
+        # [0.5, 8) m; values the instance index; checked against a stable argsort
+        n = 2_470_000
+        rng = np.random.default_rng(5)
+        tile = rng.integers(0, 8970, size=n).astype(np.uint64)
+        depth = rng.uniform(0.5, 8.0, size=n).astype(np.float32).view(np.uint32).astype(np.uint64) | np.uint64(1 << 31)
+        keys = (tile << np.uint64(32)) | depth
+        k = torch.from_numpy(keys.view(np.int64)).cuda()
+        v = torch.from_numpy(np.arange(n, dtype=np.int32)).cuda()
+        R = api.Renderer()
+        for _ in range(args.warmup):
+            ok, ov = R.sort_pairs(k, v, 46)
+        torch.cuda.synchronize()
+        assert np.array_equal(ov.cpu().numpy(), np.argsort(keys, kind="stable").astype(np.int32))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(args.steps):
+            R.sort_pairs(k, v, 46)
+        ev[1].record()
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_case": True, "sort_pairs": n, "bits": 46,
+                          "ms_per_sort": ev[0].elapsed_time(ev[1]) / max(args.steps, 1)}))
+        R.close()
+        return
     if args.train:
         from paper_2505_10144_gb300 import periphery
         R = api.Renderer()
@@ -1079,6 +1104,9 @@ def main():
     ap.add_argument("--net", action="store_true", help="--ncu-case: learned periphery (network on the periphery)")
     ap.add_argument("--train", action="store_true",
                     help="--ncu-case: periphery-network training steps only (batch 8 of 256x256 crops)")
+    ap.add_argument("--sort", action="store_true",
+                    help="--ncu-case: the radix sort alone, on 2.47 M 46-bit (tile | depth) keys (the VR "
+                         "frame's instance count), warmup + steps sorts")
     ap.add_argument("--workload", default="vr", choices=["vr", "batched", "finetune", "net"],
                     help="vr: the headline stereo frame; batched: 3 scenes x 8 poses x 2 eyes in one graph "
                          "replay; finetune: 4 views at 1280^2, render + loss + backward + Adam")

@@ -416,7 +416,7 @@ vrs_status build_instances(vrs_ctx* c, const vrs_gaussians* scenes, int n_scenes
   const long long sort_n = cap_mode ? c->key_cap : std::max(need, 1ll);
   const int cur = launch_radix_sort(kb, vb, ctr + kCtrSortN, sort_n, bits, ss, ctr + kCtrStatus, st);
   c->saved.sorted_buf = cur;
-  launches += 1 + 2 + c->last_passes;
+  launches += 1 + 1 + c->last_passes;  // clamp_n_kernel, histogram_kernel, one onesweep pass per digit
   prof_mark(c, 4, st);
   launch_ranges(kb[cur], ctr + kCtrSortN, sort_n, P<uint32_t>(c->ranges), VT, st);
   launch_workitems(P<ViewParams>(c->views), pl.n_views, pl.fovea_mode, pl.T, pl.tiles_per_view, vis.tvis,

@@ -1702,7 +1702,9 @@ __global__ void __launch_bounds__(256) reuse_composite_kernel(const float4* __re
 // quad of output pixels (2i .. 2i + 1, 2j .. 2j + 1), whose taps all lie in the 3x3
 // half-resolution neighbourhood of (i, j), loaded once for the four pixels.  Key tiles
 // have an even side, so a quad lies in one tile and takes one class lookup.  Each pixel
-// keeps the plain per-pixel formula.
+// keeps the plain per-pixel formula.  Foveated frames have even sizes (the boundary
+// rejects others), so every quad is whole; the guards keep the kernel in bounds for any
+// size all the same.
 __global__ void __launch_bounds__(256) composite_kernel(const ViewParams* __restrict__ views,
                                                         const uint8_t* __restrict__ tile_class, int tiles_per_view,
                                                         int T, const float* __restrict__ low, float* __restrict__ out,

@@ -410,6 +410,10 @@ def test_invalid_arguments_are_rejected(R):
         R.render([scene], [0], [bad], None, a.RenderConfig())
     with pytest.raises(a.VrsError, match="INVALID"):
         R.render([scene], [0], [cam], None, a.RenderConfig(sort_mode="window", windows=(0, 0, 33)))
+    for W, H in [(63, 64), (64, 63)]:  # the half-resolution periphery needs even sizes
+        with pytest.raises(a.VrsError, match="INVALID"):
+            R.render([scene], [0], [synth.identity_camera(W, H, 90.0)], [synth.Fovea(32, 32, 10, 4)],
+                     a.RenderConfig(key_tile=32, fovea_mode="bilinear"))
 
 
 # ---------------------------------------------------------------- full size (sampled)

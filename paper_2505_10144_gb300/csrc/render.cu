@@ -1235,7 +1235,9 @@ __device__ __forceinline__ void ring3_pop(Px& p, float3& hc, const unsigned long
   blend_c<STATS, BWD>(p, am, (int)(m & 0xffffffffu), mc, recv);
 }
 
-template <int K1, int K2, bool BWD, bool STATS>
+// TREE: the per-sample window is the tournament tree (k3 <= 16), else the ring; a
+// template parameter, so each instance holds only its own window's code
+template <int K1, int K2, bool BWD, bool STATS, bool TREE>
 __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_render_kernel(RenderArgs a) {
   constexpr int kStage = stage_of<K2>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1360,9 +1362,9 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
     w8.n = 0;
     float3 hc = make_float3(0.f, 0.f, 0.f);
     // per-sample window: tournament tree when K3 <= 16 (every slot starts empty), else ring
-    const bool use_tree = K3 <= 16;
+    constexpr bool use_tree = TREE;
     Tree16 tree{kTreeInitLo, kTreeInitHi};
-    if (use_tree)
+    if constexpr (use_tree)
       for (int s3 = 0; s3 < 16; ++s3) k3t[s3 * 32 + lane] = kEmptyT;
 #pragma unroll
     for (int r = 0; r < Win4<K2>::R; ++r) w2.f[r] = kEmptyKey;
@@ -1375,7 +1377,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
         float al, t;
         float3 c;
         if (eval_full<STATS, false>(r, p, al, t, c)) {
-          if (use_tree)
+          if constexpr (use_tree)
             tree3_push<STATS, BWD>(p, tree, hc, k3t, k3g, a3s, K3, lane, float_order_bits(t), g2, al, c, recv);
           else
             ring3_push<STATS, BWD>(p, hc, k3s, a3s, K3, lane, pack_key(t, g2), al, c, recv);
@@ -1462,7 +1464,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
               if (a.stream_order)  // global orders: the list order is the blend order
                 blend_c<STATS, BWD>(p, al, ge, c, recv);
               else
-                if (use_tree)
+                if constexpr (use_tree)
                   tree3_push<STATS, BWD>(p, tree, hc, k3t, k3g, a3s, K3, lane, float_order_bits(t), ge, al, c,
                                          recv);
                 else
@@ -1522,7 +1524,7 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
           pop2(win4_pop<K2>(w2, lane));
       }
     }
-    if (use_tree)
+    if constexpr (use_tree)
       while (p.n3 > 0 && p.active) tree3_pop<STATS, BWD>(p, tree, hc, k3t, k3g, a3s, lane, recv);
     else
       while (p.n3 > 0 && p.active) ring3_pop<STATS, BWD>(p, hc, k3s, a3s, K3, lane, recv);
@@ -1588,21 +1590,31 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
   }
 }
 
-template <int K1, int K2, bool BWD, bool STATS>
-void launch_warp_t(const RenderArgs& a, cudaStream_t st) {
+template <int K1, int K2, bool BWD, bool STATS, bool TREE>
+void launch_warp_tw(const RenderArgs& a, cudaStream_t st) {
   const size_t smem = warp_smem_bytes(a.k3, stage_of<K2>()) * kRegionWarps;
   // attribute and occupancy per device and per window size k3 (set outside stream capture
   // by the first eager call)
   static std::atomic<int> smem_set[kMemoDevices];
   static std::atomic<int> occupancy[kMaxWin + 1][kMemoDevices];
-  ensure_dynamic_smem(smem_set, warp_render_kernel<K1, K2, BWD, STATS>, (int)smem);
+  ensure_dynamic_smem(smem_set, warp_render_kernel<K1, K2, BWD, STATS, TREE>, (int)smem);
   int per_sm = per_device_memo(occupancy[a.k3], [smem] {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, warp_render_kernel<K1, K2, BWD, STATS>, kRegionWarps * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, warp_render_kernel<K1, K2, BWD, STATS, TREE>, kRegionWarps * 32,
+                                                  smem);
     return b > 0 ? b : 1;
   });
   if (a.max_ctas_per_sm > 0) per_sm = std::min(per_sm, a.max_ctas_per_sm * (kBlock / (kRegionWarps * 32)));
-  warp_render_kernel<K1, K2, BWD, STATS><<<(unsigned)(device_sm_count() * per_sm), kRegionWarps * 32, smem, st>>>(a);
+  warp_render_kernel<K1, K2, BWD, STATS, TREE>
+      <<<(unsigned)(device_sm_count() * per_sm), kRegionWarps * 32, smem, st>>>(a);
+}
+
+template <int K1, int K2, bool BWD, bool STATS>
+void launch_warp_t(const RenderArgs& a, cudaStream_t st) {
+  if (a.k3 <= 16)
+    launch_warp_tw<K1, K2, BWD, STATS, true>(a, st);
+  else
+    launch_warp_tw<K1, K2, BWD, STATS, false>(a, st);
 }
 
 // fast path for the common window shapes; returns false when (k1, k2) is not compiled

@@ -395,6 +395,22 @@ def test_large_and_near_gaussians_span_many_tiles(R):
         assert (ref["tile_class"] == 2).any()
 
 
+@pytest.mark.parametrize("mode,win", [("hier", (4, 8, 24)), ("window", (0, 0, 24)), ("hier", (4, 8, 5))])
+def test_window_sizes_on_deep_overlap(R, mode, win):
+    """Per-sample windows above and below the tree's 16 slots, alone and under the
+    grouped block windows (the autotuner's 4/8/24 candidate among them), on the scene of
+    large, near Gaussians (about 40 blended per pixel), where these windows reorder
+    0.01-1.8% of the pixels against the exact order; plain and foveated."""
+    rng = np.random.default_rng(77)
+    scene = random_scene(400, rng, sh_degree=1, z=(0.25, 3.0), xy=1.5, ls_mu=-1.6, ls_sd=0.5)
+    cam = synth.identity_camera(192, 160, 90.0)
+    fov = synth.fovea_for(192, (90.0, 70.0), radius_frac=0.2)
+    gpu = render_gpu(R, scene, [cam], sort_mode=mode, windows=win, key_tile=16)[0]
+    parity(gpu, scene, cam, mode, windows=win, key_tile=16, label=f"deep {mode} {win} plain")
+    gpu = render_gpu(R, scene, [cam], [fov], sort_mode=mode, windows=win, key_tile=32, fovea_mode="bilinear")[0]
+    parity(gpu, scene, cam, mode, windows=win, key_tile=32, fovea=fov, label=f"deep {mode} {win} foveated")
+
+
 def duplicated_scene(n_base, n_dup, seed):
     """n_base random Gaussians plus copies of n_dup of them with new colours: a copy's
     FP32 record, and so its depth of maximum response at every sample, is bit-identical

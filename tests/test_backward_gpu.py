@@ -62,11 +62,13 @@ def test_backward_plain_matches_oracle(R, mode, win):
         assert rel_l2(g[k], g_ref[k]) < GRAD_RTOL, (k, rel_l2(g[k], g_ref[k]))
 
 
-@pytest.mark.parametrize("mode,win", [("exact", (0, 0, 0)), ("hier", (4, 8, 16))])
+@pytest.mark.parametrize("mode,win", [("exact", (0, 0, 0)), ("hier", (4, 8, 16)), ("hier", (4, 8, 24)),
+                                      ("window", (0, 0, 24))])
 def test_backward_large_gaussians_matches_oracle(R, mode, win):
     """400 Gaussians much larger than a tile, some just beyond the near plane, 96x80: a
     pixel blends about 40 of them, so thousands of lanes add into the same Gaussian's
-    gradient."""
+    gradient.  Per-sample windows of 16 (tree) and 24 (ring) replay in the backward as in
+    the forward."""
     from paper_2505_10144_gb300 import api
     rng = np.random.default_rng(78)
     scene = random_scene(400, rng, sh_degree=1, z=(0.25, 3.0), xy=1.5, ls_mu=-1.6, ls_sd=0.5)

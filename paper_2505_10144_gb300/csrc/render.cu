@@ -1495,7 +1495,9 @@ __global__ void __launch_bounds__(kRegionWarps * 32, ctas_of<K2, BWD>()) warp_re
               const unsigned long long x1 =
                   wing_push(wg, k1 | ((unsigned long long)(unsigned)ge << 4) | ((bm >> (lane & 12)) & 0xFu), k2,
                             bm != 0u, lane, k2o);
-              if (__any_sync(kFull, x1 != kEmptyKey)) pop1g(x1, k2o);
+              // the full window pops on almost every push, so no vote guards the call:
+              // pop1g's own ballot returns at once when no lane holds a popped entry
+              pop1g(x1, k2o);
             } else {
               unsigned m1;
               const unsigned long long x1 = win16_push<K1>(w1, k1 | (unsigned)ge, bm, bm != 0u, lane, m1);
